@@ -1,0 +1,90 @@
+"""Pins of the oracle's right-preconditioned Krylov solvers (Sec. III.A, IV)
+against dense LU, independently recomputed residuals and CG."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import operator as op
+from oracle import spai, krylov
+
+
+def _problem(sigma, N=14):
+    wl = W.config1(N=N)                        # nonsymmetric, E diagonal
+    M = op.A_sigma(wl.A, wl.E, sigma)
+    b = wl.B[:, 0].astype(M.dtype)
+    return wl, M, b
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "gmres"])
+@pytest.mark.parametrize("sigma", [10.0, 30.0 + 15.0j])
+@pytest.mark.parametrize("precond", [False, True])
+def test_solution_matches_dense_lu(solver, sigma, precond):
+    wl, M, b = _problem(sigma)
+    P = None
+    if precond:
+        S = spai.spai_pattern(wl.A, wl.E)
+        Pm = spai.spai(M, S)
+        P = lambda x: Pm @ x  # noqa: E731
+    f = krylov.bicgstab if solver == "bicgstab" else krylov.gmres
+    x, it, rel, st = f(lambda v: M @ v, P, b, tol=1e-8, maxit=5000)
+    assert st == krylov.STATUS_OK
+    # residual recomputed independently with a dense product
+    Md = M.toarray()
+    r = b - Md @ x
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-8 * 1.0001
+    xref = krylov.dense_solve(M, b)
+    kappa = np.linalg.cond(Md)
+    assert np.linalg.norm(x - xref) / np.linalg.norm(xref) <= kappa * 1e-8
+
+
+def test_preconditioner_reduces_iterations():
+    wl, M, b = _problem(10.0, N=16)
+    S = spai.spai_pattern(wl.A, wl.E)
+    Pm = spai.spai(M, S)
+    _, it0, _, st0 = krylov.bicgstab(lambda v: M @ v, None, b)
+    _, it1, _, st1 = krylov.bicgstab(lambda v: M @ v, lambda v: Pm @ v, b)
+    assert st0 == st1 == krylov.STATUS_OK
+    assert it1 < it0
+
+
+def test_symmetric_case_matches_cg():
+    """Laplacian (SPD sigma I + L): BiCGSTAB and scipy CG agree."""
+    wl = W.config0(N=20)
+    M = op.A_sigma(wl.A, wl.E, 25.0)
+    b = wl.B[:, 0]
+    x, it, rel, st = krylov.bicgstab(lambda v: M @ v, None, b, tol=1e-10)
+    xcg, info = spla.cg(M, b, rtol=1e-12, maxiter=10000)
+    assert info == 0 and st == krylov.STATUS_OK
+    np.testing.assert_allclose(x, xcg, rtol=0, atol=1e-8 * np.linalg.norm(xcg))
+
+
+def test_maxit_gives_noconv_status():
+    """Unpreconditioned Krylov on a hard shift stops at maxit with NOCONV
+    (the paper's observation that unpreconditioned GMRES fails, Sec. IV)."""
+    wl, M, b = _problem(1e-3, N=14)
+    for f in (krylov.bicgstab, krylov.gmres):
+        x, it, rel, st = f(lambda v: M @ v, None, b, tol=1e-12, maxit=5)
+        assert st == krylov.STATUS_NOCONV and it == 5 and rel > 1e-12
+
+
+def test_zero_rhs():
+    wl, M, b = _problem(10.0, N=5)
+    for f in (krylov.bicgstab, krylov.gmres):
+        x, it, rel, st = f(lambda v: M @ v, None, np.zeros_like(b))
+        assert it == 0 and st == krylov.STATUS_OK and not np.any(x)
+
+
+def test_identity_preconditioned_by_exact_inverse_one_iteration():
+    """With P = A^{-1} the preconditioned operator is I: BiCGSTAB converges
+    in one iteration (a closed-form property of the right-preconditioned
+    recurrence)."""
+    rng = np.random.default_rng(1)
+    n = 20
+    Ad = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    M = sp.csr_matrix(Ad)
+    Minv = np.linalg.inv(Ad)
+    b = rng.standard_normal(n)
+    x, it, rel, st = krylov.bicgstab(lambda v: M @ v, lambda v: Minv @ v, b, tol=1e-10)
+    assert it == 1 and st == krylov.STATUS_OK
