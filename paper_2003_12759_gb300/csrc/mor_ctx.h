@@ -1,0 +1,121 @@
+// Host-side runtime state of a handle (C++, not part of the C ABI).
+#pragma once
+#include "mor_spai.h"
+#include "mor_internal.h"
+#include <cstdarg>
+#include <cstdio>
+#include <memory>
+#include <string>
+#include <vector>
+
+// grow-only device buffer
+struct DBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  DBuf() {}
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  cudaError_t alloc(size_t bytes) {
+    if (p && bytes <= n) return cudaSuccess;
+    release();
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) n = bytes; else p = nullptr;
+    return e;
+  }
+  void release() { if (p) cudaFree(p); p = nullptr; n = 0; }
+  template <class T> T* as() const { return (T*)p; }
+};
+
+struct Factor {
+  std::unique_ptr<DBuf> vals;   // layout order, type st
+  int st = ST_F64;
+  mor_c64 from{0, 0}, to{0, 0};
+  int kind = 0;                 // 0 SPAI, 1 reuse
+};
+
+// One operator: A(s) (primal) or A(s)^T (transposed).
+struct OpData {
+  int fmt = FMT_CSR;
+  int64_t n = 0, nnz = 0, nlay = 0;     // rows, CSR entries, stored layout entries
+  DBuf rowptr, col;                      // CSR (device)
+  DBuf sptr, scol;                       // SELL-32 layout (device)
+  DBuf a64, a32, e64, e32;               // values in layout order
+  DBuf ca64, ce64;                       // values in CSR order (column data for the other op's SPAI)
+  DBuf outpos;                           // int64 per column-entry: position in this op's layout
+  DBuf iptr_b, iidx_b;                   // shadow sets (owned)
+  const int64_t* iptr = nullptr;         // shadow sets (may point into the other op's buffers)
+  const int32_t* iidx = nullptr;
+  int nImax = 0, nJmax = 0;
+  std::vector<int32_t> h_rowptr, h_col;  // host CSR pattern
+  std::vector<int64_t> h_lay;            // CSR position -> layout position
+  std::vector<Factor> chain;
+  int chain_prec = -1;                   // MOR_FP64 / MOR_MIXED of the chain
+  PatView view() const {
+    PatView v;
+    v.fmt = fmt;
+    v.n = (int)n;
+    v.rowptr = rowptr.as<int32_t>();
+    v.col = (fmt == FMT_SELL) ? scol.as<int32_t>() : col.as<int32_t>();
+    v.sptr = sptr.as<int64_t>();
+    return v;
+  }
+};
+
+struct mor_ctx {
+  int dev = 0;
+  int sm_count = 152;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bool has_sys = false;
+  int order = 1;
+  double alpha = 0.0, beta = 0.0;
+  int64_t n = 0;
+  int ekind = EK_IDENTITY;
+  DBuf ediag64, ediag32;
+  OpData P, T;
+  bool sym = false;
+  DBuf B, C;        // FP64 column-major
+  int m = 0, q = 0;
+  // workspace
+  DBuf ws_vec, ws_x64, ws_r64, ws_b64, ws_part, ws_small, ws_gram, ws_basis, ws_rom;
+  DBuf ws_counter;  // unsigned counters (zeroed once)
+  DBuf ws_io;       // API conversions
+  void* pinned = nullptr;   // small pinned host buffer
+  size_t pinned_bytes = 0;
+  int grid_cap = 152 * 8;
+  // IRKA reuse schedule
+  int irka_z = 0;
+  int vlen[2] = {0, 0};
+  OpData& op(int transpose) { return (transpose && !sym) ? T : P; }
+};
+
+int mor_fail(mor_t h, int code, const char* fmt, ...);
+
+#define MOR_CK(h, call)                                                                     \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return mor_fail(h, (e_ == cudaErrorMemoryAllocation) ? MOR_ENOMEM : MOR_ECUDA,        \
+                      "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define MOR_CKI(h, call)                                                                    \
+  do {                                                                                      \
+    int e_ = (call);                                                                        \
+    if (e_ != 0)                                                                            \
+      return mor_fail(h, MOR_ECUDA, "%s failed: %s (%s:%d)", #call,                         \
+                      cudaGetErrorString((cudaError_t)e_), __FILE__, __LINE__);             \
+  } while (0)
+
+#define MOR_TRY(call)            \
+  do {                           \
+    int s_ = (call);             \
+    if (s_ != MOR_OK) return s_; \
+  } while (0)
+
+// shift -> operator coefficients
+Coef mor_coef(const mor_ctx* h, mor_c64 s);
+inline bool is_real_shift(mor_c64 s) { return s.im == 0.0; }

@@ -1,0 +1,138 @@
+// Internal declarations shared by the translation units of the library.
+// Nothing here is part of the public C ABI (include/mor_spai.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+// scalar type codes for runtime dispatch
+enum ScalarType { ST_F32 = 0, ST_F64 = 1, ST_C32 = 2, ST_C64 = 3 };
+inline bool st_is_cplx(int st) { return st >= ST_C32; }
+inline bool st_is_f32(int st) { return st == ST_F32 || st == ST_C32; }
+inline size_t st_size(int st) { return st == ST_F32 ? 4 : (st == ST_C64 ? 16 : 8); }
+
+enum { FMT_CSR = 1, FMT_SELL = 2 };
+enum { EK_IDENTITY = 0, EK_DIAG = 1, EK_CSR = 2 };
+
+// Device view of a stored sparse pattern (CSR, or SELL-32 with sigma = 1).
+// SELL: rows are cut into slices of 32; slice s holds width_s = (sptr[s+1] -
+// sptr[s]) / 32 slots, slot t of row 32 s + l is at sptr[s] + 32 t + l.
+// Padding slots carry col = the row itself and value 0.
+struct PatView {
+  int fmt;
+  int n;
+  const int32_t* rowptr;  // CSR
+  const int32_t* col;     // CSR col, or SELL col (padded)
+  const int64_t* sptr;    // SELL slice offsets (nslices + 1)
+};
+
+// Real-valued operator data for y = sE * (E x) + sA * (A x).
+struct OpVals {
+  int ekind;              // EK_IDENTITY | EK_DIAG | EK_CSR
+  const void* a;          // A values in layout order (float or double)
+  const void* e;          // E values in layout order (EK_CSR) or nullptr
+  const void* ediag;      // E diagonal (EK_DIAG) or nullptr
+};
+
+// complex FP64 coefficient pair of one column
+struct Coef { double sEr, sEi, sAr, sAi; };
+
+#define MOR_KMAX 16
+
+// ---------------------------------------------------------------------------
+// fused reduction modes of the operator SpMV
+enum {
+  RED_NONE = 0,
+  RED_DOT_W = 1,     // partial[c] = sum conj(w) * y           (r_hat^H v)
+  RED_DOT_TT = 2,    // partial[c] = (sum conj(y) * w, sum |y|^2)   ((t, s), (t, t))
+  RED_NORM = 3       // partial[c] = sum |y|^2  (and y = b + op, see b pointer)
+};
+
+// Launchers (spmv.cu).  x, y, w, b: n x k, row-major with stride k (k contiguous).
+// `part`: per-block partials scratch; `fin`: finalize stage run by the last block
+// (FIN_* in krylov), `state`: per-column solver state (type-erased), counter: block counter.
+struct RedArgs {
+  int mode;            // RED_*
+  const void* w;       // second vector of the reduction
+  void* part;          // gridDim.x * k * 2 scalars of the reduction type (double or float)
+  unsigned* counter;   // zero-initialised block counter (the last block resets it)
+  int fin;             // finalize stage id (0 = none: just write the reduced sums to `out`)
+  void* state;         // solver state for the finalize stage
+  void* out;           // reduced sums (k * 2 values of the scalar type), when fin == 0
+  const int* done;     // if non-null and *done != 0 the kernel returns at once
+};
+
+int launch_op_spmv(int st, int kb, const PatView& pv, const OpVals& ov, const Coef* coefs, int k,
+                   const void* x, void* y, const void* b, const RedArgs* red, int grid_cap,
+                   cudaStream_t s);
+int launch_factor_spmv(int st, bool fcplx, int kb, const PatView& pv, const void* fvals,
+                       const int* apply, int k, const void* x, void* y, const int* done,
+                       cudaStream_t s);
+
+// Krylov helpers (krylov.cu)
+int krylov_launch_update_p(int st, int kb, int n, int k, const void* r, void* p, const void* v,
+                           const void* state, const int* done, cudaStream_t s);
+int krylov_launch_update_s(int st, int kb, int n, int k, const void* r, const void* v, void* sv,
+                           const void* state, const int* done, cudaStream_t s);
+int krylov_launch_update_xr(int st, int kb, int n, int k, void* x, void* r, const void* phat,
+                            const void* shat, const void* sv, const void* t, const void* rhat,
+                            void* part, unsigned* counter, void* state, int* done, int grid_cap,
+                            cudaStream_t s);
+int krylov_launch_init(int st, int kb, int n, int k, const void* rhs, void* x, void* r, void* rhat,
+                       void* p, void* v, void* part, unsigned* counter, void* state,
+                       const double* target, const int* maxit, int* done, int grid_cap,
+                       cudaStream_t s);
+size_t krylov_state_bytes(int st);
+int krylov_read_state(int st, const void* state_dev, int k, int* iters, int* status,
+                      cudaStream_t s);
+// outer FP64 refinement: rhs_in = r64 / ||r64|| (cast), x64 += nrm * d
+int refine_launch_scale_cast(int st_in, int kb, int n, int k, const void* r64, const double* nrm2,
+                             const int* active, void* rhs_in, cudaStream_t s);
+int refine_launch_update(int st_in, int kb, int n, int k, void* x64, const void* d,
+                         const double* nrm2, const int* active, cudaStream_t s);
+// layout conversion: column-major complex128 (API) <-> row-major type st
+int conv_launch_colmajor_c128_to_rowmajor(int st, int n, int k, const void* src, void* dst,
+                                          cudaStream_t s);
+int conv_launch_rowmajor_to_colmajor_c128(int st, int n, int k, const void* src, void* dst,
+                                          cudaStream_t s);
+int conv_launch_real_col_to_rowmajor(int st, int n, int k, const double* src, int ld, void* dst,
+                                     cudaStream_t s);
+int conv_launch_copy_cast(int st_dst, int st_src, int64_t count, const void* src, void* dst,
+                          cudaStream_t s);
+
+// SPAI (spai.cu)
+struct SpaiArgs {
+  int n;
+  const int32_t* colptr;    // column lists of the operator = rows of the other op's CSR
+  const int32_t* colidx;
+  const double* ca;         // A values of those entries (FP64)
+  const double* ce;         // E values (EK_CSR) or nullptr
+  const double* ediag;      // E diagonal (EK_DIAG) or nullptr
+  int ekind;
+  const int64_t* outpos;    // layout position of each column entry in this operator
+  const int64_t* iptr;      // shadow sets I_j
+  const int32_t* iidx;
+  int nImax, nJmax;
+  Coef cnew, cold;          // coefficients of A(sigma_new), A(sigma_old)
+  int update;               // 0: rhs e_j (SPAI), 1: rhs = column j of A(sigma_old) (reuse Q)
+  int* nsingular;           // count of rank-deficient columns
+};
+int launch_spai(int st, const SpaiArgs& a, void* out, cudaStream_t s);
+
+// dense FP64 helpers (dense.cu)
+int dense_launch_gram(int n, int a, int b, const double* X, int64_t ldx, const double* Y,
+                      int64_t ldy, double* out, double* part, unsigned* counter, int grid_cap,
+                      cudaStream_t s);
+int dense_launch_gs_update(int n, int j, const double* V, int64_t ldv, const double* h, double* v,
+                           cudaStream_t s);
+int dense_launch_scale(int n, double* v, const double* nrm2, cudaStream_t s);
+int dense_launch_eig(int r, const double* Ar, const double* Er, double* out /*wr,wi,sr,si,status*/,
+                     cudaStream_t s);
+int dense_launch_tf(int r, int m, int q, const double* Ar, const double* Er, const double* Br,
+                    const double* Cr, const double* omega, int nw, double* H, cudaStream_t s);
+int dense_launch_diag_mul(int n, int k, const double* d, const double* X, double* Y,
+                          cudaStream_t s);
+
+// process-wide count of executed kernels (see mor_launch_count)
+void mor_count_launches(int64_t n);

@@ -1,0 +1,537 @@
+// Handle lifecycle and system set-up (host C++ runtime).
+//
+// mor_set_system builds, once per system, everything the hot path reads:
+//   * the SPAI pattern S = pattern(A) + pattern(E) + diagonal (the pattern of
+//     sigma E - A for generic sigma) with A and E values aligned to it;
+//   * the transposed pattern S^T with its values (for the W solves, which use
+//     A(sigma)^T, Algorithm 2 line 5) and the position maps between the two;
+//   * the shadow sets I_j (rows reached by the columns J_j) of every column,
+//     which fix the size of each column least-squares problem of the SPAI;
+//   * the storage layout (CSR or SELL-32), chosen by timing both (the
+//     autotuner) unless the caller fixes it.
+// All host work is O(nnz) or O(sum |I_j|), multi-threaded where it matters.
+#include "mor_ctx.h"
+#include "mor_types.cuh"
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <atomic>
+
+static std::atomic<long long> g_launches{0};
+void mor_count_launches(int64_t n) { g_launches += n; }
+
+int mor_fail(mor_t h, int code, const char* fmt, ...) {
+  if (h) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->err = buf;
+  }
+  return code;
+}
+
+Coef mor_coef(const mor_ctx* h, mor_c64 s) {
+  Coef c;
+  if (h->order == 2) {
+    // (s^2 + alpha s) M + (1 + beta s) K
+    c.sEr = s.re * s.re - s.im * s.im + h->alpha * s.re;
+    c.sEi = 2.0 * s.re * s.im + h->alpha * s.im;
+    c.sAr = 1.0 + h->beta * s.re;
+    c.sAi = h->beta * s.im;
+  } else {
+    c.sEr = s.re; c.sEi = s.im; c.sAr = -1.0; c.sAi = 0.0;
+  }
+  return c;
+}
+
+namespace {
+
+struct HostCSR {
+  int64_t n = 0;
+  std::vector<int32_t> rowptr, col;
+  std::vector<double> val;
+};
+
+int fetch_csr(mor_t h, const mor_csr* M, bool dev, const char* name, HostCSR& out) {
+  if (!M || M->n <= 0 || M->nnz < 0 || !M->rowptr || (M->nnz > 0 && (!M->col || !M->val)))
+    return mor_fail(h, MOR_EINVAL, "%s: null pointer or non-positive size", name);
+  if (M->n > 0x7fffffffLL || M->nnz > 0x7fffffffLL)
+    return mor_fail(h, MOR_EINVAL, "%s: n and nnz must fit int32", name);
+  out.n = M->n;
+  out.rowptr.resize(M->n + 1);
+  out.col.resize(M->nnz);
+  out.val.resize(M->nnz);
+  cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  MOR_CK(h, cudaMemcpy(out.rowptr.data(), M->rowptr, sizeof(int32_t) * (M->n + 1), kind));
+  if (M->nnz > 0) {
+    MOR_CK(h, cudaMemcpy(out.col.data(), M->col, sizeof(int32_t) * M->nnz, kind));
+    MOR_CK(h, cudaMemcpy(out.val.data(), M->val, sizeof(double) * M->nnz, kind));
+  }
+  // validation
+  if (out.rowptr[0] != 0) return mor_fail(h, MOR_EINVAL, "%s: rowptr[0] != 0", name);
+  if (out.rowptr[M->n] != M->nnz) return mor_fail(h, MOR_EINVAL, "%s: rowptr[n] != nnz", name);
+  for (int64_t i = 0; i < M->n; ++i) {
+    if (out.rowptr[i + 1] < out.rowptr[i]) return mor_fail(h, MOR_EINVAL, "%s: rowptr decreases at row %lld", name, (long long)i);
+    for (int32_t p = out.rowptr[i]; p < out.rowptr[i + 1]; ++p) {
+      const int32_t c = out.col[p];
+      if (c < 0 || c >= M->n) return mor_fail(h, MOR_EINVAL, "%s: column index %d out of range in row %lld", name, c, (long long)i);
+      if (p > out.rowptr[i] && c <= out.col[p - 1])
+        return mor_fail(h, MOR_EINVAL, "%s: columns not strictly increasing in row %lld", name, (long long)i);
+      if (!std::isfinite(out.val[p])) return mor_fail(h, MOR_EINVAL, "%s: non-finite value in row %lld", name, (long long)i);
+    }
+  }
+  return MOR_OK;
+}
+
+// merged pattern of A (+ E) + diagonal, values aligned
+void merge_pattern(const HostCSR& A, const HostCSR* E, HostCSR& S, std::vector<double>& sa, std::vector<double>& se) {
+  const int64_t n = A.n;
+  S.n = n;
+  S.rowptr.assign(n + 1, 0);
+  S.col.clear();
+  sa.clear();
+  se.clear();
+  S.col.reserve(A.col.size() + n + (E ? E->col.size() : 0));
+  sa.reserve(S.col.capacity());
+  if (E) se.reserve(S.col.capacity());
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t pa = A.rowptr[i], ea = A.rowptr[i + 1];
+    int32_t pe = E ? E->rowptr[i] : 0, ee = E ? E->rowptr[i + 1] : 0;
+    bool diag_done = false;
+    while (pa < ea || pe < ee || !diag_done) {
+      int64_t ca = pa < ea ? A.col[pa] : INT64_MAX;
+      int64_t ce = pe < ee ? E->col[pe] : INT64_MAX;
+      int64_t cd = diag_done ? INT64_MAX : i;
+      int64_t c = std::min(ca, std::min(ce, cd));
+      double va = 0.0, ve = 0.0;
+      if (ca == c) { va = A.val[pa]; ++pa; }
+      if (ce == c) { ve = E->val[pe]; ++pe; }
+      if (cd == c) diag_done = true;
+      S.col.push_back((int32_t)c);
+      sa.push_back(va);
+      if (E) se.push_back(ve);
+    }
+    S.rowptr[i + 1] = (int32_t)S.col.size();
+  }
+}
+
+// transpose pattern; t2p[t] = position in S of the entry at T position t
+void transpose_pattern(const HostCSR& S, HostCSR& T, std::vector<int64_t>& t2p) {
+  const int64_t n = S.n, nnz = (int64_t)S.col.size();
+  T.n = n;
+  T.rowptr.assign(n + 1, 0);
+  for (int64_t p = 0; p < nnz; ++p) T.rowptr[S.col[p] + 1]++;
+  for (int64_t i = 0; i < n; ++i) T.rowptr[i + 1] += T.rowptr[i];
+  T.col.resize(nnz);
+  t2p.resize(nnz);
+  std::vector<int32_t> next(T.rowptr.begin(), T.rowptr.end() - 1);
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t p = S.rowptr[i]; p < S.rowptr[i + 1]; ++p) {
+      const int32_t t = next[S.col[p]]++;
+      T.col[t] = (int32_t)i;
+      t2p[t] = p;
+    }
+}
+
+// shadow sets: for column j of the operator whose columns are the rows of
+// `cols` (a CSR whose row j lists J_j), I_j = union over k in J_j of row k.
+void shadow_sets(const HostCSR& cols, std::vector<int64_t>& iptr, std::vector<int32_t>& iidx, int& nImax, int& nJmax) {
+  const int64_t n = cols.n;
+  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 20000) nt = 1;
+  std::vector<std::vector<int32_t>> parts(nt);
+  std::vector<std::vector<int32_t>> counts(nt);
+  std::vector<int> maxI(nt, 0);
+  auto work = [&](unsigned t) {
+    const int64_t j0 = n * t / nt, j1 = n * (t + 1) / nt;
+    std::vector<int64_t> stamp(n, -1);
+    std::vector<int32_t> buf;
+    auto& out = parts[t];
+    auto& cnt = counts[t];
+    cnt.reserve(j1 - j0);
+    for (int64_t j = j0; j < j1; ++j) {
+      buf.clear();
+      for (int32_t p = cols.rowptr[j]; p < cols.rowptr[j + 1]; ++p) {
+        const int32_t k = cols.col[p];
+        for (int32_t q = cols.rowptr[k]; q < cols.rowptr[k + 1]; ++q) {
+          const int32_t i = cols.col[q];
+          if (stamp[i] != j) { stamp[i] = j; buf.push_back(i); }
+        }
+      }
+      std::sort(buf.begin(), buf.end());
+      out.insert(out.end(), buf.begin(), buf.end());
+      cnt.push_back((int32_t)buf.size());
+      maxI[t] = std::max(maxI[t], (int)buf.size());
+    }
+  };
+  std::vector<std::thread> th;
+  for (unsigned t = 1; t < nt; ++t) th.emplace_back(work, t);
+  work(0);
+  for (auto& x : th) x.join();
+  iptr.assign(n + 1, 0);
+  int64_t j = 0;
+  for (unsigned t = 0; t < nt; ++t)
+    for (int32_t c : counts[t]) { iptr[j + 1] = iptr[j] + c; ++j; }
+  iidx.resize(iptr[n]);
+  int64_t off = 0;
+  for (unsigned t = 0; t < nt; ++t) {
+    std::memcpy(iidx.data() + off, parts[t].data(), parts[t].size() * sizeof(int32_t));
+    off += (int64_t)parts[t].size();
+  }
+  nImax = 0;
+  for (int x : maxI) nImax = std::max(nImax, x);
+  nJmax = 0;
+  for (int64_t jj = 0; jj < n; ++jj) nJmax = std::max(nJmax, cols.rowptr[jj + 1] - cols.rowptr[jj]);
+}
+
+// SELL-32 (sigma = 1) layout of a CSR pattern: slice offsets, padded columns,
+// and the map CSR position -> layout position.
+void sell_layout(const HostCSR& S, std::vector<int64_t>& sptr, std::vector<int32_t>& scol, std::vector<int64_t>& lay) {
+  const int64_t n = S.n;
+  const int64_t ns = (n + 31) / 32;
+  sptr.assign(ns + 1, 0);
+  for (int64_t s = 0; s < ns; ++s) {
+    int w = 0;
+    for (int64_t r = s * 32; r < std::min(n, s * 32 + 32); ++r) w = std::max(w, S.rowptr[r + 1] - S.rowptr[r]);
+    sptr[s + 1] = sptr[s] + 32LL * w;
+  }
+  scol.assign(sptr[ns], 0);
+  lay.resize(S.col.size());
+  for (int64_t s = 0; s < ns; ++s) {
+    const int64_t w = (sptr[s + 1] - sptr[s]) / 32;
+    for (int64_t l = 0; l < 32; ++l) {
+      const int64_t r = s * 32 + l;
+      for (int64_t t = 0; t < w; ++t) {
+        const int64_t pos = sptr[s] + 32 * t + l;
+        if (r < n && t < S.rowptr[r + 1] - S.rowptr[r]) {
+          const int64_t p = S.rowptr[r] + t;
+          scol[pos] = S.col[p];
+          lay[p] = pos;
+        } else {
+          scol[pos] = (int32_t)std::min<int64_t>(r, n - 1);   // padding: a valid index, value 0
+        }
+      }
+    }
+  }
+}
+
+template <class T>
+int upload(mor_t h, DBuf& d, const std::vector<T>& v) {
+  MOR_CK(h, d.alloc(sizeof(T) * std::max<size_t>(1, v.size())));
+  if (!v.empty()) MOR_CK(h, cudaMemcpyAsync(d.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, h->stream));
+  return MOR_OK;
+}
+
+template <class T>
+std::vector<T> permute_to_layout(const std::vector<T>& csrv, const std::vector<int64_t>& lay, int64_t nlay) {
+  std::vector<T> out(nlay, T(0));
+  for (size_t p = 0; p < csrv.size(); ++p) out[lay[p]] = csrv[p];
+  return out;
+}
+
+// upload one operator in a given format
+int build_op(mor_t h, OpData& op, const HostCSR& S, const std::vector<double>& sa, const std::vector<double>& se,
+             int fmt, bool has_e) {
+  op.fmt = fmt;
+  op.n = S.n;
+  op.nnz = (int64_t)S.col.size();
+  op.h_rowptr = S.rowptr;
+  op.h_col = S.col;
+  std::vector<int64_t> sptr;
+  std::vector<int32_t> scol;
+  if (fmt == FMT_SELL) {
+    sell_layout(S, sptr, scol, op.h_lay);
+    op.nlay = (int64_t)scol.size();
+  } else {
+    op.h_lay.resize(op.nnz);
+    for (int64_t p = 0; p < op.nnz; ++p) op.h_lay[p] = p;
+    op.nlay = op.nnz;
+    op.sptr.release();
+    op.scol.release();
+  }
+  MOR_TRY(upload(h, op.rowptr, S.rowptr));
+  MOR_TRY(upload(h, op.col, S.col));
+  if (fmt == FMT_SELL) {
+    MOR_TRY(upload(h, op.sptr, sptr));
+    MOR_TRY(upload(h, op.scol, scol));
+  }
+  std::vector<double> la = permute_to_layout(sa, op.h_lay, op.nlay);
+  std::vector<float> la32(la.begin(), la.end());
+  MOR_TRY(upload(h, op.a64, la));
+  MOR_TRY(upload(h, op.a32, la32));
+  MOR_TRY(upload(h, op.ca64, sa));
+  if (has_e) {
+    std::vector<double> le = permute_to_layout(se, op.h_lay, op.nlay);
+    std::vector<float> le32(le.begin(), le.end());
+    MOR_TRY(upload(h, op.e64, le));
+    MOR_TRY(upload(h, op.e32, le32));
+    MOR_TRY(upload(h, op.ce64, se));
+  } else {
+    op.e64.release(); op.e32.release(); op.ce64.release();
+  }
+  return MOR_OK;
+}
+
+// time the FP32 operator SpMV (k = 1 real and k = 8 complex) of a built op
+double time_op(mor_t h, OpData& op, int& status) {
+  status = MOR_OK;
+  const int64_t n = op.n;
+  DBuf x, y;
+  if (x.alloc(n * 8 * sizeof(cfloat)) != cudaSuccess || y.alloc(n * 8 * sizeof(cfloat)) != cudaSuccess) {
+    status = MOR_ENOMEM;
+    return 1e30;
+  }
+  cudaMemsetAsync(x.p, 0, n * 8 * sizeof(cfloat), h->stream);
+  OpVals ov{h->ekind, op.a32.p, op.e32.p, h->ediag32.p};
+  Coef cf[8];
+  for (int c = 0; c < 8; ++c) cf[c] = mor_coef(h, mor_c64{1.0 + c, 0.5});
+  PatView pv = op.view();
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, h->stream);
+    launch_op_spmv(ST_F32, 1, pv, ov, cf, 1, x.p, y.p, nullptr, nullptr, 0, h->stream);
+    launch_op_spmv(ST_C32, 8, pv, ov, cf, 5, x.p, y.p, nullptr, nullptr, 0, h->stream);
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaGetLastError() != cudaSuccess) status = MOR_ECUDA;
+  return best;
+}
+
+int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std::vector<double>* Ediag, const double* B,
+                      int m, const double* C, int q, int format, bool dev) {
+  const int64_t n = A.n;
+  if (m < 1 || m > MOR_MAX_IO || q < 1 || q > MOR_MAX_IO) return mor_fail(h, MOR_EINVAL, "m and q must be in [1, %d]", MOR_MAX_IO);
+  if (!B || !C) return mor_fail(h, MOR_EINVAL, "B and C are required");
+  if (format < MOR_FMT_AUTO || format > MOR_FMT_SELL) return mor_fail(h, MOR_EINVAL, "unknown format %d", format);
+  h->has_sys = false;
+  h->P.chain.clear(); h->T.chain.clear();
+  h->P.chain_prec = h->T.chain_prec = -1;
+  h->irka_z = 0; h->vlen[0] = h->vlen[1] = 0;
+  h->n = n;
+  h->ekind = Ecsr ? EK_CSR : (Ediag ? EK_DIAG : EK_IDENTITY);
+  // pattern and transpose
+  HostCSR S, Tm;
+  std::vector<double> sa, se, ta, te;
+  merge_pattern(A, Ecsr, S, sa, se);
+  std::vector<int64_t> t2p;
+  transpose_pattern(S, Tm, t2p);
+  const int64_t nnz = (int64_t)S.col.size();
+  ta.resize(nnz);
+  for (int64_t t = 0; t < nnz; ++t) ta[t] = sa[t2p[t]];
+  if (Ecsr) { te.resize(nnz); for (int64_t t = 0; t < nnz; ++t) te[t] = se[t2p[t]]; }
+  bool psym = (Tm.rowptr == S.rowptr) && (Tm.col == S.col);
+  bool sym = psym;
+  if (sym) for (int64_t t = 0; t < nnz && sym; ++t) sym = (ta[t] == sa[t]) && (!Ecsr || te[t] == se[t]);
+  h->sym = sym;
+  // diag of E
+  if (Ediag) {
+    std::vector<float> d32(Ediag->begin(), Ediag->end());
+    MOR_TRY(upload(h, h->ediag64, *Ediag));
+    MOR_TRY(upload(h, h->ediag32, d32));
+  } else {
+    h->ediag64.release(); h->ediag32.release();
+  }
+  // layout / autotune
+  int fmt = format;
+  if (fmt == MOR_FMT_AUTO) {
+    int st1 = 0, st2 = 0;
+    MOR_TRY(build_op(h, h->P, S, sa, se, FMT_CSR, Ecsr != nullptr));
+    double tc = time_op(h, h->P, st1);
+    MOR_TRY(build_op(h, h->P, S, sa, se, FMT_SELL, Ecsr != nullptr));
+    double ts = time_op(h, h->P, st2);
+    if (st1 != MOR_OK || st2 != MOR_OK) return mor_fail(h, MOR_ECUDA, "format autotuning failed");
+    fmt = (ts <= tc) ? FMT_SELL : FMT_CSR;
+    if (fmt == FMT_CSR) MOR_TRY(build_op(h, h->P, S, sa, se, FMT_CSR, Ecsr != nullptr));
+  } else {
+    MOR_TRY(build_op(h, h->P, S, sa, se, fmt, Ecsr != nullptr));
+  }
+  if (!sym) MOR_TRY(build_op(h, h->T, Tm, ta, te, fmt, Ecsr != nullptr));
+  // shadows: columns of the primal operator are the rows of S^T
+  std::vector<int64_t> iptr;
+  std::vector<int32_t> iidx;
+  int nImax = 0, nJmax = 0;
+  shadow_sets(sym ? S : Tm, iptr, iidx, nImax, nJmax);
+  MOR_TRY(upload(h, h->P.iptr_b, iptr));
+  MOR_TRY(upload(h, h->P.iidx_b, iidx));
+  h->P.iptr = h->P.iptr_b.as<int64_t>();
+  h->P.iidx = h->P.iidx_b.as<int32_t>();
+  h->P.nImax = nImax; h->P.nJmax = nJmax;
+  // outpos for the primal SPAI: column entries = entries of S^T (positions t) -> S position t2p[t] -> layout
+  {
+    std::vector<int64_t> outp(nnz);
+    for (int64_t t = 0; t < nnz; ++t) outp[t] = h->P.h_lay[t2p[t]];
+    MOR_TRY(upload(h, h->P.outpos, outp));
+  }
+  if (!sym) {
+    if (psym) {
+      h->T.iptr = h->P.iptr; h->T.iidx = h->P.iidx;
+      h->T.nImax = nImax; h->T.nJmax = nJmax;
+    } else {
+      std::vector<int64_t> iptr2;
+      std::vector<int32_t> iidx2;
+      int a2 = 0, b2 = 0;
+      shadow_sets(S, iptr2, iidx2, a2, b2);
+      MOR_TRY(upload(h, h->T.iptr_b, iptr2));
+      MOR_TRY(upload(h, h->T.iidx_b, iidx2));
+      h->T.iptr = h->T.iptr_b.as<int64_t>();
+      h->T.iidx = h->T.iidx_b.as<int32_t>();
+      h->T.nImax = a2; h->T.nJmax = b2;
+    }
+    // transposed SPAI: column entries = entries of S (positions p); T position of (i,j) is p2t[p]
+    std::vector<int64_t> p2t(nnz);
+    for (int64_t t = 0; t < nnz; ++t) p2t[t2p[t]] = t;
+    std::vector<int64_t> outp(nnz);
+    for (int64_t p = 0; p < nnz; ++p) outp[p] = h->T.h_lay[p2t[p]];
+    MOR_TRY(upload(h, h->T.outpos, outp));
+  } else {
+    h->T.chain.clear();
+  }
+  // B, C
+  cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  MOR_CK(h, h->B.alloc(sizeof(double) * n * m));
+  MOR_CK(h, h->C.alloc(sizeof(double) * n * q));
+  MOR_CK(h, cudaMemcpyAsync(h->B.p, B, sizeof(double) * n * m, kind, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(h->C.p, C, sizeof(double) * n * q, kind, h->stream));
+  h->m = m;
+  h->q = q;
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  h->has_sys = true;
+  return MOR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mor_default_opts(mor_solve_opts* o) {
+  if (!o) return;
+  o->precision = MOR_MIXED;
+  o->solver = MOR_BICGSTAB;
+  o->tol = 1e-8;
+  o->maxit = 20000;
+  o->inner_tol = 1e-4;
+  o->max_refine = 10;
+  o->batch = 1;
+  o->use_graph = 1;
+  o->graph_chunk = 16;
+  o->precond = 0;
+  o->max_chain = 0;
+}
+
+int mor_create(mor_t* out, int device, void* stream) {
+  if (!out) return MOR_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return MOR_ECUDA;
+  if (device < 0 || device >= ndev) return MOR_EINVAL;
+  mor_ctx* h = new (std::nothrow) mor_ctx();
+  if (!h) return MOR_ENOMEM;
+  h->dev = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete h; return MOR_ECUDA; }
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+  h->grid_cap = h->sm_count * 8;
+  if (stream) { h->stream = (cudaStream_t)stream; h->own_stream = false; }
+  else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) { delete h; return MOR_ECUDA; }
+    h->own_stream = true;
+  }
+  if (h->ws_counter.alloc(64 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(h->ws_counter.p, 0, 64 * sizeof(unsigned)) != cudaSuccess) { delete h; return MOR_ENOMEM; }
+  h->pinned_bytes = 1 << 16;
+  if (cudaHostAlloc(&h->pinned, h->pinned_bytes, cudaHostAllocDefault) != cudaSuccess) { delete h; return MOR_ENOMEM; }
+  *out = h;
+  return MOR_OK;
+}
+
+int mor_destroy(mor_t h) {
+  if (!h) return MOR_OK;
+  cudaSetDevice(h->dev);
+  cudaStreamSynchronize(h->stream);
+  if (h->pinned) cudaFreeHost(h->pinned);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return MOR_OK;
+}
+
+int mor_launch_count(int64_t* count) {
+  if (!count) return MOR_EINVAL;
+  *count = (int64_t)g_launches.load();
+  return MOR_OK;
+}
+
+const char* mor_last_error(mor_t h) { return h ? h->err.c_str() : "null handle"; }
+
+int mor_set_system(mor_t h, const mor_csr* A, const mor_csr* E, const double* E_diag, const double* B, int m,
+                   const double* C, int q, int format, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  cudaSetDevice(h->dev);
+  const bool dev = (flags & MOR_DEVICE_PTRS) != 0;
+  HostCSR Ah, Eh;
+  MOR_TRY(fetch_csr(h, A, dev, "A", Ah));
+  const HostCSR* Ep = nullptr;
+  std::vector<double> ed;
+  if (E) {
+    MOR_TRY(fetch_csr(h, E, dev, "E", Eh));
+    if (Eh.n != Ah.n) return mor_fail(h, MOR_EINVAL, "E and A differ in size");
+    Ep = &Eh;
+  } else if (E_diag) {
+    ed.resize(Ah.n);
+    MOR_CK(h, cudaMemcpy(ed.data(), E_diag, sizeof(double) * Ah.n, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    for (double v : ed) if (!std::isfinite(v)) return mor_fail(h, MOR_EINVAL, "E_diag has a non-finite value");
+  }
+  h->order = 1;
+  h->alpha = h->beta = 0.0;
+  return set_system_common(h, Ah, Ep, E_diag && !E ? &ed : nullptr, B, m, C, q, format, dev);
+}
+
+int mor_set_system_2nd(mor_t h, const mor_csr* K, const double* M_diag, double alpha, double beta, const double* F,
+                       int m, const double* C, int q, int format, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (!M_diag) return mor_fail(h, MOR_EINVAL, "M_diag is required");
+  if (!std::isfinite(alpha) || !std::isfinite(beta)) return mor_fail(h, MOR_EINVAL, "alpha/beta not finite");
+  cudaSetDevice(h->dev);
+  const bool dev = (flags & MOR_DEVICE_PTRS) != 0;
+  HostCSR Kh;
+  MOR_TRY(fetch_csr(h, K, dev, "K", Kh));
+  std::vector<double> md(Kh.n);
+  MOR_CK(h, cudaMemcpy(md.data(), M_diag, sizeof(double) * Kh.n, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  for (double v : md) if (!std::isfinite(v)) return mor_fail(h, MOR_EINVAL, "M_diag has a non-finite value");
+  h->order = 2;
+  h->alpha = alpha;
+  h->beta = beta;
+  return set_system_common(h, Kh, nullptr, &md, F, m, C, q, format, dev);
+}
+
+int mor_get_info(mor_t h, int64_t* n, int64_t* nnz, int* format, int* symmetric) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (n) *n = h->n;
+  if (nnz) *nnz = h->P.nnz;
+  if (format) *format = h->P.fmt;
+  if (symmetric) *symmetric = h->sym ? 1 : 0;
+  return MOR_OK;
+}
+
+int mor_get_pattern(mor_t h, int transpose, int32_t* rowptr, int32_t* col) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  OpData& op = h->op(transpose);
+  if (rowptr) std::memcpy(rowptr, op.h_rowptr.data(), sizeof(int32_t) * op.h_rowptr.size());
+  if (col) std::memcpy(col, op.h_col.data(), sizeof(int32_t) * op.h_col.size());
+  return MOR_OK;
+}
+
+}  // extern "C"

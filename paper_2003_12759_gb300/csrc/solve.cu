@@ -1,0 +1,973 @@
+// Preconditioner chain, shifted solves, Gram-Schmidt, projection, reduced
+// poles, IRKA step and transfer-function evaluation (host C++ runtime that
+// drives the kernels).
+//
+// The solve of a batch of k <= 16 shifts:
+//   outer (FP64):  r = b - A(sigma) x  (FP64 operator SpMV, fused norms);
+//                  stop when ||r|| / ||b|| <= tol;
+//   inner:         right-preconditioned BiCGSTAB on A(sigma) d = r / ||r||
+//                  (FP32/complex64 in MOR_MIXED; FP64 in MOR_FP64, where the
+//                  outer loop is the restart-on-true-residual of the FP64
+//                  algorithm), all k columns in lock step, scalars and
+//                  convergence on the device, iterations replayed from a
+//                  CUDA graph in chunks with one 4-byte read per chunk;
+//                  x += ||r|| d.
+#include "mor_ctx.h"
+#include "krylov_state.cuh"
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+namespace {
+
+int kb_for(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 16; }
+int st_of(int precision, bool cplx) {
+  if (precision == MOR_FP64) return cplx ? ST_C64 : ST_F64;
+  return cplx ? ST_C32 : ST_F32;
+}
+bool same_shift(mor_c64 a, mor_c64 b) { return a.re == b.re && a.im == b.im; }
+
+OpVals op_vals(mor_t h, OpData& op, bool f32) {
+  OpVals v;
+  v.ekind = h->ekind;
+  v.a = f32 ? op.a32.p : op.a64.p;
+  v.e = f32 ? op.e32.p : op.e64.p;
+  v.ediag = f32 ? h->ediag32.p : h->ediag64.p;
+  return v;
+}
+
+// small device scratch: [counter area][done][kstate][targets][maxit][active][nrm2][masks][sums]
+struct Small {
+  unsigned* counter;
+  int* done;
+  void* kstate;
+  double* target;
+  int* maxit;
+  int* active;
+  double* nrm2;
+  int* masks;        // MOR_KMAX ints per factor
+  cdouble* sums;     // 2 * MOR_KMAX
+  int* nsing;
+};
+const int MAX_FACTORS = 4096;
+
+int get_small(mor_t h, Small& s) {
+  const size_t bytes = 64 * 1024 + 4096 + (size_t)MAX_FACTORS * MOR_KMAX * sizeof(int);
+  MOR_CK(h, h->ws_small.alloc(bytes));
+  char* b = h->ws_small.as<char>();
+  s.done = (int*)(b + 0);
+  s.nsing = (int*)(b + 64);
+  s.kstate = (void*)(b + 256);                          // 16 * 112 B
+  s.target = (double*)(b + 256 + 4096);
+  s.maxit = (int*)(b + 256 + 4096 + 256);
+  s.active = (int*)(b + 256 + 4096 + 512);
+  s.nrm2 = (double*)(b + 256 + 4096 + 768);
+  s.sums = (cdouble*)(b + 256 + 4096 + 1024);
+  s.masks = (int*)(b + 64 * 1024 + 4096);
+  s.counter = h->ws_counter.as<unsigned>();
+  return MOR_OK;
+}
+
+}  // namespace
+
+// forward
+static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bool update, int precision);
+
+// ---------------------------------------------------------------------------
+// preconditioner chain
+// ---------------------------------------------------------------------------
+static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bool update, int precision) {
+  OpData& X = h->op(transpose);
+  OpData& Y = (transpose && !h->sym) ? h->P : (h->sym ? h->P : h->T);   // column data source
+  const bool cplx = !is_real_shift(s_new) || (update && !is_real_shift(s_old));
+  const int st = st_of(precision, cplx);
+  Factor f;
+  f.vals.reset(new DBuf());
+  f.st = st;
+  f.from = update ? s_old : s_new;
+  f.to = s_new;
+  f.kind = update ? 1 : 0;
+  MOR_CK(h, f.vals->alloc(st_size(st) * (size_t)X.nlay));
+  MOR_CK(h, cudaMemsetAsync(f.vals->p, 0, st_size(st) * (size_t)X.nlay, h->stream));
+  Small sm;
+  MOR_TRY(get_small(h, sm));
+  MOR_CK(h, cudaMemsetAsync(sm.nsing, 0, sizeof(int), h->stream));
+  SpaiArgs a;
+  a.n = (int)X.n;
+  a.colptr = Y.rowptr.as<int32_t>();
+  a.colidx = Y.col.as<int32_t>();
+  a.ca = Y.ca64.as<double>();
+  a.ce = Y.ce64.as<double>();
+  a.ediag = h->ediag64.as<double>();
+  a.ekind = h->ekind;
+  a.outpos = X.outpos.as<int64_t>();
+  a.iptr = X.iptr;
+  a.iidx = X.iidx;
+  a.nImax = X.nImax;
+  a.nJmax = X.nJmax;
+  a.cnew = mor_coef(h, s_new);
+  a.cold = mor_coef(h, s_old);
+  a.update = update ? 1 : 0;
+  a.nsingular = sm.nsing;
+  MOR_CKI(h, launch_spai(st, a, f.vals->p, h->stream));
+  int nsing = 0;
+  MOR_CK(h, cudaMemcpyAsync(&nsing, sm.nsing, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  if (!update) { X.chain.clear(); }
+  X.chain.push_back(std::move(f));
+  X.chain_prec = precision;
+  if (nsing > 0) return mor_fail(h, MOR_ESINGULAR, "%d rank-deficient least-squares columns", nsing);
+  return MOR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one batch of k <= 16 columns
+// ---------------------------------------------------------------------------
+struct BatchIO {
+  const mor_c64* sig;   // k shifts
+  int k;
+  const int* L;         // chain prefix length per column
+  void* b64;            // row-major n x k, st64
+  void* x64;            // row-major n x k, st64 (out)
+};
+
+static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cplx, const BatchIO& io,
+                       mor_solve_stats* stats) {
+  OpData& op = h->op(transpose);
+  const int k = io.k;
+  const int kb = kb_for(k);
+  const int64_t n = op.n;
+  const int prec = o.precision;
+  const int st_in = st_of(prec, cplx);
+  const int st64 = cplx ? ST_C64 : ST_F64;
+  const size_t es = st_size(st_in), es64 = st_size(st64);
+  int Lmax = 0;
+  for (int c = 0; c < k; ++c) Lmax = std::max(Lmax, io.L[c]);
+  if (Lmax > (int)op.chain.size()) return mor_fail(h, MOR_ESTATE, "chain shorter than requested prefix");
+  if (Lmax > MAX_FACTORS) return mor_fail(h, MOR_EINVAL, "chain too long");
+  for (int f = 0; f < Lmax; ++f) {
+    const Factor& F = op.chain[f];
+    if (st_is_f32(F.st) != st_is_f32(st_in))
+      return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from the solve precision");
+    if (st_is_cplx(F.st) && !st_is_cplx(st_in)) return mor_fail(h, MOR_EINVAL, "internal: complex factor, real vectors");
+  }
+  // workspace: 12 inner vectors
+  const size_t vbytes = es * (size_t)n * k;
+  MOR_CK(h, h->ws_vec.alloc(vbytes * 12 + 256 * 12));
+  char* vb = h->ws_vec.as<char>();
+  auto vec = [&](int i) { return (void*)(vb + ((vbytes + 255) / 256 * 256) * i); };
+  void *rhs = vec(0), *d = vec(1), *r = vec(2), *rhat = vec(3), *p = vec(4), *v = vec(5), *sv = vec(6),
+       *t = vec(7), *ph = vec(8), *sh = vec(9), *tmp0 = vec(10), *tmp1 = vec(11);
+  MOR_CK(h, h->ws_r64.alloc(es64 * (size_t)n * k));
+  void* r64 = h->ws_r64.p;
+  const int gc = h->grid_cap;
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_KMAX * (size_t)std::max(gc, 2048)));
+  Small sm;
+  MOR_TRY(get_small(h, sm));
+  // per-factor application masks
+  std::vector<int> masks((size_t)std::max(Lmax, 1) * MOR_KMAX, 0);
+  for (int f = 0; f < Lmax; ++f)
+    for (int c = 0; c < k; ++c) masks[(size_t)f * MOR_KMAX + c] = (f < io.L[c]) ? 1 : 0;
+  if (Lmax > 0)
+    MOR_CK(h, cudaMemcpyAsync(sm.masks, masks.data(), sizeof(int) * masks.size(), cudaMemcpyHostToDevice, h->stream));
+  // coefficients
+  Coef cf[MOR_KMAX], ncf[MOR_KMAX];
+  for (int c = 0; c < k; ++c) {
+    cf[c] = mor_coef(h, io.sig[c]);
+    ncf[c] = Coef{-cf[c].sEr, -cf[c].sEi, -cf[c].sAr, -cf[c].sAi};
+  }
+  PatView pv = op.view();
+  OpVals ov_in = op_vals(h, op, st_is_f32(st_in));
+  OpVals ov64 = op_vals(h, op, false);
+  MOR_CK(h, cudaMemsetAsync(io.x64, 0, es64 * (size_t)n * k, h->stream));
+
+  // the iteration as a launch sequence
+  auto chain_apply = [&](void* src, void* dst) -> int {
+    if (Lmax == 0) return 0;
+    void* s = src;
+    for (int f = 0; f < Lmax; ++f) {
+      void* dd = (f == Lmax - 1) ? dst : ((f % 2 == 0) ? tmp0 : tmp1);
+      const Factor& F = op.chain[f];
+      int e = launch_factor_spmv(st_in, st_is_cplx(F.st), kb, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, k, s,
+                                 dd, sm.done, h->stream);
+      if (e) return e;
+      s = dd;
+    }
+    return 0;
+  };
+  void* phat = (Lmax == 0) ? p : ph;
+  void* shat = (Lmax == 0) ? sv : sh;
+  auto one_iter = [&]() -> int {
+    int e;
+    if ((e = krylov_launch_update_p(st_in, kb, (int)n, k, r, p, v, sm.kstate, sm.done, h->stream))) return e;
+    if ((e = chain_apply(p, ph))) return e;
+    RedArgs ra{RED_DOT_W, rhat, h->ws_part.p, sm.counter, FIN_ALPHA, sm.kstate, nullptr, sm.done};
+    if ((e = launch_op_spmv(st_in, kb, pv, ov_in, cf, k, phat, v, nullptr, &ra, gc, h->stream))) return e;
+    if ((e = krylov_launch_update_s(st_in, kb, (int)n, k, r, v, sv, sm.kstate, sm.done, h->stream))) return e;
+    if ((e = chain_apply(sv, sh))) return e;
+    RedArgs rb{RED_DOT_TT, sv, h->ws_part.p, sm.counter, FIN_OMEGA, sm.kstate, nullptr, sm.done};
+    if ((e = launch_op_spmv(st_in, kb, pv, ov_in, cf, k, shat, t, nullptr, &rb, gc, h->stream))) return e;
+    if ((e = krylov_launch_update_xr(st_in, kb, (int)n, k, d, r, phat, shat, sv, t, rhat, h->ws_part.p, sm.counter,
+                                     sm.kstate, sm.done, gc, h->stream)))
+      return e;
+    return 0;
+  };
+  const int chunk = std::max(1, o.graph_chunk);
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_nodes = 0;
+  if (o.use_graph) {
+    cudaGraph_t g = nullptr;
+    int64_t c0 = 0, c1 = 0;
+    mor_launch_count(&c0);
+    MOR_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int e = 0;
+    for (int it = 0; it < chunk && !e; ++it) e = one_iter();
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+    mor_launch_count(&c1);
+    graph_nodes = c1 - c0;
+    mor_count_launches(-graph_nodes);   // captured, not executed
+    if (e) { if (g) cudaGraphDestroy(g); return mor_fail(h, MOR_ECUDA, "kernel launch failed during capture: %s", cudaGetErrorString((cudaError_t)e)); }
+    MOR_CK(h, ce);
+    ce = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    MOR_CK(h, ce);
+  }
+  struct GraphGuard { cudaGraphExec_t g; ~GraphGuard() { if (g) cudaGraphExecDestroy(g); } } guard{gexec};
+
+  const int max_outer = (prec == MOR_FP64) ? 4 : std::max(1, o.max_refine);
+  std::vector<double> bnorm(k, 0.0), relres(k, 0.0);
+  std::vector<int> iters(k, 0), refs(k, 0), status(k, MOR_OK), act(k, 0);
+  double* hp = (double*)h->pinned;
+  for (int pass = 0;; ++pass) {
+    // true residual r64 = b - A(sigma) x64 in FP64 with fused norms
+    RedArgs rn{RED_NORM, nullptr, h->ws_part.p, sm.counter, FIN_NONE, nullptr, sm.sums, nullptr};
+    MOR_CKI(h, launch_op_spmv(st64, kb, pv, ov64, ncf, k, io.x64, r64, io.b64, &rn, gc, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(hp, sm.sums, sizeof(cdouble) * 2 * k, cudaMemcpyDeviceToHost, h->stream));
+    MOR_CK(h, cudaStreamSynchronize(h->stream));
+    std::vector<double> rn2(k);
+    for (int c = 0; c < k; ++c) rn2[c] = hp[4 * c];
+    if (pass == 0) for (int c = 0; c < k; ++c) bnorm[c] = std::sqrt(rn2[c]);
+    int nact = 0;
+    for (int c = 0; c < k; ++c) {
+      relres[c] = bnorm[c] > 0 ? std::sqrt(rn2[c]) / bnorm[c] : 0.0;
+      act[c] = (bnorm[c] > 0 && relres[c] > o.tol && status[c] == MOR_OK && iters[c] < o.maxit &&
+                std::isfinite(relres[c])) ? 1 : 0;
+      nact += act[c];
+    }
+    if (nact == 0 || pass >= max_outer) {
+      for (int c = 0; c < k; ++c) {
+        if (!(relres[c] <= o.tol)) {
+          if (status[c] == MOR_OK) status[c] = MOR_ENOCONV;
+        } else status[c] = MOR_OK;
+      }
+      break;
+    }
+    // inner targets
+    double* tg = hp + 64;
+    int* mi = (int*)(hp + 96);
+    int* ac = (int*)(hp + 128);
+    double* nr = hp + 160;
+    for (int c = 0; c < k; ++c) {
+      const double need = act[c] ? o.tol * bnorm[c] / std::sqrt(rn2[c]) : 1.0;
+      tg[c] = (prec == MOR_FP64) ? need : std::max(o.inner_tol, 0.5 * need);
+      mi[c] = act[c] ? std::max(0, o.maxit - iters[c]) : 0;
+      ac[c] = act[c];
+      nr[c] = rn2[c];
+      if (act[c]) refs[c] += 1;
+    }
+    MOR_CK(h, cudaMemcpyAsync(sm.target, tg, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(sm.maxit, mi, sizeof(int) * k, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(sm.active, ac, sizeof(int) * k, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(sm.nrm2, nr, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+    MOR_CKI(h, refine_launch_scale_cast(st_in, kb, (int)n, k, r64, sm.nrm2, sm.active, rhs, h->stream));
+    MOR_CKI(h, krylov_launch_init(st_in, kb, (int)n, k, rhs, d, r, rhat, p, v, h->ws_part.p, sm.counter, sm.kstate,
+                                  sm.target, sm.maxit, sm.done, gc, h->stream));
+    int maxrem = 0;
+    for (int c = 0; c < k; ++c) maxrem = std::max(maxrem, mi[c]);
+    int done_flag = 0;
+    int it = 0;
+    int* hd = (int*)(hp + 200);
+    while (it < maxrem) {
+      if (gexec) {
+        MOR_CK(h, cudaGraphLaunch(gexec, h->stream));
+        mor_count_launches(graph_nodes);
+        it += chunk;
+      } else {
+        MOR_CKI(h, one_iter());
+        it += 1;
+      }
+      if (gexec || (it % chunk) == 0 || it >= maxrem) {
+        MOR_CK(h, cudaMemcpyAsync(hd, sm.done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        MOR_CK(h, cudaStreamSynchronize(h->stream));
+        done_flag = *hd;
+        if (done_flag) break;
+      }
+    }
+    int kit[MOR_KMAX], kst[MOR_KMAX];
+    MOR_CKI(h, krylov_read_state(st_in, sm.kstate, k, kit, kst, h->stream));
+    for (int c = 0; c < k; ++c) {
+      if (!act[c]) continue;
+      iters[c] += kit[c];
+      if (kst[c] == KST_BREAKDOWN && prec != MOR_FP64 && pass + 1 >= max_outer) status[c] = MOR_EBREAKDOWN;
+      if (kst[c] == KST_BREAKDOWN && prec == MOR_FP64 && pass + 1 >= max_outer) status[c] = MOR_EBREAKDOWN;
+    }
+    MOR_CKI(h, refine_launch_update(st_in, kb, (int)n, k, io.x64, d, sm.nrm2, sm.active, h->stream));
+  }
+  if (stats)
+    for (int c = 0; c < k; ++c) {
+      stats[c].iters = iters[c];
+      stats[c].refinements = refs[c];
+      stats[c].relres = relres[c];
+      stats[c].status = status[c];
+    }
+  int worst = MOR_OK;
+  for (int c = 0; c < k; ++c)
+    if (status[c] != MOR_OK) worst = (worst == MOR_OK || status[c] == MOR_EBREAKDOWN) ? status[c] : worst;
+  if (worst != MOR_OK) return mor_fail(h, worst, "%s in at least one column", worst == MOR_EBREAKDOWN ? "breakdown" : "no convergence");
+  return MOR_OK;
+}
+
+// Solve k shifts (any k), batching by 16.  rhs: either R (col-major c128, host or
+// device) or the system's B/C column 0.  X out col-major c128 (host or device).
+static int solve_many(mor_t h, const mor_c64* sig, int k, int transpose, const mor_solve_opts& o,
+                      const std::vector<int>& L, bool cplx, const mor_c64* R, bool dev, void* Xrow64_keep,
+                      mor_c64* X, mor_solve_stats* stats) {
+  const int64_t n = h->n;
+  const int st64 = cplx ? ST_C64 : ST_F64;
+  const size_t es64 = st_size(st64);
+  const int bmax = o.batch ? MOR_KMAX : 1;
+  int ret = MOR_OK;
+  for (int c0 = 0; c0 < k; c0 += bmax) {
+    const int kc = std::min(bmax, k - c0);
+    MOR_CK(h, h->ws_b64.alloc(es64 * (size_t)n * kc));
+    void* xrow;
+    if (Xrow64_keep) xrow = (char*)Xrow64_keep + es64 * (size_t)n * c0;   // caller keeps row-major blocks
+    else { MOR_CK(h, h->ws_x64.alloc(es64 * (size_t)n * kc)); xrow = h->ws_x64.p; }
+    if (R) {
+      const mor_c64* Rc = R + (size_t)n * c0;
+      const void* src = Rc;
+      if (!dev) {
+        MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * kc));
+        MOR_CK(h, cudaMemcpyAsync(h->ws_io.p, Rc, sizeof(mor_c64) * (size_t)n * kc, cudaMemcpyHostToDevice, h->stream));
+        src = h->ws_io.p;
+      }
+      MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st64, (int)n, kc, src, h->ws_b64.p, h->stream));
+    } else {
+      const double* col0 = transpose ? h->C.as<double>() : h->B.as<double>();
+      MOR_CKI(h, conv_launch_real_col_to_rowmajor(st64, (int)n, kc, col0, 0, h->ws_b64.p, h->stream));
+    }
+    BatchIO io{sig + c0, kc, L.data() + c0, h->ws_b64.p, xrow};
+    int s = solve_batch(h, transpose, o, cplx, io, stats ? stats + c0 : nullptr);
+    if (s != MOR_OK && s != MOR_ENOCONV && s != MOR_EBREAKDOWN) return s;
+    if (s != MOR_OK) ret = s;
+    if (X) {
+      mor_c64* Xc = X + (size_t)n * c0;
+      if (dev) {
+        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, xrow, Xc, h->stream));
+      } else {
+        MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * kc));
+        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, xrow, h->ws_io.p, h->stream));
+        MOR_CK(h, cudaMemcpyAsync(Xc, h->ws_io.p, sizeof(mor_c64) * (size_t)n * kc, cudaMemcpyDeviceToHost, h->stream));
+      }
+    }
+  }
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  return ret;
+}
+
+static std::vector<int> prefix_lengths(OpData& op, const mor_c64* sig, int k) {
+  std::vector<int> L(k, (int)op.chain.size());
+  for (int c = 0; c < k; ++c)
+    for (int f = (int)op.chain.size() - 1; f >= 0; --f)
+      if (same_shift(op.chain[f].to, sig[c])) { L[c] = f + 1; break; }
+  return L;
+}
+
+static bool chain_cplx(const OpData& op, const std::vector<int>& L) {
+  int Lmax = 0;
+  for (int x : L) Lmax = std::max(Lmax, x);
+  for (int f = 0; f < Lmax; ++f) if (st_is_cplx(op.chain[f].st)) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Gram-Schmidt and projection helpers on device FP64 column-major blocks
+// ---------------------------------------------------------------------------
+static int orth_device(mor_t h, double* V, int64_t n, int k, int* dependent) {
+  MOR_CK(h, h->ws_gram.alloc(sizeof(double) * (2 * 2 * 128 + 4096)));
+  double* hbuf = h->ws_gram.as<double>();          // h coefficients (k), norms
+  double* norms = hbuf + 256;                       // [2j] original, [2j+1] final
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 1024 * (size_t)h->grid_cap));
+  unsigned* cnt = h->ws_counter.as<unsigned>() + 8;
+  for (int j = 0; j < k; ++j) {
+    double* v = V + (size_t)j * n;
+    MOR_CKI(h, dense_launch_gram((int)n, 1, 1, v, n, v, n, norms + 2 * j, h->ws_part.as<double>(), cnt, h->grid_cap, h->stream));
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {
+      MOR_CKI(h, dense_launch_gram((int)n, j, 1, V, n, v, n, hbuf, h->ws_part.as<double>(), cnt, h->grid_cap, h->stream));
+      MOR_CKI(h, dense_launch_gs_update((int)n, j, V, n, hbuf, v, h->stream));
+    }
+    MOR_CKI(h, dense_launch_gram((int)n, 1, 1, v, n, v, n, norms + 2 * j + 1, h->ws_part.as<double>(), cnt, h->grid_cap, h->stream));
+    MOR_CKI(h, dense_launch_scale((int)n, v, norms + 2 * j + 1, h->stream));
+  }
+  std::vector<double> nh(2 * k);
+  MOR_CK(h, cudaMemcpyAsync(nh.data(), norms, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  *dependent = 0;
+  for (int j = 0; j < k; ++j)
+    if (!(nh[2 * j + 1] > 1e-28 * nh[2 * j]) || !std::isfinite(nh[2 * j + 1])) *dependent = 1;
+  return MOR_OK;
+}
+
+// A_r = W^T A V, E_r = W^T E V, B_r = W^T B, C_r = V^T C (device V, W), into rom
+static int project_device(mor_t h, const double* V, const double* W, int r, mor_reduced* rom) {
+  const int64_t n = h->n;
+  OpData& op = h->P;
+  MOR_CK(h, h->ws_basis.alloc(sizeof(double) * (size_t)n * r * 2));
+  double* AV = h->ws_basis.as<double>();
+  double* EV = AV + (size_t)n * r;
+  PatView pv = op.view();
+  OpVals ov = op_vals(h, op, false);
+  Coef ca{0, 0, 1, 0}, ce{1, 0, 0, 0};
+  for (int j = 0; j < r; ++j) {
+    MOR_CKI(h, launch_op_spmv(ST_F64, 1, pv, ov, &ca, 1, V + (size_t)j * n, AV + (size_t)j * n, nullptr, nullptr, h->grid_cap, h->stream));
+    MOR_CKI(h, launch_op_spmv(ST_F64, 1, pv, ov, &ce, 1, V + (size_t)j * n, EV + (size_t)j * n, nullptr, nullptr, h->grid_cap, h->stream));
+  }
+  MOR_CK(h, h->ws_rom.alloc(sizeof(double) * 6 * MOR_MAX_R * MOR_MAX_R));
+  double* dAr = h->ws_rom.as<double>();
+  double* dEr = dAr + MOR_MAX_R * MOR_MAX_R;
+  double* dBr = dEr + MOR_MAX_R * MOR_MAX_R;
+  double* dCr = dBr + MOR_MAX_R * MOR_MAX_IO;
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 1024 * (size_t)h->grid_cap));
+  unsigned* cnt = h->ws_counter.as<unsigned>() + 16;
+  double* part = h->ws_part.as<double>();
+  MOR_CKI(h, dense_launch_gram((int)n, r, r, W, n, AV, n, dAr, part, cnt, h->grid_cap, h->stream));
+  MOR_CKI(h, dense_launch_gram((int)n, r, r, W, n, EV, n, dEr, part, cnt, h->grid_cap, h->stream));
+  MOR_CKI(h, dense_launch_gram((int)n, r, h->m, W, n, h->B.as<double>(), n, dBr, part, cnt, h->grid_cap, h->stream));
+  MOR_CKI(h, dense_launch_gram((int)n, r, h->q, V, n, h->C.as<double>(), n, dCr, part, cnt, h->grid_cap, h->stream));
+  rom->r = r;
+  rom->m = h->m;
+  rom->q = h->q;
+  MOR_CK(h, cudaMemcpyAsync(rom->Ar, dAr, sizeof(double) * r * r, cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(rom->Er, dEr, sizeof(double) * r * r, cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(rom->Br, dBr, sizeof(double) * r * h->m, cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(rom->Cr, dCr, sizeof(double) * r * h->q, cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  return MOR_OK;
+}
+
+static int poles_device(mor_t h, const mor_reduced* rom, mor_c64* lam, mor_c64* shifts) {
+  const int r = rom->r;
+  MOR_CK(h, h->ws_rom.alloc(sizeof(double) * 6 * MOR_MAX_R * MOR_MAX_R));
+  double* dAr = h->ws_rom.as<double>();
+  double* dEr = dAr + MOR_MAX_R * MOR_MAX_R;
+  double* out = dEr + MOR_MAX_R * MOR_MAX_R;   // 4r+1 + 2r^2 doubles + r ints fits in 2 * 64^2
+  MOR_CK(h, cudaMemcpyAsync(dAr, rom->Ar, sizeof(double) * r * r, cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(dEr, rom->Er, sizeof(double) * r * r, cudaMemcpyHostToDevice, h->stream));
+  MOR_CKI(h, dense_launch_eig(r, dAr, dEr, out, h->stream));
+  std::vector<double> ho(4 * r + 1);
+  MOR_CK(h, cudaMemcpyAsync(ho.data(), out, sizeof(double) * (4 * r + 1), cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  if (ho[4 * r] != 0.0) return mor_fail(h, MOR_ESINGULAR, ho[4 * r] == 1.0 ? "E_r is singular" : "QR iteration did not converge");
+  for (int i = 0; i < r; ++i) {
+    if (lam) lam[i] = mor_c64{ho[i], ho[r + i]};
+    if (shifts) shifts[i] = mor_c64{ho[2 * r + i], ho[3 * r + i]};
+  }
+  return MOR_OK;
+}
+
+// extract Re / Im columns of a row-major n x k (st64) block into a col-major FP64 basis
+__global__ void extract_kernel(int n, int k, int c, int part, int cplx, const double* src, double* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = cplx ? src[2 * (i * k + c) + part] : src[i * k + c];
+}
+
+extern "C" {
+
+int mor_build_precond(mor_t h, mor_c64 sigma, int transpose, int precision) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (precision != MOR_FP64 && precision != MOR_MIXED) return mor_fail(h, MOR_EINVAL, "bad precision");
+  if (!std::isfinite(sigma.re) || !std::isfinite(sigma.im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
+  cudaSetDevice(h->dev);
+  return build_factor(h, transpose, sigma, sigma, false, precision);
+}
+
+int mor_update_precond(mor_t h, mor_c64 sigma_new, int transpose) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  OpData& X = h->op(transpose);
+  if (X.chain.empty()) return mor_fail(h, MOR_ESTATE, "update_precond before build_precond");
+  if (!std::isfinite(sigma_new.re) || !std::isfinite(sigma_new.im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
+  cudaSetDevice(h->dev);
+  return build_factor(h, transpose, X.chain.back().to, sigma_new, true, X.chain_prec);
+}
+
+int mor_truncate_precond(mor_t h, int transpose, int length) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  OpData& X = h->op(transpose);
+  if (length < 0) return mor_fail(h, MOR_EINVAL, "negative length");
+  if ((size_t)length < X.chain.size()) {
+    cudaStreamSynchronize(h->stream);
+    X.chain.resize(length);
+  }
+  return MOR_OK;
+}
+
+int mor_chain_info(mor_t h, int transpose, int* length, int* precision) {
+  if (!h) return MOR_EINVAL;
+  OpData& X = h->op(transpose);
+  if (length) *length = (int)X.chain.size();
+  if (precision) *precision = X.chain_prec;
+  return MOR_OK;
+}
+
+int mor_get_factor(mor_t h, int transpose, int index, mor_c64* vals, mor_c64* sfrom, mor_c64* sto) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  OpData& X = h->op(transpose);
+  if (index < 0 || index >= (int)X.chain.size()) return mor_fail(h, MOR_EINVAL, "factor index out of range");
+  const Factor& F = X.chain[index];
+  if (sfrom) *sfrom = F.from;
+  if (sto) *sto = F.to;
+  if (vals) {
+    DBuf tmp;
+    MOR_CK(h, tmp.alloc(sizeof(mor_c64) * (size_t)X.nlay));
+    MOR_CKI(h, conv_launch_copy_cast(ST_C64, F.st, X.nlay, F.vals->p, tmp.p, h->stream));
+    std::vector<mor_c64> lay(X.nlay);
+    MOR_CK(h, cudaMemcpyAsync(lay.data(), tmp.p, sizeof(mor_c64) * X.nlay, cudaMemcpyDeviceToHost, h->stream));
+    MOR_CK(h, cudaStreamSynchronize(h->stream));
+    for (int64_t p = 0; p < X.nnz; ++p) vals[p] = lay[X.h_lay[p]];
+  }
+  return MOR_OK;
+}
+
+int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int precision, const mor_c64* X,
+                       mor_c64* Y, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (k < 1 || k > MOR_KMAX || !sigma || !X || !Y) return mor_fail(h, MOR_EINVAL, "bad arguments");
+  cudaSetDevice(h->dev);
+  const bool dev = flags & MOR_DEVICE_PTRS;
+  OpData& op = h->op(transpose);
+  const int64_t n = h->n;
+  const int st = (precision == MOR_FP64) ? ST_C64 : ST_C32;
+  MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * k * 3));
+  mor_c64* io = h->ws_io.as<mor_c64>();
+  const void* src = X;
+  if (!dev) {
+    MOR_CK(h, cudaMemcpyAsync(io, X, sizeof(mor_c64) * n * k, cudaMemcpyHostToDevice, h->stream));
+    src = io;
+  }
+  char* xr = (char*)(io + (size_t)n * k);
+  char* yr = xr + st_size(st) * (size_t)n * k;
+  MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st, (int)n, k, src, xr, h->stream));
+  Coef cf[MOR_KMAX];
+  for (int c = 0; c < k; ++c) cf[c] = mor_coef(h, sigma[c]);
+  MOR_CKI(h, launch_op_spmv(st, kb_for(k), op.view(), op_vals(h, op, precision != MOR_FP64), cf, k, xr, yr, nullptr,
+                            nullptr, h->grid_cap, h->stream));
+  if (dev) {
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, yr, Y, h->stream));
+  } else {
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, yr, io, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(Y, io, sizeof(mor_c64) * n * k, cudaMemcpyDeviceToHost, h->stream));
+  }
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  return MOR_OK;
+}
+
+int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const mor_c64* X, mor_c64* Y,
+                      unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (k < 1 || k > MOR_KMAX || !sigma || !X || !Y) return mor_fail(h, MOR_EINVAL, "bad arguments");
+  OpData& op = h->op(transpose);
+  if (op.chain.empty()) return mor_fail(h, MOR_ESTATE, "no preconditioner built");
+  cudaSetDevice(h->dev);
+  const bool dev = flags & MOR_DEVICE_PTRS;
+  const int64_t n = h->n;
+  const int st = (op.chain_prec == MOR_FP64) ? ST_C64 : ST_C32;
+  std::vector<int> L = prefix_lengths(op, sigma, k);
+  int Lmax = 0;
+  for (int x : L) Lmax = std::max(Lmax, x);
+  MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * k * 3));
+  mor_c64* io = h->ws_io.as<mor_c64>();
+  const void* src = X;
+  if (!dev) {
+    MOR_CK(h, cudaMemcpyAsync(io, X, sizeof(mor_c64) * n * k, cudaMemcpyHostToDevice, h->stream));
+    src = io;
+  }
+  char* a = (char*)(io + (size_t)n * k);
+  char* b = a + st_size(st) * (size_t)n * k;
+  MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st, (int)n, k, src, a, h->stream));
+  Small sm;
+  MOR_TRY(get_small(h, sm));
+  std::vector<int> masks((size_t)std::max(Lmax, 1) * MOR_KMAX, 0);
+  for (int f = 0; f < Lmax; ++f)
+    for (int c = 0; c < k; ++c) masks[(size_t)f * MOR_KMAX + c] = (f < L[c]) ? 1 : 0;
+  MOR_CK(h, cudaMemcpyAsync(sm.masks, masks.data(), sizeof(int) * masks.size(), cudaMemcpyHostToDevice, h->stream));
+  char* s = a;
+  char* d = b;
+  for (int f = 0; f < Lmax; ++f) {
+    MOR_CKI(h, launch_factor_spmv(st, st_is_cplx(op.chain[f].st), kb_for(k), op.view(), op.chain[f].vals->p,
+                                  sm.masks + (size_t)f * MOR_KMAX, k, s, d, nullptr, h->stream));
+    std::swap(s, d);
+  }
+  if (dev) {
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, s, Y, h->stream));
+  } else {
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, s, io, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(Y, io, sizeof(mor_c64) * n * k, cudaMemcpyDeviceToHost, h->stream));
+  }
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  return MOR_OK;
+}
+
+int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const mor_solve_opts* opts,
+                     const mor_c64* R, mor_c64* X, mor_solve_stats* stats, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (k < 1 || k > 64 || !sigma || !X) return mor_fail(h, MOR_EINVAL, "bad arguments (1 <= k <= 64)");
+  mor_solve_opts o;
+  if (opts) o = *opts; else mor_default_opts(&o);
+  if (o.precision != MOR_FP64 && o.precision != MOR_MIXED) return mor_fail(h, MOR_EINVAL, "bad precision");
+  if (!(o.tol > 0) || o.maxit < 0) return mor_fail(h, MOR_EINVAL, "bad tolerance or maxit");
+  for (int c = 0; c < k; ++c)
+    if (!std::isfinite(sigma[c].re) || !std::isfinite(sigma[c].im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
+  cudaSetDevice(h->dev);
+  const bool dev = flags & MOR_DEVICE_PTRS;
+  OpData& op = h->op(transpose);
+  bool rc = false;
+  if (R) {
+    if (dev) rc = true;
+    else for (int64_t i = 0; i < h->n * (int64_t)k && !rc; ++i) rc = (R[i].im != 0.0);
+  }
+  bool anyc = rc;
+  for (int c = 0; c < k; ++c) anyc |= !is_real_shift(sigma[c]);
+  if (o.precond == 1) {
+    // a new SPAI per shift: one column at a time
+    int ret = MOR_OK;
+    for (int c = 0; c < k; ++c) {
+      MOR_TRY(build_factor(h, transpose, sigma[c], sigma[c], false, o.precision));
+      std::vector<int> L(1, 1);
+      bool cc = anyc || chain_cplx(op, L);
+      int s = solve_many(h, sigma + c, 1, transpose, o, L, cc, R ? R + (size_t)h->n * c : nullptr, dev, nullptr,
+                         X + (size_t)h->n * c, stats ? stats + c : nullptr);
+      if (s != MOR_OK && s != MOR_ENOCONV && s != MOR_EBREAKDOWN) return s;
+      if (s != MOR_OK) ret = s;
+    }
+    return ret;
+  }
+  std::vector<int> L = (o.precond == 2) ? std::vector<int>(k, 0) : prefix_lengths(op, sigma, k);
+  if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision)
+    return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from opts.precision");
+  bool cc = anyc || chain_cplx(op, L);
+  return solve_many(h, sigma, k, transpose, o, L, cc, R, dev, nullptr, X, stats);
+}
+
+int mor_orthonormalize(mor_t h, double* X, int k, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (k < 1 || k > MOR_MAX_R || !X) return mor_fail(h, MOR_EINVAL, "bad arguments (1 <= k <= 64)");
+  cudaSetDevice(h->dev);
+  const int64_t n = h->n;
+  double* V = X;
+  DBuf tmp;
+  if (!(flags & MOR_DEVICE_PTRS)) {
+    MOR_CK(h, tmp.alloc(sizeof(double) * n * k));
+    MOR_CK(h, cudaMemcpyAsync(tmp.p, X, sizeof(double) * n * k, cudaMemcpyHostToDevice, h->stream));
+    V = tmp.as<double>();
+  }
+  int dep = 0;
+  MOR_TRY(orth_device(h, V, n, k, &dep));
+  if (!(flags & MOR_DEVICE_PTRS)) {
+    MOR_CK(h, cudaMemcpyAsync(X, V, sizeof(double) * n * k, cudaMemcpyDeviceToHost, h->stream));
+    MOR_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  if (dep) return mor_fail(h, MOR_ESINGULAR, "numerically dependent column");
+  return MOR_OK;
+}
+
+int mor_project(mor_t h, const double* V, const double* W, int r, mor_reduced* rom, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (h->order != 1) return mor_fail(h, MOR_EINVAL, "projection of second-order systems is not available");
+  if (r < 1 || r > MOR_MAX_R || !V || !W || !rom) return mor_fail(h, MOR_EINVAL, "bad arguments");
+  cudaSetDevice(h->dev);
+  const int64_t n = h->n;
+  const double *Vd = V, *Wd = W;
+  DBuf tmp;
+  if (!(flags & MOR_DEVICE_PTRS)) {
+    MOR_CK(h, tmp.alloc(sizeof(double) * n * r * 2));
+    MOR_CK(h, cudaMemcpyAsync(tmp.p, V, sizeof(double) * n * r, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(tmp.as<double>() + n * r, W, sizeof(double) * n * r, cudaMemcpyHostToDevice, h->stream));
+    Vd = tmp.as<double>();
+    Wd = Vd + n * r;
+  }
+  return project_device(h, Vd, Wd, r, rom);
+}
+
+int mor_reduced_poles(mor_t h, const mor_reduced* rom, mor_c64* lambda, mor_c64* shifts) {
+  if (!h || !rom) return MOR_EINVAL;
+  if (rom->r < 1 || rom->r > MOR_MAX_R) return mor_fail(h, MOR_EINVAL, "bad r");
+  cudaSetDevice(h->dev);
+  return poles_device(h, rom, lambda, shifts);
+}
+
+int mor_irka_reset(mor_t h) {
+  if (!h) return MOR_EINVAL;
+  h->irka_z = 0;
+  h->vlen[0] = h->vlen[1] = 0;
+  return MOR_OK;
+}
+
+int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, mor_reduced* rom_out,
+                  mor_irka_stats* st_out) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (h->order != 1) return mor_fail(h, MOR_EINVAL, "IRKA of second-order systems is not available");
+  if (r < 1 || r > MOR_MAX_R || !shifts) return mor_fail(h, MOR_EINVAL, "bad r");
+  if (h->m != 1 || h->q != 1) return mor_fail(h, MOR_EINVAL, "mor_irka_step supports SISO systems (m = q = 1)");
+  mor_solve_opts o;
+  if (opts) o = *opts; else mor_default_opts(&o);
+  cudaSetDevice(h->dev);
+  cudaEvent_t ev[5];
+  for (auto& e : ev) cudaEventCreate(&e);
+  struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]); } } eg{ev};
+  mor_irka_stats st;
+  std::memset(&st, 0, sizeof st);
+  // sort (Re, |Im|, -Im) and check conjugate closure
+  std::vector<mor_c64> s(shifts, shifts + r);
+  for (auto& x : s) if (!std::isfinite(x.re) || !std::isfinite(x.im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
+  std::sort(s.begin(), s.end(), [](mor_c64 a, mor_c64 b) {
+    if (a.re != b.re) return a.re < b.re;
+    if (std::fabs(a.im) != std::fabs(b.im)) return std::fabs(a.im) < std::fabs(b.im);
+    return -a.im < -b.im;
+  });
+  std::vector<mor_c64> sol;
+  for (int i = 0; i < r; ++i) {
+    if (s[i].im > 0) {
+      if (i + 1 >= r || s[i + 1].re != s[i].re || s[i + 1].im != -s[i].im)
+        return mor_fail(h, MOR_EINVAL, "shift set not closed under conjugation");
+      sol.push_back(s[i]);
+      ++i;
+    } else if (s[i].im == 0) sol.push_back(s[i]);
+    else return mor_fail(h, MOR_EINVAL, "shift set not closed under conjugation");
+  }
+  const int l = (int)sol.size();
+  st.nsolve = l;
+  cudaEventRecord(ev[0], h->stream);
+  // reuse schedule (Algorithm 4) for the primal and, unless symmetric, the transposed operator
+  std::vector<int> Ls[2];
+  const int nops = h->sym ? 1 : 2;
+  for (int t = 0; t < nops; ++t) {
+    OpData& X = h->op(t);
+    std::vector<int>& L = Ls[t];
+    L.assign(l, 0);
+    if (o.precond == 2) continue;
+    if (o.precond == 1) continue;   // fresh SPAI per shift: built below, one solve at a time
+    const bool rebuild = (h->irka_z == 0) || X.chain.empty() || X.chain_prec != o.precision ||
+                         (o.max_chain > 0 && h->vlen[t] + 1 > o.max_chain);
+    if (!rebuild) { X.chain.resize(h->vlen[t]); }
+    if (rebuild) {
+      MOR_TRY(build_factor(h, t, sol[0], sol[0], false, o.precision));
+      h->vlen[t] = 1;
+      st.builds_spai++;
+    } else {
+      MOR_TRY(build_factor(h, t, X.chain.back().to, sol[0], true, o.precision));
+      h->vlen[t] += 1;
+      st.builds_reuse++;
+    }
+    for (int i = 1; i < l; ++i) {
+      MOR_TRY(build_factor(h, t, sol[i - 1], sol[i], true, o.precision));
+      st.builds_reuse++;
+    }
+    for (int i = 0; i < l; ++i) L[i] = h->vlen[t] + i;
+    st.chain_len = std::max(st.chain_len, L[l - 1]);
+  }
+  if (h->sym) Ls[1] = Ls[0];
+  cudaEventRecord(ev[1], h->stream);
+  // solves: V (primal, rhs B) and W (transposed, rhs C)
+  bool cplx = false;
+  for (auto& x : sol) cplx |= (x.im != 0.0);
+  const int64_t n = h->n;
+  for (int t = 0; t < 2; ++t) {
+    OpData& X = h->op(t);
+    if (o.precond == 0) cplx |= chain_cplx(X, Ls[t]);
+  }
+  const int st64 = cplx ? ST_C64 : ST_F64;
+  DBuf xs[2];
+  std::vector<mor_solve_stats> ss(l);
+  int solve_status = MOR_OK;
+  for (int t = 0; t < 2; ++t) {
+    MOR_CK(h, xs[t].alloc(st_size(st64) * (size_t)n * l));
+    int s2;
+    if (o.precond == 1) {
+      s2 = MOR_OK;
+      for (int i = 0; i < l; ++i) {
+        MOR_TRY(build_factor(h, t, sol[i], sol[i], false, o.precision));
+        st.builds_spai++;
+        std::vector<int> L1(1, 1);
+        int s3 = solve_many(h, &sol[i], 1, t, o, L1, cplx, nullptr, false,
+                            (char*)xs[t].p + st_size(st64) * (size_t)n * i, nullptr, &ss[i]);
+        if (s3 != MOR_OK && s3 != MOR_ENOCONV && s3 != MOR_EBREAKDOWN) return s3;
+        if (s3 != MOR_OK) s2 = s3;
+      }
+    } else {
+      // solve_many keeps each 16-column block row-major at its offset
+      s2 = solve_many(h, sol.data(), l, t, o, Ls[t], cplx, nullptr, false, xs[t].p, nullptr, ss.data());
+      if (s2 != MOR_OK && s2 != MOR_ENOCONV && s2 != MOR_EBREAKDOWN) return s2;
+    }
+    if (s2 != MOR_OK) solve_status = s2;
+    for (int i = 0; i < l; ++i) {
+      (t == 0 ? st.iters_V : st.iters_W) += ss[i].iters;
+      st.max_relres = std::max(st.max_relres, ss[i].relres);
+    }
+  }
+  cudaEventRecord(ev[2], h->stream);
+  // real bases [Re v, Im v] and CGS2
+  MOR_CK(h, h->ws_basis.alloc(sizeof(double) * (size_t)n * r * 2));
+  DBuf basis;
+  MOR_CK(h, basis.alloc(sizeof(double) * (size_t)n * r * 2));
+  double* Vb = basis.as<double>();
+  double* Wb = Vb + (size_t)n * r;
+  for (int t = 0; t < 2; ++t) {
+    double* dst = t == 0 ? Vb : Wb;
+    int col = 0;
+    for (int i = 0; i < l; ++i) {
+      // block of 16 columns stored row-major with its own k
+      const int blk = i / MOR_KMAX, kc = std::min(MOR_KMAX, l - blk * MOR_KMAX), ci = i % MOR_KMAX;
+      const double* src = (const double*)((const char*)xs[t].p + st_size(st64) * (size_t)n * blk * MOR_KMAX);
+      const int g = (int)std::min<int64_t>((n + 255) / 256, h->grid_cap);
+      extract_kernel<<<g, 256, 0, h->stream>>>((int)n, kc, ci, 0, cplx ? 1 : 0, src, dst + (size_t)n * col++);
+      mor_count_launches(1);
+      if (sol[i].im != 0.0) {
+        extract_kernel<<<g, 256, 0, h->stream>>>((int)n, kc, ci, 1, 1, src, dst + (size_t)n * col++);
+        mor_count_launches(1);
+      }
+    }
+    MOR_CK(h, cudaGetLastError());
+  }
+  int dep = 0, dep2 = 0;
+  MOR_TRY(orth_device(h, Vb, n, r, &dep));
+  MOR_TRY(orth_device(h, Wb, n, r, &dep2));
+  if (dep || dep2) return mor_fail(h, MOR_ESINGULAR, "projection basis is numerically rank deficient");
+  cudaEventRecord(ev[3], h->stream);
+  mor_reduced rom;
+  MOR_TRY(project_device(h, Vb, Wb, r, &rom));
+  std::vector<mor_c64> news(r);
+  MOR_TRY(poles_device(h, &rom, nullptr, news.data()));
+  cudaEventRecord(ev[4], h->stream);
+  cudaEventSynchronize(ev[4]);
+  float ms;
+  cudaEventElapsedTime(&ms, ev[0], ev[1]); st.ms_precond = ms;
+  cudaEventElapsedTime(&ms, ev[1], ev[2]); st.ms_solve = ms;
+  cudaEventElapsedTime(&ms, ev[2], ev[3]); st.ms_orth = ms;
+  cudaEventElapsedTime(&ms, ev[3], ev[4]); st.ms_reduce = ms;
+  double chg = 0.0;
+  for (int i = 0; i < r; ++i) {
+    const double dr = news[i].re - s[i].re, di = news[i].im - s[i].im;
+    const double a = std::hypot(news[i].re, news[i].im);
+    chg = std::max(chg, std::hypot(dr, di) / (a > 0 ? a : 1.0));
+  }
+  st.shift_change = chg;
+  h->irka_z += 1;
+  st.z = h->irka_z;
+  st.status = solve_status;
+  for (int i = 0; i < r; ++i) shifts[i] = news[i];
+  if (rom_out) *rom_out = rom;
+  if (st_out) *st_out = st;
+  if (solve_status != MOR_OK) return mor_fail(h, solve_status, "a shifted solve did not converge");
+  return MOR_OK;
+}
+
+int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precision, int reps, double* ms) {
+  if (!h || !sigma || !ms) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (k < 1 || k > MOR_KMAX || reps < 1 || (which != 0 && which != 1)) return mor_fail(h, MOR_EINVAL, "bad arguments");
+  OpData& op = h->P;
+  if (which == 1 && op.chain.empty()) return mor_fail(h, MOR_ESTATE, "no preconditioner built");
+  cudaSetDevice(h->dev);
+  bool cplx = false;
+  for (int c = 0; c < k; ++c) cplx |= !is_real_shift(sigma[c]);
+  if (which == 1) {
+    cplx |= st_is_cplx(op.chain.back().st);
+    precision = op.chain_prec;
+  }
+  const int st = st_of(precision, cplx);
+  const int kb = kb_for(k);
+  const int64_t n = op.n;
+  DBuf x, y, w;
+  MOR_CK(h, x.alloc(st_size(st) * (size_t)n * k));
+  MOR_CK(h, y.alloc(st_size(st) * (size_t)n * k));
+  MOR_CK(h, w.alloc(st_size(st) * (size_t)n * k));
+  MOR_CK(h, cudaMemsetAsync(x.p, 0, st_size(st) * (size_t)n * k, h->stream));
+  MOR_CK(h, cudaMemsetAsync(w.p, 0, st_size(st) * (size_t)n * k, h->stream));
+  Small sm;
+  MOR_TRY(get_small(h, sm));
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_KMAX * (size_t)std::max(h->grid_cap, 2048)));
+  std::vector<int> ones(MOR_KMAX, 1);
+  MOR_CK(h, cudaMemcpyAsync(sm.masks, ones.data(), sizeof(int) * MOR_KMAX, cudaMemcpyHostToDevice, h->stream));
+  Coef cf[MOR_KMAX];
+  for (int c = 0; c < k; ++c) cf[c] = mor_coef(h, sigma[c]);
+  PatView pv = op.view();
+  OpVals ov = op_vals(h, op, st_is_f32(st));
+  RedArgs ra{RED_DOT_W, w.p, h->ws_part.p, sm.counter, FIN_NONE, nullptr, sm.sums, nullptr};
+  auto launch = [&]() -> int {
+    if (which == 0) return launch_op_spmv(st, kb, pv, ov, cf, k, x.p, y.p, nullptr, &ra, h->grid_cap, h->stream);
+    return launch_factor_spmv(st, st_is_cplx(op.chain.back().st), kb, pv, op.chain.back().vals->p, sm.masks, k,
+                              x.p, y.p, nullptr, h->stream);
+  };
+  for (int i = 0; i < 3; ++i) MOR_CKI(h, launch());
+  cudaEvent_t e0, e1;
+  MOR_CK(h, cudaEventCreate(&e0));
+  MOR_CK(h, cudaEventCreate(&e1));
+  cudaEventRecord(e0, h->stream);
+  for (int i = 0; i < reps; ++i) {
+    int e = launch();
+    if (e) { cudaEventDestroy(e0); cudaEventDestroy(e1); MOR_CKI(h, e); }
+  }
+  cudaEventRecord(e1, h->stream);
+  cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = (double)t / reps;
+  return MOR_OK;
+}
+
+int mor_eval_tf(mor_t h, const mor_reduced* rom, const double* omega, int nw, mor_c64* H, unsigned flags) {
+  if (!h || !rom || !omega || !H) return MOR_EINVAL;
+  if (rom->r < 1 || rom->r > MOR_MAX_R || rom->m < 1 || rom->m > MOR_MAX_IO || rom->q < 1 || rom->q > MOR_MAX_IO || nw < 1)
+    return mor_fail(h, MOR_EINVAL, "bad reduced system or nw");
+  cudaSetDevice(h->dev);
+  const int r = rom->r, m = rom->m, q = rom->q;
+  DBuf d;
+  const size_t nrom = (size_t)2 * r * r + (size_t)r * m + (size_t)r * q;
+  MOR_CK(h, d.alloc(sizeof(double) * (nrom + nw) + sizeof(mor_c64) * (size_t)nw * m * q));
+  double* dA = d.as<double>();
+  double* dE = dA + r * r;
+  double* dB = dE + r * r;
+  double* dC = dB + r * m;
+  double* dw = dC + r * q;
+  mor_c64* dH = (mor_c64*)(dw + nw);
+  MOR_CK(h, cudaMemcpyAsync(dA, rom->Ar, sizeof(double) * r * r, cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(dE, rom->Er, sizeof(double) * r * r, cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(dB, rom->Br, sizeof(double) * r * m, cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(dC, rom->Cr, sizeof(double) * r * q, cudaMemcpyHostToDevice, h->stream));
+  const bool dev = flags & MOR_DEVICE_PTRS;
+  const double* w = omega;
+  if (!dev) {
+    MOR_CK(h, cudaMemcpyAsync(dw, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, h->stream));
+    w = dw;
+  }
+  mor_c64* out = dev ? H : dH;
+  MOR_CKI(h, dense_launch_tf(r, m, q, dA, dE, dB, dC, w, nw, (double*)out, h->stream));
+  if (!dev) MOR_CK(h, cudaMemcpyAsync(H, dH, sizeof(mor_c64) * (size_t)nw * m * q, cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  return MOR_OK;
+}
+
+}  // extern "C"

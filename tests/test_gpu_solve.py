@@ -1,0 +1,166 @@
+"""GPU parity of the shifted solves (right-preconditioned BiCGSTAB with the
+reused SPAI chain; FP64, and FP32/complex64 inside FP64 refinement) against
+the CPU oracle.
+
+Bars:
+  * every solve reaches the true relative residual 1e-8, recomputed here in
+    FP64 by the oracle's operator (a 1e-3 relative slack on the bound covers
+    the different summation order of the residual itself);
+  * the GPU solution agrees with the oracle's within kappa * 2e-8, kappa the
+    2-norm condition number (both solutions have relative residual <= 1e-8);
+  * FP64 mode runs the oracle's algorithm, so its iteration counts agree
+    with the oracle's within 10% (plus 2 for very short solves).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import paper_2003_12759_gb300 as mor
+import workloads as W
+from oracle import operator as oop, spai as ospai, krylov as okry
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    mor.load_library()
+    hh = mor.mor_create(0)
+    yield hh
+    mor.mor_destroy(hh)
+
+
+def _relres(wl, sig, x, b, transpose=False):
+    M = oop.A_sigma(wl.A, wl.E, sig, transpose=transpose)
+    return np.linalg.norm(b - M @ x) / np.linalg.norm(b)
+
+
+def _set(h, wl, fmt=mor.MOR_FMT_AUTO):
+    if wl.E is None:
+        mor.mor_set_system(h, wl.A, wl.B, wl.C, fmt=fmt)
+    elif isinstance(wl.E, np.ndarray):
+        mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E, fmt=fmt)
+    else:
+        mor.mor_set_system(h, wl.A, wl.B, wl.C, E=wl.E, fmt=fmt)
+
+
+def _oracle_chain_solves(wl, shifts, transpose):
+    """Oracle solves with the same chain the library holds after
+    build(s1) + update(s2) + ... : shift i uses Q_i ... Q_2 P_1."""
+    S = ospai.spai_pattern(wl.A, wl.E, transpose=transpose)
+    Ms = [oop.A_sigma(wl.A, wl.E, s, transpose=transpose) for s in shifts]
+    F = [ospai.spai(Ms[0], S)] + [ospai.reuse_factor(Ms[i - 1], Ms[i], S) for i in range(1, len(shifts))]
+    out = []
+    b = (wl.C if transpose else wl.B)[:, 0]
+    for i, s in enumerate(shifts):
+        x, it, rel, st = okry.bicgstab(lambda v, M=Ms[i]: M @ v, lambda v, f=F[: i + 1]: ospai.chain_apply(f, v),
+                                       b.astype(Ms[i].dtype), tol=1e-8)
+        out.append((x, it, rel, st))
+    return out
+
+
+CASES = {
+    "convdiff3d_n3375": lambda: W.config1(N=15),
+    "laplace2d_n4900": lambda: W.config0(N=70),
+    "rand_csrE_n1500": lambda: W.random_sparse_system(1500, 0.004, seed=8, e_kind="csr"),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("transpose", [0, 1])
+@pytest.mark.parametrize("batch", [1, 0])
+def test_fp64_solves_match_oracle(h, name, transpose, batch):
+    wl = CASES[name]()
+    _set(h, wl)
+    shifts = [30.0, 45.0 + 20.0j, 90.0 + 5.0j]
+    mor.mor_build_precond(h, shifts[0], transpose, mor.MOR_FP64)
+    for s in shifts[1:]:
+        mor.mor_update_precond(h, s, transpose)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64, batch=batch, use_graph=batch)
+    X, stats, code = mor.mor_solve_shifts(h, shifts, transpose, opts)
+    assert code == mor.MOR_OK
+    ref = _oracle_chain_solves(wl, shifts, bool(transpose))
+    b = (wl.C if transpose else wl.B)[:, 0]
+    for c, s in enumerate(shifts):
+        rel = _relres(wl, s, X[:, c], b, bool(transpose))
+        assert rel <= 1e-8 * 1.001, (c, rel)
+        assert stats[c]["status"] == mor.MOR_OK
+        xo, ito, _, _ = ref[c]
+        itg = stats[c]["iters"]
+        assert abs(itg - ito) <= max(2, 0.1 * ito), (c, itg, ito)
+        M = oop.A_sigma(wl.A, wl.E, s, transpose=bool(transpose))
+        if wl.n <= 2000:
+            kappa = np.linalg.cond(M.toarray())
+            assert np.linalg.norm(X[:, c] - xo) <= kappa * 2e-8 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_mixed_precision_solves_reach_fp64_residual(h, name, transpose):
+    wl = CASES[name]()
+    _set(h, wl)
+    shifts = [30.0, 45.0 + 20.0j, 90.0 + 5.0j, 200.0, 400.0 + 400.0j]
+    mor.mor_build_precond(h, shifts[0], transpose, mor.MOR_MIXED)
+    for s in shifts[1:]:
+        mor.mor_update_precond(h, s, transpose)
+    X, stats, code = mor.mor_solve_shifts(h, shifts, transpose, mor.mor_default_opts())
+    assert code == mor.MOR_OK
+    b = (wl.C if transpose else wl.B)[:, 0]
+    for c, s in enumerate(shifts):
+        rel = _relres(wl, s, X[:, c], b, bool(transpose))
+        assert rel <= 1e-8 * 1.001, (c, rel)
+        assert abs(stats[c]["relres"] - rel) <= 1e-3 * rel + 1e-15
+        assert stats[c]["refinements"] >= 1
+
+
+def test_custom_rhs_and_sixteen_plus_columns(h):
+    """k = 20 shifts (two batches: 16 + 4) with user right-hand sides."""
+    wl = CASES["convdiff3d_n3375"]()
+    _set(h, wl)
+    mor.mor_build_precond(h, 50.0, 0, mor.MOR_MIXED)
+    rng = np.random.default_rng(0)
+    k = 20
+    shifts = 50.0 + 10.0 * np.arange(k) + 1j * np.linspace(0, 30, k)
+    R = rng.standard_normal((wl.n, k)) + 1j * rng.standard_normal((wl.n, k))
+    X, stats, code = mor.mor_solve_shifts(h, shifts, 0, mor.mor_default_opts(), R=R)
+    assert code == mor.MOR_OK
+    for c in range(k):
+        M = oop.A_sigma(wl.A, wl.E, shifts[c])
+        assert np.linalg.norm(R[:, c] - M @ X[:, c]) / np.linalg.norm(R[:, c]) <= 1.001e-8
+
+
+def test_unpreconditioned_hits_maxit_with_status(h):
+    """Unpreconditioned Krylov on a hard shift stops at maxit with
+    MOR_ENOCONV and a finite best iterate (Sec. IV: unpreconditioned GMRES
+    fails on the paper's models)."""
+    wl = W.config0(N=60)
+    _set(h, wl)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64, precond=2, maxit=10, tol=1e-12)
+    X, stats, code = mor.mor_solve_shifts(h, [1e-3], 0, opts)
+    assert code == mor.MOR_ENOCONV
+    assert stats[0]["status"] == mor.MOR_ENOCONV and stats[0]["iters"] == 10
+    assert np.all(np.isfinite(X))
+
+
+def test_fresh_spai_per_shift_mode(h):
+    wl = CASES["convdiff3d_n3375"]()
+    _set(h, wl)
+    shifts = [30.0, 60.0 + 10.0j]
+    opts = mor.mor_default_opts(precond=1)
+    X, stats, code = mor.mor_solve_shifts(h, shifts, 0, opts)
+    assert code == mor.MOR_OK
+    for c, s in enumerate(shifts):
+        assert _relres(wl, s, X[:, c], wl.B[:, 0]) <= 1.001e-8
+
+
+def test_tiny_and_zero_rhs(h):
+    """n = 1 system, and a zero right-hand side (0 iterations, x = 0)."""
+    A = sp.csr_matrix(np.array([[-2.0]]))
+    mor.mor_set_system(h, A, np.ones((1, 1)), np.ones((1, 1)))
+    X, stats, code = mor.mor_solve_shifts(h, [3.0], 0, mor.mor_default_opts(precond=2))
+    assert code == mor.MOR_OK and abs(X[0, 0] - 1.0 / 5.0) < 1e-12
+    wl = W.config1(N=6)
+    _set(h, wl)
+    X, stats, code = mor.mor_solve_shifts(h, [5.0], 0, mor.mor_default_opts(precond=2),
+                                          R=np.zeros((wl.n, 1), dtype=complex))
+    assert code == mor.MOR_OK and stats[0]["iters"] == 0 and not np.any(X)
