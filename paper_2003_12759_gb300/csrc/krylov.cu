@@ -26,7 +26,7 @@ template <> __device__ __forceinline__ cfloat from_cd<cfloat>(cdouble z) { retur
 template <> __device__ __forceinline__ cdouble from_cd<cdouble>(cdouble z) { return z; }
 
 inline int grid_for(int64_t n, int cap) {
-  int64_t b = (n + 255) / 256;
+  int64_t b = (n + 255) / 256;    // n = number of threads wanted
   if (cap > 0 && b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
@@ -35,21 +35,13 @@ template <typename S, int KB>
 __global__ void __launch_bounds__(256) update_p_kernel(int n, int k, const S* __restrict__ r, S* __restrict__ p,
                                                        const S* __restrict__ v, const KState* st, const int* done) {
   if (*done) return;
-  S beta[KB], omega[KB];
-  int act[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    act[c] = (c < k) ? st[c].active : 0;
-    beta[c] = (c < k) ? from_cd<S>(st[c].beta) : S(0);
-    omega[c] = (c < k) ? from_cd<S>(st[c].omega) : S(0);
-  }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k && act[c]) {
-        const int64_t q = i * k + c;
-        p[q] = r[q] + beta[c] * (p[q] - omega[c] * v[q]);
-      }
+  const int sub = threadIdx.x & (KB - 1);
+  if (sub >= k || !st[sub].active) return;
+  const S beta = from_cd<S>(st[sub].beta), omega = from_cd<S>(st[sub].omega);
+  const int rpb = blockDim.x / KB;
+  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
+    const int64_t q = i * k + sub;
+    p[q] = r[q] + beta * (p[q] - omega * v[q]);
   }
 }
 
@@ -57,20 +49,14 @@ template <typename S, int KB>
 __global__ void __launch_bounds__(256) update_s_kernel(int n, int k, const S* __restrict__ r, const S* __restrict__ v,
                                                        S* __restrict__ sv, const KState* st, const int* done) {
   if (*done) return;
-  S alpha[KB];
-  int act[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    act[c] = (c < k) ? st[c].active : 0;
-    alpha[c] = (c < k) ? from_cd<S>(st[c].alpha) : S(0);
-  }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k) {
-        const int64_t q = i * k + c;
-        sv[q] = act[c] ? r[q] - alpha[c] * v[q] : r[q];
-      }
+  const int sub = threadIdx.x & (KB - 1);
+  if (sub >= k) return;
+  const int act = st[sub].active;
+  const S alpha = from_cd<S>(st[sub].alpha);
+  const int rpb = blockDim.x / KB;
+  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
+    const int64_t q = i * k + sub;
+    sv[q] = act ? r[q] - alpha * v[q] : r[q];
   }
 }
 
@@ -81,30 +67,23 @@ __global__ void __launch_bounds__(256) update_xr_kernel(int n, int k, S* __restr
                                                         const S* __restrict__ rhat, double* part, unsigned* counter,
                                                         KState* st, int* done) {
   if (*done) return;
-  S alpha[KB], omega[KB];
-  int act[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    act[c] = (c < k) ? st[c].active : 0;
-    alpha[c] = (c < k) ? from_cd<S>(st[c].alpha) : S(0);
-    omega[c] = (c < k) ? from_cd<S>(st[c].omega) : S(0);
+  const int sub = threadIdx.x & (KB - 1);
+  const bool act = sub < k && st[sub].active;
+  const S alpha = act ? from_cd<S>(st[sub].alpha) : S(0);
+  const S omega = act ? from_cd<S>(st[sub].omega) : S(0);
+  S v0 = S(0), v1 = S(0);
+  const int rpb = blockDim.x / KB;
+  if (act) {
+    for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
+      const int64_t q = i * k + sub;
+      x[q] = x[q] + alpha * ph[q] + omega * sh[q];
+      const S rn = sv[q] - omega * t[q];
+      r[q] = rn;
+      fma_s(v0, conj_(rhat[q]), rn);
+      v1 += S(abs2_(rn));
+    }
   }
-  S vals[2 * KB];
-#pragma unroll
-  for (int i = 0; i < 2 * KB; ++i) vals[i] = S(0);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k && act[c]) {
-        const int64_t q = i * k + c;
-        x[q] = x[q] + alpha[c] * ph[q] + omega[c] * sh[q];
-        const S rn = sv[q] - omega[c] * t[q];
-        r[q] = rn;
-        fma_s(vals[2 * c], conj_(rhat[q]), rn);
-        vals[2 * c + 1] += S(abs2_(rn));
-      }
-  }
-  block_reduce_finalize<S, 2 * KB>(vals, 2 * k, part, counter, FIN_RHO, st, nullptr, done, k);
+  col_reduce_finalize<S, KB>(v0, v1, k, part, counter, FIN_RHO, st, nullptr, done);
 }
 
 // x = 0, r = r_hat = rhs, p = v = 0, then (r_hat, r), ||r||^2 -> FIN_INIT
@@ -113,25 +92,23 @@ __global__ void __launch_bounds__(256) init_kernel(int n, int k, const S* __rest
                                                    S* __restrict__ r, S* __restrict__ rhat, S* __restrict__ p,
                                                    S* __restrict__ v, double* part, unsigned* counter, KState* st,
                                                    int* done) {
-  S vals[2 * KB];
-#pragma unroll
-  for (int i = 0; i < 2 * KB; ++i) vals[i] = S(0);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k) {
-        const int64_t q = i * k + c;
-        const S b = rhs[q];
-        x[q] = S(0);
-        r[q] = b;
-        rhat[q] = b;
-        p[q] = S(0);
-        v[q] = S(0);
-        fma_s(vals[2 * c], conj_(b), b);
-        vals[2 * c + 1] += S(abs2_(b));
-      }
+  const int sub = threadIdx.x & (KB - 1);
+  S v0 = S(0), v1 = S(0);
+  const int rpb = blockDim.x / KB;
+  if (sub < k) {
+    for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
+      const int64_t q = i * k + sub;
+      const S b = rhs[q];
+      x[q] = S(0);
+      r[q] = b;
+      rhat[q] = b;
+      p[q] = S(0);
+      v[q] = S(0);
+      fma_s(v0, conj_(b), b);
+      v1 += S(abs2_(b));
+    }
   }
-  block_reduce_finalize<S, 2 * KB>(vals, 2 * k, part, counter, FIN_INIT, st, nullptr, done, k);
+  col_reduce_finalize<S, KB>(v0, v1, k, part, counter, FIN_INIT, st, nullptr, done);
 }
 
 __global__ void set_targets_kernel(int k, KState* st, const double* target, const int* maxit) {
@@ -143,40 +120,27 @@ __global__ void set_targets_kernel(int k, KState* st, const double* target, cons
 template <typename Sin, typename S64, int KB>
 __global__ void scale_cast_kernel(int n, int k, const S64* __restrict__ r64, const double* nrm2,
                                   const int* active, Sin* __restrict__ out) {
-  double inv[KB];
-  int act[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    act[c] = (c < k) ? active[c] : 0;
-    inv[c] = (c < k && act[c] && nrm2[c] > 0.0) ? 1.0 / sqrt(nrm2[c]) : 0.0;
-  }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k) {
-        const int64_t q = i * k + c;
-        out[q] = act[c] ? cvt<Sin>(inv[c] * r64[q]) : Sin(0);
-      }
+  const int sub = threadIdx.x & (KB - 1);
+  if (sub >= k) return;
+  const int act = active[sub];
+  const double inv = (act && nrm2[sub] > 0.0) ? 1.0 / sqrt(nrm2[sub]) : 0.0;
+  const int rpb = blockDim.x / KB;
+  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
+    const int64_t q = i * k + sub;
+    out[q] = act ? cvt<Sin>(inv * r64[q]) : Sin(0);
   }
 }
 
 template <typename Sin, typename S64, int KB>
 __global__ void refine_update_kernel(int n, int k, S64* __restrict__ x64, const Sin* __restrict__ d,
                                      const double* nrm2, const int* active) {
-  double sc[KB];
-  int act[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) {
-    act[c] = (c < k) ? active[c] : 0;
-    sc[c] = (c < k) ? sqrt(nrm2[c]) : 0.0;
-  }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k && act[c]) {
-        const int64_t q = i * k + c;
-        x64[q] = x64[q] + sc[c] * cvt<S64>(d[q]);
-      }
+  const int sub = threadIdx.x & (KB - 1);
+  if (sub >= k || !active[sub]) return;
+  const double sc = sqrt(nrm2[sub]);
+  const int rpb = blockDim.x / KB;
+  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
+    const int64_t q = i * k + sub;
+    x64[q] = x64[q] + sc * cvt<S64>(d[q]);
   }
 }
 
@@ -236,7 +200,7 @@ size_t krylov_state_bytes(int) { return sizeof(KState); }
 
 int krylov_launch_update_p(int st, int kb, int n, int k, const void* r, void* p, const void* v,
                            const void* state, const int* done, cudaStream_t s) {
-  const int g = grid_for(n, 152 * 8);
+  const int g = grid_for((int64_t)n * kb, 152 * 32);
   ST_SWITCH(st, KB_SWITCH(kb, (update_p_kernel<S, KBv><<<g, 256, 0, s>>>(n, k, (const S*)r, (S*)p, (const S*)v,
                                                                         (const KState*)state, done))));
   mor_count_launches(1);
@@ -245,7 +209,7 @@ int krylov_launch_update_p(int st, int kb, int n, int k, const void* r, void* p,
 
 int krylov_launch_update_s(int st, int kb, int n, int k, const void* r, const void* v, void* sv,
                            const void* state, const int* done, cudaStream_t s) {
-  const int g = grid_for(n, 152 * 8);
+  const int g = grid_for((int64_t)n * kb, 152 * 32);
   ST_SWITCH(st, KB_SWITCH(kb, (update_s_kernel<S, KBv><<<g, 256, 0, s>>>(n, k, (const S*)r, (const S*)v, (S*)sv,
                                                                         (const KState*)state, done))));
   mor_count_launches(1);
@@ -256,7 +220,7 @@ int krylov_launch_update_xr(int st, int kb, int n, int k, void* x, void* r, cons
                             const void* shat, const void* sv, const void* t, const void* rhat,
                             void* part, unsigned* counter, void* state, int* done, int grid_cap,
                             cudaStream_t s) {
-  const int g = grid_for(n, grid_cap);
+  const int g = grid_for((int64_t)n * kb, grid_cap);
   ST_SWITCH(st, KB_SWITCH(kb, (update_xr_kernel<S, KBv><<<g, 256, 0, s>>>(
                                   n, k, (S*)x, (S*)r, (const S*)phat, (const S*)shat, (const S*)sv,
                                   (const S*)t, (const S*)rhat, (double*)part, counter, (KState*)state, done))));
@@ -270,7 +234,7 @@ int krylov_launch_init(int st, int kb, int n, int k, const void* rhs, void* x, v
                        cudaStream_t s) {
   set_targets_kernel<<<1, 32, 0, s>>>(k, (KState*)state, target, maxit);
   mor_count_launches(1);
-  const int g = grid_for(n, grid_cap);
+  const int g = grid_for((int64_t)n * kb, grid_cap);
   ST_SWITCH(st, KB_SWITCH(kb, (init_kernel<S, KBv><<<g, 256, 0, s>>>(n, k, (const S*)rhs, (S*)x, (S*)r, (S*)rhat,
                                                                     (S*)p, (S*)v, (double*)part, counter,
                                                                     (KState*)state, done))));
@@ -290,7 +254,7 @@ int krylov_read_state(int, const void* state_dev, int k, int* iters, int* status
 
 int refine_launch_scale_cast(int st_in, int kb, int n, int k, const void* r64, const double* nrm2,
                              const int* active, void* rhs_in, cudaStream_t s) {
-  const int g = grid_for(n, 152 * 8);
+  const int g = grid_for((int64_t)n * kb, 152 * 32);
   switch (st_in) {
     case ST_F32: KB_SWITCH(kb, (scale_cast_kernel<float, double, KBv><<<g, 256, 0, s>>>(n, k, (const double*)r64, nrm2, active, (float*)rhs_in))); break;
     case ST_F64: KB_SWITCH(kb, (scale_cast_kernel<double, double, KBv><<<g, 256, 0, s>>>(n, k, (const double*)r64, nrm2, active, (double*)rhs_in))); break;
@@ -304,7 +268,7 @@ int refine_launch_scale_cast(int st_in, int kb, int n, int k, const void* r64, c
 
 int refine_launch_update(int st_in, int kb, int n, int k, void* x64, const void* d,
                          const double* nrm2, const int* active, cudaStream_t s) {
-  const int g = grid_for(n, 152 * 8);
+  const int g = grid_for((int64_t)n * kb, 152 * 32);
   switch (st_in) {
     case ST_F32: KB_SWITCH(kb, (refine_update_kernel<float, double, KBv><<<g, 256, 0, s>>>(n, k, (double*)x64, (const float*)d, nrm2, active))); break;
     case ST_F64: KB_SWITCH(kb, (refine_update_kernel<double, double, KBv><<<g, 256, 0, s>>>(n, k, (double*)x64, (const double*)d, nrm2, active))); break;

@@ -1,8 +1,13 @@
-// Per-column BiCGSTAB state and the scalar "finalize" stages that the last
-// block of a fused reduction runs.  The recurrence is right-preconditioned
-// BiCGSTAB (Sec. III.A: A P y = b, x = P y) started from x_0 = 0 with
-// Hermitian inner products; the scalars are kept in FP64 complex whatever
-// the vector precision.
+// Per-column BiCGSTAB state, the scalar "finalize" stages that the last
+// block of a fused reduction runs, and the block/grid reduction used by every
+// kernel that reduces per shift column.  The recurrence is right-
+// preconditioned BiCGSTAB (Sec. III.A: A P y = b, x = P y) started from
+// x_0 = 0 with Hermitian inner products; the scalars are kept in FP64 complex
+// whatever the vector precision.
+//
+// Thread mapping shared by the kernels of the solve: a row of the n x k
+// row-major block is handled by KB consecutive lanes (KB = k rounded up to a
+// power of two), lane `sub` owning column `sub`; lanes with sub >= k idle.
 #pragma once
 #include "mor_types.cuh"
 
@@ -14,7 +19,7 @@ enum {
   FIN_RHO = 4      // sums: (r_hat, r), ||r||^2         -> convergence, beta
 };
 
-enum { KST_RUNNING = 0, KST_OK = 0, KST_NOCONV = 4, KST_BREAKDOWN = 5 };
+enum { KST_OK = 0, KST_NOCONV = 4, KST_BREAKDOWN = 5 };
 
 struct KState {
   cdouble rho, rho_old, alpha, omega, beta;
@@ -65,79 +70,63 @@ __device__ inline void krylov_finalize(int stage, int k, const cdouble* sums, KS
     }
     any |= S.active;
   }
-  if (stage == FIN_INIT || stage == FIN_RHO || stage == FIN_ALPHA || stage == FIN_OMEGA) {
-    if (done) *done = any ? 0 : 1;
-  }
+  if (done) *done = any ? 0 : 1;
 }
 
 // ---------------------------------------------------------------------------
-// Block reduction of NV per-thread scalars (NV <= 2*MOR_KMAX) of type S into
-// FP64 per-block partials, then the last block (by atomic ticket) reduces the
-// partials in a fixed order and runs the finalize stage or writes the sums.
-// part layout: part[(block * nv + i) * 2 + {re, im}] (doubles).
-template <typename S, int NV>
-__device__ inline void block_reduce_finalize(const S (&vals)[NV], int nv, double* part,
-                                             unsigned* counter, int fin, KState* state,
-                                             cdouble* out, int* done, int k) {
+// Reduce two per-lane scalars (v0, v1) of column sub = lane % KB over the
+// block, write the per-block FP64 partials part[(block * 2k + 2c + q) * 2 +
+// {re, im}], and let the last block (atomic ticket) sum the partials of all
+// blocks in a fixed order and run the finalize stage (or write the sums to
+// `out`).  Every thread of the block must call it.
+template <typename S, int KB>
+__device__ inline void col_reduce_finalize(S v0, S v1, int k, double* part, unsigned* counter, int fin,
+                                           KState* state, cdouble* out, int* done) {
   typedef typename real_of<S>::type R;
-  __shared__ double sh_re[8][NV];
-  __shared__ double sh_im[8][NV];
+  __shared__ double sh[8][2 * KB][2];
   __shared__ bool am_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
+  const int nv = 2 * k;
+  R a0 = (R)real_(v0), b0 = (R)imag_(v0), a1 = (R)real_(v1), b1 = (R)imag_(v1);
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    if (i < nv) {
-      R re = warp_sum((R)real_(vals[i]));
-      R im = is_cplx<S>::value ? warp_sum((R)imag_(vals[i])) : R(0);
-      if (lane == 0) { sh_re[wid][i] = (double)re; sh_im[wid][i] = (double)im; }
-    }
+  for (int o = 16; o >= KB; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+  }
+  if (lane < KB) {
+    sh[wid][2 * lane][0] = (double)a0;
+    sh[wid][2 * lane][1] = (double)b0;
+    sh[wid][2 * lane + 1][0] = (double)a1;
+    sh[wid][2 * lane + 1][1] = (double)b1;
   }
   __syncthreads();
   if (threadIdx.x < nv) {
     double re = 0.0, im = 0.0;
-    for (int w = 0; w < nwarps; ++w) { re += sh_re[w][threadIdx.x]; im += sh_im[w][threadIdx.x]; }
+    for (int w = 0; w < nwarps; ++w) { re += sh[w][threadIdx.x][0]; im += sh[w][threadIdx.x][1]; }
     part[((size_t)blockIdx.x * nv + threadIdx.x) * 2 + 0] = re;
     part[((size_t)blockIdx.x * nv + threadIdx.x) * 2 + 1] = im;
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned ticket = atomicAdd(counter, 1u);
-    am_last = (ticket == gridDim.x - 1);
-  }
+  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  // last block: thread t sums blocks t, t + blockDim, ... for all nv values
-  double acc_re[NV], acc_im[NV];
-#pragma unroll
-  for (int i = 0; i < NV; ++i) { acc_re[i] = 0.0; acc_im[i] = 0.0; }
+  // last block: warp w sums value i = w, w + nwarps, ... over all blocks (lanes stride the blocks)
+  __shared__ cdouble sums[2 * KB];
   const volatile double* vp = part;
-  for (int blk = threadIdx.x; blk < (int)gridDim.x; blk += blockDim.x) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      if (i < nv) {
-        acc_re[i] += vp[((size_t)blk * nv + i) * 2 + 0];
-        acc_im[i] += vp[((size_t)blk * nv + i) * 2 + 1];
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    if (i < nv) {
-      double re = warp_sum(acc_re[i]);
-      double im = warp_sum(acc_im[i]);
-      if (lane == 0) { sh_re[wid][i] = re; sh_im[wid][i] = im; }
-    }
-  }
-  __syncthreads();
-  __shared__ cdouble sums[NV];
-  if (threadIdx.x < nv) {
+  for (int i = wid; i < nv; i += nwarps) {
     double re = 0.0, im = 0.0;
-    for (int w = 0; w < nwarps; ++w) { re += sh_re[w][threadIdx.x]; im += sh_im[w][threadIdx.x]; }
-    sums[threadIdx.x] = cdouble(re, im);
+    for (int blk = lane; blk < (int)gridDim.x; blk += 32) {
+      re += vp[((size_t)blk * nv + i) * 2 + 0];
+      im += vp[((size_t)blk * nv + i) * 2 + 1];
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) sums[i] = cdouble(re, im);
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -24,24 +24,10 @@ namespace {
 
 template <typename S, int KB> struct CoefS { S sE[KB]; S sA[KB]; };
 
-template <typename S> __device__ __forceinline__ S mk_coef(double re, double im);
-template <> __device__ __forceinline__ float mk_coef<float>(double re, double) { return (float)re; }
-template <> __device__ __forceinline__ double mk_coef<double>(double re, double) { return re; }
-template <> __device__ __forceinline__ cfloat mk_coef<cfloat>(double re, double im) { return cfloat((float)re, (float)im); }
-template <> __device__ __forceinline__ cdouble mk_coef<cdouble>(double re, double im) { return cdouble(re, im); }
-
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
 
-// one row of the operator: accumulate A x and E x for all k columns
-template <typename S, int KB>
-__device__ __forceinline__ void op_row(const PatView& pv, int ekind, const typename real_of<S>::type* __restrict__ a,
-                                       const typename real_of<S>::type* __restrict__ e,
-                                       const typename real_of<S>::type* __restrict__ ed, int k,
-                                       const S* __restrict__ x, int r, S (&accA)[KB], S (&accE)[KB]) {
-  typedef typename real_of<S>::type R;
-#pragma unroll
-  for (int c = 0; c < KB; ++c) { accA[c] = zero_<S>(); accE[c] = zero_<S>(); }
-  int64_t p0, p1, step;
+// [p0, p1) and step of row r in the stored layout
+__device__ __forceinline__ void row_range(const PatView& pv, int r, int64_t& p0, int64_t& p1, int& step) {
   if (pv.fmt == FMT_SELL) {
     const int64_t base = pv.sptr[r >> 5];
     const int64_t w = (pv.sptr[(r >> 5) + 1] - base) >> 5;
@@ -53,110 +39,94 @@ __device__ __forceinline__ void op_row(const PatView& pv, int ekind, const typen
     p1 = pv.rowptr[r + 1];
     step = 1;
   }
-  for (int64_t p = p0; p < p1; p += step) {
-    const int cc = __ldg(pv.col + p);
-    const R av = __ldg(a + p);
-    const S* xr = x + (int64_t)cc * k;
-    if (ekind == EK_CSR) {
-      const R ev = __ldg(e + p);
-#pragma unroll
-      for (int c = 0; c < KB; ++c)
-        if (c < k) { S xv = xr[c]; fma_r(accA[c], av, xv); fma_r(accE[c], ev, xv); }
-    } else {
-#pragma unroll
-      for (int c = 0; c < KB; ++c)
-        if (c < k) fma_r(accA[c], av, xr[c]);
-    }
-  }
-  if (ekind == EK_DIAG) {
-    const R d = __ldg(ed + r);
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k) accE[c] = scale_(d, x[(int64_t)r * k + c]);
-  } else if (ekind == EK_IDENTITY) {
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k) accE[c] = x[(int64_t)r * k + c];
-  }
 }
 
+// Y(:, c) = sE_c (E X(:, c)) + sA_c (A X(:, c)) [+ B(:, c)], with an optional
+// fused per-column reduction.  KB lanes per row, lane `sub` owns column sub.
 template <typename S, int KB>
 __global__ void __launch_bounds__(256) op_spmv_kernel(PatView pv, OpVals ov, CoefS<S, KB> cf, int k,
                                                       const S* __restrict__ x, S* __restrict__ y,
                                                       const S* __restrict__ bv, RedArgs red) {
   typedef typename real_of<S>::type R;
   if (red.done && *red.done) return;
-  const R* a = (const R*)ov.a;
-  const R* e = (const R*)ov.e;
-  const R* ed = (const R*)ov.ediag;
-  const S* w = (const S*)red.w;
-  S vals[2 * KB];
-#pragma unroll
-  for (int i = 0; i < 2 * KB; ++i) vals[i] = zero_<S>();
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < pv.n; r += gridDim.x * blockDim.x) {
-    S accA[KB], accE[KB];
-    op_row<S, KB>(pv, ov.ekind, a, e, ed, k, x, r, accA, accE);
-#pragma unroll
-    for (int c = 0; c < KB; ++c) {
-      if (c < k) {
-        S yv = cf.sE[c] * accE[c] + cf.sA[c] * accA[c];
-        if (bv) yv += bv[(int64_t)r * k + c];
-        y[(int64_t)r * k + c] = yv;
-        if (red.mode == RED_DOT_W) {
-          fma_s(vals[2 * c], conj_(w[(int64_t)r * k + c]), yv);
-        } else if (red.mode == RED_DOT_TT) {
-          fma_s(vals[2 * c], conj_(yv), w[(int64_t)r * k + c]);
-          vals[2 * c + 1] += S(abs2_(yv));
-        } else if (red.mode == RED_NORM) {
-          vals[2 * c] += S(abs2_(yv));
-        }
+  __shared__ S csE[KB], csA[KB];
+  if (threadIdx.x < KB) { csE[threadIdx.x] = cf.sE[threadIdx.x]; csA[threadIdx.x] = cf.sA[threadIdx.x]; }
+  __syncthreads();
+  const R* __restrict__ a = (const R*)ov.a;
+  const R* __restrict__ e = (const R*)ov.e;
+  const R* __restrict__ ed = (const R*)ov.ediag;
+  const S* __restrict__ w = (const S*)red.w;
+  const int sub = threadIdx.x & (KB - 1);
+  const bool act = sub < k;
+  const S sE = csE[sub], sA = csA[sub];
+  S v0 = zero_<S>(), v1 = zero_<S>();
+  const int rpb = blockDim.x / KB;
+  for (int r = blockIdx.x * rpb + threadIdx.x / KB; r < pv.n; r += gridDim.x * rpb) {
+    if (!act) continue;
+    int64_t p0, p1;
+    int step;
+    row_range(pv, r, p0, p1, step);
+    S accA = zero_<S>(), accE = zero_<S>();
+    if (ov.ekind == EK_CSR) {
+      for (int64_t p = p0; p < p1; p += step) {
+        const int cc = __ldg(pv.col + p);
+        const S xv = x[(int64_t)cc * k + sub];
+        fma_r(accA, __ldg(a + p), xv);
+        fma_r(accE, __ldg(e + p), xv);
       }
+    } else {
+#pragma unroll 4
+      for (int64_t p = p0; p < p1; p += step) {
+        const int cc = __ldg(pv.col + p);
+        fma_r(accA, __ldg(a + p), x[(int64_t)cc * k + sub]);
+      }
+      const S xr = x[(int64_t)r * k + sub];
+      accE = (ov.ekind == EK_DIAG) ? scale_(__ldg(ed + r), xr) : xr;
+    }
+    S yv = sE * accE + sA * accA;
+    const int64_t q = (int64_t)r * k + sub;
+    if (bv) yv += bv[q];
+    y[q] = yv;
+    if (red.mode == RED_DOT_W) {
+      fma_s(v0, conj_(w[q]), yv);
+    } else if (red.mode == RED_DOT_TT) {
+      fma_s(v0, conj_(yv), w[q]);
+      v1 += S(abs2_(yv));
+    } else if (red.mode == RED_NORM) {
+      v0 += S(abs2_(yv));
     }
   }
   if (red.mode != RED_NONE)
-    block_reduce_finalize<S, 2 * KB>(vals, 2 * k, (double*)red.part, red.counter, red.fin,
-                                     (KState*)red.state, (cdouble*)red.out, (int*)red.done, k);
+    col_reduce_finalize<S, KB>(v0, v1, k, (double*)red.part, red.counter, red.fin, (KState*)red.state,
+                               (cdouble*)red.out, (int*)red.done);
 }
 
+// Y(:, c) = F X(:, c) where the factor applies to column c, else Y(:, c) = X(:, c).
 template <typename S, typename V, int KB>
 __global__ void __launch_bounds__(256) factor_spmv_kernel(PatView pv, const V* __restrict__ f,
                                                           const int* __restrict__ apply, int k,
                                                           const S* __restrict__ x, S* __restrict__ y,
                                                           const int* done) {
   if (done && *done) return;
-  int ap[KB];
-#pragma unroll
-  for (int c = 0; c < KB; ++c) ap[c] = (c < k) ? apply[c] : 0;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < pv.n; r += gridDim.x * blockDim.x) {
-    S acc[KB];
-#pragma unroll
-    for (int c = 0; c < KB; ++c) acc[c] = zero_<S>();
-    int64_t p0, p1, step;
-    if (pv.fmt == FMT_SELL) {
-      const int64_t base = pv.sptr[r >> 5];
-      const int64_t w = (pv.sptr[(r >> 5) + 1] - base) >> 5;
-      p0 = base + (r & 31);
-      p1 = p0 + 32 * w;
-      step = 32;
-    } else {
-      p0 = pv.rowptr[r];
-      p1 = pv.rowptr[r + 1];
-      step = 1;
-    }
+  const int sub = threadIdx.x & (KB - 1);
+  if (sub >= k) return;
+  const int ap = apply[sub];
+  const int rpb = blockDim.x / KB;
+  for (int r = blockIdx.x * rpb + threadIdx.x / KB; r < pv.n; r += gridDim.x * rpb) {
+    const int64_t q = (int64_t)r * k + sub;
+    if (!ap) { y[q] = x[q]; continue; }
+    int64_t p0, p1;
+    int step;
+    row_range(pv, r, p0, p1, step);
+    S acc = zero_<S>();
+#pragma unroll 4
     for (int64_t p = p0; p < p1; p += step) {
       const int cc = __ldg(pv.col + p);
       const V fv = f[p];
-      const S* xr = x + (int64_t)cc * k;
-#pragma unroll
-      for (int c = 0; c < KB; ++c)
-        if (c < k) {
-          if constexpr (is_cplx<V>::value) fma_s(acc[c], fv, xr[c]);
-          else fma_r(acc[c], fv, xr[c]);
-        }
+      if constexpr (is_cplx<V>::value) fma_s(acc, fv, x[(int64_t)cc * k + sub]);
+      else fma_r(acc, fv, x[(int64_t)cc * k + sub]);
     }
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < k) y[(int64_t)r * k + c] = ap[c] ? acc[c] : x[(int64_t)r * k + c];
+    y[q] = acc;
   }
 }
 
@@ -180,7 +150,7 @@ int op_dispatch(const PatView& pv, const OpVals& ov, const Coef* coefs, int k, c
   else { ra.mode = RED_NONE; ra.w = nullptr; ra.part = nullptr; ra.counter = nullptr; ra.fin = 0;
          ra.state = nullptr; ra.out = nullptr; ra.done = nullptr; }
   const int threads = 256;
-  int64_t blocks = ((int64_t)pv.n + threads - 1) / threads;
+  int64_t blocks = ((int64_t)pv.n * KB + threads - 1) / threads;
   if (grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
   if (blocks < 1) blocks = 1;
   op_spmv_kernel<S, KB><<<(unsigned)blocks, threads, 0, s>>>(pv, ov, cf, k, (const S*)x, (S*)y,
@@ -193,8 +163,8 @@ template <typename S, typename V, int KB>
 int factor_dispatch(const PatView& pv, const void* f, const int* apply, int k, const void* x, void* y,
                     const int* done, cudaStream_t s) {
   const int threads = 256;
-  int64_t blocks = ((int64_t)pv.n + threads - 1) / threads;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  int64_t blocks = ((int64_t)pv.n * KB + threads - 1) / threads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
   factor_spmv_kernel<S, V, KB><<<(unsigned)blocks, threads, 0, s>>>(pv, (const V*)f, apply, k,
                                                                     (const S*)x, (S*)y, done);
   mor_count_launches(1);
