@@ -836,9 +836,10 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
     double* dst = t == 0 ? Vb : Wb;
     int col = 0;
     for (int i = 0; i < l; ++i) {
-      // block of 16 columns stored row-major with its own k
-      const int blk = i / MOR_KMAX, kc = std::min(MOR_KMAX, l - blk * MOR_KMAX), ci = i % MOR_KMAX;
-      const double* src = (const double*)((const char*)xs[t].p + st_size(st64) * (size_t)n * blk * MOR_KMAX);
+      // solve_many stores each batch of bw columns row-major with its own k
+      const int bw = (o.batch && o.precond != 1) ? MOR_KMAX : 1;
+      const int blk = i / bw, kc = std::min(bw, l - blk * bw), ci = i % bw;
+      const double* src = (const double*)((const char*)xs[t].p + st_size(st64) * (size_t)n * blk * bw);
       const int g = (int)std::min<int64_t>((n + 255) / 256, h->grid_cap);
       extract_kernel<<<g, 256, 0, h->stream>>>((int)n, kc, ci, 0, cplx ? 1 : 0, src, dst + (size_t)n * col++);
       mor_count_launches(1);
