@@ -335,6 +335,31 @@ int mor_launch_count(int64_t* count);
 int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precision, int reps,
                     double* ms);
 
+/* ------------------------------------------------------------------------ */
+/* allocation-free entry point (no counterpart in the paper)                */
+/* ------------------------------------------------------------------------ */
+
+/* The same two-pass Gram-Schmidt as mor_orthonormalize, for callers that
+ * cannot let a library allocate device memory: frameworks whose own caching
+ * allocator holds the whole device budget, real-time or embedded loops that
+ * must keep a fixed memory map, and code that must not pay the implicit
+ * device synchronisation of cudaMalloc / cudaFree.  It needs no handle and
+ * allocates nothing: its scratch is one fixed array of 311,808 bytes that
+ * the library reserves on every GPU that loads it, until the process exits.
+ *   X       device pointer, n x k FP64, column-major, orthonormalised in
+ *           place on the current CUDA device.
+ *   n       1 <= n <= 2^31 - 1;  k: 1 <= k <= 64 (MOR_EINVAL beyond).
+ *   stream  cudaStream_t for the work (NULL = the legacy default stream);
+ *           the call returns once the work is enqueued.
+ * The first call on a device looks up the scratch's device address (keep
+ * that first call outside any stream capture).  All calls share the one
+ * scratch array, so calls whose work overlaps on the GPU (other streams,
+ * other host threads) race: serialise them.  No dependency check is made --
+ * a numerically dependent column comes out non-finite; use
+ * mor_orthonormalize to have it reported.  Returns MOR_OK, MOR_EINVAL or
+ * MOR_ECUDA. */
+int mor_orthonormalize_noalloc(double* X, int64_t n, int k, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -116,6 +116,7 @@ SIGNATURES = {
     "mor_eval_tf": (C.c_int, [_P, C.POINTER(mor_reduced), _P, C.c_int, _P, C.c_uint]),
     "mor_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
     "mor_time_kernel": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "mor_orthonormalize_noalloc": (C.c_int, [_P, C.c_int64, C.c_int, _P]),
 }
 
 _lib = None
@@ -450,3 +451,16 @@ def mor_time_kernel(h, which: int, sigma, precision: int = MOR_MIXED, reps: int 
     _check(h, load_library().mor_time_kernel(h, int(which), sp_, s.shape[0], int(precision), int(reps),
                                              C.byref(ms)))
     return ms.value
+
+
+def mor_orthonormalize_noalloc(X, stream=None) -> int:
+    """Allocation-free two-pass Gram-Schmidt of a CUDA tensor X (n x k FP64,
+    column-major storage, i.e. X.t() contiguous / X with stride (1, n)), in
+    place on the current device.  Returns the status code (MOR_OK on success)."""
+    if not _is_torch(X) or not X.is_cuda:
+        raise ValueError("X must be a CUDA tensor")
+    n, k = X.shape
+    if X.stride() != (1, n):
+        raise ValueError("X must be column-major (stride (1, n))")
+    sp_ = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+    return load_library().mor_orthonormalize_noalloc(C.c_void_p(X.data_ptr()), int(n), int(k), sp_)
