@@ -23,8 +23,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmor_spai.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+NVCC_FLAGS = ["-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
+# the kernel files dispatch shapes with C++20 template lambdas; the host runtime stays C++17
+CXX20 = {"spmv.cu", "krylov.cu"}
 
 
 def nvcc() -> str:
@@ -45,7 +47,8 @@ def _deps_mtime():
 
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    cmd = [nvcc(), "-c", src, "-o", obj] + ARCH + NVCC_FLAGS
+    std = "-std=c++20" if os.path.basename(src) in CXX20 else "-std=c++17"
+    cmd = [nvcc(), "-c", src, "-o", obj, std] + ARCH + NVCC_FLAGS
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

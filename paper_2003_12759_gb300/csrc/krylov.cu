@@ -17,6 +17,8 @@
 #include "mor_internal.h"
 #include "krylov_state.cuh"
 
+#include "shape_dispatch.cuh"
+
 namespace {
 
 template <typename S> __device__ __forceinline__ S from_cd(cdouble z);
@@ -25,90 +27,144 @@ template <> __device__ __forceinline__ double from_cd<double>(cdouble z) { retur
 template <> __device__ __forceinline__ cfloat from_cd<cfloat>(cdouble z) { return cfloat((float)z.re, (float)z.im); }
 template <> __device__ __forceinline__ cdouble from_cd<cdouble>(cdouble z) { return z; }
 
-inline int grid_for(int64_t n, int cap) {
-  int64_t b = (n + 255) / 256;    // n = number of threads wanted
+inline int grid_for(int64_t threads, int cap) {
+  int64_t b = (threads + 255) / 256;
   if (cap > 0 && b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
+inline int grid_rows(int st, int64_t n, int ld, int cap) {
+  int tpr, cpt;
+  lane_shape(st, ld, &tpr, &cpt);
+  return grid_for(n * tpr, cap);
+}
 
-template <typename S, int KB>
-__global__ void __launch_bounds__(256) update_p_kernel(int n, int k, const S* __restrict__ r, S* __restrict__ p,
+// lane geometry shared by the elementwise kernels
+#define MOR_LANE_SETUP                                  \
+  const int sub = threadIdx.x % TPR;                   \
+  const int c0 = sub * CPT;                            \
+  const int rpb = blockDim.x / TPR;                    \
+  int64_t rb, re;                                      \
+  block_rows(n, rpb, rb, re);
+
+template <typename S, int TPR, int CPT>
+__global__ void __launch_bounds__(256) update_p_kernel(int n, int ld, const S* __restrict__ r, S* __restrict__ p,
                                                        const S* __restrict__ v, const KState* st, const int* done) {
   if (*done) return;
-  const int sub = threadIdx.x & (KB - 1);
-  if (sub >= k || !st[sub].active) return;
-  const S beta = from_cd<S>(st[sub].beta), omega = from_cd<S>(st[sub].omega);
-  const int rpb = blockDim.x / KB;
-  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
-    const int64_t q = i * k + sub;
-    p[q] = r[q] + beta * (p[q] - omega * v[q]);
+  MOR_LANE_SETUP
+  if (c0 >= ld) return;
+  S beta[CPT], omega[CPT];
+  int act[CPT];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    act[j] = st[c0 + j].active;
+    beta[j] = from_cd<S>(st[c0 + j].beta);
+    omega[j] = from_cd<S>(st[c0 + j].omega);
+    any |= (act[j] != 0);
+  }
+  if (!any) return;
+  for (int64_t i = rb + threadIdx.x / TPR; i < re; i += rpb) {
+    const int64_t q = i * ld + c0;
+    const Pack<S, CPT> rv = ldp<S, CPT>(r + q), vv = ldp<S, CPT>(v + q);
+    Pack<S, CPT> pv = ldp<S, CPT>(p + q);
+#pragma unroll
+    for (int j = 0; j < CPT; ++j)
+      if (act[j]) pv.v[j] = rv.v[j] + beta[j] * (pv.v[j] - omega[j] * vv.v[j]);
+    stp<S, CPT>(p + q, pv);
   }
 }
 
-template <typename S, int KB>
-__global__ void __launch_bounds__(256) update_s_kernel(int n, int k, const S* __restrict__ r, const S* __restrict__ v,
+template <typename S, int TPR, int CPT>
+__global__ void __launch_bounds__(256) update_s_kernel(int n, int ld, const S* __restrict__ r, const S* __restrict__ v,
                                                        S* __restrict__ sv, const KState* st, const int* done) {
   if (*done) return;
-  const int sub = threadIdx.x & (KB - 1);
-  if (sub >= k) return;
-  const int act = st[sub].active;
-  const S alpha = from_cd<S>(st[sub].alpha);
-  const int rpb = blockDim.x / KB;
-  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
-    const int64_t q = i * k + sub;
-    sv[q] = act ? r[q] - alpha * v[q] : r[q];
+  MOR_LANE_SETUP
+  if (c0 >= ld) return;
+  S alpha[CPT];
+  int act[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) { act[j] = st[c0 + j].active; alpha[j] = from_cd<S>(st[c0 + j].alpha); }
+  for (int64_t i = rb + threadIdx.x / TPR; i < re; i += rpb) {
+    const int64_t q = i * ld + c0;
+    const Pack<S, CPT> rv = ldp<S, CPT>(r + q), vv = ldp<S, CPT>(v + q);
+    Pack<S, CPT> o;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) o.v[j] = act[j] ? rv.v[j] - alpha[j] * vv.v[j] : rv.v[j];
+    stp<S, CPT>(sv + q, o);
   }
 }
 
-template <typename S, int KB>
-__global__ void __launch_bounds__(256) update_xr_kernel(int n, int k, S* __restrict__ x, S* __restrict__ r,
+template <typename S, int TPR, int CPT>
+__global__ void __launch_bounds__(256) update_xr_kernel(int n, int ld, S* __restrict__ x, S* __restrict__ r,
                                                         const S* __restrict__ ph, const S* __restrict__ sh,
                                                         const S* __restrict__ sv, const S* __restrict__ t,
                                                         const S* __restrict__ rhat, double* part, unsigned* counter,
                                                         KState* st, int* done) {
   if (*done) return;
-  const int sub = threadIdx.x & (KB - 1);
-  const bool act = sub < k && st[sub].active;
-  const S alpha = act ? from_cd<S>(st[sub].alpha) : S(0);
-  const S omega = act ? from_cd<S>(st[sub].omega) : S(0);
-  S v0 = S(0), v1 = S(0);
-  const int rpb = blockDim.x / KB;
-  if (act) {
-    for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
-      const int64_t q = i * k + sub;
-      x[q] = x[q] + alpha * ph[q] + omega * sh[q];
-      const S rn = sv[q] - omega * t[q];
-      r[q] = rn;
-      fma_s(v0, conj_(rhat[q]), rn);
-      v1 += S(abs2_(rn));
+  MOR_LANE_SETUP
+  const bool lane_on = c0 < ld;
+  S alpha[CPT], omega[CPT], v0[CPT], v1[CPT];
+  int act[CPT];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    act[j] = lane_on ? st[c0 + j].active : 0;
+    alpha[j] = act[j] ? from_cd<S>(st[c0 + j].alpha) : S(0);
+    omega[j] = act[j] ? from_cd<S>(st[c0 + j].omega) : S(0);
+    v0[j] = S(0);
+    v1[j] = S(0);
+    any |= (act[j] != 0);
+  }
+  if (any) {
+    for (int64_t i = rb + threadIdx.x / TPR; i < re; i += rpb) {
+      const int64_t q = i * ld + c0;
+      Pack<S, CPT> xv = ldp<S, CPT>(x + q);
+      const Pack<S, CPT> pv = ldp<S, CPT>(ph + q), shv = ldp<S, CPT>(sh + q), svv = ldp<S, CPT>(sv + q),
+                         tv = ldp<S, CPT>(t + q), rh = ldp<S, CPT>(rhat + q);
+      Pack<S, CPT> rn = ldp<S, CPT>(r + q);
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        if (act[j]) {
+          xv.v[j] = xv.v[j] + alpha[j] * pv.v[j] + omega[j] * shv.v[j];
+          rn.v[j] = svv.v[j] - omega[j] * tv.v[j];
+          fma_s(v0[j], conj_(rh.v[j]), rn.v[j]);
+          v1[j] += S(abs2_(rn.v[j]));
+        }
+      }
+      stp<S, CPT>(x + q, xv);
+      stp<S, CPT>(r + q, rn);
     }
   }
-  col_reduce_finalize<S, KB>(v0, v1, k, part, counter, FIN_RHO, st, nullptr, done);
+  col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, part, counter, FIN_RHO, st, nullptr, done);
 }
 
 // x = 0, r = r_hat = rhs, p = v = 0, then (r_hat, r), ||r||^2 -> FIN_INIT
-template <typename S, int KB>
-__global__ void __launch_bounds__(256) init_kernel(int n, int k, const S* __restrict__ rhs, S* __restrict__ x,
+template <typename S, int TPR, int CPT>
+__global__ void __launch_bounds__(256) init_kernel(int n, int ld, const S* __restrict__ rhs, S* __restrict__ x,
                                                    S* __restrict__ r, S* __restrict__ rhat, S* __restrict__ p,
                                                    S* __restrict__ v, double* part, unsigned* counter, KState* st,
                                                    int* done) {
-  const int sub = threadIdx.x & (KB - 1);
-  S v0 = S(0), v1 = S(0);
-  const int rpb = blockDim.x / KB;
-  if (sub < k) {
-    for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
-      const int64_t q = i * k + sub;
-      const S b = rhs[q];
-      x[q] = S(0);
-      r[q] = b;
-      rhat[q] = b;
-      p[q] = S(0);
-      v[q] = S(0);
-      fma_s(v0, conj_(b), b);
-      v1 += S(abs2_(b));
+  MOR_LANE_SETUP
+  S v0[CPT], v1[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) { v0[j] = S(0); v1[j] = S(0); }
+  if (c0 < ld) {
+    Pack<S, CPT> z;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) z.v[j] = S(0);
+    for (int64_t i = rb + threadIdx.x / TPR; i < re; i += rpb) {
+      const int64_t q = i * ld + c0;
+      const Pack<S, CPT> b = ldp<S, CPT>(rhs + q);
+      stp<S, CPT>(x + q, z);
+      stp<S, CPT>(r + q, b);
+      stp<S, CPT>(rhat + q, b);
+      stp<S, CPT>(p + q, z);
+      stp<S, CPT>(v + q, z);
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) { fma_s(v0[j], conj_(b.v[j]), b.v[j]); v1[j] += S(abs2_(b.v[j])); }
     }
   }
-  col_reduce_finalize<S, KB>(v0, v1, k, part, counter, FIN_INIT, st, nullptr, done);
+  col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, part, counter, FIN_INIT, st, nullptr, done);
 }
 
 __global__ void set_targets_kernel(int k, KState* st, const double* target, const int* maxit) {
@@ -116,57 +172,79 @@ __global__ void set_targets_kernel(int k, KState* st, const double* target, cons
   if (c < k) { st[c].target2 = target[c] * target[c]; st[c].maxit = maxit[c]; }
 }
 
+template <typename S> struct wide_of { typedef S type; };
+template <> struct wide_of<float> { typedef double type; };
+template <> struct wide_of<cfloat> { typedef cdouble type; };
+
 // rhs_in = cast(r64 / ||r64||) for active columns, 0 otherwise
-template <typename Sin, typename S64, int KB>
-__global__ void scale_cast_kernel(int n, int k, const S64* __restrict__ r64, const double* nrm2,
-                                  const int* active, Sin* __restrict__ out) {
-  const int sub = threadIdx.x & (KB - 1);
-  if (sub >= k) return;
-  const int act = active[sub];
-  const double inv = (act && nrm2[sub] > 0.0) ? 1.0 / sqrt(nrm2[sub]) : 0.0;
-  const int rpb = blockDim.x / KB;
-  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
-    const int64_t q = i * k + sub;
-    out[q] = act ? cvt<Sin>(inv * r64[q]) : Sin(0);
+template <typename S, int TPR, int CPT>
+__global__ void scale_cast_kernel(int n, int ld, const typename wide_of<S>::type* __restrict__ r64,
+                                  const double* nrm2, const int* active, S* __restrict__ out) {
+  typedef typename wide_of<S>::type W;
+  MOR_LANE_SETUP
+  if (c0 >= ld) return;
+  double inv[CPT];
+  int act[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    act[j] = active[c0 + j];
+    inv[j] = (act[j] && nrm2[c0 + j] > 0.0) ? 1.0 / sqrt(nrm2[c0 + j]) : 0.0;
+  }
+  for (int64_t i = rb + threadIdx.x / TPR; i < re; i += rpb) {
+    const int64_t q = i * ld + c0;
+    Pack<S, CPT> o;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      const W w = r64[q + j];
+      o.v[j] = act[j] ? cvt<S>(inv[j] * w) : S(0);
+    }
+    stp<S, CPT>(out + q, o);
   }
 }
 
-template <typename Sin, typename S64, int KB>
-__global__ void refine_update_kernel(int n, int k, S64* __restrict__ x64, const Sin* __restrict__ d,
-                                     const double* nrm2, const int* active) {
-  const int sub = threadIdx.x & (KB - 1);
-  if (sub >= k || !active[sub]) return;
-  const double sc = sqrt(nrm2[sub]);
-  const int rpb = blockDim.x / KB;
-  for (int64_t i = blockIdx.x * (int64_t)rpb + threadIdx.x / KB; i < n; i += (int64_t)gridDim.x * rpb) {
-    const int64_t q = i * k + sub;
-    x64[q] = x64[q] + sc * cvt<S64>(d[q]);
+template <typename S, int TPR, int CPT>
+__global__ void refine_update_kernel(int n, int ld, typename wide_of<S>::type* __restrict__ x64,
+                                     const S* __restrict__ d, const double* nrm2, const int* active) {
+  typedef typename wide_of<S>::type W;
+  MOR_LANE_SETUP
+  if (c0 >= ld) return;
+  double sc[CPT];
+  int act[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) { act[j] = active[c0 + j]; sc[j] = sqrt(nrm2[c0 + j]); }
+  for (int64_t i = rb + threadIdx.x / TPR; i < re; i += rpb) {
+    const int64_t q = i * ld + c0;
+    const Pack<S, CPT> dv = ldp<S, CPT>(d + q);
+#pragma unroll
+    for (int j = 0; j < CPT; ++j)
+      if (act[j]) x64[q + j] = x64[q + j] + sc[j] * cvt<W>(dv.v[j]);
   }
 }
 
-// column-major complex128 (n x k) -> row-major S
+// column-major complex128 (n x k) -> row-major S with stride ld (columns k..ld-1 untouched)
 template <typename S>
-__global__ void c128_col_to_row_kernel(int n, int k, const cdouble* __restrict__ src, S* __restrict__ dst) {
+__global__ void c128_col_to_row_kernel(int n, int k, int ld, const cdouble* __restrict__ src, S* __restrict__ dst) {
   int64_t total = (int64_t)n * k;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = t / k, c = t % k;
-    dst[t] = cvt<S>(src[c * n + i]);
+    dst[i * ld + c] = cvt<S>(src[c * n + i]);
   }
 }
 template <typename S>
-__global__ void row_to_c128_col_kernel(int n, int k, const S* __restrict__ src, cdouble* __restrict__ dst) {
+__global__ void row_to_c128_col_kernel(int n, int k, int ld, const S* __restrict__ src, cdouble* __restrict__ dst) {
   int64_t total = (int64_t)n * k;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = t % n, c = t / n;
-    dst[t] = cvt<cdouble>(src[i * k + c]);
+    dst[t] = cvt<cdouble>(src[i * ld + c]);
   }
 }
 template <typename S>
-__global__ void real_col_to_row_kernel(int n, int k, const double* __restrict__ src, int ld, S* __restrict__ dst) {
+__global__ void real_col_to_row_kernel(int n, int k, int ld, const double* __restrict__ src, int64_t lds,
+                                       S* __restrict__ dst) {
   int64_t total = (int64_t)n * k;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = t / k, c = t % k;
-    dst[t] = cvt<S>(src[c * (int64_t)ld + i]);
+    dst[i * ld + c] = cvt<S>(src[c * lds + i]);
   }
 }
 template <typename D, typename S>
@@ -175,15 +253,31 @@ __global__ void copy_cast_kernel(int64_t count, const S* __restrict__ src, D* __
     dst[t] = cvt<D>(src[t]);
 }
 
-#define KB_SWITCH(kb, CALL)                 \
-  switch (kb) {                             \
-    case 1: { constexpr int KBv = 1; CALL; break; } \
-    case 2: { constexpr int KBv = 2; CALL; break; } \
-    case 4: { constexpr int KBv = 4; CALL; break; } \
-    case 8: { constexpr int KBv = 8; CALL; break; } \
-    case 16: { constexpr int KBv = 16; CALL; break; } \
-    default: return (int)cudaErrorInvalidValue; \
+// dst(i, c) = c < ncols ? src(i, map[c]) : 0 for c < ld_dst (column compaction)
+template <typename T>
+__global__ void gather_cols_kernel(int64_t n, int ld_src, int ld_dst, int ncols, const int* __restrict__ map,
+                                   const T* __restrict__ src, T* __restrict__ dst) {
+  const int64_t total = n * ld_dst;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ld_dst;
+    const int c = (int)(t - i * ld_dst);
+    T v;
+    memset(&v, 0, sizeof(T));
+    if (c < ncols) v = src[i * ld_src + map[c]];
+    dst[t] = v;
   }
+}
+// dst(i, dmap[c]) = src(i, smap[c]) for c < ncols
+template <typename T>
+__global__ void scatter_cols_kernel(int64_t n, int ld_src, int ld_dst, int ncols, const int* __restrict__ smap,
+                                    const int* __restrict__ dmap, const T* __restrict__ src, T* __restrict__ dst) {
+  const int64_t total = n * ncols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / ncols;
+    const int c = (int)(t - i * ncols);
+    dst[i * ld_dst + dmap[c]] = src[i * ld_src + smap[c]];
+  }
+}
 
 #define ST_SWITCH(st, CALL)                                   \
   switch (st) {                                               \
@@ -198,52 +292,63 @@ __global__ void copy_cast_kernel(int64_t count, const S* __restrict__ src, D* __
 
 size_t krylov_state_bytes(int) { return sizeof(KState); }
 
-int krylov_launch_update_p(int st, int kb, int n, int k, const void* r, void* p, const void* v,
-                           const void* state, const int* done, cudaStream_t s) {
-  const int g = grid_for((int64_t)n * kb, 152 * 32);
-  ST_SWITCH(st, KB_SWITCH(kb, (update_p_kernel<S, KBv><<<g, 256, 0, s>>>(n, k, (const S*)r, (S*)p, (const S*)v,
-                                                                        (const KState*)state, done))));
+int krylov_launch_update_p(int st, int n, int ld, const void* r, void* p, const void* v, const void* state,
+                           const int* done, cudaStream_t s) {
+  const int g = grid_rows(st, n, ld, 152 * 8);
+  int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    update_p_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (const S*)r, (S*)p, (const S*)v, (const KState*)state, done);
+    return 0;
+  });
+  if (e) return e;
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
-int krylov_launch_update_s(int st, int kb, int n, int k, const void* r, const void* v, void* sv,
-                           const void* state, const int* done, cudaStream_t s) {
-  const int g = grid_for((int64_t)n * kb, 152 * 32);
-  ST_SWITCH(st, KB_SWITCH(kb, (update_s_kernel<S, KBv><<<g, 256, 0, s>>>(n, k, (const S*)r, (const S*)v, (S*)sv,
-                                                                        (const KState*)state, done))));
+int krylov_launch_update_s(int st, int n, int ld, const void* r, const void* v, void* sv, const void* state,
+                           const int* done, cudaStream_t s) {
+  const int g = grid_rows(st, n, ld, 152 * 8);
+  int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    update_s_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (const S*)r, (const S*)v, (S*)sv, (const KState*)state, done);
+    return 0;
+  });
+  if (e) return e;
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
-int krylov_launch_update_xr(int st, int kb, int n, int k, void* x, void* r, const void* phat,
-                            const void* shat, const void* sv, const void* t, const void* rhat,
-                            void* part, unsigned* counter, void* state, int* done, int grid_cap,
-                            cudaStream_t s) {
-  const int g = grid_for((int64_t)n * kb, grid_cap);
-  ST_SWITCH(st, KB_SWITCH(kb, (update_xr_kernel<S, KBv><<<g, 256, 0, s>>>(
-                                  n, k, (S*)x, (S*)r, (const S*)phat, (const S*)shat, (const S*)sv,
-                                  (const S*)t, (const S*)rhat, (double*)part, counter, (KState*)state, done))));
+int krylov_launch_update_xr(int st, int n, int ld, void* x, void* r, const void* phat, const void* shat,
+                            const void* sv, const void* t, const void* rhat, void* part, unsigned* counter,
+                            void* state, int* done, int grid_cap, cudaStream_t s) {
+  const int g = grid_rows(st, n, ld, grid_cap);
+  int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    update_xr_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (S*)x, (S*)r, (const S*)phat, (const S*)shat,
+                                                    (const S*)sv, (const S*)t, (const S*)rhat, (double*)part,
+                                                    counter, (KState*)state, done);
+    return 0;
+  });
+  if (e) return e;
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
-int krylov_launch_init(int st, int kb, int n, int k, const void* rhs, void* x, void* r, void* rhat,
-                       void* p, void* v, void* part, unsigned* counter, void* state,
-                       const double* target, const int* maxit, int* done, int grid_cap,
-                       cudaStream_t s) {
-  set_targets_kernel<<<1, 32, 0, s>>>(k, (KState*)state, target, maxit);
+int krylov_launch_init(int st, int n, int ld, const void* rhs, void* x, void* r, void* rhat, void* p, void* v,
+                       void* part, unsigned* counter, void* state, const double* target, const int* maxit,
+                       int* done, int grid_cap, cudaStream_t s) {
+  set_targets_kernel<<<1, 32, 0, s>>>(ld, (KState*)state, target, maxit);
   mor_count_launches(1);
-  const int g = grid_for((int64_t)n * kb, grid_cap);
-  ST_SWITCH(st, KB_SWITCH(kb, (init_kernel<S, KBv><<<g, 256, 0, s>>>(n, k, (const S*)rhs, (S*)x, (S*)r, (S*)rhat,
-                                                                    (S*)p, (S*)v, (double*)part, counter,
-                                                                    (KState*)state, done))));
+  const int g = grid_rows(st, n, ld, grid_cap);
+  int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    init_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (const S*)rhs, (S*)x, (S*)r, (S*)rhat, (S*)p, (S*)v,
+                                               (double*)part, counter, (KState*)state, done);
+    return 0;
+  });
+  if (e) return e;
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
 int krylov_read_state(int, const void* state_dev, int k, int* iters, int* status, cudaStream_t s) {
-  KState h[MOR_KMAX];
+  KState h[MOR_LDMAX];
   cudaError_t e = cudaMemcpyAsync(h, state_dev, sizeof(KState) * k, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return (int)e;
   e = cudaStreamSynchronize(s);
@@ -252,49 +357,48 @@ int krylov_read_state(int, const void* state_dev, int k, int* iters, int* status
   return 0;
 }
 
-int refine_launch_scale_cast(int st_in, int kb, int n, int k, const void* r64, const double* nrm2,
-                             const int* active, void* rhs_in, cudaStream_t s) {
-  const int g = grid_for((int64_t)n * kb, 152 * 32);
-  switch (st_in) {
-    case ST_F32: KB_SWITCH(kb, (scale_cast_kernel<float, double, KBv><<<g, 256, 0, s>>>(n, k, (const double*)r64, nrm2, active, (float*)rhs_in))); break;
-    case ST_F64: KB_SWITCH(kb, (scale_cast_kernel<double, double, KBv><<<g, 256, 0, s>>>(n, k, (const double*)r64, nrm2, active, (double*)rhs_in))); break;
-    case ST_C32: KB_SWITCH(kb, (scale_cast_kernel<cfloat, cdouble, KBv><<<g, 256, 0, s>>>(n, k, (const cdouble*)r64, nrm2, active, (cfloat*)rhs_in))); break;
-    case ST_C64: KB_SWITCH(kb, (scale_cast_kernel<cdouble, cdouble, KBv><<<g, 256, 0, s>>>(n, k, (const cdouble*)r64, nrm2, active, (cdouble*)rhs_in))); break;
-    default: return (int)cudaErrorInvalidValue;
-  }
+int refine_launch_scale_cast(int st_in, int n, int ld, const void* r64, const double* nrm2, const int* active,
+                             void* rhs_in, cudaStream_t s) {
+  const int g = grid_rows(st_in, n, ld, 152 * 8);
+  int e = dispatch_shape(st_in, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    typedef typename wide_of<S>::type W;
+    scale_cast_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (const W*)r64, nrm2, active, (S*)rhs_in);
+    return 0;
+  });
+  if (e) return e;
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
-int refine_launch_update(int st_in, int kb, int n, int k, void* x64, const void* d,
-                         const double* nrm2, const int* active, cudaStream_t s) {
-  const int g = grid_for((int64_t)n * kb, 152 * 32);
-  switch (st_in) {
-    case ST_F32: KB_SWITCH(kb, (refine_update_kernel<float, double, KBv><<<g, 256, 0, s>>>(n, k, (double*)x64, (const float*)d, nrm2, active))); break;
-    case ST_F64: KB_SWITCH(kb, (refine_update_kernel<double, double, KBv><<<g, 256, 0, s>>>(n, k, (double*)x64, (const double*)d, nrm2, active))); break;
-    case ST_C32: KB_SWITCH(kb, (refine_update_kernel<cfloat, cdouble, KBv><<<g, 256, 0, s>>>(n, k, (cdouble*)x64, (const cfloat*)d, nrm2, active))); break;
-    case ST_C64: KB_SWITCH(kb, (refine_update_kernel<cdouble, cdouble, KBv><<<g, 256, 0, s>>>(n, k, (cdouble*)x64, (const cdouble*)d, nrm2, active))); break;
-    default: return (int)cudaErrorInvalidValue;
-  }
+int refine_launch_update(int st_in, int n, int ld, void* x64, const void* d, const double* nrm2, const int* active,
+                         cudaStream_t s) {
+  const int g = grid_rows(st_in, n, ld, 152 * 8);
+  int e = dispatch_shape(st_in, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    typedef typename wide_of<S>::type W;
+    refine_update_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (W*)x64, (const S*)d, nrm2, active);
+    return 0;
+  });
+  if (e) return e;
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
-int conv_launch_colmajor_c128_to_rowmajor(int st, int n, int k, const void* src, void* dst, cudaStream_t s) {
+int conv_launch_colmajor_c128_to_rowmajor(int st, int n, int k, int ld, const void* src, void* dst, cudaStream_t s) {
   const int g = grid_for((int64_t)n * k, 152 * 8);
-  ST_SWITCH(st, (c128_col_to_row_kernel<S><<<g, 256, 0, s>>>(n, k, (const cdouble*)src, (S*)dst)));
+  ST_SWITCH(st, (c128_col_to_row_kernel<S><<<g, 256, 0, s>>>(n, k, ld, (const cdouble*)src, (S*)dst)));
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
-int conv_launch_rowmajor_to_colmajor_c128(int st, int n, int k, const void* src, void* dst, cudaStream_t s) {
+int conv_launch_rowmajor_to_colmajor_c128(int st, int n, int k, int ld, const void* src, void* dst, cudaStream_t s) {
   const int g = grid_for((int64_t)n * k, 152 * 8);
-  ST_SWITCH(st, (row_to_c128_col_kernel<S><<<g, 256, 0, s>>>(n, k, (const S*)src, (cdouble*)dst)));
+  ST_SWITCH(st, (row_to_c128_col_kernel<S><<<g, 256, 0, s>>>(n, k, ld, (const S*)src, (cdouble*)dst)));
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
-int conv_launch_real_col_to_rowmajor(int st, int n, int k, const double* src, int ld, void* dst, cudaStream_t s) {
+int conv_launch_real_col_to_rowmajor(int st, int n, int k, int ld, const double* src, int64_t lds, void* dst,
+                                     cudaStream_t s) {
   const int g = grid_for((int64_t)n * k, 152 * 8);
-  ST_SWITCH(st, (real_col_to_row_kernel<S><<<g, 256, 0, s>>>(n, k, src, ld, (S*)dst)));
+  ST_SWITCH(st, (real_col_to_row_kernel<S><<<g, 256, 0, s>>>(n, k, ld, src, lds, (S*)dst)));
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
@@ -313,4 +417,43 @@ int conv_launch_copy_cast(int st_dst, int st_src, int64_t count, const void* src
   else return (int)cudaErrorInvalidValue;
   mor_count_launches(1);
   return (int)cudaGetLastError();
+}
+
+int conv_launch_gather_cols(int st, int64_t n, int ld_src, int ld_dst, int ncols, const int* map, const void* src,
+                            void* dst, cudaStream_t s) {
+  const int g = grid_for(n * ld_dst, 152 * 8);
+  const size_t es = st_size(st);
+  if (es == 4) gather_cols_kernel<uint32_t><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, map, (const uint32_t*)src, (uint32_t*)dst);
+  else if (es == 8) gather_cols_kernel<uint2><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, map, (const uint2*)src, (uint2*)dst);
+  else gather_cols_kernel<uint4><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, map, (const uint4*)src, (uint4*)dst);
+  mor_count_launches(1);
+  return (int)cudaGetLastError();
+}
+
+int conv_launch_scatter_cols(int st, int64_t n, int ld_src, int ld_dst, int ncols, const int* smap, const int* dmap,
+                             const void* src, void* dst, cudaStream_t s) {
+  const int g = grid_for(n * ncols, 152 * 8);
+  const size_t es = st_size(st);
+  if (es == 4) scatter_cols_kernel<uint32_t><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, smap, dmap, (const uint32_t*)src, (uint32_t*)dst);
+  else if (es == 8) scatter_cols_kernel<uint2><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, smap, dmap, (const uint2*)src, (uint2*)dst);
+  else scatter_cols_kernel<uint4><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, smap, dmap, (const uint4*)src, (uint4*)dst);
+  mor_count_launches(1);
+  return (int)cudaGetLastError();
+}
+
+int krylov_write_state(const void* host_states, void* state_dev, int k, cudaStream_t s) {
+  return (int)cudaMemcpyAsync(state_dev, host_states, sizeof(KState) * k, cudaMemcpyHostToDevice, s);
+}
+int krylov_read_states(void* host_states, const void* state_dev, int k, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(host_states, state_dev, sizeof(KState) * k, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaStreamSynchronize(s);
+}
+int krylov_state_active(const void* host_state) { return ((const KState*)host_state)->active; }
+int krylov_state_iters(const void* host_state) { return ((const KState*)host_state)->iters; }
+int krylov_state_status(const void* host_state) { return ((const KState*)host_state)->status; }
+void krylov_state_make_dummy(void* host_state) {
+  KState* k = (KState*)host_state;
+  memset(k, 0, sizeof(KState));
+  k->target2 = 1.0;
 }

@@ -5,11 +5,16 @@
 // x_0 = 0 with Hermitian inner products; the scalars are kept in FP64 complex
 // whatever the vector precision.
 //
-// Thread mapping shared by the kernels of the solve: a row of the n x k
-// row-major block is handled by KB consecutive lanes (KB = k rounded up to a
-// power of two), lane `sub` owning column `sub`; lanes with sub >= k idle.
+// Thread mapping shared by the kernels of the solve: a row of the n x ld
+// row-major block is handled by TPR consecutive lanes, lane `sub` owning the
+// CPT consecutive columns sub * CPT ... (a 16-byte vector when CPT * size =
+// 16); each block walks one contiguous range of rows, so that neighbouring
+// rows of a stencil reuse the gathered vector entries from L1.
 #pragma once
 #include "mor_types.cuh"
+#include <string.h>
+
+#define MOR_LDMAX_DEV 16
 
 enum {
   FIN_NONE = 0,
@@ -74,33 +79,75 @@ __device__ inline void krylov_finalize(int stage, int k, const cdouble* sums, KS
 }
 
 // ---------------------------------------------------------------------------
-// Reduce two per-lane scalars (v0, v1) of column sub = lane % KB over the
-// block, write the per-block FP64 partials part[(block * 2k + 2c + q) * 2 +
-// {re, im}], and let the last block (atomic ticket) sum the partials of all
-// blocks in a fixed order and run the finalize stage (or write the sums to
-// `out`).  Every thread of the block must call it.
-template <typename S, int KB>
-__device__ inline void col_reduce_finalize(S v0, S v1, int k, double* part, unsigned* counter, int fin,
-                                           KState* state, cdouble* out, int* done) {
+// Vector access to the CPT consecutive columns a lane owns: one 16-byte load
+// or store when CPT * sizeof(S) == 16, scalar accesses otherwise.
+template <typename S, int CPT> struct Pack { S v[CPT]; };
+
+template <typename S, int CPT>
+__device__ __forceinline__ Pack<S, CPT> ldp(const S* p) {
+  Pack<S, CPT> o;
+  if constexpr (CPT * sizeof(S) == 16) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    memcpy(&o, &t, 16);
+  } else {
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) o.v[j] = p[j];
+  }
+  return o;
+}
+template <typename S, int CPT>
+__device__ __forceinline__ void stp(S* p, const Pack<S, CPT>& o) {
+  if constexpr (CPT * sizeof(S) == 16) {
+    float4 t;
+    memcpy(&t, &o, 16);
+    *reinterpret_cast<float4*>(p) = t;
+  } else {
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) p[j] = o.v[j];
+  }
+}
+
+// Contiguous row range of this block: [r0, r1), processed rpb rows at a time.
+__device__ __forceinline__ void block_rows(int64_t n, int rpb, int64_t& r0, int64_t& r1) {
+  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  chunk = (chunk + rpb - 1) / rpb * rpb;
+  r0 = (int64_t)blockIdx.x * chunk;
+  r1 = r0 + chunk < n ? r0 + chunk : n;
+}
+
+// ---------------------------------------------------------------------------
+// Reduce two per-column values (v0[j], v1[j]) of the CPT columns lane `sub`
+// owns (columns sub * CPT + j; sub = lane % TPR) over the block, write the
+// per-block FP64 partials part[(block * 2 ld + 2c + q) * 2 + {re, im}], and
+// let the last block (atomic ticket) sum the partials of all blocks in a fixed
+// order and run the finalize stage (or write the sums to `out`).  Every thread
+// of the block must call it.
+template <typename S, int TPR, int CPT>
+__device__ inline void col_reduce_finalize(const S (&v0)[CPT], const S (&v1)[CPT], int ld, double* part,
+                                           unsigned* counter, int fin, KState* state, cdouble* out, int* done) {
   typedef typename real_of<S>::type R;
-  __shared__ double sh[8][2 * KB][2];
+  __shared__ double sh[8][2 * MOR_LDMAX_DEV][2];
   __shared__ bool am_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int nv = 2 * k;
-  R a0 = (R)real_(v0), b0 = (R)imag_(v0), a1 = (R)real_(v1), b1 = (R)imag_(v1);
+  const int nv = 2 * ld;
 #pragma unroll
-  for (int o = 16; o >= KB; o >>= 1) {
-    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-    b0 += __shfl_xor_sync(0xffffffffu, b0, o);
-    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-    b1 += __shfl_xor_sync(0xffffffffu, b1, o);
-  }
-  if (lane < KB) {
-    sh[wid][2 * lane][0] = (double)a0;
-    sh[wid][2 * lane][1] = (double)b0;
-    sh[wid][2 * lane + 1][0] = (double)a1;
-    sh[wid][2 * lane + 1][1] = (double)b1;
+  for (int j = 0; j < CPT; ++j) {
+    R a0 = (R)real_(v0[j]), b0 = (R)imag_(v0[j]), a1 = (R)real_(v1[j]), b1 = (R)imag_(v1[j]);
+#pragma unroll
+    for (int o = 16; o >= TPR; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      b0 += __shfl_xor_sync(0xffffffffu, b0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+    }
+    const int c = lane * CPT + j;
+    if (lane < TPR && c < ld) {
+      sh[wid][2 * c][0] = (double)a0;
+      sh[wid][2 * c][1] = (double)b0;
+      sh[wid][2 * c + 1][0] = (double)a1;
+      sh[wid][2 * c + 1][1] = (double)b1;
+    }
   }
   __syncthreads();
   if (threadIdx.x < nv) {
@@ -115,8 +162,8 @@ __device__ inline void col_reduce_finalize(S v0, S v1, int k, double* part, unsi
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  // last block: warp w sums value i = w, w + nwarps, ... over all blocks (lanes stride the blocks)
-  __shared__ cdouble sums[2 * KB];
+  // last block: warp w sums values w, w + nwarps, ... over all blocks (lanes stride the blocks)
+  __shared__ cdouble sums[2 * MOR_LDMAX_DEV];
   const volatile double* vp = part;
   for (int i = wid; i < nv; i += nwarps) {
     double re = 0.0, im = 0.0;
@@ -130,7 +177,7 @@ __device__ inline void col_reduce_finalize(S v0, S v1, int k, double* part, unsi
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (fin != FIN_NONE) krylov_finalize(fin, k, sums, state, done);
+    if (fin != FIN_NONE) krylov_finalize(fin, ld, sums, state, done);
     else if (out) for (int i = 0; i < nv; ++i) out[i] = sums[i];
     *counter = 0u;   // ready for the next launch (stream order makes this safe)
   }

@@ -49,37 +49,72 @@ enum {
   RED_NORM = 3       // partial[c] = sum |y|^2  (and y = b + op, see b pointer)
 };
 
-// Launchers (spmv.cu).  x, y, w, b: n x k, row-major with stride k (k contiguous).
-// `part`: per-block partials scratch; `fin`: finalize stage run by the last block
-// (FIN_* in krylov), `state`: per-column solver state (type-erased), counter: block counter.
+// ---------------------------------------------------------------------------
+// Row layout of the n x k blocks of a solve: row-major with a padded stride ld
+// (the k columns of one row contiguous, ld - k dummy columns kept at zero), so
+// that rows are whole 16-byte vectors.  A row is handled by `tpr` lanes, each
+// owning `cpt` consecutive columns (one 16-byte vector load when cpt * size =
+// 16).  Narrow rows (ld * size < 16) use one thread per row.
+inline int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
+inline bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+// Padded row stride for k columns of type st.  Rows of whole 16-byte vectors
+// over a power-of-two number of lanes when that wastes little; otherwise (k <=
+// 8) one thread per row over the unpadded row; wider rows pad to 16 bytes x
+// a power of two.
+inline int row_stride(int st, int k) {
+  const int es = (int)st_size(st);
+  if (k * es < 16) return k;
+  const int c = 16 / es;
+  const int t = (k + c - 1) / c;
+  if (is_pow2(t)) return t * c;
+  if (k <= 8) return k;
+  return next_pow2(t) * c;
+}
+// Lanes per row (tpr) and columns per lane (cpt) for rows of stride ld.
+inline void lane_shape(int st, int ld, int* tpr, int* cpt) {
+  const int es = (int)st_size(st);
+  if (ld * es < 16) { *tpr = 1; *cpt = ld; return; }
+  const int c = 16 / es;
+  if (ld % c == 0 && is_pow2(ld / c)) { *cpt = c; *tpr = ld / c; return; }
+  if (ld <= 8) { *tpr = 1; *cpt = ld; return; }
+  *cpt = 1;
+  *tpr = next_pow2(ld);
+}
+
+#define MOR_LDMAX 16
+
+// Fused reductions: `part` holds per-block FP64 partials, the last block (by
+// ticket on `counter`) reduces them in a fixed order and runs the finalize
+// stage `fin` on `state` (or writes the 2 * ld sums to `out`).
 struct RedArgs {
   int mode;            // RED_*
   const void* w;       // second vector of the reduction
-  void* part;          // gridDim.x * k * 2 scalars of the reduction type (double or float)
+  void* part;          // gridDim.x * ld * 2 complex partials (doubles)
   unsigned* counter;   // zero-initialised block counter (the last block resets it)
   int fin;             // finalize stage id (0 = none: just write the reduced sums to `out`)
   void* state;         // solver state for the finalize stage
-  void* out;           // reduced sums (k * 2 values of the scalar type), when fin == 0
+  void* out;           // reduced sums (2 * ld complex doubles), when fin == 0
   const int* done;     // if non-null and *done != 0 the kernel returns at once
 };
 
-int launch_op_spmv(int st, int kb, const PatView& pv, const OpVals& ov, const Coef* coefs, int k,
+// Launchers (spmv.cu).  x, y, w, b: n x ld row-major blocks of type st.
+int launch_op_spmv(int st, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
                    const void* x, void* y, const void* b, const RedArgs* red, int grid_cap,
                    cudaStream_t s);
-int launch_factor_spmv(int st, bool fcplx, int kb, const PatView& pv, const void* fvals,
-                       const int* apply, int k, const void* x, void* y, const int* done,
+int launch_factor_spmv(int st, bool fcplx, const PatView& pv, const void* fvals,
+                       const int* apply, int ld, const void* x, void* y, const int* done,
                        cudaStream_t s);
 
 // Krylov helpers (krylov.cu)
-int krylov_launch_update_p(int st, int kb, int n, int k, const void* r, void* p, const void* v,
+int krylov_launch_update_p(int st, int n, int ld, const void* r, void* p, const void* v,
                            const void* state, const int* done, cudaStream_t s);
-int krylov_launch_update_s(int st, int kb, int n, int k, const void* r, const void* v, void* sv,
+int krylov_launch_update_s(int st, int n, int ld, const void* r, const void* v, void* sv,
                            const void* state, const int* done, cudaStream_t s);
-int krylov_launch_update_xr(int st, int kb, int n, int k, void* x, void* r, const void* phat,
+int krylov_launch_update_xr(int st, int n, int ld, void* x, void* r, const void* phat,
                             const void* shat, const void* sv, const void* t, const void* rhat,
                             void* part, unsigned* counter, void* state, int* done, int grid_cap,
                             cudaStream_t s);
-int krylov_launch_init(int st, int kb, int n, int k, const void* rhs, void* x, void* r, void* rhat,
+int krylov_launch_init(int st, int n, int ld, const void* rhs, void* x, void* r, void* rhat,
                        void* p, void* v, void* part, unsigned* counter, void* state,
                        const double* target, const int* maxit, int* done, int grid_cap,
                        cudaStream_t s);
@@ -87,19 +122,31 @@ size_t krylov_state_bytes(int st);
 int krylov_read_state(int st, const void* state_dev, int k, int* iters, int* status,
                       cudaStream_t s);
 // outer FP64 refinement: rhs_in = r64 / ||r64|| (cast), x64 += nrm * d
-int refine_launch_scale_cast(int st_in, int kb, int n, int k, const void* r64, const double* nrm2,
+int refine_launch_scale_cast(int st_in, int n, int ld, const void* r64, const double* nrm2,
                              const int* active, void* rhs_in, cudaStream_t s);
-int refine_launch_update(int st_in, int kb, int n, int k, void* x64, const void* d,
+int refine_launch_update(int st_in, int n, int ld, void* x64, const void* d,
                          const double* nrm2, const int* active, cudaStream_t s);
-// layout conversion: column-major complex128 (API) <-> row-major type st
-int conv_launch_colmajor_c128_to_rowmajor(int st, int n, int k, const void* src, void* dst,
+// layout conversion: column-major complex128 (API, k columns) <-> row-major type st, stride ld
+int conv_launch_colmajor_c128_to_rowmajor(int st, int n, int k, int ld, const void* src, void* dst,
                                           cudaStream_t s);
-int conv_launch_rowmajor_to_colmajor_c128(int st, int n, int k, const void* src, void* dst,
+int conv_launch_rowmajor_to_colmajor_c128(int st, int n, int k, int ld, const void* src, void* dst,
                                           cudaStream_t s);
-int conv_launch_real_col_to_rowmajor(int st, int n, int k, const double* src, int ld, void* dst,
-                                     cudaStream_t s);
+int conv_launch_real_col_to_rowmajor(int st, int n, int k, int ld, const double* src, int64_t lds,
+                                     void* dst, cudaStream_t s);
 int conv_launch_copy_cast(int st_dst, int st_src, int64_t count, const void* src, void* dst,
                           cudaStream_t s);
+// active-column compaction: gather map[c] -> c into a narrower stride, scatter back
+int conv_launch_gather_cols(int st, int64_t n, int ld_src, int ld_dst, int ncols, const int* map, const void* src,
+                            void* dst, cudaStream_t s);
+int conv_launch_scatter_cols(int st, int64_t n, int ld_src, int ld_dst, int ncols, const int* smap, const int* dmap,
+                             const void* src, void* dst, cudaStream_t s);
+// host access to the per-column Krylov state (opaque, krylov_state_bytes() each)
+int krylov_write_state(const void* host_states, void* state_dev, int k, cudaStream_t s);
+int krylov_read_states(void* host_states, const void* state_dev, int k, cudaStream_t s);
+int krylov_state_active(const void* host_state);
+int krylov_state_iters(const void* host_state);
+int krylov_state_status(const void* host_state);
+void krylov_state_make_dummy(void* host_state);
 
 // SPAI (spai.cu)
 struct SpaiArgs {

@@ -296,8 +296,8 @@ double time_op(mor_t h, OpData& op, int& status) {
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0, h->stream);
-    launch_op_spmv(ST_F32, 1, pv, ov, cf, 1, x.p, y.p, nullptr, nullptr, 0, h->stream);
-    launch_op_spmv(ST_C32, 8, pv, ov, cf, 5, x.p, y.p, nullptr, nullptr, 0, h->stream);
+    launch_op_spmv(ST_F32, pv, ov, cf, 1, x.p, y.p, nullptr, nullptr, h->grid_cap, h->stream);
+    launch_op_spmv(ST_C32, pv, ov, cf, 8, x.p, y.p, nullptr, nullptr, h->grid_cap, h->stream);
     cudaEventRecord(e1, h->stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;

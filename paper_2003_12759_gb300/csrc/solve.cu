@@ -18,10 +18,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 
 namespace {
 
-int kb_for(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 16; }
 int st_of(int precision, bool cplx) {
   if (precision == MOR_FP64) return cplx ? ST_C64 : ST_F64;
   return cplx ? ST_C32 : ST_F32;
@@ -127,6 +127,7 @@ static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bo
 struct BatchIO {
   const mor_c64* sig;   // k shifts
   int k;
+  int ld;               // padded row stride of the blocks
   const int* L;         // chain prefix length per column
   void* b64;            // row-major n x k, st64
   void* x64;            // row-major n x k, st64 (out)
@@ -136,79 +137,92 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
                        mor_solve_stats* stats) {
   OpData& op = h->op(transpose);
   const int k = io.k;
-  const int kb = kb_for(k);
   const int64_t n = op.n;
   const int prec = o.precision;
   const int st_in = st_of(prec, cplx);
   const int st64 = cplx ? ST_C64 : ST_F64;
+  const int ld = io.ld;                              // padded row stride, columns k..ld-1 are dummies
   const size_t es = st_size(st_in), es64 = st_size(st64);
   int Lmax = 0;
   for (int c = 0; c < k; ++c) Lmax = std::max(Lmax, io.L[c]);
   if (Lmax > (int)op.chain.size()) return mor_fail(h, MOR_ESTATE, "chain shorter than requested prefix");
-  if (Lmax > MAX_FACTORS) return mor_fail(h, MOR_EINVAL, "chain too long");
+  if (Lmax > MAX_FACTORS - 4) return mor_fail(h, MOR_EINVAL, "chain too long");
   for (int f = 0; f < Lmax; ++f) {
     const Factor& F = op.chain[f];
     if (st_is_f32(F.st) != st_is_f32(st_in))
       return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from the solve precision");
     if (st_is_cplx(F.st) && !st_is_cplx(st_in)) return mor_fail(h, MOR_EINVAL, "internal: complex factor, real vectors");
   }
-  // workspace: 12 inner vectors
-  const size_t vbytes = es * (size_t)n * k;
-  MOR_CK(h, h->ws_vec.alloc(vbytes * 12 + 256 * 12));
+  // workspace: 12 inner vectors of n x ld
+  const size_t vbytes = ((es * (size_t)n * ld) + 255) / 256 * 256;
+  MOR_CK(h, h->ws_vec.alloc(vbytes * 12));
   char* vb = h->ws_vec.as<char>();
-  auto vec = [&](int i) { return (void*)(vb + ((vbytes + 255) / 256 * 256) * i); };
+  auto vec = [&](int i) { return (void*)(vb + vbytes * i); };
   void *rhs = vec(0), *d = vec(1), *r = vec(2), *rhat = vec(3), *p = vec(4), *v = vec(5), *sv = vec(6),
        *t = vec(7), *ph = vec(8), *sh = vec(9), *tmp0 = vec(10), *tmp1 = vec(11);
-  MOR_CK(h, h->ws_r64.alloc(es64 * (size_t)n * k));
+  MOR_CK(h, h->ws_r64.alloc(es64 * (size_t)n * ld));
   void* r64 = h->ws_r64.p;
   const int gc = h->grid_cap;
-  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_KMAX * (size_t)std::max(gc, 2048)));
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * (size_t)std::max(gc, 2048)));
   Small sm;
   MOR_TRY(get_small(h, sm));
-  // per-factor application masks
-  std::vector<int> masks((size_t)std::max(Lmax, 1) * MOR_KMAX, 0);
-  for (int f = 0; f < Lmax; ++f)
-    for (int c = 0; c < k; ++c) masks[(size_t)f * MOR_KMAX + c] = (f < io.L[c]) ? 1 : 0;
-  if (Lmax > 0)
-    MOR_CK(h, cudaMemcpyAsync(sm.masks, masks.data(), sizeof(int) * masks.size(), cudaMemcpyHostToDevice, h->stream));
-  // coefficients
-  Coef cf[MOR_KMAX], ncf[MOR_KMAX];
-  for (int c = 0; c < k; ++c) {
-    cf[c] = mor_coef(h, io.sig[c]);
+  // coefficients (dummy columns reuse column 0's)
+  Coef cf[MOR_LDMAX], ncf[MOR_LDMAX];
+  for (int c = 0; c < ld; ++c) {
+    cf[c] = mor_coef(h, io.sig[c < k ? c : 0]);
     ncf[c] = Coef{-cf[c].sEr, -cf[c].sEi, -cf[c].sAr, -cf[c].sAi};
   }
   PatView pv = op.view();
   OpVals ov_in = op_vals(h, op, st_is_f32(st_in));
   OpVals ov64 = op_vals(h, op, false);
-  MOR_CK(h, cudaMemsetAsync(io.x64, 0, es64 * (size_t)n * k, h->stream));
+  MOR_CK(h, cudaMemsetAsync(io.x64, 0, es64 * (size_t)n * ld, h->stream));
 
-  // the iteration as a launch sequence
+  // Current geometry of the batch.  When enough columns have converged that
+  // the live ones fit a narrower stride, the converged columns are flushed
+  // to d_full (in the original layout) and the state-carrying vectors
+  // (d, r, r_hat, p, v) are repacked into the free scratch vectors.
+  int ldc = ld;
+  std::vector<int> cmap(ld);                 // current column -> original column
+  void* d_full = rhs;                        // free after init: collects flushed columns
+  void* dd = d;
+  void *rr = r, *rh = rhat, *pp = p, *vv = v, *ssv = sv, *tt = t, *pph = ph, *ssh = sh, *t0 = tmp0, *t1 = tmp1;
+  Coef cfc[MOR_LDMAX];
+  auto upload_masks = [&]() -> int {
+    if (Lmax == 0) return 0;
+    std::vector<int> mk((size_t)Lmax * MOR_KMAX, 0);
+    for (int f = 0; f < Lmax; ++f)
+      for (int c = 0; c < ldc; ++c) {
+        const int oc = cmap[c];
+        mk[(size_t)f * MOR_KMAX + c] = (oc < 0 || oc >= k || f < io.L[oc]) ? 1 : 0;
+      }
+    return (int)cudaMemcpyAsync(sm.masks, mk.data(), sizeof(int) * mk.size(), cudaMemcpyHostToDevice, h->stream);
+  };
   auto chain_apply = [&](void* src, void* dst) -> int {
     if (Lmax == 0) return 0;
     void* s = src;
     for (int f = 0; f < Lmax; ++f) {
-      void* dd = (f == Lmax - 1) ? dst : ((f % 2 == 0) ? tmp0 : tmp1);
+      void* dd2 = (f == Lmax - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
       const Factor& F = op.chain[f];
-      int e = launch_factor_spmv(st_in, st_is_cplx(F.st), kb, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, k, s,
-                                 dd, sm.done, h->stream);
+      int e = launch_factor_spmv(st_in, st_is_cplx(F.st), pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
+                                 dd2, sm.done, h->stream);
       if (e) return e;
-      s = dd;
+      s = dd2;
     }
     return 0;
   };
-  void* phat = (Lmax == 0) ? p : ph;
-  void* shat = (Lmax == 0) ? sv : sh;
   auto one_iter = [&]() -> int {
     int e;
-    if ((e = krylov_launch_update_p(st_in, kb, (int)n, k, r, p, v, sm.kstate, sm.done, h->stream))) return e;
-    if ((e = chain_apply(p, ph))) return e;
-    RedArgs ra{RED_DOT_W, rhat, h->ws_part.p, sm.counter, FIN_ALPHA, sm.kstate, nullptr, sm.done};
-    if ((e = launch_op_spmv(st_in, kb, pv, ov_in, cf, k, phat, v, nullptr, &ra, gc, h->stream))) return e;
-    if ((e = krylov_launch_update_s(st_in, kb, (int)n, k, r, v, sv, sm.kstate, sm.done, h->stream))) return e;
-    if ((e = chain_apply(sv, sh))) return e;
-    RedArgs rb{RED_DOT_TT, sv, h->ws_part.p, sm.counter, FIN_OMEGA, sm.kstate, nullptr, sm.done};
-    if ((e = launch_op_spmv(st_in, kb, pv, ov_in, cf, k, shat, t, nullptr, &rb, gc, h->stream))) return e;
-    if ((e = krylov_launch_update_xr(st_in, kb, (int)n, k, d, r, phat, shat, sv, t, rhat, h->ws_part.p, sm.counter,
+    void* phat = (Lmax == 0) ? pp : pph;
+    void* shat = (Lmax == 0) ? ssv : ssh;
+    if ((e = krylov_launch_update_p(st_in, (int)n, ldc, rr, pp, vv, sm.kstate, sm.done, h->stream))) return e;
+    if ((e = chain_apply(pp, pph))) return e;
+    RedArgs ra{RED_DOT_W, rh, h->ws_part.p, sm.counter, FIN_ALPHA, sm.kstate, nullptr, sm.done};
+    if ((e = launch_op_spmv(st_in, pv, ov_in, cfc, ldc, phat, vv, nullptr, &ra, gc, h->stream))) return e;
+    if ((e = krylov_launch_update_s(st_in, (int)n, ldc, rr, vv, ssv, sm.kstate, sm.done, h->stream))) return e;
+    if ((e = chain_apply(ssv, ssh))) return e;
+    RedArgs rb{RED_DOT_TT, ssv, h->ws_part.p, sm.counter, FIN_OMEGA, sm.kstate, nullptr, sm.done};
+    if ((e = launch_op_spmv(st_in, pv, ov_in, cfc, ldc, shat, tt, nullptr, &rb, gc, h->stream))) return e;
+    if ((e = krylov_launch_update_xr(st_in, (int)n, ldc, dd, rr, phat, shat, ssv, tt, rh, h->ws_part.p, sm.counter,
                                      sm.kstate, sm.done, gc, h->stream)))
       return e;
     return 0;
@@ -216,7 +230,11 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   const int chunk = std::max(1, o.graph_chunk);
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_nodes = 0;
-  if (o.use_graph) {
+  auto drop_graph = [&]() { if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; } };
+  struct GraphGuard { std::function<void()> f; ~GraphGuard() { f(); } } guard{drop_graph};
+  auto capture = [&]() -> int {
+    drop_graph();
+    if (!o.use_graph) return MOR_OK;
     cudaGraph_t g = nullptr;
     int64_t c0 = 0, c1 = 0;
     mor_launch_count(&c0);
@@ -232,18 +250,20 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     ce = cudaGraphInstantiate(&gexec, g, 0);
     cudaGraphDestroy(g);
     MOR_CK(h, ce);
-  }
-  struct GraphGuard { cudaGraphExec_t g; ~GraphGuard() { if (g) cudaGraphExecDestroy(g); } } guard{gexec};
+    return MOR_OK;
+  };
 
   const int max_outer = (prec == MOR_FP64) ? 4 : std::max(1, o.max_refine);
   std::vector<double> bnorm(k, 0.0), relres(k, 0.0);
   std::vector<int> iters(k, 0), refs(k, 0), status(k, MOR_OK), act(k, 0);
   double* hp = (double*)h->pinned;
+  const size_t ksb = krylov_state_bytes(st_in);
+  std::vector<unsigned char> kst_host(ksb * MOR_LDMAX), kst_new(ksb * MOR_LDMAX);
   for (int pass = 0;; ++pass) {
     // true residual r64 = b - A(sigma) x64 in FP64 with fused norms
     RedArgs rn{RED_NORM, nullptr, h->ws_part.p, sm.counter, FIN_NONE, nullptr, sm.sums, nullptr};
-    MOR_CKI(h, launch_op_spmv(st64, kb, pv, ov64, ncf, k, io.x64, r64, io.b64, &rn, gc, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(hp, sm.sums, sizeof(cdouble) * 2 * k, cudaMemcpyDeviceToHost, h->stream));
+    MOR_CKI(h, launch_op_spmv(st64, pv, ov64, ncf, ld, io.x64, r64, io.b64, &rn, gc, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(hp, sm.sums, sizeof(cdouble) * 2 * ld, cudaMemcpyDeviceToHost, h->stream));
     MOR_CK(h, cudaStreamSynchronize(h->stream));
     std::vector<double> rn2(k);
     for (int c = 0; c < k; ++c) rn2[c] = hp[4 * c];
@@ -263,12 +283,13 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
       }
       break;
     }
-    // inner targets
-    double* tg = hp + 64;
-    int* mi = (int*)(hp + 96);
-    int* ac = (int*)(hp + 128);
-    double* nr = hp + 160;
-    for (int c = 0; c < k; ++c) {
+    // inner targets (dummy columns: inactive)
+    double* tg = hp + 128;
+    int* mi = (int*)(hp + 160);
+    int* ac = (int*)(hp + 192);
+    double* nr = hp + 224;
+    for (int c = 0; c < ld; ++c) {
+      if (c >= k) { tg[c] = 1.0; mi[c] = 0; ac[c] = 0; nr[c] = 0.0; continue; }
       const double need = act[c] ? o.tol * bnorm[c] / std::sqrt(rn2[c]) : 1.0;
       tg[c] = (prec == MOR_FP64) ? need : std::max(o.inner_tol, 0.5 * need);
       mi[c] = act[c] ? std::max(0, o.maxit - iters[c]) : 0;
@@ -276,18 +297,24 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
       nr[c] = rn2[c];
       if (act[c]) refs[c] += 1;
     }
-    MOR_CK(h, cudaMemcpyAsync(sm.target, tg, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(sm.maxit, mi, sizeof(int) * k, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(sm.active, ac, sizeof(int) * k, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(sm.nrm2, nr, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
-    MOR_CKI(h, refine_launch_scale_cast(st_in, kb, (int)n, k, r64, sm.nrm2, sm.active, rhs, h->stream));
-    MOR_CKI(h, krylov_launch_init(st_in, kb, (int)n, k, rhs, d, r, rhat, p, v, h->ws_part.p, sm.counter, sm.kstate,
+    MOR_CK(h, cudaMemcpyAsync(sm.target, tg, sizeof(double) * ld, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(sm.maxit, mi, sizeof(int) * ld, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(sm.active, ac, sizeof(int) * ld, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(sm.nrm2, nr, sizeof(double) * ld, cudaMemcpyHostToDevice, h->stream));
+    // full geometry for this inner solve
+    ldc = ld;
+    for (int c = 0; c < ld; ++c) { cmap[c] = c < k ? c : -1; cfc[c] = cf[c]; }
+    dd = d; rr = r; rh = rhat; pp = p; vv = v; ssv = sv; tt = t; pph = ph; ssh = sh; t0 = tmp0; t1 = tmp1;
+    bool compacted = false;
+    MOR_CKI(h, upload_masks());
+    MOR_CKI(h, refine_launch_scale_cast(st_in, (int)n, ld, r64, sm.nrm2, sm.active, rhs, h->stream));
+    MOR_CKI(h, krylov_launch_init(st_in, (int)n, ld, rhs, dd, rr, rh, pp, vv, h->ws_part.p, sm.counter, sm.kstate,
                                   sm.target, sm.maxit, sm.done, gc, h->stream));
+    MOR_TRY(capture());
     int maxrem = 0;
-    for (int c = 0; c < k; ++c) maxrem = std::max(maxrem, mi[c]);
-    int done_flag = 0;
+    for (int c = 0; c < ld; ++c) maxrem = std::max(maxrem, mi[c]);
     int it = 0;
-    int* hd = (int*)(hp + 200);
+    std::vector<int> kit(k, 0), kstat(k, KST_OK);
     while (it < maxrem) {
       if (gexec) {
         MOR_CK(h, cudaGraphLaunch(gexec, h->stream));
@@ -296,23 +323,89 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
       } else {
         MOR_CKI(h, one_iter());
         it += 1;
+        if ((it % chunk) != 0 && it < maxrem) continue;
       }
-      if (gexec || (it % chunk) == 0 || it >= maxrem) {
-        MOR_CK(h, cudaMemcpyAsync(hd, sm.done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-        MOR_CK(h, cudaStreamSynchronize(h->stream));
-        done_flag = *hd;
-        if (done_flag) break;
+      MOR_CKI(h, krylov_read_states(kst_host.data(), sm.kstate, ldc, h->stream));
+      int nlive = 0;
+      for (int c = 0; c < ldc; ++c) nlive += krylov_state_active(kst_host.data() + ksb * c) ? 1 : 0;
+      if (nlive == 0) break;
+      const int ld_new = row_stride(st_in, nlive);
+      if (ld_new >= ldc || it >= maxrem) continue;
+      // ---- compaction: flush dropped real columns, repack the live ones
+      std::vector<int> live, drop_src, drop_dst;
+      for (int c = 0; c < ldc; ++c) {
+        const unsigned char* ks = kst_host.data() + ksb * c;
+        if (krylov_state_active(ks)) { live.push_back(c); continue; }
+        const int oc = cmap[c];
+        if (oc >= 0 && oc < k) {
+          drop_src.push_back(c);
+          drop_dst.push_back(oc);
+          kit[oc] = krylov_state_iters(ks);
+          kstat[oc] = krylov_state_status(ks);
+        }
+      }
+      int* dmaps = sm.masks + (size_t)MAX_FACTORS * MOR_KMAX - 3 * MOR_LDMAX;   // tail of the mask area
+      std::vector<int> maps(3 * MOR_LDMAX, 0);
+      for (size_t i = 0; i < drop_src.size(); ++i) { maps[i] = drop_src[i]; maps[MOR_LDMAX + i] = drop_dst[i]; }
+      for (size_t i = 0; i < live.size(); ++i) maps[2 * MOR_LDMAX + i] = live[i];
+      MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, h->stream));
+      if (!drop_src.empty())
+        MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, (int)drop_src.size(), dmaps, dmaps + MOR_LDMAX, dd,
+                                            d_full, h->stream));
+      const int* gmap = dmaps + 2 * MOR_LDMAX;
+      void* src[5] = {dd, rr, rh, pp, vv};
+      void* dst[5] = {ssv, tt, pph, ssh, t0};
+      for (int q = 0; q < 5; ++q)
+        MOR_CKI(h, conv_launch_gather_cols(st_in, n, ldc, ld_new, (int)live.size(), gmap, src[q], dst[q], h->stream));
+      // the old state vectors become the scratch set
+      dd = dst[0]; rr = dst[1]; rh = dst[2]; pp = dst[3]; vv = dst[4];
+      ssv = src[0]; tt = src[1]; pph = src[2]; ssh = src[3]; t0 = src[4];
+      std::vector<int> nmap(ld_new, -1);
+      for (int c = 0; c < ld_new; ++c) {
+        if (c < (int)live.size()) {
+          nmap[c] = cmap[live[c]];
+          memcpy(kst_new.data() + ksb * c, kst_host.data() + ksb * live[c], ksb);
+          cfc[c] = cfc[live[c]];
+        } else {
+          krylov_state_make_dummy(kst_new.data() + ksb * c);
+          cfc[c] = cfc[live[0]];
+        }
+      }
+      cmap = nmap;
+      ldc = ld_new;
+      MOR_CKI(h, krylov_write_state(kst_new.data(), sm.kstate, ldc, h->stream));
+      MOR_CKI(h, upload_masks());
+      compacted = true;
+      MOR_TRY(capture());
+    }
+    // final per-column state of this inner solve
+    MOR_CKI(h, krylov_read_states(kst_host.data(), sm.kstate, ldc, h->stream));
+    for (int c = 0; c < ldc; ++c) {
+      const int oc = cmap[c];
+      if (oc >= 0 && oc < k) {
+        kit[oc] = krylov_state_iters(kst_host.data() + ksb * c);
+        kstat[oc] = krylov_state_status(kst_host.data() + ksb * c);
       }
     }
-    int kit[MOR_KMAX], kst[MOR_KMAX];
-    MOR_CKI(h, krylov_read_state(st_in, sm.kstate, k, kit, kst, h->stream));
+    void* dres = dd;
+    if (compacted) {
+      // collect the remaining columns into d_full (original layout)
+      std::vector<int> maps(2 * MOR_LDMAX, 0);
+      int nrem = 0;
+      for (int c = 0; c < ldc; ++c)
+        if (cmap[c] >= 0 && cmap[c] < k) { maps[nrem] = c; maps[MOR_LDMAX + nrem] = cmap[c]; ++nrem; }
+      int* dmaps = sm.masks + (size_t)MAX_FACTORS * MOR_KMAX - 3 * MOR_LDMAX;
+      MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, h->stream));
+      if (nrem > 0)
+        MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, nrem, dmaps, dmaps + MOR_LDMAX, dd, d_full, h->stream));
+      dres = d_full;
+    }
     for (int c = 0; c < k; ++c) {
       if (!act[c]) continue;
       iters[c] += kit[c];
-      if (kst[c] == KST_BREAKDOWN && prec != MOR_FP64 && pass + 1 >= max_outer) status[c] = MOR_EBREAKDOWN;
-      if (kst[c] == KST_BREAKDOWN && prec == MOR_FP64 && pass + 1 >= max_outer) status[c] = MOR_EBREAKDOWN;
+      if (kstat[c] == KST_BREAKDOWN && pass + 1 >= max_outer) status[c] = MOR_EBREAKDOWN;
     }
-    MOR_CKI(h, refine_launch_update(st_in, kb, (int)n, k, io.x64, d, sm.nrm2, sm.active, h->stream));
+    MOR_CKI(h, refine_launch_update(st_in, (int)n, ld, io.x64, dres, sm.nrm2, sm.active, h->stream));
   }
   if (stats)
     for (int c = 0; c < k; ++c) {
@@ -331,19 +424,21 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
 // Solve k shifts (any k), batching by 16.  rhs: either R (col-major c128, host or
 // device) or the system's B/C column 0.  X out col-major c128 (host or device).
 static int solve_many(mor_t h, const mor_c64* sig, int k, int transpose, const mor_solve_opts& o,
-                      const std::vector<int>& L, bool cplx, const mor_c64* R, bool dev, void* Xrow64_keep,
-                      mor_c64* X, mor_solve_stats* stats) {
+                      const std::vector<int>& L, bool cplx, const mor_c64* R, bool dev, mor_c64* X,
+                      mor_solve_stats* stats) {
   const int64_t n = h->n;
   const int st64 = cplx ? ST_C64 : ST_F64;
+  const int st_in = st_of(o.precision, cplx);
   const size_t es64 = st_size(st64);
   const int bmax = o.batch ? MOR_KMAX : 1;
   int ret = MOR_OK;
   for (int c0 = 0; c0 < k; c0 += bmax) {
     const int kc = std::min(bmax, k - c0);
-    MOR_CK(h, h->ws_b64.alloc(es64 * (size_t)n * kc));
-    void* xrow;
-    if (Xrow64_keep) xrow = (char*)Xrow64_keep + es64 * (size_t)n * c0;   // caller keeps row-major blocks
-    else { MOR_CK(h, h->ws_x64.alloc(es64 * (size_t)n * kc)); xrow = h->ws_x64.p; }
+    const int ld = row_stride(st_in, kc);
+    MOR_CK(h, h->ws_b64.alloc(es64 * (size_t)n * ld));
+    MOR_CK(h, h->ws_x64.alloc(es64 * (size_t)n * ld));
+    void* xrow = h->ws_x64.p;
+    if (ld > kc) MOR_CK(h, cudaMemsetAsync(h->ws_b64.p, 0, es64 * (size_t)n * ld, h->stream));
     if (R) {
       const mor_c64* Rc = R + (size_t)n * c0;
       const void* src = Rc;
@@ -352,22 +447,22 @@ static int solve_many(mor_t h, const mor_c64* sig, int k, int transpose, const m
         MOR_CK(h, cudaMemcpyAsync(h->ws_io.p, Rc, sizeof(mor_c64) * (size_t)n * kc, cudaMemcpyHostToDevice, h->stream));
         src = h->ws_io.p;
       }
-      MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st64, (int)n, kc, src, h->ws_b64.p, h->stream));
+      MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st64, (int)n, kc, ld, src, h->ws_b64.p, h->stream));
     } else {
       const double* col0 = transpose ? h->C.as<double>() : h->B.as<double>();
-      MOR_CKI(h, conv_launch_real_col_to_rowmajor(st64, (int)n, kc, col0, 0, h->ws_b64.p, h->stream));
+      MOR_CKI(h, conv_launch_real_col_to_rowmajor(st64, (int)n, kc, ld, col0, 0, h->ws_b64.p, h->stream));
     }
-    BatchIO io{sig + c0, kc, L.data() + c0, h->ws_b64.p, xrow};
+    BatchIO io{sig + c0, kc, ld, L.data() + c0, h->ws_b64.p, xrow};
     int s = solve_batch(h, transpose, o, cplx, io, stats ? stats + c0 : nullptr);
     if (s != MOR_OK && s != MOR_ENOCONV && s != MOR_EBREAKDOWN) return s;
     if (s != MOR_OK) ret = s;
     if (X) {
       mor_c64* Xc = X + (size_t)n * c0;
       if (dev) {
-        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, xrow, Xc, h->stream));
+        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, ld, xrow, Xc, h->stream));
       } else {
         MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * kc));
-        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, xrow, h->ws_io.p, h->stream));
+        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, ld, xrow, h->ws_io.p, h->stream));
         MOR_CK(h, cudaMemcpyAsync(Xc, h->ws_io.p, sizeof(mor_c64) * (size_t)n * kc, cudaMemcpyDeviceToHost, h->stream));
       }
     }
@@ -430,8 +525,8 @@ static int project_device(mor_t h, const double* V, const double* W, int r, mor_
   OpVals ov = op_vals(h, op, false);
   Coef ca{0, 0, 1, 0}, ce{1, 0, 0, 0};
   for (int j = 0; j < r; ++j) {
-    MOR_CKI(h, launch_op_spmv(ST_F64, 1, pv, ov, &ca, 1, V + (size_t)j * n, AV + (size_t)j * n, nullptr, nullptr, h->grid_cap, h->stream));
-    MOR_CKI(h, launch_op_spmv(ST_F64, 1, pv, ov, &ce, 1, V + (size_t)j * n, EV + (size_t)j * n, nullptr, nullptr, h->grid_cap, h->stream));
+    MOR_CKI(h, launch_op_spmv(ST_F64, pv, ov, &ca, 1, V + (size_t)j * n, AV + (size_t)j * n, nullptr, nullptr, h->grid_cap, h->stream));
+    MOR_CKI(h, launch_op_spmv(ST_F64, pv, ov, &ce, 1, V + (size_t)j * n, EV + (size_t)j * n, nullptr, nullptr, h->grid_cap, h->stream));
   }
   MOR_CK(h, h->ws_rom.alloc(sizeof(double) * 6 * MOR_MAX_R * MOR_MAX_R));
   double* dAr = h->ws_rom.as<double>();
@@ -476,10 +571,10 @@ static int poles_device(mor_t h, const mor_reduced* rom, mor_c64* lam, mor_c64* 
   return MOR_OK;
 }
 
-// extract Re / Im columns of a row-major n x k (st64) block into a col-major FP64 basis
-__global__ void extract_kernel(int n, int k, int c, int part, int cplx, const double* src, double* dst) {
+// real (part 0) or imaginary (part 1) part of a complex128 column into an FP64 basis column
+__global__ void extract_kernel(int n, int part, const double* src, double* dst) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = cplx ? src[2 * (i * k + c) + part] : src[i * k + c];
+    dst[i] = src[2 * i + part];
 }
 
 extern "C" {
@@ -553,7 +648,8 @@ int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int 
   OpData& op = h->op(transpose);
   const int64_t n = h->n;
   const int st = (precision == MOR_FP64) ? ST_C64 : ST_C32;
-  MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * k * 3));
+  const int ld = row_stride(st, k);
+  MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * (k + 2 * ld)));
   mor_c64* io = h->ws_io.as<mor_c64>();
   const void* src = X;
   if (!dev) {
@@ -561,16 +657,17 @@ int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int 
     src = io;
   }
   char* xr = (char*)(io + (size_t)n * k);
-  char* yr = xr + st_size(st) * (size_t)n * k;
-  MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st, (int)n, k, src, xr, h->stream));
-  Coef cf[MOR_KMAX];
-  for (int c = 0; c < k; ++c) cf[c] = mor_coef(h, sigma[c]);
-  MOR_CKI(h, launch_op_spmv(st, kb_for(k), op.view(), op_vals(h, op, precision != MOR_FP64), cf, k, xr, yr, nullptr,
+  char* yr = xr + st_size(st) * (size_t)n * ld;
+  if (ld > k) MOR_CK(h, cudaMemsetAsync(xr, 0, st_size(st) * (size_t)n * ld, h->stream));
+  MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st, (int)n, k, ld, src, xr, h->stream));
+  Coef cf[MOR_LDMAX];
+  for (int c = 0; c < ld; ++c) cf[c] = mor_coef(h, sigma[c < k ? c : 0]);
+  MOR_CKI(h, launch_op_spmv(st, op.view(), op_vals(h, op, precision != MOR_FP64), cf, ld, xr, yr, nullptr,
                             nullptr, h->grid_cap, h->stream));
   if (dev) {
-    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, yr, Y, h->stream));
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, ld, yr, Y, h->stream));
   } else {
-    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, yr, io, h->stream));
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, ld, yr, io, h->stream));
     MOR_CK(h, cudaMemcpyAsync(Y, io, sizeof(mor_c64) * n * k, cudaMemcpyDeviceToHost, h->stream));
   }
   MOR_CK(h, cudaStreamSynchronize(h->stream));
@@ -591,7 +688,8 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   std::vector<int> L = prefix_lengths(op, sigma, k);
   int Lmax = 0;
   for (int x : L) Lmax = std::max(Lmax, x);
-  MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * k * 3));
+  const int ld = row_stride(st, k);
+  MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * (k + 2 * ld)));
   mor_c64* io = h->ws_io.as<mor_c64>();
   const void* src = X;
   if (!dev) {
@@ -599,25 +697,26 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
     src = io;
   }
   char* a = (char*)(io + (size_t)n * k);
-  char* b = a + st_size(st) * (size_t)n * k;
-  MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st, (int)n, k, src, a, h->stream));
+  char* b = a + st_size(st) * (size_t)n * ld;
+  if (ld > k) MOR_CK(h, cudaMemsetAsync(a, 0, st_size(st) * (size_t)n * ld, h->stream));
+  MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st, (int)n, k, ld, src, a, h->stream));
   Small sm;
   MOR_TRY(get_small(h, sm));
   std::vector<int> masks((size_t)std::max(Lmax, 1) * MOR_KMAX, 0);
   for (int f = 0; f < Lmax; ++f)
-    for (int c = 0; c < k; ++c) masks[(size_t)f * MOR_KMAX + c] = (f < L[c]) ? 1 : 0;
+    for (int c = 0; c < ld; ++c) masks[(size_t)f * MOR_KMAX + c] = (c >= k || f < L[c]) ? 1 : 0;
   MOR_CK(h, cudaMemcpyAsync(sm.masks, masks.data(), sizeof(int) * masks.size(), cudaMemcpyHostToDevice, h->stream));
   char* s = a;
   char* d = b;
   for (int f = 0; f < Lmax; ++f) {
-    MOR_CKI(h, launch_factor_spmv(st, st_is_cplx(op.chain[f].st), kb_for(k), op.view(), op.chain[f].vals->p,
-                                  sm.masks + (size_t)f * MOR_KMAX, k, s, d, nullptr, h->stream));
+    MOR_CKI(h, launch_factor_spmv(st, st_is_cplx(op.chain[f].st), op.view(), op.chain[f].vals->p,
+                                  sm.masks + (size_t)f * MOR_KMAX, ld, s, d, nullptr, h->stream));
     std::swap(s, d);
   }
   if (dev) {
-    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, s, Y, h->stream));
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, ld, s, Y, h->stream));
   } else {
-    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, s, io, h->stream));
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, ld, s, io, h->stream));
     MOR_CK(h, cudaMemcpyAsync(Y, io, sizeof(mor_c64) * n * k, cudaMemcpyDeviceToHost, h->stream));
   }
   MOR_CK(h, cudaStreamSynchronize(h->stream));
@@ -652,7 +751,7 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
       MOR_TRY(build_factor(h, transpose, sigma[c], sigma[c], false, o.precision));
       std::vector<int> L(1, 1);
       bool cc = anyc || chain_cplx(op, L);
-      int s = solve_many(h, sigma + c, 1, transpose, o, L, cc, R ? R + (size_t)h->n * c : nullptr, dev, nullptr,
+      int s = solve_many(h, sigma + c, 1, transpose, o, L, cc, R ? R + (size_t)h->n * c : nullptr, dev,
                          X + (size_t)h->n * c, stats ? stats + c : nullptr);
       if (s != MOR_OK && s != MOR_ENOCONV && s != MOR_EBREAKDOWN) return s;
       if (s != MOR_OK) ret = s;
@@ -663,7 +762,7 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
   if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision)
     return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from opts.precision");
   bool cc = anyc || chain_cplx(op, L);
-  return solve_many(h, sigma, k, transpose, o, L, cc, R, dev, nullptr, X, stats);
+  return solve_many(h, sigma, k, transpose, o, L, cc, R, dev, X, stats);
 }
 
 int mor_orthonormalize(mor_t h, double* X, int k, unsigned flags) {
@@ -796,12 +895,12 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
     OpData& X = h->op(t);
     if (o.precond == 0) cplx |= chain_cplx(X, Ls[t]);
   }
-  const int st64 = cplx ? ST_C64 : ST_F64;
-  DBuf xs[2];
+  DBuf xs[2];                       // solutions, n x l complex128 column-major (device)
   std::vector<mor_solve_stats> ss(l);
   int solve_status = MOR_OK;
   for (int t = 0; t < 2; ++t) {
-    MOR_CK(h, xs[t].alloc(st_size(st64) * (size_t)n * l));
+    MOR_CK(h, xs[t].alloc(sizeof(mor_c64) * (size_t)n * l));
+    mor_c64* X = xs[t].as<mor_c64>();
     int s2;
     if (o.precond == 1) {
       s2 = MOR_OK;
@@ -809,14 +908,12 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
         MOR_TRY(build_factor(h, t, sol[i], sol[i], false, o.precision));
         st.builds_spai++;
         std::vector<int> L1(1, 1);
-        int s3 = solve_many(h, &sol[i], 1, t, o, L1, cplx, nullptr, false,
-                            (char*)xs[t].p + st_size(st64) * (size_t)n * i, nullptr, &ss[i]);
+        int s3 = solve_many(h, &sol[i], 1, t, o, L1, cplx, nullptr, true, X + (size_t)n * i, &ss[i]);
         if (s3 != MOR_OK && s3 != MOR_ENOCONV && s3 != MOR_EBREAKDOWN) return s3;
         if (s3 != MOR_OK) s2 = s3;
       }
     } else {
-      // solve_many keeps each 16-column block row-major at its offset
-      s2 = solve_many(h, sol.data(), l, t, o, Ls[t], cplx, nullptr, false, xs[t].p, nullptr, ss.data());
+      s2 = solve_many(h, sol.data(), l, t, o, Ls[t], cplx, nullptr, true, X, ss.data());
       if (s2 != MOR_OK && s2 != MOR_ENOCONV && s2 != MOR_EBREAKDOWN) return s2;
     }
     if (s2 != MOR_OK) solve_status = s2;
@@ -827,24 +924,20 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
   }
   cudaEventRecord(ev[2], h->stream);
   // real bases [Re v, Im v] and CGS2
-  MOR_CK(h, h->ws_basis.alloc(sizeof(double) * (size_t)n * r * 2));
   DBuf basis;
   MOR_CK(h, basis.alloc(sizeof(double) * (size_t)n * r * 2));
   double* Vb = basis.as<double>();
   double* Wb = Vb + (size_t)n * r;
+  const int g = (int)std::min<int64_t>((n + 255) / 256, h->grid_cap);
   for (int t = 0; t < 2; ++t) {
     double* dst = t == 0 ? Vb : Wb;
     int col = 0;
     for (int i = 0; i < l; ++i) {
-      // solve_many stores each batch of bw columns row-major with its own k
-      const int bw = (o.batch && o.precond != 1) ? MOR_KMAX : 1;
-      const int blk = i / bw, kc = std::min(bw, l - blk * bw), ci = i % bw;
-      const double* src = (const double*)((const char*)xs[t].p + st_size(st64) * (size_t)n * blk * bw);
-      const int g = (int)std::min<int64_t>((n + 255) / 256, h->grid_cap);
-      extract_kernel<<<g, 256, 0, h->stream>>>((int)n, kc, ci, 0, cplx ? 1 : 0, src, dst + (size_t)n * col++);
+      const double* src = (const double*)(xs[t].as<mor_c64>() + (size_t)n * i);
+      extract_kernel<<<g, 256, 0, h->stream>>>((int)n, 0, src, dst + (size_t)n * col++);
       mor_count_launches(1);
       if (sol[i].im != 0.0) {
-        extract_kernel<<<g, 256, 0, h->stream>>>((int)n, kc, ci, 1, 1, src, dst + (size_t)n * col++);
+        extract_kernel<<<g, 256, 0, h->stream>>>((int)n, 1, src, dst + (size_t)n * col++);
         mor_count_launches(1);
       }
     }
@@ -897,27 +990,27 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
     precision = op.chain_prec;
   }
   const int st = st_of(precision, cplx);
-  const int kb = kb_for(k);
+  const int ld = row_stride(st, k);
   const int64_t n = op.n;
   DBuf x, y, w;
-  MOR_CK(h, x.alloc(st_size(st) * (size_t)n * k));
-  MOR_CK(h, y.alloc(st_size(st) * (size_t)n * k));
-  MOR_CK(h, w.alloc(st_size(st) * (size_t)n * k));
-  MOR_CK(h, cudaMemsetAsync(x.p, 0, st_size(st) * (size_t)n * k, h->stream));
-  MOR_CK(h, cudaMemsetAsync(w.p, 0, st_size(st) * (size_t)n * k, h->stream));
+  MOR_CK(h, x.alloc(st_size(st) * (size_t)n * ld));
+  MOR_CK(h, y.alloc(st_size(st) * (size_t)n * ld));
+  MOR_CK(h, w.alloc(st_size(st) * (size_t)n * ld));
+  MOR_CK(h, cudaMemsetAsync(x.p, 0, st_size(st) * (size_t)n * ld, h->stream));
+  MOR_CK(h, cudaMemsetAsync(w.p, 0, st_size(st) * (size_t)n * ld, h->stream));
   Small sm;
   MOR_TRY(get_small(h, sm));
-  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_KMAX * (size_t)std::max(h->grid_cap, 2048)));
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * (size_t)std::max(h->grid_cap, 2048)));
   std::vector<int> ones(MOR_KMAX, 1);
   MOR_CK(h, cudaMemcpyAsync(sm.masks, ones.data(), sizeof(int) * MOR_KMAX, cudaMemcpyHostToDevice, h->stream));
-  Coef cf[MOR_KMAX];
-  for (int c = 0; c < k; ++c) cf[c] = mor_coef(h, sigma[c]);
+  Coef cf[MOR_LDMAX];
+  for (int c = 0; c < ld; ++c) cf[c] = mor_coef(h, sigma[c < k ? c : 0]);
   PatView pv = op.view();
   OpVals ov = op_vals(h, op, st_is_f32(st));
   RedArgs ra{RED_DOT_W, w.p, h->ws_part.p, sm.counter, FIN_NONE, nullptr, sm.sums, nullptr};
   auto launch = [&]() -> int {
-    if (which == 0) return launch_op_spmv(st, kb, pv, ov, cf, k, x.p, y.p, nullptr, &ra, h->grid_cap, h->stream);
-    return launch_factor_spmv(st, st_is_cplx(op.chain.back().st), kb, pv, op.chain.back().vals->p, sm.masks, k,
+    if (which == 0) return launch_op_spmv(st, pv, ov, cf, ld, x.p, y.p, nullptr, &ra, h->grid_cap, h->stream);
+    return launch_factor_spmv(st, st_is_cplx(op.chain.back().st), pv, op.chain.back().vals->p, sm.masks, ld,
                               x.p, y.p, nullptr, h->stream);
   };
   for (int i = 0; i < 3; ++i) MOR_CKI(h, launch());

@@ -20,14 +20,16 @@
 #include "mor_internal.h"
 #include "krylov_state.cuh"
 
+#include "shape_dispatch.cuh"
+
 namespace {
 
-template <typename S, int KB> struct CoefS { S sE[KB]; S sA[KB]; };
+template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
 
 // [p0, p1) and step of row r in the stored layout
-__device__ __forceinline__ void row_range(const PatView& pv, int r, int64_t& p0, int64_t& p1, int& step) {
+__device__ __forceinline__ void row_range(const PatView& pv, int64_t r, int64_t& p0, int64_t& p1, int& step) {
   if (pv.fmt == FMT_SELL) {
     const int64_t base = pv.sptr[r >> 5];
     const int64_t w = (pv.sptr[(r >> 5) + 1] - base) >> 5;
@@ -42,171 +44,201 @@ __device__ __forceinline__ void row_range(const PatView& pv, int r, int64_t& p0,
 }
 
 // Y(:, c) = sE_c (E X(:, c)) + sA_c (A X(:, c)) [+ B(:, c)], with an optional
-// fused per-column reduction.  KB lanes per row, lane `sub` owns column sub.
-template <typename S, int KB>
-__global__ void __launch_bounds__(256) op_spmv_kernel(PatView pv, OpVals ov, CoefS<S, KB> cf, int k,
+// fused per-column reduction.  TPR lanes per row, lane `sub` owns the CPT
+// columns sub * CPT ... sub * CPT + CPT - 1 of the n x ld blocks.
+template <typename S, int TPR, int CPT>
+__global__ void __launch_bounds__(256) op_spmv_kernel(PatView pv, OpVals ov, CoefS<S> cf, int ld,
                                                       const S* __restrict__ x, S* __restrict__ y,
                                                       const S* __restrict__ bv, RedArgs red) {
   typedef typename real_of<S>::type R;
   if (red.done && *red.done) return;
-  __shared__ S csE[KB], csA[KB];
-  if (threadIdx.x < KB) { csE[threadIdx.x] = cf.sE[threadIdx.x]; csA[threadIdx.x] = cf.sA[threadIdx.x]; }
+  __shared__ S csE[MOR_LDMAX], csA[MOR_LDMAX];
+  if (threadIdx.x < ld) { csE[threadIdx.x] = cf.sE[threadIdx.x]; csA[threadIdx.x] = cf.sA[threadIdx.x]; }
   __syncthreads();
   const R* __restrict__ a = (const R*)ov.a;
   const R* __restrict__ e = (const R*)ov.e;
   const R* __restrict__ ed = (const R*)ov.ediag;
   const S* __restrict__ w = (const S*)red.w;
-  const int sub = threadIdx.x & (KB - 1);
-  const bool act = sub < k;
-  const S sE = csE[sub], sA = csA[sub];
-  S v0 = zero_<S>(), v1 = zero_<S>();
-  const int rpb = blockDim.x / KB;
-  for (int r = blockIdx.x * rpb + threadIdx.x / KB; r < pv.n; r += gridDim.x * rpb) {
-    if (!act) continue;
-    int64_t p0, p1;
-    int step;
-    row_range(pv, r, p0, p1, step);
-    S accA = zero_<S>(), accE = zero_<S>();
-    if (ov.ekind == EK_CSR) {
-      for (int64_t p = p0; p < p1; p += step) {
-        const int cc = __ldg(pv.col + p);
-        const S xv = x[(int64_t)cc * k + sub];
-        fma_r(accA, __ldg(a + p), xv);
-        fma_r(accE, __ldg(e + p), xv);
-      }
-    } else {
+  const int sub = threadIdx.x % TPR;
+  const int c0 = sub * CPT;
+  const bool act = c0 < ld;
+  S sE[CPT], sA[CPT], v0[CPT], v1[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    sE[j] = act ? csE[c0 + j] : zero_<S>();
+    sA[j] = act ? csA[c0 + j] : zero_<S>();
+    v0[j] = zero_<S>();
+    v1[j] = zero_<S>();
+  }
+  const int rpb = blockDim.x / TPR;
+  int64_t rb, re;
+  block_rows(pv.n, rpb, rb, re);
+  if (act) {
+    for (int64_t r = rb + threadIdx.x / TPR; r < re; r += rpb) {
+      int64_t p0, p1;
+      int step;
+      row_range(pv, r, p0, p1, step);
+      S accA[CPT], accE[CPT];
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) { accA[j] = zero_<S>(); accE[j] = zero_<S>(); }
+      if (ov.ekind == EK_CSR) {
+        for (int64_t p = p0; p < p1; p += step) {
+          const int cc = __ldg(pv.col + p);
+          const R av = __ldg(a + p), ev = __ldg(e + p);
+          const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) { fma_r(accA[j], av, xv.v[j]); fma_r(accE[j], ev, xv.v[j]); }
+        }
+      } else {
 #pragma unroll 4
-      for (int64_t p = p0; p < p1; p += step) {
-        const int cc = __ldg(pv.col + p);
-        fma_r(accA, __ldg(a + p), x[(int64_t)cc * k + sub]);
+        for (int64_t p = p0; p < p1; p += step) {
+          const int cc = __ldg(pv.col + p);
+          const R av = __ldg(a + p);
+          const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) fma_r(accA[j], av, xv.v[j]);
+        }
+        const Pack<S, CPT> xr = ldp<S, CPT>(x + r * ld + c0);
+        const R d = (ov.ekind == EK_DIAG) ? __ldg(ed + r) : R(1);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) accE[j] = scale_(d, xr.v[j]);
       }
-      const S xr = x[(int64_t)r * k + sub];
-      accE = (ov.ekind == EK_DIAG) ? scale_(__ldg(ed + r), xr) : xr;
-    }
-    S yv = sE * accE + sA * accA;
-    const int64_t q = (int64_t)r * k + sub;
-    if (bv) yv += bv[q];
-    y[q] = yv;
-    if (red.mode == RED_DOT_W) {
-      fma_s(v0, conj_(w[q]), yv);
-    } else if (red.mode == RED_DOT_TT) {
-      fma_s(v0, conj_(yv), w[q]);
-      v1 += S(abs2_(yv));
-    } else if (red.mode == RED_NORM) {
-      v0 += S(abs2_(yv));
+      const int64_t q = r * ld + c0;
+      Pack<S, CPT> yv;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) yv.v[j] = sE[j] * accE[j] + sA[j] * accA[j];
+      if (bv) {
+        const Pack<S, CPT> bb = ldp<S, CPT>(bv + q);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) yv.v[j] += bb.v[j];
+      }
+      stp<S, CPT>(y + q, yv);
+      if (red.mode == RED_DOT_W) {
+        const Pack<S, CPT> wv = ldp<S, CPT>(w + q);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) fma_s(v0[j], conj_(wv.v[j]), yv.v[j]);
+      } else if (red.mode == RED_DOT_TT) {
+        const Pack<S, CPT> wv = ldp<S, CPT>(w + q);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) { fma_s(v0[j], conj_(yv.v[j]), wv.v[j]); v1[j] += S(abs2_(yv.v[j])); }
+      } else if (red.mode == RED_NORM) {
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) v0[j] += S(abs2_(yv.v[j]));
+      }
     }
   }
   if (red.mode != RED_NONE)
-    col_reduce_finalize<S, KB>(v0, v1, k, (double*)red.part, red.counter, red.fin, (KState*)red.state,
-                               (cdouble*)red.out, (int*)red.done);
+    col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, (double*)red.part, red.counter, red.fin, (KState*)red.state,
+                                     (cdouble*)red.out, (int*)red.done);
 }
 
 // Y(:, c) = F X(:, c) where the factor applies to column c, else Y(:, c) = X(:, c).
-template <typename S, typename V, int KB>
+template <typename S, typename V, int TPR, int CPT>
 __global__ void __launch_bounds__(256) factor_spmv_kernel(PatView pv, const V* __restrict__ f,
-                                                          const int* __restrict__ apply, int k,
+                                                          const int* __restrict__ apply, int ld,
                                                           const S* __restrict__ x, S* __restrict__ y,
                                                           const int* done) {
   if (done && *done) return;
-  const int sub = threadIdx.x & (KB - 1);
-  if (sub >= k) return;
-  const int ap = apply[sub];
-  const int rpb = blockDim.x / KB;
-  for (int r = blockIdx.x * rpb + threadIdx.x / KB; r < pv.n; r += gridDim.x * rpb) {
-    const int64_t q = (int64_t)r * k + sub;
-    if (!ap) { y[q] = x[q]; continue; }
-    int64_t p0, p1;
-    int step;
-    row_range(pv, r, p0, p1, step);
-    S acc = zero_<S>();
+  const int sub = threadIdx.x % TPR;
+  const int c0 = sub * CPT;
+  if (c0 >= ld) return;
+  int ap[CPT];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) { ap[j] = apply[c0 + j]; any |= (ap[j] != 0); }
+  const int rpb = blockDim.x / TPR;
+  int64_t rb, re;
+  block_rows(pv.n, rpb, rb, re);
+  for (int64_t r = rb + threadIdx.x / TPR; r < re; r += rpb) {
+    const int64_t q = r * ld + c0;
+    const Pack<S, CPT> xo = ldp<S, CPT>(x + q);
+    Pack<S, CPT> acc;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) acc.v[j] = zero_<S>();
+    if (any) {
+      int64_t p0, p1;
+      int step;
+      row_range(pv, r, p0, p1, step);
 #pragma unroll 4
-    for (int64_t p = p0; p < p1; p += step) {
-      const int cc = __ldg(pv.col + p);
-      const V fv = f[p];
-      if constexpr (is_cplx<V>::value) fma_s(acc, fv, x[(int64_t)cc * k + sub]);
-      else fma_r(acc, fv, x[(int64_t)cc * k + sub]);
+      for (int64_t p = p0; p < p1; p += step) {
+        const int cc = __ldg(pv.col + p);
+        const V fv = f[p];
+        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv, xv.v[j]);
+          else fma_r(acc.v[j], fv, xv.v[j]);
+        }
+      }
     }
-    y[q] = acc;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) if (!ap[j]) acc.v[j] = xo.v[j];
+    stp<S, CPT>(y + q, acc);
   }
 }
 
-template <typename S, int KB>
-int op_dispatch(const PatView& pv, const OpVals& ov, const Coef* coefs, int k, const void* x, void* y,
-                const void* b, const RedArgs* red, int grid_cap, cudaStream_t s) {
-  CoefS<S, KB> cf;
-  for (int c = 0; c < KB; ++c) {
-    const Coef q = (c < k) ? coefs[c] : Coef{0, 0, 0, 0};
-    if constexpr (is_cplx<S>::value) {
-      typedef typename real_of<S>::type R;
-      cf.sE[c] = S((R)q.sEr, (R)q.sEi);
-      cf.sA[c] = S((R)q.sAr, (R)q.sAi);
-    } else {
-      cf.sE[c] = (S)q.sEr;
-      cf.sA[c] = (S)q.sAr;
-    }
-  }
+inline int64_t blocks_for(int64_t n, int ld, int st, int cap) {
+  int tpr, cpt;
+  lane_shape(st, ld, &tpr, &cpt);
+  int64_t b = (n * tpr + 255) / 256;
+  if (cap > 0 && b > cap) b = cap;
+  return b < 1 ? 1 : b;
+}
+
+}  // namespace
+
+int launch_op_spmv(int st, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
+                   const void* x, void* y, const void* b, const RedArgs* red, int grid_cap,
+                   cudaStream_t s) {
+  if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
   RedArgs ra;
   if (red) ra = *red;
   else { ra.mode = RED_NONE; ra.w = nullptr; ra.part = nullptr; ra.counter = nullptr; ra.fin = 0;
          ra.state = nullptr; ra.out = nullptr; ra.done = nullptr; }
-  const int threads = 256;
-  int64_t blocks = ((int64_t)pv.n * KB + threads - 1) / threads;
-  if (grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
-  if (blocks < 1) blocks = 1;
-  op_spmv_kernel<S, KB><<<(unsigned)blocks, threads, 0, s>>>(pv, ov, cf, k, (const S*)x, (S*)y,
-                                                             (const S*)b, ra);
+  const int64_t blocks = blocks_for(pv.n, ld, st, grid_cap > 0 ? grid_cap : 152 * 8);
+  int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    CoefS<S> cf;
+    for (int c = 0; c < MOR_LDMAX; ++c) {
+      const Coef q = (c < ld) ? coefs[c] : Coef{0, 0, 0, 0};
+      if constexpr (is_cplx<S>::value) {
+        typedef typename real_of<S>::type R;
+        cf.sE[c] = S((R)q.sEr, (R)q.sEi);
+        cf.sA[c] = S((R)q.sAr, (R)q.sAi);
+      } else {
+        cf.sE[c] = (S)q.sEr;
+        cf.sA[c] = (S)q.sAr;
+      }
+    }
+    op_spmv_kernel<S, TPR, CPT><<<(unsigned)blocks, 256, 0, s>>>(pv, ov, cf, ld, (const S*)x, (S*)y,
+                                                                 (const S*)b, ra);
+    return 0;
+  });
+  if (e) return e;
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
-template <typename S, typename V, int KB>
-int factor_dispatch(const PatView& pv, const void* f, const int* apply, int k, const void* x, void* y,
-                    const int* done, cudaStream_t s) {
-  const int threads = 256;
-  int64_t blocks = ((int64_t)pv.n * KB + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  factor_spmv_kernel<S, V, KB><<<(unsigned)blocks, threads, 0, s>>>(pv, (const V*)f, apply, k,
-                                                                    (const S*)x, (S*)y, done);
+int launch_factor_spmv(int st, bool fcplx, const PatView& pv, const void* fvals, const int* apply, int ld,
+                       const void* x, void* y, const int* done, cudaStream_t s) {
+  if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
+  const int64_t blocks = blocks_for(pv.n, ld, st, 152 * 8);
+  int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    typedef typename real_of<S>::type R;
+    if constexpr (is_cplx<S>::value) {
+      if (fcplx)
+        factor_spmv_kernel<S, S, TPR, CPT><<<(unsigned)blocks, 256, 0, s>>>(pv, (const S*)fvals, apply, ld,
+                                                                            (const S*)x, (S*)y, done);
+      else
+        factor_spmv_kernel<S, R, TPR, CPT><<<(unsigned)blocks, 256, 0, s>>>(pv, (const R*)fvals, apply, ld,
+                                                                            (const S*)x, (S*)y, done);
+    } else {
+      if (fcplx) return (int)cudaErrorInvalidValue;
+      factor_spmv_kernel<S, S, TPR, CPT><<<(unsigned)blocks, 256, 0, s>>>(pv, (const S*)fvals, apply, ld,
+                                                                          (const S*)x, (S*)y, done);
+    }
+    return 0;
+  });
+  if (e) return e;
   mor_count_launches(1);
   return (int)cudaGetLastError();
-}
-
-#define KB_SWITCH(kb, CALL)                 \
-  switch (kb) {                             \
-    case 1: { constexpr int KBv = 1; return CALL; } \
-    case 2: { constexpr int KBv = 2; return CALL; } \
-    case 4: { constexpr int KBv = 4; return CALL; } \
-    case 8: { constexpr int KBv = 8; return CALL; } \
-    case 16: { constexpr int KBv = 16; return CALL; } \
-    default: return (int)cudaErrorInvalidValue; \
-  }
-
-}  // namespace
-
-int launch_op_spmv(int st, int kb, const PatView& pv, const OpVals& ov, const Coef* coefs, int k,
-                   const void* x, void* y, const void* b, const RedArgs* red, int grid_cap,
-                   cudaStream_t s) {
-  switch (st) {
-    case ST_F32: KB_SWITCH(kb, (op_dispatch<float, KBv>(pv, ov, coefs, k, x, y, b, red, grid_cap, s)));
-    case ST_F64: KB_SWITCH(kb, (op_dispatch<double, KBv>(pv, ov, coefs, k, x, y, b, red, grid_cap, s)));
-    case ST_C32: KB_SWITCH(kb, (op_dispatch<cfloat, KBv>(pv, ov, coefs, k, x, y, b, red, grid_cap, s)));
-    case ST_C64: KB_SWITCH(kb, (op_dispatch<cdouble, KBv>(pv, ov, coefs, k, x, y, b, red, grid_cap, s)));
-  }
-  return (int)cudaErrorInvalidValue;
-}
-
-int launch_factor_spmv(int st, bool fcplx, int kb, const PatView& pv, const void* fvals,
-                       const int* apply, int k, const void* x, void* y, const int* done,
-                       cudaStream_t s) {
-  switch (st) {
-    case ST_F32: KB_SWITCH(kb, (factor_dispatch<float, float, KBv>(pv, fvals, apply, k, x, y, done, s)));
-    case ST_F64: KB_SWITCH(kb, (factor_dispatch<double, double, KBv>(pv, fvals, apply, k, x, y, done, s)));
-    case ST_C32:
-      if (fcplx) KB_SWITCH(kb, (factor_dispatch<cfloat, cfloat, KBv>(pv, fvals, apply, k, x, y, done, s)))
-      else KB_SWITCH(kb, (factor_dispatch<cfloat, float, KBv>(pv, fvals, apply, k, x, y, done, s)));
-    case ST_C64:
-      if (fcplx) KB_SWITCH(kb, (factor_dispatch<cdouble, cdouble, KBv>(pv, fvals, apply, k, x, y, done, s)))
-      else KB_SWITCH(kb, (factor_dispatch<cdouble, double, KBv>(pv, fvals, apply, k, x, y, done, s)));
-  }
-  return (int)cudaErrorInvalidValue;
 }
