@@ -174,7 +174,7 @@ def max_over_ranks(ws, x):
     return float(t.item())
 
 
-def run_ours(args, ws, rank, local):
+def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False):
     import torch
     import paper_2003_12759_gb300 as mor
     import workloads as W
@@ -187,8 +187,10 @@ def run_ours(args, ws, rank, local):
     fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
     mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E, fmt=fmt)
     info = mor.mor_get_info(h)
-    opts = mor.mor_default_opts(precision=mor.MOR_FP64 if args.precision == "fp64" else mor.MOR_MIXED,
-                                batch=0 if args.one_shift else 1, use_graph=0 if args.one_shift else 1,
+    prec_name = precision or args.precision
+    one = args.one_shift if one_shift is None else one_shift
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64 if prec_name == "fp64" else mor.MOR_MIXED,
+                                batch=0 if one else 1, use_graph=0 if one else 1,
                                 max_chain=args.max_chain)
     omega = np.logspace(0, 5, 1000)
     shifts = wl.shifts.copy()
@@ -223,7 +225,7 @@ def run_ours(args, ws, rank, local):
     value = solves * ws / tmax
     out = {"t": tmax, "value": value, "stats": stats, "launches": launches, "clocks": clocks, "info": info,
            "n": n, "shifts": shifts}
-    if rank != 0:
+    if rank != 0 or light:
         mor.mor_destroy(h)
         return out
     # ---- roofline of the hot-loop kernels (live CUDA-event timing on the handle's stream)
@@ -283,6 +285,57 @@ def run_ours(args, ws, rank, local):
     return out
 
 
+def run_batch(args, ws, rank, local):
+    """Uneven batch: 256 independent 2D Laplacian-plus-diagonal systems, n_s in
+    [2000, 60000], 8 real shifts logspace(0, 4, 8) each.  One step = SPAI at the
+    first shift for all systems + 7 horizontal reuse factors + all 2048
+    (system, shift) solves in the same lock-step launches (FP32 in FP64
+    refinement)."""
+    import torch
+    import paper_2003_12759_gb300 as mor
+    import workloads as W
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    sysl = W.config2(num_systems=args.nsys)
+    h = mor.mor_create(local, stream)
+    fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
+    mor.mor_set_batch(h, [w.A for w in sysl], [w.B[:, 0] for w in sysl], [w.C[:, 0] for w in sysl], fmt=fmt)
+    nsys, off = mor.mor_batch_info(h)
+    shifts = list(np.logspace(0, 4, 8).astype(np.complex128))
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64 if args.precision == "fp64" else mor.MOR_MIXED)
+
+    def step():
+        mor.mor_build_precond(h, shifts[0], 0, opts.precision)
+        for z in shifts[1:]:
+            mor.mor_update_precond(h, z, 0)
+        X, st, code = mor.mor_batch_solve(h, shifts, 0, opts)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    clk = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    l0 = mor.mor_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clk.start()
+    e0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(ws)
+    t = max_over_ranks(ws, e0.elapsed_time(e1) / 1000.0)
+    solves = args.steps * nsys * len(shifts)
+    its = [x["iters"] for st in stats for row in st for x in row]
+    rel = max(x["relres"] for st in stats for row in st for x in row)
+    mor.mor_destroy(h)
+    return {"t": t, "value": solves * ws / t, "launches": mor.mor_launch_count() - l0, "clocks": clocks,
+            "nsys": nsys, "rows": int(off[-1]), "iters_mean": float(np.mean(its)), "iters_max": int(max(its)),
+            "max_relres": rel}
+
+
 def kernels_only(args):
     """Short run for profilers: the hot-loop kernels on the full-size workload."""
     import paper_2003_12759_gb300 as mor
@@ -315,7 +368,13 @@ def main():
     ap.add_argument("--max-chain", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true",
+                    help="skip timing the plain FP64 one-shift-per-launch form next to the default")
     ap.add_argument("--fmt", default="auto", choices=["auto", "csr", "sell"])
+    ap.add_argument("--workload", default="convdiff", choices=["convdiff", "batch"],
+                    help="convdiff: IRKA sweeps on the 3D convection-diffusion system (default); "
+                         "batch: 256 uneven independent systems x 8 shifts")
+    ap.add_argument("--nsys", type=int, default=256)
     ap.add_argument("--kernels-only", action="store_true",
                     help="set up the workload, build a 7-factor chain and time the hot-loop SpMVs "
                          "a few times (a short launch list for profilers)")
@@ -353,6 +412,23 @@ def main():
     if args.kernels_only:
         kernels_only(args)
         return
+    if args.workload == "batch":
+        r = run_batch(args, ws, rank, local)
+        if rank == 0:
+            line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": 1000 * r["t"] / args.steps, "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None,
+                    "dtype": "f32 inner / f64 refinement" if args.precision == "mixed" else "f64",
+                    "data": "synthetic (seeded uneven Laplacian batch)",
+                    "config": {"workload": "batch_%d_laplace2d_uneven_n%d_8shifts" % (r["nsys"], r["rows"]),
+                               "systems": r["nsys"], "rows": r["rows"], "shifts": "logspace(0,4,8), real",
+                               "step": "SPAI + 7 reuse factors + all (system, shift) solves, one lock-step launch "
+                                       "sequence", "tol": 1e-8},
+                    "clocks": r["clocks"], "gpu_launches": int(r["launches"]),
+                    "batch": {"iters_mean": r["iters_mean"], "iters_max": r["iters_max"],
+                              "max_relres": r["max_relres"]}}
+            print(json.dumps(line))
+        return
     r = run_ours(args, ws, rank, local)
     if rank != 0:
         return
@@ -374,6 +450,17 @@ def main():
                      "ms_reduce": float(np.mean([st["ms_reduce"] for st in stats]))}}
     if "e2e" in r:
         line["e2e"] = r["e2e"]
+    if not args.no_comparator and args.precision == "mixed" and not args.one_shift:
+        # the plain FP64 one-shift-per-launch form on the same workload (no batching, no graphs)
+        a2 = argparse.Namespace(**vars(args))
+        a2.steps, a2.warmup = max(1, min(args.steps, 2)), args.warmup
+        c = run_ours(a2, ws, rank, local, precision="fp64", one_shift=True, light=True)
+        line["comparator_fp64_one_shift"] = {
+            "value": c["value"], "unit": UNIT, "ms_per_step": 1000 * c["t"] / a2.steps,
+            "iters_per_solve": float(np.mean([(st["iters_V"] + st["iters_W"]) / (2 * st["nsolve"]) for st in c["stats"]])),
+            "ms_precond": float(np.mean([st["ms_precond"] for st in c["stats"]])),
+            "ms_solve": float(np.mean([st["ms_solve"] for st in c["stats"]])),
+            "speedup_of_mixed_multishift": r["value"] / c["value"]}
     if not args.no_cpu and ws == 1:
         cb = cpu_baseline(args.grid, iters_per_solve)
         line["cpu_baseline"] = {"value": 1.0 / cb["per_solve_s"], "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -316,6 +316,39 @@ int mor_eval_tf(mor_t h, const mor_reduced* rom, const double* omega, int nw,
                 mor_c64* H, unsigned flags);
 
 /* ------------------------------------------------------------------------ */
+/* batches of independent systems                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Set nsys independent SISO first-order systems E_s x' = A_s x + b_s u,
+ * y = c_s^T x of uneven sizes n_s as one batch (replacing any system of h).
+ * They are stored as one block-diagonal operator whose blocks keep separate
+ * Krylov scalars and convergence: every reduction of a solve is per
+ * (system, shift) (Eq. gen-precond-par's column independence also keeps
+ * every SPAI column inside its own block).  A: nsys CSR matrices (host);
+ * E_diag: NULL (all E_s = I) or nsys pointers (each NULL for I, or a
+ * length-n_s diagonal); B, C: nsys pointers to length-n_s vectors.  The
+ * preconditioner calls (mor_build_precond, mor_update_precond) then act on
+ * all systems at once with the same shift.  Host pointers only
+ * (MOR_DEVICE_PTRS is rejected).  Errors as mor_set_system. */
+int mor_set_batch(mor_t h, int nsys, const mor_csr* A, const double* const* E_diag,
+                  const double* const* B, const double* const* C, int format, unsigned flags);
+
+/* Number of systems of the batch and its row offsets (nsys + 1 entries;
+ * system s owns rows offsets[s] .. offsets[s+1]-1 of the batch). */
+int mor_batch_info(mor_t h, int* nsys, int64_t* offsets);
+
+/* Solve A_s(sigma_c) x_{s,c} = b_s (transpose = 0) or A_s(sigma_c)^T
+ * x_{s,c} = c_s (transpose = 1) for every system s of the batch and every
+ * shift c = 0..k-1, all in the same lock-step launches (the shift columns of
+ * all systems advance together; each (system, shift) pair converges on its
+ * own relative residual).  Preconditioning, precision and options as in
+ * mor_solve_shifts.  X: N x k complex128 column-major over the batch rows
+ * (N = offsets[nsys]); stats: nsys x k entries, stats[s * k + c] (may be
+ * NULL).  1 <= k <= 64. */
+int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const mor_solve_opts* opts,
+                    mor_c64* X, mor_solve_stats* stats, unsigned flags);
+
+/* ------------------------------------------------------------------------ */
 /* measurement                                                              */
 /* ------------------------------------------------------------------------ */
 

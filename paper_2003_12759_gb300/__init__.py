@@ -117,6 +117,10 @@ SIGNATURES = {
     "mor_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
     "mor_time_kernel": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "mor_orthonormalize_noalloc": (C.c_int, [_P, C.c_int64, C.c_int, _P]),
+    "mor_set_batch": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_int, C.c_uint]),
+    "mor_batch_info": (C.c_int, [_P, C.POINTER(C.c_int), _P]),
+    "mor_batch_solve": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(mor_solve_opts), _P,
+                                  C.POINTER(mor_solve_stats), C.c_uint]),
 }
 
 _lib = None
@@ -464,3 +468,55 @@ def mor_orthonormalize_noalloc(X, stream=None) -> int:
         raise ValueError("X must be column-major (stride (1, n))")
     sp_ = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
     return load_library().mor_orthonormalize_noalloc(C.c_void_p(X.data_ptr()), int(n), int(k), sp_)
+
+
+def mor_set_batch(h, As, Bs, Cs, E_diags=None, fmt: int = MOR_FMT_AUTO):
+    """A batch of independent SISO systems (lists of scipy.sparse A_s and
+    length-n_s vectors b_s, c_s, optional E_s diagonals)."""
+    lib = load_library()
+    nsys = len(As)
+    structs = (mor_csr * nsys)()
+    keep = []
+    for i, A in enumerate(As):
+        st, kp = _csr_struct(A)
+        structs[i] = st
+        keep.append(kp)
+    def ptrs(vs):
+        if vs is None:
+            return None, None
+        arrs = [None if v is None else np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel()) for v in vs]
+        P = (C.c_void_p * nsys)(*[None if a is None else a.ctypes.data for a in arrs])
+        return P, arrs
+    Bp, Bk = ptrs(Bs)
+    Cp, Ck = ptrs(Cs)
+    Ep, Ek = ptrs(E_diags)
+    code = lib.mor_set_batch(h, nsys, structs, Ep, Bp, Cp, fmt, 0)
+    return _check(h, code)
+
+
+def mor_batch_info(h):
+    n = C.c_int()
+    _check(h, load_library().mor_batch_info(h, C.byref(n), None))
+    off = np.empty(n.value + 1, dtype=np.int64)
+    _check(h, load_library().mor_batch_info(h, C.byref(n), off.ctypes.data_as(C.c_void_p)))
+    return n.value, off
+
+
+def mor_batch_solve(h, sigma, transpose: int = 0, opts: Optional[mor_solve_opts] = None,
+                    allow=(MOR_ENOCONV, MOR_EBREAKDOWN)):
+    """Solve every (system, shift) pair of the batch.  Returns (X N x k
+    complex128, stats as an nsys x k list of dicts, status)."""
+    lib = load_library()
+    nsys, off = mor_batch_info(h)
+    N = int(off[-1])
+    s, sp_ = _shifts(sigma)
+    k = s.shape[0]
+    o = opts if opts is not None else mor_default_opts()
+    X = np.empty((N, k), dtype=np.complex128, order="F")
+    st = (mor_solve_stats * (nsys * k))()
+    code = lib.mor_batch_solve(h, sp_, k, int(transpose), C.byref(o), X.ctypes.data_as(C.c_void_p), st, 0)
+    _check(h, code, allow)
+    stats = [[{"iters": st[i * k + c].iters, "refinements": st[i * k + c].refinements,
+               "relres": st[i * k + c].relres, "status": st[i * k + c].status} for c in range(k)]
+             for i in range(nsys)]
+    return X, stats, code

@@ -38,20 +38,22 @@ inline int grid_rows(int st, int64_t n, int ld, int cap) {
   return grid_for(n * tpr, cap);
 }
 
-// lane geometry shared by the elementwise kernels
+// lane geometry shared by the elementwise kernels: segment, rows, owned columns
 #define MOR_LANE_SETUP                                  \
   const int sub = threadIdx.x % TPR;                   \
   const int c0 = sub * CPT;                            \
   const int rpb = blockDim.x / TPR;                    \
+  const int seg = seg_of_chunk(sg, blockIdx.x);                    \
   int64_t rb, re;                                      \
-  block_rows(n, rpb, rb, re);
+  chunk_rows(sg, seg, blockIdx.x, rb, re);
 
 template <typename S, int TPR, int CPT>
-__global__ void __launch_bounds__(256) update_p_kernel(int n, int ld, const S* __restrict__ r, S* __restrict__ p,
+__global__ void __launch_bounds__(256) update_p_kernel(SegView sg, int ld, const S* __restrict__ r, S* __restrict__ p,
                                                        const S* __restrict__ v, const KState* st, const int* done) {
   if (*done) return;
   MOR_LANE_SETUP
   if (c0 >= ld) return;
+  st += (size_t)seg * ld;
   S beta[CPT], omega[CPT];
   int act[CPT];
   bool any = false;
@@ -75,11 +77,12 @@ __global__ void __launch_bounds__(256) update_p_kernel(int n, int ld, const S* _
 }
 
 template <typename S, int TPR, int CPT>
-__global__ void __launch_bounds__(256) update_s_kernel(int n, int ld, const S* __restrict__ r, const S* __restrict__ v,
+__global__ void __launch_bounds__(256) update_s_kernel(SegView sg, int ld, const S* __restrict__ r, const S* __restrict__ v,
                                                        S* __restrict__ sv, const KState* st, const int* done) {
   if (*done) return;
   MOR_LANE_SETUP
   if (c0 >= ld) return;
+  st += (size_t)seg * ld;
   S alpha[CPT];
   int act[CPT];
 #pragma unroll
@@ -95,22 +98,23 @@ __global__ void __launch_bounds__(256) update_s_kernel(int n, int ld, const S* _
 }
 
 template <typename S, int TPR, int CPT>
-__global__ void __launch_bounds__(256) update_xr_kernel(int n, int ld, S* __restrict__ x, S* __restrict__ r,
+__global__ void __launch_bounds__(256) update_xr_kernel(SegView sg, int ld, S* __restrict__ x, S* __restrict__ r,
                                                         const S* __restrict__ ph, const S* __restrict__ sh,
                                                         const S* __restrict__ sv, const S* __restrict__ t,
-                                                        const S* __restrict__ rhat, double* part, unsigned* counter,
-                                                        KState* st, int* done) {
+                                                        const S* __restrict__ rhat, double* part, KState* st,
+                                                        int* done) {
   if (*done) return;
   MOR_LANE_SETUP
   const bool lane_on = c0 < ld;
+  const KState* sts = st + (size_t)seg * ld;
   S alpha[CPT], omega[CPT], v0[CPT], v1[CPT];
   int act[CPT];
   bool any = false;
 #pragma unroll
   for (int j = 0; j < CPT; ++j) {
-    act[j] = lane_on ? st[c0 + j].active : 0;
-    alpha[j] = act[j] ? from_cd<S>(st[c0 + j].alpha) : S(0);
-    omega[j] = act[j] ? from_cd<S>(st[c0 + j].omega) : S(0);
+    act[j] = lane_on ? sts[c0 + j].active : 0;
+    alpha[j] = act[j] ? from_cd<S>(sts[c0 + j].alpha) : S(0);
+    omega[j] = act[j] ? from_cd<S>(sts[c0 + j].omega) : S(0);
     v0[j] = S(0);
     v1[j] = S(0);
     any |= (act[j] != 0);
@@ -135,15 +139,14 @@ __global__ void __launch_bounds__(256) update_xr_kernel(int n, int ld, S* __rest
       stp<S, CPT>(r + q, rn);
     }
   }
-  col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, part, counter, FIN_RHO, st, nullptr, done);
+  col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, sg, seg, blockIdx.x, part, FIN_RHO, st, nullptr, done);
 }
 
 // x = 0, r = r_hat = rhs, p = v = 0, then (r_hat, r), ||r||^2 -> FIN_INIT
 template <typename S, int TPR, int CPT>
-__global__ void __launch_bounds__(256) init_kernel(int n, int ld, const S* __restrict__ rhs, S* __restrict__ x,
+__global__ void __launch_bounds__(256) init_kernel(SegView sg, int ld, const S* __restrict__ rhs, S* __restrict__ x,
                                                    S* __restrict__ r, S* __restrict__ rhat, S* __restrict__ p,
-                                                   S* __restrict__ v, double* part, unsigned* counter, KState* st,
-                                                   int* done) {
+                                                   S* __restrict__ v, double* part, KState* st, int* done) {
   MOR_LANE_SETUP
   S v0[CPT], v1[CPT];
 #pragma unroll
@@ -164,13 +167,16 @@ __global__ void __launch_bounds__(256) init_kernel(int n, int ld, const S* __res
       for (int j = 0; j < CPT; ++j) { fma_s(v0[j], conj_(b.v[j]), b.v[j]); v1[j] += S(abs2_(b.v[j])); }
     }
   }
-  col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, part, counter, FIN_INIT, st, nullptr, done);
+  col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, sg, seg, blockIdx.x, part, FIN_INIT, st, nullptr, done);
 }
 
-__global__ void set_targets_kernel(int k, KState* st, const double* target, const int* maxit) {
-  int c = threadIdx.x;
-  if (c < k) { st[c].target2 = target[c] * target[c]; st[c].maxit = maxit[c]; }
+__global__ void set_targets_kernel(int count, KState* st, const double* target, const int* maxit) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
+    st[c].target2 = target[c] * target[c];
+    st[c].maxit = maxit[c];
+  }
 }
+__global__ void set_done_kernel(const int* live, int* done) { *done = (*live == 0) ? 1 : 0; }
 
 template <typename S> struct wide_of { typedef S type; };
 template <> struct wide_of<float> { typedef double type; };
@@ -178,11 +184,13 @@ template <> struct wide_of<cfloat> { typedef cdouble type; };
 
 // rhs_in = cast(r64 / ||r64||) for active columns, 0 otherwise
 template <typename S, int TPR, int CPT>
-__global__ void scale_cast_kernel(int n, int ld, const typename wide_of<S>::type* __restrict__ r64,
+__global__ void scale_cast_kernel(SegView sg, int ld, const typename wide_of<S>::type* __restrict__ r64,
                                   const double* nrm2, const int* active, S* __restrict__ out) {
   typedef typename wide_of<S>::type W;
   MOR_LANE_SETUP
   if (c0 >= ld) return;
+  active += (size_t)seg * ld;
+  nrm2 += (size_t)seg * ld;
   double inv[CPT];
   int act[CPT];
 #pragma unroll
@@ -203,11 +211,13 @@ __global__ void scale_cast_kernel(int n, int ld, const typename wide_of<S>::type
 }
 
 template <typename S, int TPR, int CPT>
-__global__ void refine_update_kernel(int n, int ld, typename wide_of<S>::type* __restrict__ x64,
+__global__ void refine_update_kernel(SegView sg, int ld, typename wide_of<S>::type* __restrict__ x64,
                                      const S* __restrict__ d, const double* nrm2, const int* active) {
   typedef typename wide_of<S>::type W;
   MOR_LANE_SETUP
   if (c0 >= ld) return;
+  active += (size_t)seg * ld;
+  nrm2 += (size_t)seg * ld;
   double sc[CPT];
   int act[CPT];
 #pragma unroll
@@ -292,11 +302,11 @@ __global__ void scatter_cols_kernel(int64_t n, int ld_src, int ld_dst, int ncols
 
 size_t krylov_state_bytes(int) { return sizeof(KState); }
 
-int krylov_launch_update_p(int st, int n, int ld, const void* r, void* p, const void* v, const void* state,
+int krylov_launch_update_p(int st, const SegView& sg, int ld, const void* r, void* p, const void* v, const void* state,
                            const int* done, cudaStream_t s) {
-  const int g = grid_rows(st, n, ld, 152 * 8);
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    update_p_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (const S*)r, (S*)p, (const S*)v, (const KState*)state, done);
+    update_p_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (const S*)r, (S*)p, (const S*)v,
+                                                            (const KState*)state, done);
     return 0;
   });
   if (e) return e;
@@ -304,11 +314,11 @@ int krylov_launch_update_p(int st, int n, int ld, const void* r, void* p, const 
   return (int)cudaGetLastError();
 }
 
-int krylov_launch_update_s(int st, int n, int ld, const void* r, const void* v, void* sv, const void* state,
+int krylov_launch_update_s(int st, const SegView& sg, int ld, const void* r, const void* v, void* sv, const void* state,
                            const int* done, cudaStream_t s) {
-  const int g = grid_rows(st, n, ld, 152 * 8);
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    update_s_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (const S*)r, (const S*)v, (S*)sv, (const KState*)state, done);
+    update_s_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (const S*)r, (const S*)v, (S*)sv,
+                                                            (const KState*)state, done);
     return 0;
   });
   if (e) return e;
@@ -316,14 +326,13 @@ int krylov_launch_update_s(int st, int n, int ld, const void* r, const void* v, 
   return (int)cudaGetLastError();
 }
 
-int krylov_launch_update_xr(int st, int n, int ld, void* x, void* r, const void* phat, const void* shat,
-                            const void* sv, const void* t, const void* rhat, void* part, unsigned* counter,
-                            void* state, int* done, int grid_cap, cudaStream_t s) {
-  const int g = grid_rows(st, n, ld, grid_cap);
+int krylov_launch_update_xr(int st, const SegView& sg, int ld, void* x, void* r, const void* phat, const void* shat,
+                            const void* sv, const void* t, const void* rhat, void* part, void* state, int* done,
+                            cudaStream_t s) {
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    update_xr_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (S*)x, (S*)r, (const S*)phat, (const S*)shat,
-                                                    (const S*)sv, (const S*)t, (const S*)rhat, (double*)part,
-                                                    counter, (KState*)state, done);
+    update_xr_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (S*)x, (S*)r, (const S*)phat, (const S*)shat,
+                                                             (const S*)sv, (const S*)t, (const S*)rhat, (double*)part,
+                                                             (KState*)state, done);
     return 0;
   });
   if (e) return e;
@@ -331,23 +340,28 @@ int krylov_launch_update_xr(int st, int n, int ld, void* x, void* r, const void*
   return (int)cudaGetLastError();
 }
 
-int krylov_launch_init(int st, int n, int ld, const void* rhs, void* x, void* r, void* rhat, void* p, void* v,
-                       void* part, unsigned* counter, void* state, const double* target, const int* maxit,
-                       int* done, int grid_cap, cudaStream_t s) {
-  set_targets_kernel<<<1, 32, 0, s>>>(ld, (KState*)state, target, maxit);
+int krylov_launch_init(int st, const SegView& sg, int ld, const void* rhs, void* x, void* r, void* rhat, void* p,
+                       void* v, void* part, void* state, const double* target, const int* maxit, int* done,
+                       cudaStream_t s) {
+  const int count = sg.nseg * ld;
+  set_targets_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, (KState*)state, target, maxit);
   mor_count_launches(1);
-  const int g = grid_rows(st, n, ld, grid_cap);
+  cudaError_t ce = cudaMemsetAsync(sg.live, 0, sizeof(int), s);
+  if (ce != cudaSuccess) return (int)ce;
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    init_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (const S*)rhs, (S*)x, (S*)r, (S*)rhat, (S*)p, (S*)v,
-                                               (double*)part, counter, (KState*)state, done);
+    init_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (const S*)rhs, (S*)x, (S*)r, (S*)rhat, (S*)p, (S*)v,
+                                                        (double*)part, (KState*)state, done);
     return 0;
   });
   if (e) return e;
+  mor_count_launches(1);
+  set_done_kernel<<<1, 1, 0, s>>>(sg.live, done);
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
 int krylov_read_state(int, const void* state_dev, int k, int* iters, int* status, cudaStream_t s) {
+  if (k > MOR_LDMAX) return (int)cudaErrorInvalidValue;
   KState h[MOR_LDMAX];
   cudaError_t e = cudaMemcpyAsync(h, state_dev, sizeof(KState) * k, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return (int)e;
@@ -357,12 +371,11 @@ int krylov_read_state(int, const void* state_dev, int k, int* iters, int* status
   return 0;
 }
 
-int refine_launch_scale_cast(int st_in, int n, int ld, const void* r64, const double* nrm2, const int* active,
+int refine_launch_scale_cast(int st_in, const SegView& sg, int ld, const void* r64, const double* nrm2, const int* active,
                              void* rhs_in, cudaStream_t s) {
-  const int g = grid_rows(st_in, n, ld, 152 * 8);
   int e = dispatch_shape(st_in, ld, [&]<typename S, int TPR, int CPT>() -> int {
     typedef typename wide_of<S>::type W;
-    scale_cast_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (const W*)r64, nrm2, active, (S*)rhs_in);
+    scale_cast_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (const W*)r64, nrm2, active, (S*)rhs_in);
     return 0;
   });
   if (e) return e;
@@ -370,12 +383,11 @@ int refine_launch_scale_cast(int st_in, int n, int ld, const void* r64, const do
   return (int)cudaGetLastError();
 }
 
-int refine_launch_update(int st_in, int n, int ld, void* x64, const void* d, const double* nrm2, const int* active,
-                         cudaStream_t s) {
-  const int g = grid_rows(st_in, n, ld, 152 * 8);
+int refine_launch_update(int st_in, const SegView& sg, int ld, void* x64, const void* d, const double* nrm2,
+                         const int* active, cudaStream_t s) {
   int e = dispatch_shape(st_in, ld, [&]<typename S, int TPR, int CPT>() -> int {
     typedef typename wide_of<S>::type W;
-    refine_update_kernel<S, TPR, CPT><<<g, 256, 0, s>>>(n, ld, (W*)x64, (const S*)d, nrm2, active);
+    refine_update_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (W*)x64, (const S*)d, nrm2, active);
     return 0;
   });
   if (e) return e;

@@ -12,6 +12,7 @@
 // rows of a stencil reuse the gathered vector entries from L1.
 #pragma once
 #include "mor_types.cuh"
+#include "mor_internal.h"
 #include <string.h>
 
 #define MOR_LDMAX_DEV 16
@@ -33,7 +34,7 @@ struct KState {
 };
 
 // sums[c*2 + q] for column c, reduction q
-__device__ inline void krylov_finalize(int stage, int k, const cdouble* sums, KState* st, int* done) {
+__device__ inline int krylov_finalize(int stage, int k, const cdouble* sums, KState* st) {
   int any = 0;
   for (int c = 0; c < k; ++c) {
     KState& S = st[c];
@@ -75,7 +76,13 @@ __device__ inline void krylov_finalize(int stage, int k, const cdouble* sums, KS
     }
     any |= S.active;
   }
-  if (done) *done = any ? 0 : 1;
+  return any;
+}
+
+__device__ inline int krylov_any_active(int k, const KState* st) {
+  int any = 0;
+  for (int c = 0; c < k; ++c) any |= st[c].active;
+  return any;
 }
 
 // ---------------------------------------------------------------------------
@@ -107,27 +114,41 @@ __device__ __forceinline__ void stp(S* p, const Pack<S, CPT>& o) {
   }
 }
 
-// Contiguous row range of this block: [r0, r1), processed rpb rows at a time.
-__device__ __forceinline__ void block_rows(int64_t n, int rpb, int64_t& r0, int64_t& r1) {
-  int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-  chunk = (chunk + rpb - 1) / rpb * rpb;
-  r0 = (int64_t)blockIdx.x * chunk;
-  r1 = r0 + chunk < n ? r0 + chunk : n;
+// Segment of chunk b and the chunk's row range [r0, r1).  Kernels are
+// persistent: a resident wave of blocks walks the chunks b = blockIdx.x,
+// blockIdx.x + gridDim.x, ... of the segment table.
+__device__ __forceinline__ int seg_of_chunk(const SegView& sg, int b) {
+  int lo = 0, hi = sg.nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sg.blk0[mid] <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ void chunk_rows(const SegView& sg, int s, int b, int64_t& r0, int64_t& r1) {
+  r0 = sg.row0[s] + (int64_t)(b - sg.blk0[s]) * sg.rows_per_block;
+  const int64_t e = r0 + sg.rows_per_block;
+  r1 = e < sg.row0[s + 1] ? e : sg.row0[s + 1];
 }
 
 // ---------------------------------------------------------------------------
 // Reduce two per-column values (v0[j], v1[j]) of the CPT columns lane `sub`
-// owns (columns sub * CPT + j; sub = lane % TPR) over the block, write the
-// per-block FP64 partials part[(block * 2 ld + 2c + q) * 2 + {re, im}], and
-// let the last block (atomic ticket) sum the partials of all blocks in a fixed
-// order and run the finalize stage (or write the sums to `out`).  Every thread
-// of the block must call it.
+// owns (columns sub * CPT + j; sub = lane % TPR) over the block for chunk
+// `chunk`, write the chunk's FP64 partials part[(chunk * 2 ld + 2c + q) * 2 +
+// {re, im}], and let the block that finishes the last chunk of segment `seg`
+// (ticket counters[seg]) sum the segment's partials in a fixed order and run
+// the finalize stage on that segment's states (or write the sums to
+// out[seg * 2 ld ...]).  The finalize keeps sg.live (segments with an active
+// column) and `done` (no segment active) current.  Every thread of the block
+// must call it, once per chunk.
 template <typename S, int TPR, int CPT>
-__device__ inline void col_reduce_finalize(const S (&v0)[CPT], const S (&v1)[CPT], int ld, double* part,
-                                           unsigned* counter, int fin, KState* state, cdouble* out, int* done) {
+__device__ inline void col_reduce_finalize(const S (&v0)[CPT], const S (&v1)[CPT], int ld, const SegView& sg, int seg,
+                                           int chunk, double* part, int fin, KState* state, cdouble* out, int* done) {
   typedef typename real_of<S>::type R;
   __shared__ double sh[8][2 * MOR_LDMAX_DEV][2];
   __shared__ bool am_last;
+  __shared__ cdouble sums[2 * MOR_LDMAX_DEV];
+  __syncthreads();   // the shared buffers are reused chunk after chunk
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int nv = 2 * ld;
@@ -153,21 +174,21 @@ __device__ inline void col_reduce_finalize(const S (&v0)[CPT], const S (&v1)[CPT
   if (threadIdx.x < nv) {
     double re = 0.0, im = 0.0;
     for (int w = 0; w < nwarps; ++w) { re += sh[w][threadIdx.x][0]; im += sh[w][threadIdx.x][1]; }
-    part[((size_t)blockIdx.x * nv + threadIdx.x) * 2 + 0] = re;
-    part[((size_t)blockIdx.x * nv + threadIdx.x) * 2 + 1] = im;
+    part[((size_t)chunk * nv + threadIdx.x) * 2 + 0] = re;
+    part[((size_t)chunk * nv + threadIdx.x) * 2 + 1] = im;
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  const int b0s = sg.blk0[seg], b1s = sg.blk0[seg + 1];
+  if (threadIdx.x == 0) am_last = (atomicAdd(sg.counters + seg, 1u) == (unsigned)(b1s - b0s - 1));
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  // last block: warp w sums values w, w + nwarps, ... over all blocks (lanes stride the blocks)
-  __shared__ cdouble sums[2 * MOR_LDMAX_DEV];
+  // last chunk of the segment: warp w sums values w, w + nwarps, ... over the segment's chunks
   const volatile double* vp = part;
   for (int i = wid; i < nv; i += nwarps) {
     double re = 0.0, im = 0.0;
-    for (int blk = lane; blk < (int)gridDim.x; blk += 32) {
+    for (int blk = b0s + lane; blk < b1s; blk += 32) {
       re += vp[((size_t)blk * nv + i) * 2 + 0];
       im += vp[((size_t)blk * nv + i) * 2 + 1];
     }
@@ -177,8 +198,18 @@ __device__ inline void col_reduce_finalize(const S (&v0)[CPT], const S (&v1)[CPT
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (fin != FIN_NONE) krylov_finalize(fin, ld, sums, state, done);
-    else if (out) for (int i = 0; i < nv; ++i) out[i] = sums[i];
-    *counter = 0u;   // ready for the next launch (stream order makes this safe)
+    if (fin != FIN_NONE) {
+      KState* st = state + (size_t)seg * ld;
+      const int was = (fin == FIN_INIT) ? 0 : krylov_any_active(ld, st);
+      const int now = krylov_finalize(fin, ld, sums, st);
+      if (fin == FIN_INIT) {
+        if (now) atomicAdd(sg.live, 1);
+      } else if (was && !now) {
+        if (atomicSub(sg.live, 1) == 1 && done) *done = 1;
+      }
+    } else if (out) {
+      for (int i = 0; i < nv; ++i) out[(size_t)seg * nv + i] = sums[i];
+    }
+    sg.counters[seg] = 0u;   // ready for the next launch (stream order makes this safe)
   }
 }

@@ -86,6 +86,11 @@ struct mor_ctx {
   void* pinned = nullptr;   // small pinned host buffer
   size_t pinned_bytes = 0;
   int grid_cap = 152 * 8;
+  // segment table: one segment per independent system (1 for mor_set_system)
+  DBuf seg_blk0, seg_row0, seg_counters, seg_live;
+  SegView seg{};
+  std::vector<int64_t> seg_rows_h;   // nseg + 1 row offsets (host)
+  DBuf ws_kstate, ws_segarr, ws_sums;
   // IRKA reuse schedule
   int irka_z = 0;
   int vlen[2] = {0, 0};
@@ -118,4 +123,6 @@ int mor_fail(mor_t h, int code, const char* fmt, ...);
 
 // shift -> operator coefficients
 Coef mor_coef(const mor_ctx* h, mor_c64 s);
+// (re)build the segment table for the given row offsets (nseg + 1 entries)
+int mor_build_segments(mor_t h, const std::vector<int64_t>& row_offsets);
 inline bool is_real_shift(mor_c64 s) { return s.im == 0.0; }

@@ -83,48 +83,62 @@ inline void lane_shape(int st, int ld, int* tpr, int* cpt) {
 
 #define MOR_LDMAX 16
 
+// Independent systems stored as one block-diagonal operator ("segments").
+// Every kernel of the solve runs on nblocks blocks; block b belongs to the
+// segment s with blk0[s] <= b < blk0[s+1] and walks rows row0[s] + (b -
+// blk0[s]) * rows_per_block ... (clipped to the segment).  Reductions are
+// per (segment, column): the last block of a segment (ticket counters[s])
+// finalizes that segment's columns; `live` counts segments with an active
+// column.  A single system is the one-segment case.
+struct SegView {
+  int nseg;
+  int nblocks;
+  int64_t rows_per_block;
+  const int* blk0;         // nseg + 1
+  const int64_t* row0;     // nseg + 1
+  unsigned* counters;      // nseg, zero between launches
+  int* live;               // segments with an active column
+};
+
 // Fused reductions: `part` holds per-block FP64 partials, the last block (by
 // ticket on `counter`) reduces them in a fixed order and runs the finalize
 // stage `fin` on `state` (or writes the 2 * ld sums to `out`).
 struct RedArgs {
   int mode;            // RED_*
   const void* w;       // second vector of the reduction
-  void* part;          // gridDim.x * ld * 2 complex partials (doubles)
-  unsigned* counter;   // zero-initialised block counter (the last block resets it)
+  void* part;          // nblocks * ld * 2 complex partials (doubles)
+  unsigned* counter;   // unused (the segment tickets live in SegView)
   int fin;             // finalize stage id (0 = none: just write the reduced sums to `out`)
   void* state;         // solver state for the finalize stage
-  void* out;           // reduced sums (2 * ld complex doubles), when fin == 0
+  void* out;           // reduced sums (nseg x 2 ld complex doubles), when fin == 0
   const int* done;     // if non-null and *done != 0 the kernel returns at once
 };
 
 // Launchers (spmv.cu).  x, y, w, b: n x ld row-major blocks of type st.
-int launch_op_spmv(int st, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
-                   const void* x, void* y, const void* b, const RedArgs* red, int grid_cap,
-                   cudaStream_t s);
-int launch_factor_spmv(int st, bool fcplx, const PatView& pv, const void* fvals,
+int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
+                   const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s);
+int launch_factor_spmv(int st, bool fcplx, const SegView& sg, const PatView& pv, const void* fvals,
                        const int* apply, int ld, const void* x, void* y, const int* done,
                        cudaStream_t s);
 
 // Krylov helpers (krylov.cu)
-int krylov_launch_update_p(int st, int n, int ld, const void* r, void* p, const void* v,
+int krylov_launch_update_p(int st, const SegView& sg, int ld, const void* r, void* p, const void* v,
                            const void* state, const int* done, cudaStream_t s);
-int krylov_launch_update_s(int st, int n, int ld, const void* r, const void* v, void* sv,
+int krylov_launch_update_s(int st, const SegView& sg, int ld, const void* r, const void* v, void* sv,
                            const void* state, const int* done, cudaStream_t s);
-int krylov_launch_update_xr(int st, int n, int ld, void* x, void* r, const void* phat,
+int krylov_launch_update_xr(int st, const SegView& sg, int ld, void* x, void* r, const void* phat,
                             const void* shat, const void* sv, const void* t, const void* rhat,
-                            void* part, unsigned* counter, void* state, int* done, int grid_cap,
-                            cudaStream_t s);
-int krylov_launch_init(int st, int n, int ld, const void* rhs, void* x, void* r, void* rhat,
-                       void* p, void* v, void* part, unsigned* counter, void* state,
-                       const double* target, const int* maxit, int* done, int grid_cap,
-                       cudaStream_t s);
+                            void* part, void* state, int* done, cudaStream_t s);
+int krylov_launch_init(int st, const SegView& sg, int ld, const void* rhs, void* x, void* r, void* rhat,
+                       void* p, void* v, void* part, void* state, const double* target, const int* maxit,
+                       int* done, cudaStream_t s);
 size_t krylov_state_bytes(int st);
 int krylov_read_state(int st, const void* state_dev, int k, int* iters, int* status,
                       cudaStream_t s);
 // outer FP64 refinement: rhs_in = r64 / ||r64|| (cast), x64 += nrm * d
-int refine_launch_scale_cast(int st_in, int n, int ld, const void* r64, const double* nrm2,
+int refine_launch_scale_cast(int st_in, const SegView& sg, int ld, const void* r64, const double* nrm2,
                              const int* active, void* rhs_in, cudaStream_t s);
-int refine_launch_update(int st_in, int n, int ld, void* x64, const void* d,
+int refine_launch_update(int st_in, const SegView& sg, int ld, void* x64, const void* d,
                          const double* nrm2, const int* active, cudaStream_t s);
 // layout conversion: column-major complex128 (API, k columns) <-> row-major type st, stride ld
 int conv_launch_colmajor_c128_to_rowmajor(int st, int n, int k, int ld, const void* src, void* dst,

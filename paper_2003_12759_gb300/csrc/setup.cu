@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <thread>
 #include <atomic>
 
@@ -46,6 +47,45 @@ Coef mor_coef(const mor_ctx* h, mor_c64 s) {
     c.sEr = s.re; c.sEi = s.im; c.sAr = -1.0; c.sAi = 0.0;
   }
   return c;
+}
+
+int mor_build_segments(mor_t h, const std::vector<int64_t>& rows) {
+  const int nseg = (int)rows.size() - 1;
+  if (nseg < 1) return mor_fail(h, MOR_EINVAL, "no segments");
+  const int64_t N = rows[nseg];
+  // blocks of 256 threads per SM in total: a whole number of resident waves
+  // for the solve kernels (override: MOR_SEG_BLOCKS_PER_SM)
+  int bps = nseg == 1 ? 8 : 12;
+  if (const char* ev = std::getenv("MOR_SEG_BLOCKS_PER_SM")) {
+    const int v = std::atoi(ev);
+    if (v >= 1 && v <= 64) bps = v;
+  }
+  const int64_t target = (int64_t)h->sm_count * bps;
+  int64_t R = (N + target - 1) / target;
+  if (R < 64) R = 64;
+  std::vector<int> blk0(nseg + 1, 0);
+  for (int s = 0; s < nseg; ++s) {
+    const int64_t ns = rows[s + 1] - rows[s];
+    blk0[s + 1] = blk0[s] + (int)std::max<int64_t>(1, (ns + R - 1) / R);
+  }
+  MOR_CK(h, h->seg_blk0.alloc(sizeof(int) * (nseg + 1)));
+  MOR_CK(h, h->seg_row0.alloc(sizeof(int64_t) * (nseg + 1)));
+  MOR_CK(h, h->seg_counters.alloc(sizeof(unsigned) * nseg));
+  MOR_CK(h, h->seg_live.alloc(sizeof(int) * 2));
+  MOR_CK(h, cudaMemcpyAsync(h->seg_blk0.p, blk0.data(), sizeof(int) * (nseg + 1), cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(h->seg_row0.p, rows.data(), sizeof(int64_t) * (nseg + 1), cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemsetAsync(h->seg_counters.p, 0, sizeof(unsigned) * nseg, h->stream));
+  MOR_CK(h, cudaMemsetAsync(h->seg_live.p, 0, sizeof(int) * 2, h->stream));
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  h->seg.nseg = nseg;
+  h->seg.nblocks = blk0[nseg];
+  h->seg.rows_per_block = R;
+  h->seg.blk0 = h->seg_blk0.as<int>();
+  h->seg.row0 = h->seg_row0.as<int64_t>();
+  h->seg.counters = h->seg_counters.as<unsigned>();
+  h->seg.live = h->seg_live.as<int>();
+  h->seg_rows_h = rows;
+  return MOR_OK;
 }
 
 namespace {
@@ -296,8 +336,8 @@ double time_op(mor_t h, OpData& op, int& status) {
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0, h->stream);
-    launch_op_spmv(ST_F32, pv, ov, cf, 1, x.p, y.p, nullptr, nullptr, h->grid_cap, h->stream);
-    launch_op_spmv(ST_C32, pv, ov, cf, 8, x.p, y.p, nullptr, nullptr, h->grid_cap, h->stream);
+    launch_op_spmv(ST_F32, h->seg, pv, ov, cf, 1, x.p, y.p, nullptr, nullptr, h->stream);
+    launch_op_spmv(ST_C32, h->seg, pv, ov, cf, 8, x.p, y.p, nullptr, nullptr, h->stream);
     cudaEventRecord(e1, h->stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;
@@ -311,7 +351,8 @@ double time_op(mor_t h, OpData& op, int& status) {
 }
 
 int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std::vector<double>* Ediag, const double* B,
-                      int m, const double* C, int q, int format, bool dev) {
+                      int m, const double* C, int q, int format, bool dev,
+                      const std::vector<int64_t>* seg_rows = nullptr) {
   const int64_t n = A.n;
   if (m < 1 || m > MOR_MAX_IO || q < 1 || q > MOR_MAX_IO) return mor_fail(h, MOR_EINVAL, "m and q must be in [1, %d]", MOR_MAX_IO);
   if (!B || !C) return mor_fail(h, MOR_EINVAL, "B and C are required");
@@ -344,6 +385,8 @@ int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std:
   } else {
     h->ediag64.release(); h->ediag32.release();
   }
+  // segment table (one segment unless the caller is mor_set_batch, which passes its own)
+  MOR_TRY(mor_build_segments(h, seg_rows ? *seg_rows : std::vector<int64_t>{0, n}));
   // layout / autotune
   int fmt = format;
   if (fmt == MOR_FMT_AUTO) {
@@ -450,7 +493,7 @@ int mor_create(mor_t* out, int device, void* stream) {
   }
   if (h->ws_counter.alloc(64 * sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(h->ws_counter.p, 0, 64 * sizeof(unsigned)) != cudaSuccess) { delete h; return MOR_ENOMEM; }
-  h->pinned_bytes = 1 << 16;
+  h->pinned_bytes = 1 << 21;
   if (cudaHostAlloc(&h->pinned, h->pinned_bytes, cudaHostAllocDefault) != cudaSuccess) { delete h; return MOR_ENOMEM; }
   *out = h;
   return MOR_OK;
@@ -513,6 +556,67 @@ int mor_set_system_2nd(mor_t h, const mor_csr* K, const double* M_diag, double a
   h->alpha = alpha;
   h->beta = beta;
   return set_system_common(h, Kh, nullptr, &md, F, m, C, q, format, dev);
+}
+
+int mor_set_batch(mor_t h, int nsys, const mor_csr* A, const double* const* E_diag, const double* const* B,
+                  const double* const* C, int format, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (nsys < 1 || !A || !B || !C) return mor_fail(h, MOR_EINVAL, "nsys >= 1, A, B and C are required");
+  if (flags & MOR_DEVICE_PTRS) return mor_fail(h, MOR_EINVAL, "mor_set_batch takes host pointers only");
+  cudaSetDevice(h->dev);
+  std::vector<int64_t> rows(nsys + 1, 0);
+  std::vector<HostCSR> parts(nsys);
+  for (int s = 0; s < nsys; ++s) {
+    MOR_TRY(fetch_csr(h, &A[s], false, "A[s]", parts[s]));
+    if (!B[s] || !C[s]) return mor_fail(h, MOR_EINVAL, "B[%d] or C[%d] is null", s, s);
+    rows[s + 1] = rows[s] + parts[s].n;
+  }
+  const int64_t N = rows[nsys];
+  int64_t nnz = 0;
+  for (auto& pa : parts) nnz += (int64_t)pa.col.size();
+  if (N > 0x7fffffffLL || nnz > 0x7fffffffLL) return mor_fail(h, MOR_EINVAL, "batch too large for int32 indices");
+  HostCSR cat;
+  cat.n = N;
+  cat.rowptr.resize(N + 1);
+  cat.col.resize(nnz);
+  cat.val.resize(nnz);
+  std::vector<double> bcat(N), ccat(N), ecat;
+  bool anyE = false;
+  if (E_diag) for (int s = 0; s < nsys; ++s) anyE |= (E_diag[s] != nullptr);
+  if (anyE) ecat.assign(N, 1.0);
+  int64_t pos = 0;
+  for (int s = 0; s < nsys; ++s) {
+    const HostCSR& pa = parts[s];
+    const int64_t r0 = rows[s];
+    for (int64_t i = 0; i < pa.n; ++i) {
+      cat.rowptr[r0 + i] = (int32_t)(pos + pa.rowptr[i]);
+      if (anyE && E_diag[s]) {
+        const double e = E_diag[s][i];
+        if (!std::isfinite(e)) return mor_fail(h, MOR_EINVAL, "E_diag[%d] has a non-finite value", s);
+        ecat[r0 + i] = e;
+      }
+      bcat[r0 + i] = B[s][i];
+      ccat[r0 + i] = C[s][i];
+    }
+    for (size_t q = 0; q < pa.col.size(); ++q) {
+      cat.col[pos + q] = (int32_t)(pa.col[q] + r0);
+      cat.val[pos + q] = pa.val[q];
+    }
+    pos += (int64_t)pa.col.size();
+  }
+  cat.rowptr[N] = (int32_t)pos;
+  h->order = 1;
+  h->alpha = h->beta = 0.0;
+  return set_system_common(h, cat, nullptr, anyE ? &ecat : nullptr, bcat.data(), 1, ccat.data(), 1, format, false,
+                           &rows);
+}
+
+int mor_batch_info(mor_t h, int* nsys, int64_t* offsets) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (nsys) *nsys = h->seg.nseg;
+  if (offsets) std::memcpy(offsets, h->seg_rows_h.data(), sizeof(int64_t) * h->seg_rows_h.size());
+  return MOR_OK;
 }
 
 int mor_get_info(mor_t h, int64_t* n, int64_t* nnz, int* format, int* symmetric) {

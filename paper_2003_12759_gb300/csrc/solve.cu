@@ -136,6 +136,8 @@ struct BatchIO {
 static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cplx, const BatchIO& io,
                        mor_solve_stats* stats) {
   OpData& op = h->op(transpose);
+  const SegView& sg = h->seg;
+  const int nseg = sg.nseg;
   const int k = io.k;
   const int64_t n = op.n;
   const int prec = o.precision;
@@ -162,10 +164,21 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
        *t = vec(7), *ph = vec(8), *sh = vec(9), *tmp0 = vec(10), *tmp1 = vec(11);
   MOR_CK(h, h->ws_r64.alloc(es64 * (size_t)n * ld));
   void* r64 = h->ws_r64.p;
-  const int gc = h->grid_cap;
-  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * (size_t)std::max(gc, 2048)));
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * (size_t)std::max(sg.nblocks, 2048)));
   Small sm;
   MOR_TRY(get_small(h, sm));
+  const size_t ksb = krylov_state_bytes(st_in);
+  const size_t nsc = (size_t)nseg * ld;                 // (segment, column) slots
+  MOR_CK(h, h->ws_kstate.alloc(ksb * (size_t)nseg * MOR_LDMAX));
+  void* kstate = h->ws_kstate.p;
+  MOR_CK(h, h->ws_segarr.alloc((sizeof(double) * 2 + sizeof(int) * 2) * (size_t)nseg * MOR_LDMAX));
+  double* d_target = h->ws_segarr.as<double>();
+  double* d_nrm2 = d_target + (size_t)nseg * MOR_LDMAX;
+  int* d_maxit = (int*)(d_nrm2 + (size_t)nseg * MOR_LDMAX);
+  int* d_active = d_maxit + (size_t)nseg * MOR_LDMAX;
+  MOR_CK(h, h->ws_sums.alloc(sizeof(cdouble) * 2 * (size_t)nseg * MOR_LDMAX));
+  cdouble* d_sums = h->ws_sums.as<cdouble>();
+  if ((sizeof(cdouble) * 2 + 64) * nsc > h->pinned_bytes / 2) return mor_fail(h, MOR_EINVAL, "too many systems");
   // coefficients (dummy columns reuse column 0's)
   Coef cf[MOR_LDMAX], ncf[MOR_LDMAX];
   for (int c = 0; c < ld; ++c) {
@@ -180,7 +193,8 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   // Current geometry of the batch.  When enough columns have converged that
   // the live ones fit a narrower stride, the converged columns are flushed
   // to d_full (in the original layout) and the state-carrying vectors
-  // (d, r, r_hat, p, v) are repacked into the free scratch vectors.
+  // (d, r, r_hat, p, v) are repacked into the free scratch vectors (single
+  // system only: with several systems a column lives while any system needs it).
   int ldc = ld;
   std::vector<int> cmap(ld);                 // current column -> original column
   void* d_full = rhs;                        // free after init: collects flushed columns
@@ -203,7 +217,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     for (int f = 0; f < Lmax; ++f) {
       void* dd2 = (f == Lmax - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
       const Factor& F = op.chain[f];
-      int e = launch_factor_spmv(st_in, st_is_cplx(F.st), pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
+      int e = launch_factor_spmv(st_in, st_is_cplx(F.st), sg, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
                                  dd2, sm.done, h->stream);
       if (e) return e;
       s = dd2;
@@ -214,16 +228,16 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     int e;
     void* phat = (Lmax == 0) ? pp : pph;
     void* shat = (Lmax == 0) ? ssv : ssh;
-    if ((e = krylov_launch_update_p(st_in, (int)n, ldc, rr, pp, vv, sm.kstate, sm.done, h->stream))) return e;
+    if ((e = krylov_launch_update_p(st_in, sg, ldc, rr, pp, vv, kstate, sm.done, h->stream))) return e;
     if ((e = chain_apply(pp, pph))) return e;
-    RedArgs ra{RED_DOT_W, rh, h->ws_part.p, sm.counter, FIN_ALPHA, sm.kstate, nullptr, sm.done};
-    if ((e = launch_op_spmv(st_in, pv, ov_in, cfc, ldc, phat, vv, nullptr, &ra, gc, h->stream))) return e;
-    if ((e = krylov_launch_update_s(st_in, (int)n, ldc, rr, vv, ssv, sm.kstate, sm.done, h->stream))) return e;
+    RedArgs ra{RED_DOT_W, rh, h->ws_part.p, nullptr, FIN_ALPHA, kstate, nullptr, sm.done};
+    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, phat, vv, nullptr, &ra, h->stream))) return e;
+    if ((e = krylov_launch_update_s(st_in, sg, ldc, rr, vv, ssv, kstate, sm.done, h->stream))) return e;
     if ((e = chain_apply(ssv, ssh))) return e;
-    RedArgs rb{RED_DOT_TT, ssv, h->ws_part.p, sm.counter, FIN_OMEGA, sm.kstate, nullptr, sm.done};
-    if ((e = launch_op_spmv(st_in, pv, ov_in, cfc, ldc, shat, tt, nullptr, &rb, gc, h->stream))) return e;
-    if ((e = krylov_launch_update_xr(st_in, (int)n, ldc, dd, rr, phat, shat, ssv, tt, rh, h->ws_part.p, sm.counter,
-                                     sm.kstate, sm.done, gc, h->stream)))
+    RedArgs rb{RED_DOT_TT, ssv, h->ws_part.p, nullptr, FIN_OMEGA, kstate, nullptr, sm.done};
+    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, shat, tt, nullptr, &rb, h->stream))) return e;
+    if ((e = krylov_launch_update_xr(st_in, sg, ldc, dd, rr, phat, shat, ssv, tt, rh, h->ws_part.p, kstate, sm.done,
+                                     h->stream)))
       return e;
     return 0;
   };
@@ -254,67 +268,73 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   };
 
   const int max_outer = (prec == MOR_FP64) ? 4 : std::max(1, o.max_refine);
-  std::vector<double> bnorm(k, 0.0), relres(k, 0.0);
-  std::vector<int> iters(k, 0), refs(k, 0), status(k, MOR_OK), act(k, 0);
+  const size_t NK = (size_t)nseg * k;                  // (segment, real column) pairs
+  std::vector<double> bnorm(NK, 0.0), relres(NK, 0.0), rn2(NK, 0.0);
+  std::vector<int> iters(NK, 0), refs(NK, 0), status(NK, MOR_OK), act(NK, 0);
   double* hp = (double*)h->pinned;
-  const size_t ksb = krylov_state_bytes(st_in);
-  std::vector<unsigned char> kst_host(ksb * MOR_LDMAX), kst_new(ksb * MOR_LDMAX);
+  cdouble* h_sums = (cdouble*)hp;                                  // 2 ld per segment
+  double* tg = hp + 4 * nsc;
+  double* nr = tg + nsc;
+  int* mi = (int*)(nr + nsc);
+  int* ac = mi + nsc;
+  std::vector<unsigned char> kst_host(ksb * MOR_LDMAX * std::max(nseg, 1)), kst_new(ksb * MOR_LDMAX);
   for (int pass = 0;; ++pass) {
-    // true residual r64 = b - A(sigma) x64 in FP64 with fused norms
-    RedArgs rn{RED_NORM, nullptr, h->ws_part.p, sm.counter, FIN_NONE, nullptr, sm.sums, nullptr};
-    MOR_CKI(h, launch_op_spmv(st64, pv, ov64, ncf, ld, io.x64, r64, io.b64, &rn, gc, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(hp, sm.sums, sizeof(cdouble) * 2 * ld, cudaMemcpyDeviceToHost, h->stream));
+    // true residual r64 = b - A(sigma) x64 in FP64 with fused norms, per (system, column)
+    RedArgs rn{RED_NORM, nullptr, h->ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
+    MOR_CKI(h, launch_op_spmv(st64, sg, pv, ov64, ncf, ld, io.x64, r64, io.b64, &rn, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(h_sums, d_sums, sizeof(cdouble) * 2 * nsc, cudaMemcpyDeviceToHost, h->stream));
     MOR_CK(h, cudaStreamSynchronize(h->stream));
-    std::vector<double> rn2(k);
-    for (int c = 0; c < k; ++c) rn2[c] = hp[4 * c];
-    if (pass == 0) for (int c = 0; c < k; ++c) bnorm[c] = std::sqrt(rn2[c]);
     int nact = 0;
-    for (int c = 0; c < k; ++c) {
-      relres[c] = bnorm[c] > 0 ? std::sqrt(rn2[c]) / bnorm[c] : 0.0;
-      act[c] = (bnorm[c] > 0 && relres[c] > o.tol && status[c] == MOR_OK && iters[c] < o.maxit &&
-                std::isfinite(relres[c])) ? 1 : 0;
-      nact += act[c];
-    }
-    if (nact == 0 || pass >= max_outer) {
+    for (int sgi = 0; sgi < nseg; ++sgi)
       for (int c = 0; c < k; ++c) {
-        if (!(relres[c] <= o.tol)) {
-          if (status[c] == MOR_OK) status[c] = MOR_ENOCONV;
-        } else status[c] = MOR_OK;
+        const size_t q = (size_t)sgi * k + c;
+        rn2[q] = h_sums[(size_t)sgi * 2 * ld + 2 * c].re;
+        if (pass == 0) bnorm[q] = std::sqrt(rn2[q]);
+        relres[q] = bnorm[q] > 0 ? std::sqrt(rn2[q]) / bnorm[q] : 0.0;
+        act[q] = (bnorm[q] > 0 && relres[q] > o.tol && status[q] == MOR_OK && iters[q] < o.maxit &&
+                  std::isfinite(relres[q])) ? 1 : 0;
+        nact += act[q];
+      }
+    if (nact == 0 || pass >= max_outer) {
+      for (size_t q = 0; q < NK; ++q) {
+        if (!(relres[q] <= o.tol)) {
+          if (status[q] == MOR_OK) status[q] = MOR_ENOCONV;
+        } else status[q] = MOR_OK;
       }
       break;
     }
     // inner targets (dummy columns: inactive)
-    double* tg = hp + 128;
-    int* mi = (int*)(hp + 160);
-    int* ac = (int*)(hp + 192);
-    double* nr = hp + 224;
-    for (int c = 0; c < ld; ++c) {
-      if (c >= k) { tg[c] = 1.0; mi[c] = 0; ac[c] = 0; nr[c] = 0.0; continue; }
-      const double need = act[c] ? o.tol * bnorm[c] / std::sqrt(rn2[c]) : 1.0;
-      tg[c] = (prec == MOR_FP64) ? need : std::max(o.inner_tol, 0.5 * need);
-      mi[c] = act[c] ? std::max(0, o.maxit - iters[c]) : 0;
-      ac[c] = act[c];
-      nr[c] = rn2[c];
-      if (act[c]) refs[c] += 1;
-    }
-    MOR_CK(h, cudaMemcpyAsync(sm.target, tg, sizeof(double) * ld, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(sm.maxit, mi, sizeof(int) * ld, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(sm.active, ac, sizeof(int) * ld, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(sm.nrm2, nr, sizeof(double) * ld, cudaMemcpyHostToDevice, h->stream));
+    for (int sgi = 0; sgi < nseg; ++sgi)
+      for (int c = 0; c < ld; ++c) {
+        const size_t z = (size_t)sgi * ld + c;
+        if (c >= k) { tg[z] = 1.0; mi[z] = 0; ac[z] = 0; nr[z] = 0.0; continue; }
+        const size_t q = (size_t)sgi * k + c;
+        const double need = act[q] ? o.tol * bnorm[q] / std::sqrt(rn2[q]) : 1.0;
+        tg[z] = (prec == MOR_FP64) ? need : std::max(o.inner_tol, 0.5 * need);
+        mi[z] = act[q] ? std::max(0, o.maxit - iters[q]) : 0;
+        ac[z] = act[q];
+        nr[z] = rn2[q];
+        if (act[q]) refs[q] += 1;
+      }
+    MOR_CK(h, cudaMemcpyAsync(d_target, tg, sizeof(double) * nsc, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(d_maxit, mi, sizeof(int) * nsc, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(d_active, ac, sizeof(int) * nsc, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(d_nrm2, nr, sizeof(double) * nsc, cudaMemcpyHostToDevice, h->stream));
     // full geometry for this inner solve
     ldc = ld;
     for (int c = 0; c < ld; ++c) { cmap[c] = c < k ? c : -1; cfc[c] = cf[c]; }
     dd = d; rr = r; rh = rhat; pp = p; vv = v; ssv = sv; tt = t; pph = ph; ssh = sh; t0 = tmp0; t1 = tmp1;
     bool compacted = false;
     MOR_CKI(h, upload_masks());
-    MOR_CKI(h, refine_launch_scale_cast(st_in, (int)n, ld, r64, sm.nrm2, sm.active, rhs, h->stream));
-    MOR_CKI(h, krylov_launch_init(st_in, (int)n, ld, rhs, dd, rr, rh, pp, vv, h->ws_part.p, sm.counter, sm.kstate,
-                                  sm.target, sm.maxit, sm.done, gc, h->stream));
+    MOR_CKI(h, refine_launch_scale_cast(st_in, sg, ld, r64, d_nrm2, d_active, rhs, h->stream));
+    MOR_CKI(h, krylov_launch_init(st_in, sg, ld, rhs, dd, rr, rh, pp, vv, h->ws_part.p, kstate, d_target, d_maxit,
+                                  sm.done, h->stream));
     MOR_TRY(capture());
     int maxrem = 0;
-    for (int c = 0; c < ld; ++c) maxrem = std::max(maxrem, mi[c]);
+    for (size_t z = 0; z < nsc; ++z) maxrem = std::max(maxrem, mi[z]);
     int it = 0;
-    std::vector<int> kit(k, 0), kstat(k, KST_OK);
+    std::vector<int> kit(NK, 0), kstat(NK, KST_OK);
+    int* hd = (int*)(ac + nsc);
     while (it < maxrem) {
       if (gexec) {
         MOR_CK(h, cudaGraphLaunch(gexec, h->stream));
@@ -325,7 +345,13 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
         it += 1;
         if ((it % chunk) != 0 && it < maxrem) continue;
       }
-      MOR_CKI(h, krylov_read_states(kst_host.data(), sm.kstate, ldc, h->stream));
+      if (nseg > 1) {
+        MOR_CK(h, cudaMemcpyAsync(hd, sm.done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        MOR_CK(h, cudaStreamSynchronize(h->stream));
+        if (*hd) break;
+        continue;
+      }
+      MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, ldc, h->stream));
       int nlive = 0;
       for (int c = 0; c < ldc; ++c) nlive += krylov_state_active(kst_host.data() + ksb * c) ? 1 : 0;
       if (nlive == 0) break;
@@ -373,20 +399,22 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
       }
       cmap = nmap;
       ldc = ld_new;
-      MOR_CKI(h, krylov_write_state(kst_new.data(), sm.kstate, ldc, h->stream));
+      MOR_CKI(h, krylov_write_state(kst_new.data(), kstate, ldc, h->stream));
       MOR_CKI(h, upload_masks());
       compacted = true;
       MOR_TRY(capture());
     }
-    // final per-column state of this inner solve
-    MOR_CKI(h, krylov_read_states(kst_host.data(), sm.kstate, ldc, h->stream));
-    for (int c = 0; c < ldc; ++c) {
-      const int oc = cmap[c];
-      if (oc >= 0 && oc < k) {
-        kit[oc] = krylov_state_iters(kst_host.data() + ksb * c);
-        kstat[oc] = krylov_state_status(kst_host.data() + ksb * c);
+    // final per-(system, column) state of this inner solve
+    MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, nseg * ldc, h->stream));
+    for (int sgi = 0; sgi < nseg; ++sgi)
+      for (int c = 0; c < ldc; ++c) {
+        const int oc = cmap[c];
+        if (oc >= 0 && oc < k) {
+          const unsigned char* ks = kst_host.data() + ksb * ((size_t)sgi * ldc + c);
+          kit[(size_t)sgi * k + oc] = krylov_state_iters(ks);
+          kstat[(size_t)sgi * k + oc] = krylov_state_status(ks);
+        }
       }
-    }
     void* dres = dd;
     if (compacted) {
       // collect the remaining columns into d_full (original layout)
@@ -400,23 +428,24 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
         MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, nrem, dmaps, dmaps + MOR_LDMAX, dd, d_full, h->stream));
       dres = d_full;
     }
-    for (int c = 0; c < k; ++c) {
-      if (!act[c]) continue;
-      iters[c] += kit[c];
-      if (kstat[c] == KST_BREAKDOWN && pass + 1 >= max_outer) status[c] = MOR_EBREAKDOWN;
+    for (size_t q = 0; q < NK; ++q) {
+      if (!act[q]) continue;
+      iters[q] += kit[q];
+      if (kstat[q] == KST_BREAKDOWN && pass + 1 >= max_outer) status[q] = MOR_EBREAKDOWN;
     }
-    MOR_CKI(h, refine_launch_update(st_in, (int)n, ld, io.x64, dres, sm.nrm2, sm.active, h->stream));
+    MOR_CKI(h, refine_launch_update(st_in, sg, ld, io.x64, dres, d_nrm2, d_active, h->stream));
   }
+  // per-column statistics: with several systems, stats has nseg x k entries
   if (stats)
-    for (int c = 0; c < k; ++c) {
-      stats[c].iters = iters[c];
-      stats[c].refinements = refs[c];
-      stats[c].relres = relres[c];
-      stats[c].status = status[c];
+    for (size_t q = 0; q < NK; ++q) {
+      stats[q].iters = iters[q];
+      stats[q].refinements = refs[q];
+      stats[q].relres = relres[q];
+      stats[q].status = status[q];
     }
   int worst = MOR_OK;
-  for (int c = 0; c < k; ++c)
-    if (status[c] != MOR_OK) worst = (worst == MOR_OK || status[c] == MOR_EBREAKDOWN) ? status[c] : worst;
+  for (size_t q = 0; q < NK; ++q)
+    if (status[q] != MOR_OK) worst = (worst == MOR_OK || status[q] == MOR_EBREAKDOWN) ? status[q] : worst;
   if (worst != MOR_OK) return mor_fail(h, worst, "%s in at least one column", worst == MOR_EBREAKDOWN ? "breakdown" : "no convergence");
   return MOR_OK;
 }
@@ -453,7 +482,12 @@ static int solve_many(mor_t h, const mor_c64* sig, int k, int transpose, const m
       MOR_CKI(h, conv_launch_real_col_to_rowmajor(st64, (int)n, kc, ld, col0, 0, h->ws_b64.p, h->stream));
     }
     BatchIO io{sig + c0, kc, ld, L.data() + c0, h->ws_b64.p, xrow};
-    int s = solve_batch(h, transpose, o, cplx, io, stats ? stats + c0 : nullptr);
+    const int nseg = h->seg.nseg;
+    std::vector<mor_solve_stats> sb((size_t)nseg * kc);
+    int s = solve_batch(h, transpose, o, cplx, io, sb.data());
+    if (stats)   // stats has nseg x k entries: [seg * k + c]
+      for (int sgi = 0; sgi < nseg; ++sgi)
+        for (int c = 0; c < kc; ++c) stats[(size_t)sgi * k + c0 + c] = sb[(size_t)sgi * kc + c];
     if (s != MOR_OK && s != MOR_ENOCONV && s != MOR_EBREAKDOWN) return s;
     if (s != MOR_OK) ret = s;
     if (X) {
@@ -525,8 +559,8 @@ static int project_device(mor_t h, const double* V, const double* W, int r, mor_
   OpVals ov = op_vals(h, op, false);
   Coef ca{0, 0, 1, 0}, ce{1, 0, 0, 0};
   for (int j = 0; j < r; ++j) {
-    MOR_CKI(h, launch_op_spmv(ST_F64, pv, ov, &ca, 1, V + (size_t)j * n, AV + (size_t)j * n, nullptr, nullptr, h->grid_cap, h->stream));
-    MOR_CKI(h, launch_op_spmv(ST_F64, pv, ov, &ce, 1, V + (size_t)j * n, EV + (size_t)j * n, nullptr, nullptr, h->grid_cap, h->stream));
+    MOR_CKI(h, launch_op_spmv(ST_F64, h->seg, pv, ov, &ca, 1, V + (size_t)j * n, AV + (size_t)j * n, nullptr, nullptr, h->stream));
+    MOR_CKI(h, launch_op_spmv(ST_F64, h->seg, pv, ov, &ce, 1, V + (size_t)j * n, EV + (size_t)j * n, nullptr, nullptr, h->stream));
   }
   MOR_CK(h, h->ws_rom.alloc(sizeof(double) * 6 * MOR_MAX_R * MOR_MAX_R));
   double* dAr = h->ws_rom.as<double>();
@@ -662,8 +696,8 @@ int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int 
   MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st, (int)n, k, ld, src, xr, h->stream));
   Coef cf[MOR_LDMAX];
   for (int c = 0; c < ld; ++c) cf[c] = mor_coef(h, sigma[c < k ? c : 0]);
-  MOR_CKI(h, launch_op_spmv(st, op.view(), op_vals(h, op, precision != MOR_FP64), cf, ld, xr, yr, nullptr,
-                            nullptr, h->grid_cap, h->stream));
+  MOR_CKI(h, launch_op_spmv(st, h->seg, op.view(), op_vals(h, op, precision != MOR_FP64), cf, ld, xr, yr, nullptr,
+                            nullptr, h->stream));
   if (dev) {
     MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, ld, yr, Y, h->stream));
   } else {
@@ -709,7 +743,7 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   char* s = a;
   char* d = b;
   for (int f = 0; f < Lmax; ++f) {
-    MOR_CKI(h, launch_factor_spmv(st, st_is_cplx(op.chain[f].st), op.view(), op.chain[f].vals->p,
+    MOR_CKI(h, launch_factor_spmv(st, st_is_cplx(op.chain[f].st), h->seg, op.view(), op.chain[f].vals->p,
                                   sm.masks + (size_t)f * MOR_KMAX, ld, s, d, nullptr, h->stream));
     std::swap(s, d);
   }
@@ -744,6 +778,7 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
   }
   bool anyc = rc;
   for (int c = 0; c < k; ++c) anyc |= !is_real_shift(sigma[c]);
+  if (o.precond == 1 && h->seg.nseg != 1) return mor_fail(h, MOR_EINVAL, "a fresh SPAI per shift needs a single system");
   if (o.precond == 1) {
     // a new SPAI per shift: one column at a time
     int ret = MOR_OK;
@@ -762,7 +797,48 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
   if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision)
     return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from opts.precision");
   bool cc = anyc || chain_cplx(op, L);
-  return solve_many(h, sigma, k, transpose, o, L, cc, R, dev, X, stats);
+  const int nseg = h->seg.nseg;
+  if (nseg == 1 || !stats) return solve_many(h, sigma, k, transpose, o, L, cc, R, dev, X, stats);
+  // several systems: report, per shift, the worst over the systems
+  std::vector<mor_solve_stats> all((size_t)nseg * k);
+  int ret = solve_many(h, sigma, k, transpose, o, L, cc, R, dev, X, all.data());
+  for (int c = 0; c < k; ++c) {
+    mor_solve_stats a = all[c];
+    for (int sgi = 1; sgi < nseg; ++sgi) {
+      const mor_solve_stats& b = all[(size_t)sgi * k + c];
+      a.iters = std::max(a.iters, b.iters);
+      a.refinements = std::max(a.refinements, b.refinements);
+      a.relres = std::max(a.relres, b.relres);
+      if (b.status != MOR_OK) a.status = b.status;
+    }
+    stats[c] = a;
+  }
+  return ret;
+}
+
+int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const mor_solve_opts* opts, mor_c64* X,
+                    mor_solve_stats* stats, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (k < 1 || k > 64 || !sigma || !X) return mor_fail(h, MOR_EINVAL, "bad arguments (1 <= k <= 64)");
+  mor_solve_opts o;
+  if (opts) o = *opts; else mor_default_opts(&o);
+  if (o.precision != MOR_FP64 && o.precision != MOR_MIXED) return mor_fail(h, MOR_EINVAL, "bad precision");
+  if (!(o.tol > 0) || o.maxit < 0) return mor_fail(h, MOR_EINVAL, "bad tolerance or maxit");
+  if (o.precond == 1) return mor_fail(h, MOR_EINVAL, "mor_batch_solve: build the preconditioner with mor_build_precond");
+  for (int c = 0; c < k; ++c)
+    if (!std::isfinite(sigma[c].re) || !std::isfinite(sigma[c].im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
+  cudaSetDevice(h->dev);
+  OpData& op = h->op(transpose);
+  std::vector<int> L = (o.precond == 2) ? std::vector<int>(k, 0) : prefix_lengths(op, sigma, k);
+  if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision)
+    return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from opts.precision");
+  bool cc = chain_cplx(op, L);
+  for (int c = 0; c < k; ++c) cc |= !is_real_shift(sigma[c]);
+  std::vector<mor_solve_stats> all((size_t)h->seg.nseg * k);
+  int ret = solve_many(h, sigma, k, transpose, o, L, cc, nullptr, (flags & MOR_DEVICE_PTRS) != 0, X, all.data());
+  if (stats) std::memcpy(stats, all.data(), sizeof(mor_solve_stats) * all.size());
+  return ret;
 }
 
 int mor_orthonormalize(mor_t h, double* X, int k, unsigned flags) {
@@ -828,6 +904,7 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
   if (h->order != 1) return mor_fail(h, MOR_EINVAL, "IRKA of second-order systems is not available");
   if (r < 1 || r > MOR_MAX_R || !shifts) return mor_fail(h, MOR_EINVAL, "bad r");
   if (h->m != 1 || h->q != 1) return mor_fail(h, MOR_EINVAL, "mor_irka_step supports SISO systems (m = q = 1)");
+  if (h->seg.nseg != 1) return mor_fail(h, MOR_EINVAL, "mor_irka_step needs a single system, not a batch");
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
   cudaSetDevice(h->dev);
@@ -1000,17 +1077,18 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
   MOR_CK(h, cudaMemsetAsync(w.p, 0, st_size(st) * (size_t)n * ld, h->stream));
   Small sm;
   MOR_TRY(get_small(h, sm));
-  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * (size_t)std::max(h->grid_cap, 2048)));
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * (size_t)std::max(h->seg.nblocks, 2048)));
   std::vector<int> ones(MOR_KMAX, 1);
   MOR_CK(h, cudaMemcpyAsync(sm.masks, ones.data(), sizeof(int) * MOR_KMAX, cudaMemcpyHostToDevice, h->stream));
   Coef cf[MOR_LDMAX];
   for (int c = 0; c < ld; ++c) cf[c] = mor_coef(h, sigma[c < k ? c : 0]);
   PatView pv = op.view();
   OpVals ov = op_vals(h, op, st_is_f32(st));
-  RedArgs ra{RED_DOT_W, w.p, h->ws_part.p, sm.counter, FIN_NONE, nullptr, sm.sums, nullptr};
+  MOR_CK(h, h->ws_sums.alloc(sizeof(cdouble) * 2 * (size_t)h->seg.nseg * MOR_LDMAX));
+  RedArgs ra{RED_DOT_W, w.p, h->ws_part.p, nullptr, FIN_NONE, nullptr, h->ws_sums.p, nullptr};
   auto launch = [&]() -> int {
-    if (which == 0) return launch_op_spmv(st, pv, ov, cf, ld, x.p, y.p, nullptr, &ra, h->grid_cap, h->stream);
-    return launch_factor_spmv(st, st_is_cplx(op.chain.back().st), pv, op.chain.back().vals->p, sm.masks, ld,
+    if (which == 0) return launch_op_spmv(st, h->seg, pv, ov, cf, ld, x.p, y.p, nullptr, &ra, h->stream);
+    return launch_factor_spmv(st, st_is_cplx(op.chain.back().st), h->seg, pv, op.chain.back().vals->p, sm.masks, ld,
                               x.p, y.p, nullptr, h->stream);
   };
   for (int i = 0; i < 3; ++i) MOR_CKI(h, launch());

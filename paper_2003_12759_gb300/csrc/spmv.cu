@@ -26,6 +26,13 @@ namespace {
 
 template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 
+// nonzeros of a row gathered per chunk: up to 8 (a 7-point row in one chunk),
+// fewer when a lane's slice of a row is wide, to keep the gathers in registers
+template <typename S, int CPT> constexpr int gather_chunk() {
+  constexpr int b = (int)(CPT * sizeof(S));
+  return b <= 16 ? 8 : (b <= 32 ? 4 : 1);
+}
+
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
 
 // [p0, p1) and step of row r in the stored layout
@@ -47,7 +54,7 @@ __device__ __forceinline__ void row_range(const PatView& pv, int64_t r, int64_t&
 // fused per-column reduction.  TPR lanes per row, lane `sub` owns the CPT
 // columns sub * CPT ... sub * CPT + CPT - 1 of the n x ld blocks.
 template <typename S, int TPR, int CPT>
-__global__ void __launch_bounds__(256) op_spmv_kernel(PatView pv, OpVals ov, CoefS<S> cf, int ld,
+__global__ void __launch_bounds__(256) op_spmv_kernel(SegView sg, PatView pv, OpVals ov, CoefS<S> cf, int ld,
                                                       const S* __restrict__ x, S* __restrict__ y,
                                                       const S* __restrict__ bv, RedArgs red) {
   typedef typename real_of<S>::type R;
@@ -71,8 +78,9 @@ __global__ void __launch_bounds__(256) op_spmv_kernel(PatView pv, OpVals ov, Coe
     v1[j] = zero_<S>();
   }
   const int rpb = blockDim.x / TPR;
+  const int seg = seg_of_chunk(sg, blockIdx.x);
   int64_t rb, re;
-  block_rows(pv.n, rpb, rb, re);
+  chunk_rows(sg, seg, blockIdx.x, rb, re);
   if (act) {
     for (int64_t r = rb + threadIdx.x / TPR; r < re; r += rpb) {
       int64_t p0, p1;
@@ -128,13 +136,13 @@ __global__ void __launch_bounds__(256) op_spmv_kernel(PatView pv, OpVals ov, Coe
     }
   }
   if (red.mode != RED_NONE)
-    col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, (double*)red.part, red.counter, red.fin, (KState*)red.state,
+    col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, sg, seg, blockIdx.x, (double*)red.part, red.fin, (KState*)red.state,
                                      (cdouble*)red.out, (int*)red.done);
 }
 
 // Y(:, c) = F X(:, c) where the factor applies to column c, else Y(:, c) = X(:, c).
 template <typename S, typename V, int TPR, int CPT>
-__global__ void __launch_bounds__(256) factor_spmv_kernel(PatView pv, const V* __restrict__ f,
+__global__ void __launch_bounds__(256) factor_spmv_kernel(SegView sg, PatView pv, const V* __restrict__ f,
                                                           const int* __restrict__ apply, int ld,
                                                           const S* __restrict__ x, S* __restrict__ y,
                                                           const int* done) {
@@ -148,7 +156,7 @@ __global__ void __launch_bounds__(256) factor_spmv_kernel(PatView pv, const V* _
   for (int j = 0; j < CPT; ++j) { ap[j] = apply[c0 + j]; any |= (ap[j] != 0); }
   const int rpb = blockDim.x / TPR;
   int64_t rb, re;
-  block_rows(pv.n, rpb, rb, re);
+  chunk_rows(sg, seg_of_chunk(sg, blockIdx.x), blockIdx.x, rb, re);
   for (int64_t r = rb + threadIdx.x / TPR; r < re; r += rpb) {
     const int64_t q = r * ld + c0;
     const Pack<S, CPT> xo = ldp<S, CPT>(x + q);
@@ -159,16 +167,31 @@ __global__ void __launch_bounds__(256) factor_spmv_kernel(PatView pv, const V* _
       int64_t p0, p1;
       int step;
       row_range(pv, r, p0, p1, step);
-#pragma unroll 4
-      for (int64_t p = p0; p < p1; p += step) {
-        const int cc = __ldg(pv.col + p);
-        const V fv = f[p];
-        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+      // chunks of GCH nonzeros: all indices and values first, then every gather in flight
+      constexpr int GCH = gather_chunk<S, CPT>();
+      for (int64_t pc = p0; pc < p1; pc += GCH * step) {
+        int cc[GCH];
+        V fv[GCH];
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-          if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv, xv.v[j]);
-          else fma_r(acc.v[j], fv, xv.v[j]);
+        for (int u = 0; u < GCH; ++u) {
+          const int64_t pu = pc + u * step;
+          const bool ok = pu < p1;
+          cc[u] = ok ? __ldg(pv.col + pu) : -1;
+          fv[u] = ok ? f[pu] : V(0);
         }
+        Pack<S, CPT> xv[GCH];
+#pragma unroll
+        for (int u = 0; u < GCH; ++u)
+          if (cc[u] >= 0) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+#pragma unroll
+        for (int u = 0; u < GCH; ++u)
+          if (cc[u] >= 0) {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+              if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
+              else fma_r(acc.v[j], fv[u], xv[u].v[j]);
+            }
+          }
       }
     }
 #pragma unroll
@@ -177,25 +200,16 @@ __global__ void __launch_bounds__(256) factor_spmv_kernel(PatView pv, const V* _
   }
 }
 
-inline int64_t blocks_for(int64_t n, int ld, int st, int cap) {
-  int tpr, cpt;
-  lane_shape(st, ld, &tpr, &cpt);
-  int64_t b = (n * tpr + 255) / 256;
-  if (cap > 0 && b > cap) b = cap;
-  return b < 1 ? 1 : b;
-}
-
 }  // namespace
 
-int launch_op_spmv(int st, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
-                   const void* x, void* y, const void* b, const RedArgs* red, int grid_cap,
-                   cudaStream_t s) {
+int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
+                   const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
   RedArgs ra;
   if (red) ra = *red;
   else { ra.mode = RED_NONE; ra.w = nullptr; ra.part = nullptr; ra.counter = nullptr; ra.fin = 0;
          ra.state = nullptr; ra.out = nullptr; ra.done = nullptr; }
-  const int64_t blocks = blocks_for(pv.n, ld, st, grid_cap > 0 ? grid_cap : 152 * 8);
+  const unsigned blocks = (unsigned)sg.nblocks;
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
     CoefS<S> cf;
     for (int c = 0; c < MOR_LDMAX; ++c) {
@@ -209,8 +223,7 @@ int launch_op_spmv(int st, const PatView& pv, const OpVals& ov, const Coef* coef
         cf.sA[c] = (S)q.sAr;
       }
     }
-    op_spmv_kernel<S, TPR, CPT><<<(unsigned)blocks, 256, 0, s>>>(pv, ov, cf, ld, (const S*)x, (S*)y,
-                                                                 (const S*)b, ra);
+    op_spmv_kernel<S, TPR, CPT><<<blocks, 256, 0, s>>>(sg, pv, ov, cf, ld, (const S*)x, (S*)y, (const S*)b, ra);
     return 0;
   });
   if (e) return e;
@@ -218,23 +231,23 @@ int launch_op_spmv(int st, const PatView& pv, const OpVals& ov, const Coef* coef
   return (int)cudaGetLastError();
 }
 
-int launch_factor_spmv(int st, bool fcplx, const PatView& pv, const void* fvals, const int* apply, int ld,
-                       const void* x, void* y, const int* done, cudaStream_t s) {
+int launch_factor_spmv(int st, bool fcplx, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
+                       int ld, const void* x, void* y, const int* done, cudaStream_t s) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
-  const int64_t blocks = blocks_for(pv.n, ld, st, 152 * 8);
+  const unsigned blocks = (unsigned)sg.nblocks;
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
     typedef typename real_of<S>::type R;
     if constexpr (is_cplx<S>::value) {
       if (fcplx)
-        factor_spmv_kernel<S, S, TPR, CPT><<<(unsigned)blocks, 256, 0, s>>>(pv, (const S*)fvals, apply, ld,
-                                                                            (const S*)x, (S*)y, done);
+        factor_spmv_kernel<S, S, TPR, CPT><<<blocks, 256, 0, s>>>(sg, pv, (const S*)fvals, apply, ld,
+                                                                  (const S*)x, (S*)y, done);
       else
-        factor_spmv_kernel<S, R, TPR, CPT><<<(unsigned)blocks, 256, 0, s>>>(pv, (const R*)fvals, apply, ld,
-                                                                            (const S*)x, (S*)y, done);
+        factor_spmv_kernel<S, R, TPR, CPT><<<blocks, 256, 0, s>>>(sg, pv, (const R*)fvals, apply, ld,
+                                                                  (const S*)x, (S*)y, done);
     } else {
       if (fcplx) return (int)cudaErrorInvalidValue;
-      factor_spmv_kernel<S, S, TPR, CPT><<<(unsigned)blocks, 256, 0, s>>>(pv, (const S*)fvals, apply, ld,
-                                                                          (const S*)x, (S*)y, done);
+      factor_spmv_kernel<S, S, TPR, CPT><<<blocks, 256, 0, s>>>(sg, pv, (const S*)fvals, apply, ld,
+                                                                (const S*)x, (S*)y, done);
     }
     return 0;
   });
