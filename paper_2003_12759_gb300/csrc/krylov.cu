@@ -19,6 +19,10 @@
 
 #include "shape_dispatch.cuh"
 
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
 namespace {
 
 template <typename S> __device__ __forceinline__ S from_cd(cdouble z);
@@ -302,10 +306,35 @@ __global__ void scatter_cols_kernel(int64_t n, int ld_src, int ld_dst, int ncols
 
 size_t krylov_state_bytes(int) { return sizeof(KState); }
 
+SegView fit_grid(const SegView& sg, const void* kern, int tpr) {
+  if (sg.nseg != 1) return sg;
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> occ_cache;
+  int occ = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = occ_cache.find(kern);
+    if (it != occ_cache.end()) occ = it->second;
+  }
+  if (occ <= 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+    std::lock_guard<std::mutex> lk(mu);
+    occ_cache[kern] = occ;
+  }
+  const int64_t pass = 256 / tpr;
+  const int64_t passes = (sg.nrows + pass - 1) / pass;
+  int64_t grid = std::min<int64_t>((int64_t)sg.sms * occ, std::max<int64_t>(passes, 1));
+  const int64_t ppb = (passes + grid - 1) / grid;   // passes per block
+  SegView g = sg;
+  g.rows_per_block = std::max<int64_t>(ppb, 1) * pass;
+  g.nblocks = (int)std::max<int64_t>((sg.nrows + g.rows_per_block - 1) / g.rows_per_block, 1);
+  return g;
+}
+
 int krylov_launch_update_p(int st, const SegView& sg, int ld, const void* r, void* p, const void* v, const void* state,
                            const int* done, cudaStream_t s) {
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    update_p_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (const S*)r, (S*)p, (const S*)v,
+    const SegView g = fit_grid(sg, (const void*)update_p_kernel<S, TPR, CPT>, TPR); update_p_kernel<S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, ld, (const S*)r, (S*)p, (const S*)v,
                                                             (const KState*)state, done);
     return 0;
   });
@@ -317,7 +346,7 @@ int krylov_launch_update_p(int st, const SegView& sg, int ld, const void* r, voi
 int krylov_launch_update_s(int st, const SegView& sg, int ld, const void* r, const void* v, void* sv, const void* state,
                            const int* done, cudaStream_t s) {
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    update_s_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (const S*)r, (const S*)v, (S*)sv,
+    const SegView g = fit_grid(sg, (const void*)update_s_kernel<S, TPR, CPT>, TPR); update_s_kernel<S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, ld, (const S*)r, (const S*)v, (S*)sv,
                                                             (const KState*)state, done);
     return 0;
   });
@@ -330,7 +359,7 @@ int krylov_launch_update_xr(int st, const SegView& sg, int ld, void* x, void* r,
                             const void* sv, const void* t, const void* rhat, void* part, void* state, int* done,
                             cudaStream_t s) {
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    update_xr_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (S*)x, (S*)r, (const S*)phat, (const S*)shat,
+    const SegView g = fit_grid(sg, (const void*)update_xr_kernel<S, TPR, CPT>, TPR); update_xr_kernel<S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, ld, (S*)x, (S*)r, (const S*)phat, (const S*)shat,
                                                              (const S*)sv, (const S*)t, (const S*)rhat, (double*)part,
                                                              (KState*)state, done);
     return 0;
@@ -349,7 +378,7 @@ int krylov_launch_init(int st, const SegView& sg, int ld, const void* rhs, void*
   cudaError_t ce = cudaMemsetAsync(sg.live, 0, sizeof(int), s);
   if (ce != cudaSuccess) return (int)ce;
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    init_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (const S*)rhs, (S*)x, (S*)r, (S*)rhat, (S*)p, (S*)v,
+    const SegView g = fit_grid(sg, (const void*)init_kernel<S, TPR, CPT>, TPR); init_kernel<S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, ld, (const S*)rhs, (S*)x, (S*)r, (S*)rhat, (S*)p, (S*)v,
                                                         (double*)part, (KState*)state, done);
     return 0;
   });
@@ -375,7 +404,7 @@ int refine_launch_scale_cast(int st_in, const SegView& sg, int ld, const void* r
                              void* rhs_in, cudaStream_t s) {
   int e = dispatch_shape(st_in, ld, [&]<typename S, int TPR, int CPT>() -> int {
     typedef typename wide_of<S>::type W;
-    scale_cast_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (const W*)r64, nrm2, active, (S*)rhs_in);
+    const SegView g = fit_grid(sg, (const void*)scale_cast_kernel<S, TPR, CPT>, TPR); scale_cast_kernel<S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, ld, (const W*)r64, nrm2, active, (S*)rhs_in);
     return 0;
   });
   if (e) return e;
@@ -387,7 +416,7 @@ int refine_launch_update(int st_in, const SegView& sg, int ld, void* x64, const 
                          const int* active, cudaStream_t s) {
   int e = dispatch_shape(st_in, ld, [&]<typename S, int TPR, int CPT>() -> int {
     typedef typename wide_of<S>::type W;
-    refine_update_kernel<S, TPR, CPT><<<sg.nblocks, 256, 0, s>>>(sg, ld, (W*)x64, (const S*)d, nrm2, active);
+    const SegView g = fit_grid(sg, (const void*)refine_update_kernel<S, TPR, CPT>, TPR); refine_update_kernel<S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, ld, (W*)x64, (const S*)d, nrm2, active);
     return 0;
   });
   if (e) return e;

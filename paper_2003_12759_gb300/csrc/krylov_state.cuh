@@ -118,6 +118,7 @@ __device__ __forceinline__ void stp(S* p, const Pack<S, CPT>& o) {
 // persistent: a resident wave of blocks walks the chunks b = blockIdx.x,
 // blockIdx.x + gridDim.x, ... of the segment table.
 __device__ __forceinline__ int seg_of_chunk(const SegView& sg, int b) {
+  if (sg.nseg == 1) return 0;
   int lo = 0, hi = sg.nseg - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -126,9 +127,56 @@ __device__ __forceinline__ int seg_of_chunk(const SegView& sg, int b) {
   return lo;
 }
 __device__ __forceinline__ void chunk_rows(const SegView& sg, int s, int b, int64_t& r0, int64_t& r1) {
+  if (sg.nseg == 1) {
+    r0 = (int64_t)b * sg.rows_per_block;
+    r1 = r0 + sg.rows_per_block < sg.nrows ? r0 + sg.rows_per_block : sg.nrows;
+    return;
+  }
   r0 = sg.row0[s] + (int64_t)(b - sg.blk0[s]) * sg.rows_per_block;
   const int64_t e = r0 + sg.rows_per_block;
   r1 = e < sg.row0[s + 1] ? e : sg.row0[s + 1];
+}
+
+// The block that finishes a segment's last chunk: sum the segment's chunk
+// partials in a fixed order and run the finalize stage.  Kept out of line: it
+// runs once per segment and launch, so its register needs must not raise the
+// allocation (and lower the residency) of the streaming kernels that call it.
+static __device__ __noinline__ void seg_finalize(int ld, const SegView& sg, int seg, int b0s, int b1s, double* part, int fin,
+                                          KState* state, cdouble* out, int* done) {
+  __shared__ __align__(16) double sums_raw[2 * MOR_LDMAX_DEV * 2];
+  cdouble* sums = reinterpret_cast<cdouble*>(sums_raw);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int nv = 2 * ld;
+  __threadfence();
+  // warp w sums values w, w + nwarps, ... over the segment's chunks
+  const volatile double* vp = part;
+  for (int i = wid; i < nv; i += nwarps) {
+    double re = 0.0, im = 0.0;
+    for (int blk = b0s + lane; blk < b1s; blk += 32) {
+      re += vp[((size_t)blk * nv + i) * 2 + 0];
+      im += vp[((size_t)blk * nv + i) * 2 + 1];
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) sums[i] = cdouble(re, im);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (fin != FIN_NONE) {
+      KState* st = state + (size_t)seg * ld;
+      const int was = (fin == FIN_INIT) ? 0 : krylov_any_active(ld, st);
+      const int now = krylov_finalize(fin, ld, sums, st);
+      if (fin == FIN_INIT) {
+        if (now) atomicAdd(sg.live, 1);
+      } else if (was && !now) {
+        if (atomicSub(sg.live, 1) == 1 && done) *done = 1;
+      }
+    } else if (out) {
+      for (int i = 0; i < nv; ++i) out[(size_t)seg * nv + i] = sums[i];
+    }
+    sg.counters[seg] = 0u;   // ready for the next launch (stream order makes this safe)
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -147,7 +195,6 @@ __device__ inline void col_reduce_finalize(const S (&v0)[CPT], const S (&v1)[CPT
   typedef typename real_of<S>::type R;
   __shared__ double sh[8][2 * MOR_LDMAX_DEV][2];
   __shared__ bool am_last;
-  __shared__ cdouble sums[2 * MOR_LDMAX_DEV];
   __syncthreads();   // the shared buffers are reused chunk after chunk
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -179,37 +226,10 @@ __device__ inline void col_reduce_finalize(const S (&v0)[CPT], const S (&v1)[CPT
   }
   __threadfence();
   __syncthreads();
-  const int b0s = sg.blk0[seg], b1s = sg.blk0[seg + 1];
+  const int b0s = sg.nseg == 1 ? 0 : sg.blk0[seg];
+  const int b1s = sg.nseg == 1 ? sg.nblocks : sg.blk0[seg + 1];
   if (threadIdx.x == 0) am_last = (atomicAdd(sg.counters + seg, 1u) == (unsigned)(b1s - b0s - 1));
   __syncthreads();
   if (!am_last) return;
-  __threadfence();
-  // last chunk of the segment: warp w sums values w, w + nwarps, ... over the segment's chunks
-  const volatile double* vp = part;
-  for (int i = wid; i < nv; i += nwarps) {
-    double re = 0.0, im = 0.0;
-    for (int blk = b0s + lane; blk < b1s; blk += 32) {
-      re += vp[((size_t)blk * nv + i) * 2 + 0];
-      im += vp[((size_t)blk * nv + i) * 2 + 1];
-    }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if (lane == 0) sums[i] = cdouble(re, im);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (fin != FIN_NONE) {
-      KState* st = state + (size_t)seg * ld;
-      const int was = (fin == FIN_INIT) ? 0 : krylov_any_active(ld, st);
-      const int now = krylov_finalize(fin, ld, sums, st);
-      if (fin == FIN_INIT) {
-        if (now) atomicAdd(sg.live, 1);
-      } else if (was && !now) {
-        if (atomicSub(sg.live, 1) == 1 && done) *done = 1;
-      }
-    } else if (out) {
-      for (int i = 0; i < nv; ++i) out[(size_t)seg * nv + i] = sums[i];
-    }
-    sg.counters[seg] = 0u;   // ready for the next launch (stream order makes this safe)
-  }
+  seg_finalize(ld, sg, seg, b0s, b1s, part, fin, state, out, done);
 }

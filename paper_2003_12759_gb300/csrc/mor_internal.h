@@ -94,6 +94,8 @@ struct SegView {
   int nseg;
   int nblocks;
   int64_t rows_per_block;
+  int64_t nrows;           // total rows (row0[nseg])
+  int sms;                 // SMs of the device
   const int* blk0;         // nseg + 1
   const int64_t* row0;     // nseg + 1
   unsigned* counters;      // nseg, zero between launches
@@ -113,6 +115,12 @@ struct RedArgs {
   void* out;           // reduced sums (nseg x 2 ld complex doubles), when fin == 0
   const int* done;     // if non-null and *done != 0 the kernel returns at once
 };
+
+// Grid of one launch.  A single system (nseg == 1) is split into one resident
+// wave of the kernel `kern` (blocks of 256 threads, occupancy queried once per
+// kernel), each block a contiguous range of whole passes of 256 / tpr rows;
+// a batch keeps the segment table's blocks (krylov.cu).
+SegView fit_grid(const SegView& sg, const void* kern, int tpr);
 
 // Launchers (spmv.cu).  x, y, w, b: n x ld row-major blocks of type st.
 int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,

@@ -55,7 +55,7 @@ int mor_build_segments(mor_t h, const std::vector<int64_t>& rows) {
   const int64_t N = rows[nseg];
   // blocks of 256 threads per SM in total: a whole number of resident waves
   // for the solve kernels (override: MOR_SEG_BLOCKS_PER_SM)
-  int bps = nseg == 1 ? 8 : 12;
+  int bps = nseg == 1 ? 4 : 12;
   if (const char* ev = std::getenv("MOR_SEG_BLOCKS_PER_SM")) {
     const int v = std::atoi(ev);
     if (v >= 1 && v <= 64) bps = v;
@@ -80,6 +80,8 @@ int mor_build_segments(mor_t h, const std::vector<int64_t>& rows) {
   h->seg.nseg = nseg;
   h->seg.nblocks = blk0[nseg];
   h->seg.rows_per_block = R;
+  h->seg.nrows = N;
+  h->seg.sms = h->sm_count;
   h->seg.blk0 = h->seg_blk0.as<int>();
   h->seg.row0 = h->seg_row0.as<int64_t>();
   h->seg.counters = h->seg_counters.as<unsigned>();
@@ -286,6 +288,8 @@ int build_op(mor_t h, OpData& op, const HostCSR& S, const std::vector<double>& s
   if (fmt == FMT_SELL) {
     sell_layout(S, sptr, scol, op.h_lay);
     op.nlay = (int64_t)scol.size();
+    // the kernels index stored entries with 32-bit positions
+    if (op.nlay > (int64_t)INT32_MAX) return mor_fail(h, MOR_EINVAL, "SELL layout exceeds 2^31 stored entries");
   } else {
     op.h_lay.resize(op.nnz);
     for (int64_t p = 0; p < op.nnz; ++p) op.h_lay[p] = p;
@@ -393,8 +397,8 @@ int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std:
     int st1 = 0, st2 = 0;
     MOR_TRY(build_op(h, h->P, S, sa, se, FMT_CSR, Ecsr != nullptr));
     double tc = time_op(h, h->P, st1);
-    MOR_TRY(build_op(h, h->P, S, sa, se, FMT_SELL, Ecsr != nullptr));
-    double ts = time_op(h, h->P, st2);
+    double ts = 1e300;
+    if (build_op(h, h->P, S, sa, se, FMT_SELL, Ecsr != nullptr) == MOR_OK) ts = time_op(h, h->P, st2);
     if (st1 != MOR_OK || st2 != MOR_OK) return mor_fail(h, MOR_ECUDA, "format autotuning failed");
     fmt = (ts <= tc) ? FMT_SELL : FMT_CSR;
     if (fmt == FMT_CSR) MOR_TRY(build_op(h, h->P, S, sa, se, FMT_CSR, Ecsr != nullptr));

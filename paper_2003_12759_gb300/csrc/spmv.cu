@@ -26,37 +26,43 @@ namespace {
 
 template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 
-// nonzeros of a row gathered per chunk: up to 8 (a 7-point row in one chunk),
-// fewer when a lane's slice of a row is wide, to keep the gathers in registers
+// nonzeros of a row gathered per chunk: 2 when a lane's slice of a row is at
+// most 16 bytes, 1 when it is wider.  Deeper chunks keep more gathers in
+// flight per thread but cost registers and resident warps, and on this
+// latency-bound kernel warps win: complex64, 4 lanes x 16 B per row, measured
+// 8-deep (80 registers, 3 blocks/SM) 78 us, 4-deep (48, 5) 63 us, 2-deep
+// (32, 8) 56 us on the 7-point 100^3 pattern.
 template <typename S, int CPT> constexpr int gather_chunk() {
   constexpr int b = (int)(CPT * sizeof(S));
-  return b <= 16 ? 8 : (b <= 32 ? 4 : 1);
+  return b <= 16 ? 2 : 1;
 }
+
+// resident blocks the register allocation is held to: 8 (32 registers, a
+// full SM) for lane slices of at most 16 bytes (6 for two real FP64 columns,
+// whose FP64 values would spill at 32), no bound for wider slices
+template <typename S, int CPT> constexpr int min_blocks() {
+  return CPT * sizeof(S) <= 16 ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1) ? 6 : 8) : 1;
+}
+
+// the operator kernel carries the fused reduction accumulators: 5 blocks (48 registers)
+#ifndef MOR_OP_MINB
+#define MOR_OP_MINB 5
+#endif
+template <typename S, int CPT> constexpr int op_min_blocks() { return CPT * sizeof(S) <= 16 ? MOR_OP_MINB : 1; }
 
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
 
-// [p0, p1) and step of row r in the stored layout
-__device__ __forceinline__ void row_range(const PatView& pv, int64_t r, int64_t& p0, int64_t& p1, int& step) {
-  if (pv.fmt == FMT_SELL) {
-    const int64_t base = pv.sptr[r >> 5];
-    const int64_t w = (pv.sptr[(r >> 5) + 1] - base) >> 5;
-    p0 = base + (r & 31);
-    p1 = p0 + 32 * w;
-    step = 32;
-  } else {
-    p0 = pv.rowptr[r];
-    p1 = pv.rowptr[r + 1];
-    step = 1;
-  }
-}
 
 // Y(:, c) = sE_c (E X(:, c)) + sA_c (A X(:, c)) [+ B(:, c)], with an optional
 // fused per-column reduction.  TPR lanes per row, lane `sub` owns the CPT
-// columns sub * CPT ... sub * CPT + CPT - 1 of the n x ld blocks.
+// columns sub * CPT ... sub * CPT + CPT - 1 of the n x ld blocks.  The
+// coefficients are read from shared memory where they are used and row
+// indices are 32-bit, to hold the register bound of op_min_blocks.
 template <typename S, int TPR, int CPT>
-__global__ void __launch_bounds__(256) op_spmv_kernel(SegView sg, PatView pv, OpVals ov, CoefS<S> cf, int ld,
-                                                      const S* __restrict__ x, S* __restrict__ y,
-                                                      const S* __restrict__ bv, RedArgs red) {
+__global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(SegView sg, PatView pv, OpVals ov,
+                                                                                CoefS<S> cf, int ld,
+                                                                                const S* __restrict__ x, S* __restrict__ y,
+                                                                                const S* __restrict__ bv, RedArgs red) {
   typedef typename real_of<S>::type R;
   if (red.done && *red.done) return;
   __shared__ S csE[MOR_LDMAX], csA[MOR_LDMAX];
@@ -69,52 +75,69 @@ __global__ void __launch_bounds__(256) op_spmv_kernel(SegView sg, PatView pv, Op
   const int sub = threadIdx.x % TPR;
   const int c0 = sub * CPT;
   const bool act = c0 < ld;
-  S sE[CPT], sA[CPT], v0[CPT], v1[CPT];
+  S v0[CPT], v1[CPT];
 #pragma unroll
-  for (int j = 0; j < CPT; ++j) {
-    sE[j] = act ? csE[c0 + j] : zero_<S>();
-    sA[j] = act ? csA[c0 + j] : zero_<S>();
-    v0[j] = zero_<S>();
-    v1[j] = zero_<S>();
-  }
+  for (int j = 0; j < CPT; ++j) { v0[j] = zero_<S>(); v1[j] = zero_<S>(); }
   const int rpb = blockDim.x / TPR;
   const int seg = seg_of_chunk(sg, blockIdx.x);
-  int64_t rb, re;
-  chunk_rows(sg, seg, blockIdx.x, rb, re);
+  int64_t rb64, re64;
+  chunk_rows(sg, seg, blockIdx.x, rb64, re64);
+  const int re = (int)re64;
+  const bool sell = pv.fmt == FMT_SELL;
+  const int ekind = ov.ekind;
+  constexpr int GCH = gather_chunk<S, CPT>();
   if (act) {
-    for (int64_t r = rb + threadIdx.x / TPR; r < re; r += rpb) {
-      int64_t p0, p1;
-      int step;
-      row_range(pv, r, p0, p1, step);
+    for (int r = (int)rb64 + (int)threadIdx.x / TPR; r < re; r += rpb) {
+      int p0, p1, step;
+      if (sell) {
+        const int64_t base = pv.sptr[r >> 5];
+        const int wd = (int)((pv.sptr[(r >> 5) + 1] - base) >> 5);
+        p0 = (int)base + (r & 31);
+        p1 = p0 + 32 * wd;
+        step = 32;
+      } else {
+        p0 = pv.rowptr[r];
+        p1 = pv.rowptr[r + 1];
+        step = 1;
+      }
       S accA[CPT], accE[CPT];
 #pragma unroll
       for (int j = 0; j < CPT; ++j) { accA[j] = zero_<S>(); accE[j] = zero_<S>(); }
-      if (ov.ekind == EK_CSR) {
-        for (int64_t p = p0; p < p1; p += step) {
-          const int cc = __ldg(pv.col + p);
-          const R av = __ldg(a + p), ev = __ldg(e + p);
-          const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+      for (int pc = p0; pc < p1; pc += GCH * step) {
+        int cc[GCH];
+        R av[GCH], ev[GCH];
 #pragma unroll
-          for (int j = 0; j < CPT; ++j) { fma_r(accA[j], av, xv.v[j]); fma_r(accE[j], ev, xv.v[j]); }
+        for (int u = 0; u < GCH; ++u) {
+          const int pu = pc + u * step;
+          const bool ok = pu < p1;
+          cc[u] = ok ? __ldg(pv.col + pu) : -1;
+          av[u] = ok ? __ldg(a + pu) : R(0);
+          ev[u] = (ok && ekind == EK_CSR) ? __ldg(e + pu) : R(0);
         }
-      } else {
-#pragma unroll 4
-        for (int64_t p = p0; p < p1; p += step) {
-          const int cc = __ldg(pv.col + p);
-          const R av = __ldg(a + p);
-          const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+        Pack<S, CPT> xv[GCH];
 #pragma unroll
-          for (int j = 0; j < CPT; ++j) fma_r(accA[j], av, xv.v[j]);
-        }
-        const Pack<S, CPT> xr = ldp<S, CPT>(x + r * ld + c0);
-        const R d = (ov.ekind == EK_DIAG) ? __ldg(ed + r) : R(1);
+        for (int u = 0; u < GCH; ++u)
+          if (cc[u] >= 0) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+#pragma unroll
+        for (int u = 0; u < GCH; ++u)
+          if (cc[u] >= 0) {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+              fma_r(accA[j], av[u], xv[u].v[j]);
+              if (ekind == EK_CSR) fma_r(accE[j], ev[u], xv[u].v[j]);
+            }
+          }
+      }
+      const int64_t q = (int64_t)r * ld + c0;
+      if (ekind != EK_CSR) {
+        const Pack<S, CPT> xr = ldp<S, CPT>(x + q);
+        const R d = (ekind == EK_DIAG) ? __ldg(ed + r) : R(1);
 #pragma unroll
         for (int j = 0; j < CPT; ++j) accE[j] = scale_(d, xr.v[j]);
       }
-      const int64_t q = r * ld + c0;
       Pack<S, CPT> yv;
 #pragma unroll
-      for (int j = 0; j < CPT; ++j) yv.v[j] = sE[j] * accE[j] + sA[j] * accA[j];
+      for (int j = 0; j < CPT; ++j) yv.v[j] = csE[c0 + j] * accE[j] + csA[c0 + j] * accA[j];
       if (bv) {
         const Pack<S, CPT> bb = ldp<S, CPT>(bv + q);
 #pragma unroll
@@ -141,8 +164,11 @@ __global__ void __launch_bounds__(256) op_spmv_kernel(SegView sg, PatView pv, Op
 }
 
 // Y(:, c) = F X(:, c) where the factor applies to column c, else Y(:, c) = X(:, c).
+// Kept lean (32-bit row indices, a column bit mask, the copy-through value
+// loaded only at the end) so that the register bound of min_blocks holds
+// without spills.
 template <typename S, typename V, int TPR, int CPT>
-__global__ void __launch_bounds__(256) factor_spmv_kernel(SegView sg, PatView pv, const V* __restrict__ f,
+__global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(SegView sg, PatView pv, const V* __restrict__ f,
                                                           const int* __restrict__ apply, int ld,
                                                           const S* __restrict__ x, S* __restrict__ y,
                                                           const int* done) {
@@ -150,31 +176,40 @@ __global__ void __launch_bounds__(256) factor_spmv_kernel(SegView sg, PatView pv
   const int sub = threadIdx.x % TPR;
   const int c0 = sub * CPT;
   if (c0 >= ld) return;
-  int ap[CPT];
-  bool any = false;
+  unsigned mask = 0;
 #pragma unroll
-  for (int j = 0; j < CPT; ++j) { ap[j] = apply[c0 + j]; any |= (ap[j] != 0); }
+  for (int j = 0; j < CPT; ++j) mask |= (apply[c0 + j] != 0 ? 1u : 0u) << j;
   const int rpb = blockDim.x / TPR;
-  int64_t rb, re;
-  chunk_rows(sg, seg_of_chunk(sg, blockIdx.x), blockIdx.x, rb, re);
-  for (int64_t r = rb + threadIdx.x / TPR; r < re; r += rpb) {
-    const int64_t q = r * ld + c0;
-    const Pack<S, CPT> xo = ldp<S, CPT>(x + q);
+  int64_t rb64, re64;
+  chunk_rows(sg, seg_of_chunk(sg, blockIdx.x), blockIdx.x, rb64, re64);
+  const int re = (int)re64;
+  const bool sell = pv.fmt == FMT_SELL;
+  for (int r = (int)rb64 + (int)threadIdx.x / TPR; r < re; r += rpb) {
     Pack<S, CPT> acc;
 #pragma unroll
     for (int j = 0; j < CPT; ++j) acc.v[j] = zero_<S>();
-    if (any) {
-      int64_t p0, p1;
-      int step;
-      row_range(pv, r, p0, p1, step);
-      // chunks of GCH nonzeros: all indices and values first, then every gather in flight
+    if (mask) {
+      int p0, p1, step;
+      if (sell) {
+        const int64_t base = pv.sptr[r >> 5];
+        const int w = (int)((pv.sptr[(r >> 5) + 1] - base) >> 5);
+        // SELL positions exceed 32 bits only for > 2^31 stored entries, which the set-up rejects
+        p0 = (int)base + (r & 31);
+        p1 = p0 + 32 * w;
+        step = 32;
+      } else {
+        p0 = pv.rowptr[r];
+        p1 = pv.rowptr[r + 1];
+        step = 1;
+      }
+      // chunks of GCH nonzeros: indices and values first, then every gather in flight
       constexpr int GCH = gather_chunk<S, CPT>();
-      for (int64_t pc = p0; pc < p1; pc += GCH * step) {
+      for (int pc = p0; pc < p1; pc += GCH * step) {
         int cc[GCH];
         V fv[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          const int64_t pu = pc + u * step;
+          const int pu = pc + u * step;
           const bool ok = pu < p1;
           cc[u] = ok ? __ldg(pv.col + pu) : -1;
           fv[u] = ok ? f[pu] : V(0);
@@ -194,8 +229,12 @@ __global__ void __launch_bounds__(256) factor_spmv_kernel(SegView sg, PatView pv
           }
       }
     }
+    const int64_t q = (int64_t)r * ld + c0;
+    if (mask != (1u << CPT) - 1u) {
+      const Pack<S, CPT> xo = ldp<S, CPT>(x + q);
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) if (!ap[j]) acc.v[j] = xo.v[j];
+      for (int j = 0; j < CPT; ++j) if (!((mask >> j) & 1u)) acc.v[j] = xo.v[j];
+    }
     stp<S, CPT>(y + q, acc);
   }
 }
@@ -209,7 +248,6 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
   if (red) ra = *red;
   else { ra.mode = RED_NONE; ra.w = nullptr; ra.part = nullptr; ra.counter = nullptr; ra.fin = 0;
          ra.state = nullptr; ra.out = nullptr; ra.done = nullptr; }
-  const unsigned blocks = (unsigned)sg.nblocks;
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
     CoefS<S> cf;
     for (int c = 0; c < MOR_LDMAX; ++c) {
@@ -223,7 +261,8 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
         cf.sA[c] = (S)q.sAr;
       }
     }
-    op_spmv_kernel<S, TPR, CPT><<<blocks, 256, 0, s>>>(sg, pv, ov, cf, ld, (const S*)x, (S*)y, (const S*)b, ra);
+    const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT>, TPR);
+    op_spmv_kernel<S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y, (const S*)b, ra);
     return 0;
   });
   if (e) return e;
@@ -234,20 +273,23 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
 int launch_factor_spmv(int st, bool fcplx, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
                        int ld, const void* x, void* y, const int* done, cudaStream_t s) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
-  const unsigned blocks = (unsigned)sg.nblocks;
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
     typedef typename real_of<S>::type R;
     if constexpr (is_cplx<S>::value) {
-      if (fcplx)
-        factor_spmv_kernel<S, S, TPR, CPT><<<blocks, 256, 0, s>>>(sg, pv, (const S*)fvals, apply, ld,
-                                                                  (const S*)x, (S*)y, done);
-      else
-        factor_spmv_kernel<S, R, TPR, CPT><<<blocks, 256, 0, s>>>(sg, pv, (const R*)fvals, apply, ld,
-                                                                  (const S*)x, (S*)y, done);
+      if (fcplx) {
+        const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, S, TPR, CPT>, TPR);
+        factor_spmv_kernel<S, S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const S*)fvals, apply, ld,
+                                                                     (const S*)x, (S*)y, done);
+      } else {
+        const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, R, TPR, CPT>, TPR);
+        factor_spmv_kernel<S, R, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const R*)fvals, apply, ld,
+                                                                     (const S*)x, (S*)y, done);
+      }
     } else {
       if (fcplx) return (int)cudaErrorInvalidValue;
-      factor_spmv_kernel<S, S, TPR, CPT><<<blocks, 256, 0, s>>>(sg, pv, (const S*)fvals, apply, ld,
-                                                                (const S*)x, (S*)y, done);
+      const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, S, TPR, CPT>, TPR);
+      factor_spmv_kernel<S, S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const S*)fvals, apply, ld,
+                                                                   (const S*)x, (S*)y, done);
     }
     return 0;
   });
