@@ -5,6 +5,9 @@ objects are linked into paper_2003_12759_gb300/libmor_spai.so.  No cmake and
 no torch build machinery: the library has a plain C ABI (include/mor_spai.h).
 
     python -m paper_2003_12759_gb300.build [--force]
+
+MOR_NVCC_FLAGS (environment) appends flags to every nvcc compile, e.g. a
+-D override of a tuning constant; rebuild with --force after changing it.
 """
 from __future__ import annotations
 
@@ -48,7 +51,7 @@ def _deps_mtime():
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     std = "-std=c++20" if os.path.basename(src) in CXX20 else "-std=c++17"
-    cmd = [nvcc(), "-c", src, "-o", obj, std] + ARCH + NVCC_FLAGS
+    cmd = [nvcc(), "-c", src, "-o", obj, std] + ARCH + NVCC_FLAGS + os.environ.get("MOR_NVCC_FLAGS", "").split()
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

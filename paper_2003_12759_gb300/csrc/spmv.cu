@@ -26,29 +26,33 @@ namespace {
 
 template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 
-// nonzeros of a row gathered per chunk: 2 when a lane's slice of a row is at
-// most 16 bytes, 1 when it is wider.  Deeper chunks keep more gathers in
-// flight per thread but cost registers and resident warps, and on this
-// latency-bound kernel warps win: complex64, 4 lanes x 16 B per row, measured
-// 8-deep (80 registers, 3 blocks/SM) 78 us, 4-deep (48, 5) 63 us, 2-deep
-// (32, 8) 56 us on the 7-point 100^3 pattern.
-template <typename S, int CPT> constexpr int gather_chunk() {
-  constexpr int b = (int)(CPT * sizeof(S));
-  return b <= 16 ? 2 : 1;
-}
-
-// resident blocks the register allocation is held to: 8 (32 registers, a
-// full SM) for lane slices of at most 16 bytes (6 for two real FP64 columns,
-// whose FP64 values would spill at 32), no bound for wider slices
-template <typename S, int CPT> constexpr int min_blocks() {
-  return CPT * sizeof(S) <= 16 ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1) ? 6 : 8) : 1;
-}
-
-// the operator kernel carries the fused reduction accumulators: 5 blocks (48 registers)
-#ifndef MOR_OP_MINB
-#define MOR_OP_MINB 5
+// Tuning of the two SpMV kernels, measured on the 7-point 100^3 pattern with
+// seven complex64 shift columns (4 lanes x 16 B per row).  Both kernels are
+// latency-bound, so resident warps matter more than gathers in flight per
+// thread: the register allocation is held to a full SM of 256-thread blocks
+// (32 registers) for lane slices of at most 16 bytes, and a row's nonzeros
+// are gathered in whole chunks (all gathers of a chunk in flight) plus a
+// one-by-one remainder.  Factor SpMV: chunk 4 -> 52 us (8-deep chunks at 80
+// registers and 3 blocks/SM took 78 us).  Operator SpMV (with its fused
+// reduction): chunk 2 -> 96 us (chunk 1: 105 us, chunk 4: 126 us).  FP64
+// data keeps fewer blocks (6 in the factor kernel for two real columns, 5 in
+// the operator kernel), where 32 registers would spill.  Wider lane slices
+// take no bound and chunk 1.
+#ifndef MOR_FACTOR_GCH
+#define MOR_FACTOR_GCH 4
 #endif
-template <typename S, int CPT> constexpr int op_min_blocks() { return CPT * sizeof(S) <= 16 ? MOR_OP_MINB : 1; }
+#ifndef MOR_OP_GCH
+#define MOR_OP_GCH 2
+#endif
+template <typename S, int CPT> constexpr bool narrow_slice() { return CPT * sizeof(S) <= 16; }
+template <typename S, int CPT> constexpr int factor_chunk() { return narrow_slice<S, CPT>() ? MOR_FACTOR_GCH : 1; }
+template <typename S, int CPT> constexpr int op_chunk() { return narrow_slice<S, CPT>() ? MOR_OP_GCH : 1; }
+template <typename S, int CPT> constexpr int min_blocks() {
+  return narrow_slice<S, CPT>() ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1) ? 6 : 8) : 1;
+}
+template <typename S, int CPT> constexpr int op_min_blocks() {
+  return narrow_slice<S, CPT>() ? (sizeof(typename real_of<S>::type) == 8 ? 5 : 8) : 1;
+}
 
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
 
@@ -85,7 +89,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
   const int re = (int)re64;
   const bool sell = pv.fmt == FMT_SELL;
   const int ekind = ov.ekind;
-  constexpr int GCH = gather_chunk<S, CPT>();
+  constexpr int GCH = op_chunk<S, CPT>();
   if (act) {
     for (int r = (int)rb64 + (int)threadIdx.x / TPR; r < re; r += rpb) {
       int p0, p1, step;
@@ -103,30 +107,37 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
       S accA[CPT], accE[CPT];
 #pragma unroll
       for (int j = 0; j < CPT; ++j) { accA[j] = zero_<S>(); accE[j] = zero_<S>(); }
-      for (int pc = p0; pc < p1; pc += GCH * step) {
+      int pc = p0;
+      for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
         int cc[GCH];
         R av[GCH], ev[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          const int pu = pc + u * step;
-          const bool ok = pu < p1;
-          cc[u] = ok ? __ldg(pv.col + pu) : -1;
-          av[u] = ok ? __ldg(a + pu) : R(0);
-          ev[u] = (ok && ekind == EK_CSR) ? __ldg(e + pu) : R(0);
+          cc[u] = __ldg(pv.col + pc + u * step);
+          av[u] = __ldg(a + pc + u * step);
+          ev[u] = ekind == EK_CSR ? __ldg(e + pc + u * step) : R(0);
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
-        for (int u = 0; u < GCH; ++u)
-          if (cc[u] >= 0) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+        for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
 #pragma unroll
         for (int u = 0; u < GCH; ++u)
-          if (cc[u] >= 0) {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-              fma_r(accA[j], av[u], xv[u].v[j]);
-              if (ekind == EK_CSR) fma_r(accE[j], ev[u], xv[u].v[j]);
-            }
+          for (int j = 0; j < CPT; ++j) {
+            fma_r(accA[j], av[u], xv[u].v[j]);
+            if (ekind == EK_CSR) fma_r(accE[j], ev[u], xv[u].v[j]);
           }
+      }
+      for (; pc < p1; pc += step) {
+        const int cc = __ldg(pv.col + pc);
+        const R av = __ldg(a + pc);
+        const R ev = ekind == EK_CSR ? __ldg(e + pc) : R(0);
+        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          fma_r(accA[j], av, xv.v[j]);
+          if (ekind == EK_CSR) fma_r(accE[j], ev, xv.v[j]);
+        }
       }
       const int64_t q = (int64_t)r * ld + c0;
       if (ekind != EK_CSR) {
@@ -203,30 +214,39 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
         step = 1;
       }
       // chunks of GCH nonzeros: indices and values first, then every gather in flight
-      constexpr int GCH = gather_chunk<S, CPT>();
-      for (int pc = p0; pc < p1; pc += GCH * step) {
+      // whole chunks of GCH nonzeros (indices and values first, then every
+      // gather in flight), then the remainder one by one; the sum runs in
+      // storage order either way
+      constexpr int GCH = factor_chunk<S, CPT>();
+      int pc = p0;
+      for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
         int cc[GCH];
         V fv[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          const int pu = pc + u * step;
-          const bool ok = pu < p1;
-          cc[u] = ok ? __ldg(pv.col + pu) : -1;
-          fv[u] = ok ? f[pu] : V(0);
+          cc[u] = __ldg(pv.col + pc + u * step);
+          fv[u] = f[pc + u * step];
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
-        for (int u = 0; u < GCH; ++u)
-          if (cc[u] >= 0) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+        for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
 #pragma unroll
         for (int u = 0; u < GCH; ++u)
-          if (cc[u] >= 0) {
 #pragma unroll
-            for (int j = 0; j < CPT; ++j) {
-              if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
-              else fma_r(acc.v[j], fv[u], xv[u].v[j]);
-            }
+          for (int j = 0; j < CPT; ++j) {
+            if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
+            else fma_r(acc.v[j], fv[u], xv[u].v[j]);
           }
+      }
+      for (; pc < p1; pc += step) {
+        const int cc = __ldg(pv.col + pc);
+        const V fv = f[pc];
+        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv, xv.v[j]);
+          else fma_r(acc.v[j], fv, xv.v[j]);
+        }
       }
     }
     const int64_t q = (int64_t)r * ld + c0;
