@@ -81,7 +81,12 @@ enum mor_precision {
                        inside FP64 iterative refinement of b - A(sigma) x          */
 };
 
-enum mor_solver { MOR_BICGSTAB = 0 };
+enum mor_solver {
+    MOR_BICGSTAB = 0,  /* right-preconditioned BiCGSTAB (default)                  */
+    MOR_GMRES = 1      /* right-preconditioned restarted GMRES(m), m = restart: the
+                          solver of the paper's experiments (Sec. IV); one system
+                          only (not mor_batch_solve)                               */
+};
 
 /* sparse storage of the operator and of every preconditioner factor */
 enum mor_format {
@@ -111,6 +116,8 @@ typedef struct {
                             SPAI for every shift; 2: no preconditioner               */
     int    max_chain;    /* irka_step: rebuild P_1 when the vertical chain would
                             exceed this many factors; 0 = unlimited (default)        */
+    int    restart;      /* MOR_GMRES: Krylov basis size m per cycle, 1..64,
+                            default 50                                               */
 } mor_solve_opts;
 
 /* Per-column statistics of a solve. */

@@ -35,6 +35,7 @@ STATUS_NAMES = {0: "MOR_OK", 1: "MOR_EINVAL", 2: "MOR_ENOMEM", 3: "MOR_ECUDA", 4
 MOR_DEVICE_PTRS = 1
 MOR_FP64, MOR_MIXED = 0, 1
 MOR_BICGSTAB = 0
+MOR_GMRES = 1
 MOR_FMT_AUTO, MOR_FMT_CSR, MOR_FMT_SELL = 0, 1, 2
 MOR_MAX_R = 64
 MOR_MAX_IO = 8
@@ -52,7 +53,7 @@ class mor_csr(C.Structure):
 class mor_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("batch", C.c_int), ("use_graph", C.c_int),
-                ("graph_chunk", C.c_int), ("precond", C.c_int), ("max_chain", C.c_int)]
+                ("graph_chunk", C.c_int), ("precond", C.c_int), ("max_chain", C.c_int), ("restart", C.c_int)]
 
 
 class mor_solve_stats(C.Structure):

@@ -91,6 +91,7 @@ struct mor_ctx {
   SegView seg{};
   std::vector<int64_t> seg_rows_h;   // nseg + 1 row offsets (host)
   DBuf ws_kstate, ws_segarr, ws_sums;
+  DBuf ws_gm_vec, ws_gm_small, ws_gm_part;   // GMRES(m): basis, scalars, reduction partials
   // IRKA reuse schedule
   int irka_z = 0;
   int vlen[2] = {0, 0};

@@ -122,6 +122,25 @@ struct RedArgs {
 // a batch keeps the segment table's blocks (krylov.cu).
 SegView fit_grid(const SegView& sg, const void* kern, int tpr);
 
+// GMRES(m) kernels (gmres.cu): single system, basis vectors V_i at
+// V + i * vstride (n x ld blocks of type st), per-column FP64 state.
+#define GM_MMAX 64
+size_t gmres_state_bytes();
+int gmres_state_iters(const void* state_entry);
+int gmres_state_status(const void* state_entry);
+int gmres_state_conv(const void* state_entry);
+int gmres_launch_dot(int st, const SegView& sg, int ld, const void* V, int64_t vstride, int nv, const void* w,
+                     double* part, unsigned* counter, void* out, const int* done, cudaStream_t s);
+int gmres_launch_axpy(int st, const SegView& sg, int ld, const void* V, int64_t vstride, int nv, const void* coef,
+                      void* w, int mode, int fin, double* part, unsigned* counter, void* state, void* H, int m,
+                      const void* h1, const void* h2, int* done, cudaStream_t s);
+int gmres_launch_scale(int st, const SegView& sg, int ld, const void* w, void* v, const void* state, int use_active,
+                       const int* done, cudaStream_t s);
+int gmres_launch_add(int st, const SegView& sg, int ld, void* x, const void* z, cudaStream_t s);
+int gmres_launch_begin(int ld, const void* sums, void* state, const double* target, const int* maxit,
+                       const int* enabled, int first, int* done_cycle, int* done_all, cudaStream_t s);
+int gmres_launch_solve_y(int ld, int m, void* state, const void* H, void* ycoef, cudaStream_t s);
+
 // Launchers (spmv.cu).  x, y, w, b: n x ld row-major blocks of type st.
 int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
                    const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s);

@@ -211,19 +211,20 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
       }
     return (int)cudaMemcpyAsync(sm.masks, mk.data(), sizeof(int) * mk.size(), cudaMemcpyHostToDevice, h->stream);
   };
-  auto chain_apply = [&](void* src, void* dst) -> int {
+  auto chain_apply_d = [&](void* src, void* dst, const int* dn) -> int {
     if (Lmax == 0) return 0;
     void* s = src;
     for (int f = 0; f < Lmax; ++f) {
       void* dd2 = (f == Lmax - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
       const Factor& F = op.chain[f];
       int e = launch_factor_spmv(st_in, st_is_cplx(F.st), sg, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
-                                 dd2, sm.done, h->stream);
+                                 dd2, dn, h->stream);
       if (e) return e;
       s = dd2;
     }
     return 0;
   };
+  auto chain_apply = [&](void* src, void* dst) -> int { return chain_apply_d(src, dst, sm.done); };
   auto one_iter = [&]() -> int {
     int e;
     void* phat = (Lmax == 0) ? pp : pph;
@@ -278,6 +279,127 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   int* mi = (int*)(nr + nsc);
   int* ac = mi + nsc;
   std::vector<unsigned char> kst_host(ksb * MOR_LDMAX * std::max(nseg, 1)), kst_new(ksb * MOR_LDMAX);
+  // ---- GMRES(m) inner solve of A P y = rhs, x_in = P y (single system): the
+  // basis V_0..V_m, then w, z (chain output), u (V y); one captured graph per
+  // cycle (m Arnoldi steps, the update x_in += P V y and the next cycle's
+  // start: true inner residual, beta, v_0).
+  auto gmres_inner = [&](void* xin, std::vector<int>& kit_out, std::vector<int>& kst_out) -> int {
+    if (nseg != 1) return mor_fail(h, MOR_EINVAL, "GMRES solves one system (not a batch of systems)");
+    const int m = o.restart;
+    if (m < 1 || m > GM_MMAX) return mor_fail(h, MOR_EINVAL, "GMRES restart %d outside 1..%d", m, GM_MMAX);
+    const int64_t vst = (int64_t)(vbytes / es);
+    MOR_CK(h, h->ws_gm_vec.alloc(vbytes * (size_t)(m + 4)));
+    char* gb = h->ws_gm_vec.as<char>();
+    auto V = [&](int i) { return (void*)(gb + vbytes * (size_t)i); };
+    void* W = V(m + 1);
+    void* Z = V(m + 2);
+    void* U = V(m + 3);
+    size_t off = 0;
+    auto take = [&](size_t b) { const size_t o2 = off; off += (b + 255) / 256 * 256; return o2; };
+    const size_t hb = sizeof(cdouble) * (size_t)(m + 1) * ld;
+    const size_t o_st = take(gmres_state_bytes() * ld);
+    const size_t o_H = take(sizeof(cdouble) * (size_t)ld * (m + 1) * m);
+    const size_t o_h1 = take(hb), o_h2 = take(hb), o_y = take(hb), o_fl = take(64);
+    MOR_CK(h, h->ws_gm_small.alloc(off));
+    char* sb = h->ws_gm_small.as<char>();
+    void* gst = sb + o_st;
+    void* Hm = sb + o_H;
+    void *h1 = sb + o_h1, *h2 = sb + o_h2, *yc = sb + o_y;
+    unsigned* gcnt = (unsigned*)(sb + o_fl);
+    int* done_cycle = (int*)(sb + o_fl + 16);
+    int* done_all = (int*)(sb + o_fl + 32);
+    MOR_CK(h, cudaMemsetAsync(sb, 0, off, h->stream));
+    MOR_CK(h, h->ws_gm_part.alloc(sizeof(double) * 2 * (size_t)(m + 1) * ld * (size_t)(h->sm_count * 8)));
+    double* gpart = h->ws_gm_part.as<double>();
+    MOR_CK(h, cudaMemsetAsync(gb, 0, vbytes * (size_t)(m + 4), h->stream));   // no stale values in the basis
+    MOR_CK(h, cudaMemsetAsync(xin, 0, vbytes, h->stream));
+    RedArgs rn{RED_NORM, nullptr, h->ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
+    RedArgs none{RED_NONE, nullptr, nullptr, nullptr, 0, nullptr, nullptr, done_cycle};
+    auto start_cycle = [&](int first) -> int {
+      int e;
+      if ((e = launch_op_spmv(st_in, sg, pv, ov_in, ncf, ld, xin, W, rhs, &rn, h->stream))) return e;
+      if ((e = gmres_launch_begin(ld, d_sums, gst, d_target, d_maxit, d_active, first, done_cycle, done_all,
+                                  h->stream)))
+        return e;
+      return gmres_launch_scale(st_in, sg, ld, W, V(0), gst, 1, done_cycle, h->stream);
+    };
+    auto cycle = [&]() -> int {
+      int e;
+      for (int j = 0; j < m; ++j) {
+        void* src = V(j);
+        if (Lmax > 0) {
+          if ((e = chain_apply_d(V(j), Z, done_cycle))) return e;
+          src = Z;
+        }
+        if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cf, ld, src, W, nullptr, &none, h->stream))) return e;
+        if ((e = gmres_launch_dot(st_in, sg, ld, V(0), vst, j + 1, W, gpart, gcnt, h1, done_cycle, h->stream))) return e;
+        if ((e = gmres_launch_axpy(st_in, sg, ld, V(0), vst, j + 1, h1, W, 0, 0, gpart, gcnt, gst, Hm, m, h1, h2,
+                                   done_cycle, h->stream)))
+          return e;
+        if ((e = gmres_launch_dot(st_in, sg, ld, V(0), vst, j + 1, W, gpart, gcnt, h2, done_cycle, h->stream))) return e;
+        if ((e = gmres_launch_axpy(st_in, sg, ld, V(0), vst, j + 1, h2, W, 0, 1, gpart, gcnt, gst, Hm, m, h1, h2,
+                                   done_cycle, h->stream)))
+          return e;
+        if ((e = gmres_launch_scale(st_in, sg, ld, W, V(j + 1), gst, 1, done_cycle, h->stream))) return e;
+      }
+      if ((e = gmres_launch_solve_y(ld, m, gst, Hm, yc, h->stream))) return e;
+      if ((e = gmres_launch_axpy(st_in, sg, ld, V(0), vst, m, yc, U, 1, 0, gpart, gcnt, gst, Hm, m, h1, h2, nullptr,
+                                 h->stream)))
+        return e;
+      void* upd = U;
+      if (Lmax > 0) {
+        if ((e = chain_apply_d(U, Z, nullptr))) return e;
+        upd = Z;
+      }
+      if ((e = gmres_launch_add(st_in, sg, ld, xin, upd, h->stream))) return e;
+      return start_cycle(0);
+    };
+    MOR_CKI(h, start_cycle(1));
+    cudaGraphExec_t gx = nullptr;
+    struct GxGuard { cudaGraphExec_t* g; ~GxGuard() { if (*g) cudaGraphExecDestroy(*g); } } gxg{&gx};
+    int64_t gnodes = 0;
+    if (o.use_graph) {
+      cudaGraph_t g = nullptr;
+      int64_t c0 = 0, c1 = 0;
+      mor_launch_count(&c0);
+      MOR_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      const int e = cycle();
+      const cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
+      mor_launch_count(&c1);
+      gnodes = c1 - c0;
+      mor_count_launches(-gnodes);
+      if (e) { if (g) cudaGraphDestroy(g); return mor_fail(h, MOR_ECUDA, "launch failed during capture: %s", cudaGetErrorString((cudaError_t)e)); }
+      MOR_CK(h, ce);
+      const cudaError_t ie = cudaGraphInstantiate(&gx, g, 0);
+      cudaGraphDestroy(g);
+      MOR_CK(h, ie);
+    }
+    int maxrem = 0;
+    for (int c = 0; c < ld; ++c) maxrem = std::max(maxrem, mi[c]);
+    int* hd = (int*)(ac + nsc);
+    for (int cyc = 0; cyc <= maxrem; ++cyc) {
+      MOR_CK(h, cudaMemcpyAsync(hd, done_all, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      MOR_CK(h, cudaStreamSynchronize(h->stream));
+      if (*hd) break;
+      if (gx) {
+        MOR_CK(h, cudaGraphLaunch(gx, h->stream));
+        mor_count_launches(gnodes);
+      } else {
+        MOR_CKI(h, cycle());
+      }
+    }
+    std::vector<unsigned char> gs(gmres_state_bytes() * ld);
+    MOR_CK(h, cudaMemcpyAsync(gs.data(), gst, gs.size(), cudaMemcpyDeviceToHost, h->stream));
+    MOR_CK(h, cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < k; ++c) {
+      const void* e = gs.data() + gmres_state_bytes() * c;
+      kit_out[c] = gmres_state_iters(e);
+      const int stt = gmres_state_status(e);
+      kst_out[c] = gmres_state_conv(e) ? KST_OK : (stt == KST_BREAKDOWN ? KST_BREAKDOWN : KST_NOCONV);
+    }
+    return MOR_OK;
+  };
+
   for (int pass = 0;; ++pass) {
     // true residual r64 = b - A(sigma) x64 in FP64 with fused norms, per (system, column)
     RedArgs rn{RED_NORM, nullptr, h->ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
@@ -327,106 +449,110 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     bool compacted = false;
     MOR_CKI(h, upload_masks());
     MOR_CKI(h, refine_launch_scale_cast(st_in, sg, ld, r64, d_nrm2, d_active, rhs, h->stream));
-    MOR_CKI(h, krylov_launch_init(st_in, sg, ld, rhs, dd, rr, rh, pp, vv, h->ws_part.p, kstate, d_target, d_maxit,
-                                  sm.done, h->stream));
-    MOR_TRY(capture());
-    int maxrem = 0;
-    for (size_t z = 0; z < nsc; ++z) maxrem = std::max(maxrem, mi[z]);
-    int it = 0;
     std::vector<int> kit(NK, 0), kstat(NK, KST_OK);
-    int* hd = (int*)(ac + nsc);
-    while (it < maxrem) {
-      if (gexec) {
-        MOR_CK(h, cudaGraphLaunch(gexec, h->stream));
-        mor_count_launches(graph_nodes);
-        it += chunk;
-      } else {
-        MOR_CKI(h, one_iter());
-        it += 1;
-        if ((it % chunk) != 0 && it < maxrem) continue;
-      }
-      if (nseg > 1) {
-        MOR_CK(h, cudaMemcpyAsync(hd, sm.done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-        MOR_CK(h, cudaStreamSynchronize(h->stream));
-        if (*hd) break;
-        continue;
-      }
-      MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, ldc, h->stream));
-      int nlive = 0;
-      for (int c = 0; c < ldc; ++c) nlive += krylov_state_active(kst_host.data() + ksb * c) ? 1 : 0;
-      if (nlive == 0) break;
-      const int ld_new = row_stride(st_in, nlive);
-      if (ld_new >= ldc || it >= maxrem) continue;
-      // ---- compaction: flush dropped real columns, repack the live ones
-      std::vector<int> live, drop_src, drop_dst;
-      for (int c = 0; c < ldc; ++c) {
-        const unsigned char* ks = kst_host.data() + ksb * c;
-        if (krylov_state_active(ks)) { live.push_back(c); continue; }
-        const int oc = cmap[c];
-        if (oc >= 0 && oc < k) {
-          drop_src.push_back(c);
-          drop_dst.push_back(oc);
-          kit[oc] = krylov_state_iters(ks);
-          kstat[oc] = krylov_state_status(ks);
-        }
-      }
-      int* dmaps = sm.masks + (size_t)MAX_FACTORS * MOR_KMAX - 3 * MOR_LDMAX;   // tail of the mask area
-      std::vector<int> maps(3 * MOR_LDMAX, 0);
-      for (size_t i = 0; i < drop_src.size(); ++i) { maps[i] = drop_src[i]; maps[MOR_LDMAX + i] = drop_dst[i]; }
-      for (size_t i = 0; i < live.size(); ++i) maps[2 * MOR_LDMAX + i] = live[i];
-      MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, h->stream));
-      if (!drop_src.empty())
-        MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, (int)drop_src.size(), dmaps, dmaps + MOR_LDMAX, dd,
-                                            d_full, h->stream));
-      const int* gmap = dmaps + 2 * MOR_LDMAX;
-      void* src[5] = {dd, rr, rh, pp, vv};
-      void* dst[5] = {ssv, tt, pph, ssh, t0};
-      for (int q = 0; q < 5; ++q)
-        MOR_CKI(h, conv_launch_gather_cols(st_in, n, ldc, ld_new, (int)live.size(), gmap, src[q], dst[q], h->stream));
-      // the old state vectors become the scratch set
-      dd = dst[0]; rr = dst[1]; rh = dst[2]; pp = dst[3]; vv = dst[4];
-      ssv = src[0]; tt = src[1]; pph = src[2]; ssh = src[3]; t0 = src[4];
-      std::vector<int> nmap(ld_new, -1);
-      for (int c = 0; c < ld_new; ++c) {
-        if (c < (int)live.size()) {
-          nmap[c] = cmap[live[c]];
-          memcpy(kst_new.data() + ksb * c, kst_host.data() + ksb * live[c], ksb);
-          cfc[c] = cfc[live[c]];
-        } else {
-          krylov_state_make_dummy(kst_new.data() + ksb * c);
-          cfc[c] = cfc[live[0]];
-        }
-      }
-      cmap = nmap;
-      ldc = ld_new;
-      MOR_CKI(h, krylov_write_state(kst_new.data(), kstate, ldc, h->stream));
-      MOR_CKI(h, upload_masks());
-      compacted = true;
-      MOR_TRY(capture());
-    }
-    // final per-(system, column) state of this inner solve
-    MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, nseg * ldc, h->stream));
-    for (int sgi = 0; sgi < nseg; ++sgi)
-      for (int c = 0; c < ldc; ++c) {
-        const int oc = cmap[c];
-        if (oc >= 0 && oc < k) {
-          const unsigned char* ks = kst_host.data() + ksb * ((size_t)sgi * ldc + c);
-          kit[(size_t)sgi * k + oc] = krylov_state_iters(ks);
-          kstat[(size_t)sgi * k + oc] = krylov_state_status(ks);
-        }
-      }
     void* dres = dd;
-    if (compacted) {
-      // collect the remaining columns into d_full (original layout)
-      std::vector<int> maps(2 * MOR_LDMAX, 0);
-      int nrem = 0;
-      for (int c = 0; c < ldc; ++c)
-        if (cmap[c] >= 0 && cmap[c] < k) { maps[nrem] = c; maps[MOR_LDMAX + nrem] = cmap[c]; ++nrem; }
-      int* dmaps = sm.masks + (size_t)MAX_FACTORS * MOR_KMAX - 3 * MOR_LDMAX;
-      MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, h->stream));
-      if (nrem > 0)
-        MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, nrem, dmaps, dmaps + MOR_LDMAX, dd, d_full, h->stream));
-      dres = d_full;
+    if (o.solver == MOR_GMRES) {
+      MOR_TRY(gmres_inner(dd, kit, kstat));
+    } else {
+      MOR_CKI(h, krylov_launch_init(st_in, sg, ld, rhs, dd, rr, rh, pp, vv, h->ws_part.p, kstate, d_target, d_maxit,
+                                    sm.done, h->stream));
+      MOR_TRY(capture());
+      int maxrem = 0;
+      for (size_t z = 0; z < nsc; ++z) maxrem = std::max(maxrem, mi[z]);
+      int it = 0;
+      int* hd = (int*)(ac + nsc);
+      while (it < maxrem) {
+        if (gexec) {
+          MOR_CK(h, cudaGraphLaunch(gexec, h->stream));
+          mor_count_launches(graph_nodes);
+          it += chunk;
+        } else {
+          MOR_CKI(h, one_iter());
+          it += 1;
+          if ((it % chunk) != 0 && it < maxrem) continue;
+        }
+        if (nseg > 1) {
+          MOR_CK(h, cudaMemcpyAsync(hd, sm.done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+          MOR_CK(h, cudaStreamSynchronize(h->stream));
+          if (*hd) break;
+          continue;
+        }
+        MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, ldc, h->stream));
+        int nlive = 0;
+        for (int c = 0; c < ldc; ++c) nlive += krylov_state_active(kst_host.data() + ksb * c) ? 1 : 0;
+        if (nlive == 0) break;
+        const int ld_new = row_stride(st_in, nlive);
+        if (ld_new >= ldc || it >= maxrem) continue;
+        // ---- compaction: flush dropped real columns, repack the live ones
+        std::vector<int> live, drop_src, drop_dst;
+        for (int c = 0; c < ldc; ++c) {
+          const unsigned char* ks = kst_host.data() + ksb * c;
+          if (krylov_state_active(ks)) { live.push_back(c); continue; }
+          const int oc = cmap[c];
+          if (oc >= 0 && oc < k) {
+            drop_src.push_back(c);
+            drop_dst.push_back(oc);
+            kit[oc] = krylov_state_iters(ks);
+            kstat[oc] = krylov_state_status(ks);
+          }
+        }
+        int* dmaps = sm.masks + (size_t)MAX_FACTORS * MOR_KMAX - 3 * MOR_LDMAX;   // tail of the mask area
+        std::vector<int> maps(3 * MOR_LDMAX, 0);
+        for (size_t i = 0; i < drop_src.size(); ++i) { maps[i] = drop_src[i]; maps[MOR_LDMAX + i] = drop_dst[i]; }
+        for (size_t i = 0; i < live.size(); ++i) maps[2 * MOR_LDMAX + i] = live[i];
+        MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, h->stream));
+        if (!drop_src.empty())
+          MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, (int)drop_src.size(), dmaps, dmaps + MOR_LDMAX, dd,
+                                              d_full, h->stream));
+        const int* gmap = dmaps + 2 * MOR_LDMAX;
+        void* src[5] = {dd, rr, rh, pp, vv};
+        void* dst[5] = {ssv, tt, pph, ssh, t0};
+        for (int q = 0; q < 5; ++q)
+          MOR_CKI(h, conv_launch_gather_cols(st_in, n, ldc, ld_new, (int)live.size(), gmap, src[q], dst[q], h->stream));
+        // the old state vectors become the scratch set
+        dd = dst[0]; rr = dst[1]; rh = dst[2]; pp = dst[3]; vv = dst[4];
+        ssv = src[0]; tt = src[1]; pph = src[2]; ssh = src[3]; t0 = src[4];
+        std::vector<int> nmap(ld_new, -1);
+        for (int c = 0; c < ld_new; ++c) {
+          if (c < (int)live.size()) {
+            nmap[c] = cmap[live[c]];
+            memcpy(kst_new.data() + ksb * c, kst_host.data() + ksb * live[c], ksb);
+            cfc[c] = cfc[live[c]];
+          } else {
+            krylov_state_make_dummy(kst_new.data() + ksb * c);
+            cfc[c] = cfc[live[0]];
+          }
+        }
+        cmap = nmap;
+        ldc = ld_new;
+        MOR_CKI(h, krylov_write_state(kst_new.data(), kstate, ldc, h->stream));
+        MOR_CKI(h, upload_masks());
+        compacted = true;
+        MOR_TRY(capture());
+      }
+      // final per-(system, column) state of this inner solve
+      MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, nseg * ldc, h->stream));
+      for (int sgi = 0; sgi < nseg; ++sgi)
+        for (int c = 0; c < ldc; ++c) {
+          const int oc = cmap[c];
+          if (oc >= 0 && oc < k) {
+            const unsigned char* ks = kst_host.data() + ksb * ((size_t)sgi * ldc + c);
+            kit[(size_t)sgi * k + oc] = krylov_state_iters(ks);
+            kstat[(size_t)sgi * k + oc] = krylov_state_status(ks);
+          }
+        }
+      if (compacted) {
+        // collect the remaining columns into d_full (original layout)
+        std::vector<int> maps(2 * MOR_LDMAX, 0);
+        int nrem = 0;
+        for (int c = 0; c < ldc; ++c)
+          if (cmap[c] >= 0 && cmap[c] < k) { maps[nrem] = c; maps[MOR_LDMAX + nrem] = cmap[c]; ++nrem; }
+        int* dmaps = sm.masks + (size_t)MAX_FACTORS * MOR_KMAX - 3 * MOR_LDMAX;
+        MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, h->stream));
+        if (nrem > 0)
+          MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, nrem, dmaps, dmaps + MOR_LDMAX, dd, d_full, h->stream));
+        dres = d_full;
+      }
     }
     for (size_t q = 0; q < NK; ++q) {
       if (!act[q]) continue;

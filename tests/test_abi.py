@@ -59,3 +59,31 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """sizeof / offsetof of the option and statistics structs as gcc lays them
+    out from include/mor_spai.h equal the ctypes binding's."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mor_spai.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(mor_solve_opts), '
+                   'offsetof(mor_solve_opts, restart), offsetof(mor_solve_opts, max_chain), '
+                   'sizeof(mor_solve_stats), sizeof(mor_reduced)); return 0; }\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(mor.mor_solve_opts), mor.mor_solve_opts.restart.offset, mor.mor_solve_opts.max_chain.offset,
+            ctypes.sizeof(mor.mor_solve_stats), ctypes.sizeof(mor.mor_reduced)]
+    assert got == want
+
+
+def test_default_options(lib):
+    """mor_default_opts fills host memory only (no GPU call)."""
+    o = mor.mor_default_opts()
+    assert o.solver == mor.MOR_BICGSTAB and o.precision == mor.MOR_MIXED and o.restart == 50
+    assert o.tol == 1e-8 and o.precond == 0 and o.max_chain == 0

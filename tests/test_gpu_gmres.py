@@ -1,0 +1,167 @@
+"""GPU parity of the GMRES(m) solver option (the paper's Krylov method,
+Sec. IV) against the oracle's restarted right-preconditioned GMRES.
+
+The GPU orthogonalises the Arnoldi basis by CGS2 (fused multi-dot and
+multi-axpy passes), the oracle by modified Gram-Schmidt; both are
+orthogonal to working accuracy, so the iteration counts of FP64 mode agree up
+to rounding: each solve within max(3, 25%), the total over a sweep within 10%.
+Every solve reaches the true relative residual 1e-8, recomputed here in FP64.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import paper_2003_12759_gb300 as mor
+import workloads as W
+from oracle import operator as oop, spai as ospai, krylov as okry
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    mor.load_library()
+    hh = mor.mor_create(0)
+    yield hh
+    mor.mor_destroy(hh)
+
+
+def _set(h, wl):
+    if wl.E is None:
+        mor.mor_set_system(h, wl.A, wl.B, wl.C)
+    elif isinstance(wl.E, np.ndarray):
+        mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E)
+    else:
+        mor.mor_set_system(h, wl.A, wl.B, wl.C, E=wl.E)
+
+
+def _chain(wl, shifts, transpose):
+    S = ospai.spai_pattern(wl.A, wl.E, transpose=transpose)
+    Ms = [oop.A_sigma(wl.A, wl.E, s, transpose=transpose) for s in shifts]
+    F = [ospai.spai(Ms[0], S)] + [ospai.reuse_factor(Ms[i - 1], Ms[i], S) for i in range(1, len(shifts))]
+    return Ms, F
+
+
+CASES = {
+    "convdiff3d_n3375": lambda: W.config1(N=15),
+    "laplace2d_n4900": lambda: W.config0(N=70),
+    "rand_csrE_n1500": lambda: W.random_sparse_system(1500, 0.004, seed=8, e_kind="csr"),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("transpose", [0, 1])
+@pytest.mark.parametrize("m", [50, 7])
+def test_fp64_gmres_matches_oracle(h, name, transpose, m):
+    wl = CASES[name]()
+    _set(h, wl)
+    shifts = [30.0, 45.0 + 20.0j, 90.0 + 5.0j]
+    mor.mor_build_precond(h, shifts[0], transpose, mor.MOR_FP64)
+    for s in shifts[1:]:
+        mor.mor_update_precond(h, s, transpose)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64, solver=mor.MOR_GMRES, restart=m)
+    X, stats, code = mor.mor_solve_shifts(h, shifts, transpose, opts)
+    assert code == mor.MOR_OK
+    Ms, F = _chain(wl, shifts, bool(transpose))
+    b = (wl.C if transpose else wl.B)[:, 0]
+    tot_g = tot_o = 0
+    for c in range(len(shifts)):
+        rel = np.linalg.norm(b - Ms[c] @ X[:, c]) / np.linalg.norm(b)
+        assert rel <= 1.001e-8, (c, rel)
+        assert stats[c]["status"] == mor.MOR_OK
+        xo, ito, relo, sto = okry.gmres(lambda v, M=Ms[c]: M @ v, lambda v, f=F[: c + 1]: ospai.chain_apply(f, v),
+                                        b.astype(Ms[c].dtype), tol=1e-8, m=m)
+        assert sto == okry.STATUS_OK
+        itg = stats[c]["iters"]
+        assert abs(itg - ito) <= max(3, 0.25 * ito), (c, itg, ito)
+        tot_g += itg
+        tot_o += ito
+        if wl.n <= 2000:
+            kappa = np.linalg.cond(Ms[c].toarray())
+            assert np.linalg.norm(X[:, c] - xo) <= kappa * 2e-8 * np.linalg.norm(xo)
+    assert abs(tot_g - tot_o) <= 0.1 * tot_o, (tot_g, tot_o)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_gmres_reaches_fp64_residual(h, name):
+    wl = CASES[name]()
+    _set(h, wl)
+    shifts = [30.0, 45.0 + 20.0j, 90.0 + 5.0j, 200.0, 400.0 + 400.0j]
+    mor.mor_build_precond(h, shifts[0], 0, mor.MOR_MIXED)
+    for s in shifts[1:]:
+        mor.mor_update_precond(h, s, 0)
+    X, stats, code = mor.mor_solve_shifts(h, shifts, 0, mor.mor_default_opts(solver=mor.MOR_GMRES))
+    assert code == mor.MOR_OK
+    b = wl.B[:, 0]
+    for c, s in enumerate(shifts):
+        M = oop.A_sigma(wl.A, wl.E, s)
+        rel = np.linalg.norm(b - M @ X[:, c]) / np.linalg.norm(b)
+        assert rel <= 1.001e-8, (c, rel)
+        assert abs(stats[c]["relres"] - rel) <= 1e-3 * rel + 1e-15
+        assert stats[c]["refinements"] >= 1
+
+
+def test_gmres_sixteen_plus_columns_and_custom_rhs(h):
+    """k = 20 (two lock-step batches) with user right-hand sides, no graph."""
+    wl = CASES["convdiff3d_n3375"]()
+    _set(h, wl)
+    mor.mor_build_precond(h, 50.0, 0, mor.MOR_MIXED)
+    rng = np.random.default_rng(3)
+    k = 20
+    shifts = 50.0 + 10.0 * np.arange(k) + 1j * np.linspace(0, 30, k)
+    R = rng.standard_normal((wl.n, k)) + 1j * rng.standard_normal((wl.n, k))
+    X, stats, code = mor.mor_solve_shifts(h, shifts, 0, mor.mor_default_opts(solver=mor.MOR_GMRES, restart=20,
+                                                                             use_graph=0), R=R)
+    assert code == mor.MOR_OK
+    for c in range(k):
+        M = oop.A_sigma(wl.A, wl.E, shifts[c])
+        assert np.linalg.norm(R[:, c] - M @ X[:, c]) / np.linalg.norm(R[:, c]) <= 1.001e-8
+
+
+def test_gmres_unpreconditioned_noconv_and_zero_rhs(h):
+    """Unpreconditioned GMRES on a hard shift stops at maxit with MOR_ENOCONV
+    (Sec. IV: plain GMRES fails on the paper's models); a zero right-hand
+    side takes no iteration and returns x = 0."""
+    wl = W.config0(N=60)
+    _set(h, wl)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64, precond=2, maxit=12, tol=1e-12, solver=mor.MOR_GMRES,
+                                restart=5)
+    X, stats, code = mor.mor_solve_shifts(h, [1e-3], 0, opts)
+    assert code == mor.MOR_ENOCONV
+    assert stats[0]["status"] == mor.MOR_ENOCONV and stats[0]["iters"] == 12
+    assert np.all(np.isfinite(X))
+    wl = W.config1(N=6)
+    _set(h, wl)
+    X, stats, code = mor.mor_solve_shifts(h, [5.0], 0, mor.mor_default_opts(precond=2, solver=mor.MOR_GMRES),
+                                          R=np.zeros((wl.n, 1), dtype=complex))
+    assert code == mor.MOR_OK and stats[0]["iters"] == 0 and not np.any(X)
+
+
+def test_gmres_unpreconditioned_matches_oracle_iterations(h):
+    """No preconditioner: the Arnoldi process alone, restart 10."""
+    A = sp.diags([np.linspace(1.0, 50.0, 400)], [0], format="csr") + sp.random(400, 400, density=0.01,
+                                                                                 random_state=5, format="csr") * 0.5
+    A = (-A).tocsr()
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((400, 1))
+    mor.mor_set_system(h, A, B, B)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64, precond=2, solver=mor.MOR_GMRES, restart=10)
+    X, stats, code = mor.mor_solve_shifts(h, [2.0], 0, opts)
+    assert code == mor.MOR_OK
+    M = oop.A_sigma(A, None, 2.0)
+    _, ito, _, sto = okry.gmres(lambda v: M @ v, None, B[:, 0], tol=1e-8, m=10)
+    assert sto == okry.STATUS_OK
+    assert abs(stats[0]["iters"] - ito) <= max(3, 0.25 * ito), (stats[0]["iters"], ito)
+
+
+def test_gmres_rejects_batches_and_bad_restart(h):
+    systems = [W.random_sparse_system(300 + 50 * i, 0.02, seed=20 + i, e_kind="diag") for i in range(2)]
+    mor.mor_set_batch(h, [s.A for s in systems], [s.B for s in systems], [s.C for s in systems],
+                      E_diags=[s.E for s in systems])
+    opts = mor.mor_default_opts(solver=mor.MOR_GMRES, precond=2)
+    with pytest.raises(RuntimeError):
+        mor.mor_batch_solve(h, [1.0], 0, opts)
+    wl = W.config1(N=6)
+    _set(h, wl)
+    with pytest.raises(RuntimeError):
+        mor.mor_solve_shifts(h, [5.0], 0, mor.mor_default_opts(precond=2, solver=mor.MOR_GMRES, restart=65))
