@@ -252,6 +252,91 @@ def irka_step(A, E, B, C, shifts, sched_V: ReuseSchedule, sched_W: Optional[Reus
     return new, (Ar, Er, Br, Cr), its, rr, herm
 
 
+# ----------------------------------------------------------------------------
+# tangential (MIMO) IRKA: the directions of Algorithm 2 line 3
+# ----------------------------------------------------------------------------
+def tangential_directions(Ar, Er, Br, Cr):
+    """Reduced poles and tangential directions, Algorithm 2 line 3 with
+    N_j = 0, read on the pencil: K = E_r^{-1} A_r = R Lambda R^{-1}
+    (eigenvectors R by LAPACK), F = E_r^{-1} B_r, C = C_r^T.  The pole
+    lambda_i = Lambda_ii carries the right direction b_i = column i of
+    F^T R^{-T}, i.e. row i of R^{-1} F, and the left direction c_i = column i
+    of C R.  Returns (lam (r,), btil (r, m), ctil (r, q)), row i belonging to
+    lambda_i."""
+    K = np.linalg.solve(Er, Ar)
+    F = np.linalg.solve(Er, Br)
+    lam, R = sla.eig(K)
+    btil = np.linalg.solve(R, F.astype(np.complex128))
+    ctil = (Cr.T.astype(np.complex128) @ R).T
+    return np.asarray(lam, dtype=np.complex128), btil, ctil
+
+
+def mirror_with_directions(lam, btil, ctil):
+    """New shifts sigma_i = |Re lambda_i| - i Im lambda_i (as mirror_shifts)
+    with each pole's directions, sorted by (Re, |Im|, -Im); the -Im member of
+    a conjugate pair gets the conjugate directions of the +Im member."""
+    lam = pair_conjugates(lam)
+    sig = np.abs(lam.real) - 1j * lam.imag
+    order = np.lexsort((-sig.imag, np.abs(sig.imag), sig.real))
+    sig, bt, ct = sig[order], np.array(btil[order]), np.array(ctil[order])
+    i = 0
+    while i < len(sig):
+        if sig[i].imag > 0:
+            bt[i + 1] = np.conj(bt[i])
+            ct[i + 1] = np.conj(ct[i])
+            i += 2
+        else:
+            i += 1
+    return sig, bt, ct
+
+
+def irka_step_tangential(A, E, B, C, shifts, btil, ctil, sched_V: ReuseSchedule,
+                         sched_W: Optional[ReuseSchedule], z: int, solver: str = "bicgstab",
+                         tol: float = 1e-8, maxit: int = 20000):
+    """One tangential IRKA iteration for a MIMO system (Algorithm 2 lines 3-7
+    with N_j = 0): at each solved shift sigma_i with directions b_i, c_i,
+    v_i = A(sigma_i)^{-1} B b_i and w_i = A(sigma_i)^{-T} C c_i (lines 4-5),
+    V, W by CGS2 of the real bases (line 6), the reduced pencil (line 7), and
+    the new shifts and directions from its eigenvectors (line 3 of the next
+    iteration).  btil (r x m) and ctil (r x q) hold the directions row by row
+    in the order of `shifts`.  Returns (new shifts, new btil, new ctil,
+    (Ar, Er, Br, Cr), iteration counts, true relative residuals, solved data)."""
+    shifts = np.asarray(shifts, dtype=np.complex128)
+    order = np.lexsort((-shifts.imag, np.abs(shifts.imag), shifts.real))
+    keep = shifts[order].imag >= 0.0
+    s_solve = shifts[order][keep]
+    b_solve = np.asarray(btil)[order][keep]
+    c_solve = np.asarray(ctil)[order][keep]
+    chains_V = sched_V.chains(z, s_solve)
+    chains_W = chains_V if sched_W is None else sched_W.chains(z, s_solve)
+    if solver == "dense":
+        krylov = _dense_krylov
+    else:
+        krylov = bicgstab if solver == "bicgstab" else gmres
+    vs, ws, its, rr = [], [], [], []
+    for s, bi, ci, cv, cw in zip(s_solve, b_solve, c_solve, chains_V, chains_W):
+        M = A_sigma(A, E, s)
+        MT = sp.csr_matrix(M.T)
+        dt = np.result_type(M.dtype, bi.dtype, ci.dtype)
+        b = (B @ bi).astype(dt)
+        c = (C @ ci).astype(dt)
+        v, itv, rv, _ = krylov(lambda x, M=M: M @ x, (lambda x, f=cv: chain_apply(f, x)) if cv else None,
+                               b, tol=tol, maxit=maxit)
+        w, itw, rw, _ = krylov(lambda x, MT=MT: MT @ x, (lambda x, f=cw: chain_apply(f, x)) if cw else None,
+                               c, tol=tol, maxit=maxit)
+        vs.append(v)
+        ws.append(w)
+        its += [itv, itw]
+        rr += [rv, rw]
+    V, _ = cgs2(real_basis(vs, s_solve))
+    W, _ = cgs2(real_basis(ws, s_solve))
+    rom = project(A, E, B, C, V, W)
+    lam, bt, ct = tangential_directions(*rom)
+    new, bnew, cnew = mirror_with_directions(lam, bt, ct)
+    solved = {"sigma": s_solve, "b": b_solve, "c": c_solve}
+    return new, bnew, cnew, rom, its, rr, solved
+
+
 def _dense_krylov(apply_A, apply_P, b, tol=None, maxit=None):
     """Exact solve for pins: assemble the operator column by column and use
     dense LU (small n only).  The preconditioner is ignored."""
@@ -290,3 +375,28 @@ def irka(A, E, B, C, shifts, iters: int, mode: str = "reuse", solver: str = "bic
             res.hermite.append(herm)
     res.builds = sV.builds + ([] if sW is None else sW.builds)
     return res
+
+
+def irka_tangential(A, E, B, C, shifts, btil, ctil, iters: int, mode: str = "reuse",
+                    solver: str = "bicgstab", tol: float = 1e-8, maxit: int = 20000,
+                    max_chain: Optional[int] = None):
+    """``iters`` tangential IRKA iterations (MIMO) from the initial shifts and
+    directions.  Returns (IrkaResult, list of per-iteration solved data: the
+    shifts solved and the directions used)."""
+    sym = _is_symmetric(A, E)
+    sV = ReuseSchedule(A, E, transpose=False, mode=mode, max_chain=max_chain)
+    sW = None if sym else ReuseSchedule(A, E, transpose=True, mode=mode, max_chain=max_chain)
+    s, bt, ct = np.asarray(shifts, dtype=np.complex128), np.asarray(btil), np.asarray(ctil)
+    res = IrkaResult([sort_shifts(s)], None, None, None, None)
+    used = []
+    for z in range(1, iters + 1):
+        s, bt, ct, rom, its, rr, solved = irka_step_tangential(A, E, B, C, s, bt, ct, sV, sW, z, solver=solver,
+                                                               tol=tol, maxit=maxit)
+        res.shifts_history.append(s)
+        res.Ar, res.Er, res.Br, res.Cr = rom
+        res.iters.append(its)
+        res.relres.append(rr)
+        used.append(solved)
+    res.builds = sV.builds + ([] if sW is None else sW.builds)
+    res.btil, res.ctil = bt, ct
+    return res, used

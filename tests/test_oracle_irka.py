@@ -125,3 +125,127 @@ def test_reuse_vs_fresh_vs_none_same_rom():
     H = op.transfer_function(wl.A, wl.E, wl.B, wl.C, w)[:, 0, 0]
     for Hx in Hs[1:]:
         assert np.max(np.abs(Hx - Hs[0]) / np.abs(H)) <= 1e-6
+
+
+# ----------------------------------------------------------------------------
+# tangential (MIMO) IRKA
+# ----------------------------------------------------------------------------
+def _mimo(n=50, m=3, q=2, seed=31, e_kind="diag"):
+    return W.random_sparse_system(n, 0.08, seed=seed, e_kind=e_kind, m=m, q=q)
+
+
+def _H_and_dH(wl, s):
+    """H(s) = C^T K^{-1} B and H'(s) = -C^T K^{-1} E K^{-1} B, K = sE - A (dense)."""
+    K = op.A_sigma(wl.A, wl.E, s).toarray()
+    Em = op.E_matrix(wl.E, wl.A.shape[0])
+    Em = Em.toarray() if sp.issparse(Em) else Em
+    X = np.linalg.solve(K, wl.B.astype(complex))
+    return wl.C.T @ X, -(wl.C.T @ np.linalg.solve(K, Em @ X))
+
+
+def _Hr_and_dHr(rom, s):
+    Ar, Er, Br, Cr = rom
+    K = s * Er - Ar
+    X = np.linalg.solve(K, Br.astype(complex))
+    return Cr.T @ X, -(Cr.T @ np.linalg.solve(K, Er @ X))
+
+
+@pytest.mark.parametrize("e_kind", ["identity", "diag", "csr"])
+def test_tangential_bitangential_hermite_every_iteration(e_kind):
+    """With V, W from the tangential solves (exact), the reduced model
+    interpolates H along the directions at every solved shift, from the right
+    (H b = H_r b) and the left (c^T H = c^T H_r), and matches the bitangential
+    derivative c^T H' b = c^T H_r' b (Gugercin, Antoulas & Beattie 2008)."""
+    wl = _mimo(e_kind=e_kind)
+    rng = np.random.default_rng(5)
+    shifts = np.array([0.5, 2.0 + 1.0j, 2.0 - 1.0j, 6.0, 15.0 + 4.0j, 15.0 - 4.0j])
+    bt = rng.standard_normal((6, 3)) + 0j
+    ct = rng.standard_normal((6, 2)) + 0j
+    for i in (1, 4):                      # conjugate directions for conjugate shifts
+        bt[i + 1], ct[i + 1] = np.conj(bt[i]), np.conj(ct[i])
+    sym = irka._is_symmetric(wl.A, wl.E)
+    sV = irka.ReuseSchedule(wl.A, wl.E, transpose=False)
+    sW = None if sym else irka.ReuseSchedule(wl.A, wl.E, transpose=True)
+    s = shifts
+    for z in range(1, 4):
+        s, bt, ct, rom, _, _, solved = irka.irka_step_tangential(wl.A, wl.E, wl.B, wl.C, s, bt, ct, sV, sW, z,
+                                                                 solver="dense")
+        for sig, b, c in zip(solved["sigma"], solved["b"], solved["c"]):
+            H, dH = _H_and_dH(wl, sig)
+            Hr, dHr = _Hr_and_dHr(rom, sig)
+            scale = np.linalg.norm(H)
+            assert np.linalg.norm(H @ b - Hr @ b) <= 1e-8 * scale * np.linalg.norm(b)
+            assert np.linalg.norm(c @ H - c @ Hr) <= 1e-8 * scale * np.linalg.norm(c)
+            d = c @ dH @ b
+            assert abs(d - c @ dHr @ b) <= 1e-7 * abs(d)
+        # the new shifts are closed under conjugation with conjugate directions
+        for i in range(len(s)):
+            if s[i].imag > 0:
+                assert s[i + 1] == np.conj(s[i])
+                np.testing.assert_array_equal(bt[i + 1], np.conj(bt[i]))
+                np.testing.assert_array_equal(ct[i + 1], np.conj(ct[i]))
+
+
+def test_tangential_directions_from_eigenvectors():
+    """Line 3 on a pencil with a known eigen-decomposition: A_r = E_r X D X^{-1}
+    gives poles D and, up to the scale of each eigenvector, b_i ~ row i of
+    X^{-1} E_r^{-1} B_r and c_i ~ column i of C_r^T X; their products c_i b_i^T
+    (the residues, independent of the scale) must match exactly."""
+    rng = np.random.default_rng(11)
+    r, m, q = 5, 3, 2
+    X = rng.standard_normal((r, r))
+    D = np.array([-1.0, -2.0, -3.5, -5.0, -9.0])
+    Er = np.eye(r) + 0.1 * rng.standard_normal((r, r))
+    Ar = Er @ X @ np.diag(D) @ np.linalg.inv(X)
+    Br = rng.standard_normal((r, m))
+    Cr = rng.standard_normal((r, q))
+    lam, bt, ct = irka.tangential_directions(Ar, Er, Br, Cr)
+    order = np.argsort(lam.real)[::-1]
+    lam, bt, ct = lam[order], bt[order], ct[order]
+    np.testing.assert_allclose(lam.real, D, rtol=1e-10)
+    Binv = np.linalg.solve(X, np.linalg.solve(Er, Br))       # rows: X^{-1} E_r^{-1} B_r
+    Cx = Cr.T @ X                                           # columns: C_r^T X
+    for i in range(r):
+        np.testing.assert_allclose(np.outer(ct[i], bt[i]), np.outer(Cx[:, i], Binv[i]), rtol=1e-8, atol=1e-10)
+    # residue form of H_r: sum_i c_i b_i^T / (s - lambda_i)
+    s = 0.7 + 2.0j
+    Hr = Cr.T @ np.linalg.solve(s * Er - Ar, Br)
+    Hres = sum(np.outer(ct[i], bt[i]) / (s - lam[i]) for i in range(r))
+    np.testing.assert_allclose(Hres, Hr, rtol=1e-9)
+
+
+def test_tangential_with_one_input_output_is_siso_irka():
+    """m = q = 1: the directions are scalars, the subspaces are the SISO ones,
+    so H_r follows the SISO iteration to rounding (1e-12).  The shifts agree
+    to 1e-6 only: the scalar directions change the bases (not their spans),
+    and the poles of this non-normal reduced pencil move by ~1e-7 under
+    that change of basis while H_r does not."""
+    wl = W.config1(N=5)
+    res_s = irka.irka(wl.A, wl.E, wl.B, wl.C, wl.shifts, iters=3, solver="dense")
+    r = len(wl.shifts)
+    res_t, _ = irka.irka_tangential(wl.A, wl.E, wl.B, wl.C, wl.shifts, np.ones((r, 1)), np.ones((r, 1)), iters=3,
+                                    solver="dense")
+    for a, b in zip(res_s.shifts_history, res_t.shifts_history):
+        np.testing.assert_allclose(a, b, rtol=1e-6)
+    w = 1j * np.logspace(0, 4, 50)
+    Hs = op.transfer_function_reduced(res_s.Ar, res_s.Er, res_s.Br, res_s.Cr, w)
+    Ht = op.transfer_function_reduced(res_t.Ar, res_t.Er, res_t.Br, res_t.Cr, w)
+    np.testing.assert_allclose(Ht, Hs, rtol=1e-12)
+
+
+def test_tangential_iterative_matches_dense():
+    """BiCGSTAB with reused SPAI to 1e-8 reproduces the exact tangential
+    IRKA's H_r to 1e-6 (MIMO, 3 inputs, 2 outputs)."""
+    wl = _mimo(n=120, seed=32)
+    r = 6
+    shifts = np.array([0.5, 2.0 + 1.0j, 2.0 - 1.0j, 6.0, 15.0 + 4.0j, 15.0 - 4.0j])
+    bt = np.ones((r, 3), dtype=complex)
+    ct = np.ones((r, 2), dtype=complex)
+    rd, _ = irka.irka_tangential(wl.A, wl.E, wl.B, wl.C, shifts, bt, ct, iters=3, solver="dense")
+    ri, _ = irka.irka_tangential(wl.A, wl.E, wl.B, wl.C, shifts, bt, ct, iters=3, solver="bicgstab")
+    w = 1j * np.logspace(-1, 3, 80)
+    H = op.transfer_function(wl.A, wl.E, wl.B, wl.C, w)
+    Hd = op.transfer_function_reduced(rd.Ar, rd.Er, rd.Br, rd.Cr, w)
+    Hi = op.transfer_function_reduced(ri.Ar, ri.Er, ri.Br, ri.Cr, w)
+    err = np.max(np.abs(Hi - Hd), axis=0) / np.max(np.abs(H), axis=0)
+    assert np.max(err) <= 1e-6
