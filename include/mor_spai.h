@@ -206,6 +206,9 @@ int mor_set_system_2nd(mor_t h, const mor_csr* K, const double* M_diag,
 /* n, nnz of the stored pattern, chosen format, and 1 if A(sigma)^T = A(sigma). */
 int mor_get_info(mor_t h, int64_t* n, int64_t* nnz, int* format, int* symmetric);
 
+/* Number of inputs m (columns of B, or F) and outputs q (columns of C). */
+int mor_get_io(mor_t h, int* m, int* q);
+
 /* ------------------------------------------------------------------------ */
 /* preconditioner (Sec. III)                                                */
 /* ------------------------------------------------------------------------ */
@@ -307,10 +310,29 @@ int mor_reduced_poles(mor_t h, const mor_reduced* rom, mor_c64* lambda, mor_c64*
  * Gram-Schmidt, projection, reduced poles and new shifts.
  *   shifts  in: r current shifts (closed under conjugation); out: next shifts
  *   rom     out (may be NULL); st out (may be NULL).
+ * SISO form: MOR_EINVAL unless m = q = 1 (MIMO: mor_irka_step_tangential).
  * Errors as mor_solve_shifts; MOR_EINVAL if r > MOR_MAX_R or the shift set
  * is not closed under conjugation. */
 int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts,
                   mor_reduced* rom, mor_irka_stats* st);
+
+/* One tangential IRKA iteration for a MIMO system (Algorithm 2 lines 3-7
+ * with N_j = 0, the directions of its line 3 read on the pencil) with the
+ * reuse schedule of mor_irka_step: v_i = (s_i E - A)^{-1} B b_i and
+ * w_i = (s_i E - A)^{-T} C c_i at the solved shifts, real bases, CGS2,
+ * projection, then the next shifts and directions: for the pole lambda_i of
+ * E_r^{-1} A_r = R Lambda R^{-1}, b_i = row i of R^{-1} E_r^{-1} B_r and
+ * c_i = column i of C_r^T R (eigenvectors by inverse iteration on the GPU,
+ * FP64).
+ *   shifts  in/out as in mor_irka_step.
+ *   btil    r x m complex, row-major: row i is b_i of shifts[i] (in/out).
+ *   ctil    r x q complex, row-major: row i is c_i (in/out).
+ * On return the rows follow the sorted new shifts and the -Im member of a
+ * conjugate pair carries the conjugate directions.  The scale of b_i and c_i
+ * is that of the eigenvectors; only the products c_i b_i^T are invariant.
+ * Errors as mor_irka_step. */
+int mor_irka_step_tangential(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil, int r,
+                             const mor_solve_opts* opts, mor_reduced* rom, mor_irka_stats* st);
 
 /* Restart the reuse schedule (the next mor_irka_step is iteration 1). */
 int mor_irka_reset(mor_t h);

@@ -96,6 +96,7 @@ SIGNATURES = {
                                  C.c_int, C.c_uint]),
     "mor_set_system_2nd": (C.c_int, [_P, C.POINTER(mor_csr), _P, C.c_double, C.c_double, _P, C.c_int, _P,
                                      C.c_int, C.c_int, C.c_uint]),
+    "mor_get_io": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mor_get_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int),
                                C.POINTER(C.c_int)]),
     "mor_build_precond": (C.c_int, [_P, mor_c64, C.c_int, C.c_int]),
@@ -113,6 +114,8 @@ SIGNATURES = {
     "mor_reduced_poles": (C.c_int, [_P, C.POINTER(mor_reduced), _P, _P]),
     "mor_irka_step": (C.c_int, [_P, _P, C.c_int, C.POINTER(mor_solve_opts), C.POINTER(mor_reduced),
                                 C.POINTER(mor_irka_stats)]),
+    "mor_irka_step_tangential": (C.c_int, [_P, _P, _P, _P, C.c_int, C.POINTER(mor_solve_opts), C.POINTER(mor_reduced),
+                                            C.POINTER(mor_irka_stats)]),
     "mor_irka_reset": (C.c_int, [_P]),
     "mor_eval_tf": (C.c_int, [_P, C.POINTER(mor_reduced), _P, C.c_int, _P, C.c_uint]),
     "mor_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
@@ -273,6 +276,13 @@ def mor_get_info(h):
     return {"n": n.value, "nnz": nnz.value, "format": fmt.value, "symmetric": bool(sym.value)}
 
 
+def mor_get_io(h):
+    """(m, q): the numbers of inputs and outputs of the system."""
+    m, q = C.c_int(), C.c_int()
+    _check(h, load_library().mor_get_io(h, C.byref(m), C.byref(q)))
+    return m.value, q.value
+
+
 def mor_build_precond(h, sigma, transpose: int = 0, precision: int = MOR_MIXED, allow=()):
     s = complex(sigma)
     return _check(h, load_library().mor_build_precond(h, mor_c64(s.real, s.imag), int(transpose), int(precision)),
@@ -425,6 +435,25 @@ def mor_irka_step(h, shifts, opts: Optional[mor_solve_opts] = None, allow=()):
     code = lib.mor_irka_step(h, s.ctypes.data_as(C.c_void_p), s.shape[0], C.byref(o), C.byref(rom), C.byref(st))
     _check(h, code, allow)
     return s, rom, st.as_dict()
+
+
+def mor_irka_step_tangential(h, shifts, btil, ctil, opts: Optional[mor_solve_opts] = None, allow=()):
+    """One tangential IRKA iteration (MIMO).  btil: r x m, ctil: r x q
+    complex directions, row i for shifts[i].  Returns (new shifts, new btil,
+    new ctil, mor_reduced, stats dict)."""
+    lib = load_library()
+    s = np.ascontiguousarray(np.asarray(shifts, dtype=np.complex128).ravel()).copy()
+    r = s.shape[0]
+    m, q = mor_get_io(h)
+    bt = np.ascontiguousarray(np.asarray(btil, dtype=np.complex128).reshape(r, m)).copy()
+    ct = np.ascontiguousarray(np.asarray(ctil, dtype=np.complex128).reshape(r, q)).copy()
+    rom = mor_reduced()
+    st = mor_irka_stats()
+    o = opts if opts is not None else mor_default_opts()
+    code = lib.mor_irka_step_tangential(h, s.ctypes.data_as(C.c_void_p), bt.ctypes.data_as(C.c_void_p),
+                                        ct.ctypes.data_as(C.c_void_p), r, C.byref(o), C.byref(rom), C.byref(st))
+    _check(h, code, allow)
+    return s, bt, ct, rom, st.as_dict()
 
 
 def mor_irka_reset(h):

@@ -11,6 +11,7 @@
 #include "mor_internal.h"
 #include "mor_types.cuh"
 #include "small_eig.cuh"
+#include "small_tangent.cuh"
 
 namespace {
 
@@ -103,6 +104,30 @@ __global__ void eig_kernel(int r, const double* Ar, const double* Er, double* ou
   int st = small_eig(r, Ar, Er, work, work + r * r, iwork, wr, wi);
   if (st == 0) mirror_sort(r, wr, wi, sr, si);
   out[4 * r] = (double)st;
+}
+
+// Tangential directions of r poles, one thread per pole (r <= 64): thread 0
+// forms M = E_r^{-1} A_r and F = E_r^{-1} B_r, then every thread runs the
+// inverse iterations of its pole.  out: r x m right directions, then r x q
+// left ones (complex, row i for pole i), then the status (1: E_r singular).
+__global__ void tangent_kernel(int r, int m, int q, const double* Ar, const double* Er, const double* Br,
+                               const double* Cr, const double* lam, double* out, double* work, int* iwork) {
+  double* M = work;
+  double* F = M + (size_t)r * r;
+  double* LU = F + (size_t)r * m;
+  double* per = LU + (size_t)r * r;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = tangent_prepare(r, m, Ar, Er, Br, M, F, LU, iwork);
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t == 0) out[2 * (size_t)r * (m + q)] = (double)bad;
+  if (bad || t >= r) return;
+  tz* K = (tz*)(per + (size_t)t * (2 * r * r + 4 * r));
+  tz* x = K + (size_t)r * r;
+  tz* y = x + r;
+  tz* bt = (tz*)out + (size_t)t * m;
+  tz* ct = (tz*)(out + 2 * (size_t)r * m) + (size_t)t * q;
+  tangent_dirs(r, m, q, M, F, Cr, tz_c(lam[2 * t], lam[2 * t + 1]), K, iwork + r + t * r, x, y, bt, ct);
 }
 
 // one block per frequency; (i w E_r - A_r) X = B_r by LU with partial
@@ -215,6 +240,16 @@ int dense_launch_eig(int r, const double* Ar, const double* Er, double* out, cud
   double* work = out + 4 * r + 1;
   int* iwork = (int*)(work + 2 * r * r);
   eig_kernel<<<1, 32, 0, s>>>(r, Ar, Er, out, work, iwork);
+  mor_count_launches(1);
+  return (int)cudaGetLastError();
+}
+
+size_t dense_tangent_work(int r, int m) { return (size_t)2 * r * r + (size_t)r * m + (size_t)r * (2 * r * r + 4 * r); }
+
+int dense_launch_tangent(int r, int m, int q, const double* Ar, const double* Er, const double* Br, const double* Cr,
+                         const double* lam, double* out, double* work, int* iwork, cudaStream_t s) {
+  if (r < 1 || r > 64) return (int)cudaErrorInvalidValue;
+  tangent_kernel<<<1, 64, 0, s>>>(r, m, q, Ar, Er, Br, Cr, lam, out, work, iwork);
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }

@@ -217,6 +217,12 @@ int dense_launch_gs_update(int n, int j, const double* V, int64_t ldv, const dou
 int dense_launch_scale(int n, double* v, const double* nrm2, cudaStream_t s);
 int dense_launch_eig(int r, const double* Ar, const double* Er, double* out /*wr,wi,sr,si,status*/,
                      cudaStream_t s);
+// tangential directions of r poles (lam: r complex as 2r doubles); out gets
+// r x m then r x q complex directions and a status double; work holds
+// dense_tangent_work(r, m) doubles, iwork r * (r + 1) ints
+size_t dense_tangent_work(int r, int m);
+int dense_launch_tangent(int r, int m, int q, const double* Ar, const double* Er, const double* Br, const double* Cr,
+                         const double* lam, double* out, double* work, int* iwork, cudaStream_t s);
 int dense_launch_tf(int r, int m, int q, const double* Ar, const double* Er, const double* Br,
                     const double* Cr, const double* omega, int nw, double* H, cudaStream_t s);
 int dense_launch_diag_mul(int n, int k, const double* d, const double* X, double* Y,

@@ -634,6 +634,14 @@ int mor_get_info(mor_t h, int64_t* n, int64_t* nnz, int* format, int* symmetric)
   return MOR_OK;
 }
 
+int mor_get_io(mor_t h, int* m, int* q) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (m) *m = h->m;
+  if (q) *q = h->q;
+  return MOR_OK;
+}
+
 int mor_get_pattern(mor_t h, int transpose, int32_t* rowptr, int32_t* col) {
   if (!h) return MOR_EINVAL;
   if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");

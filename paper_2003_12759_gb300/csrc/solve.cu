@@ -731,6 +731,24 @@ static int poles_device(mor_t h, const mor_reduced* rom, mor_c64* lam, mor_c64* 
   return MOR_OK;
 }
 
+// out(:, i) = M b_i for i < l, M n x m FP64 column-major, b_i = coef[i m .. i m + m - 1]
+// complex: the tangential right-hand sides B b_i and C c_i (complex128 columns)
+__global__ void combine_kernel(int64_t n, int m, int l, const double* M, const mor_c64* coef, double* out) {
+  const int64_t tot = n * l;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx % n;
+    const int i = (int)(idx / n);
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double v = M[row + (int64_t)j * n];
+      re += v * coef[(size_t)i * m + j].re;
+      im += v * coef[(size_t)i * m + j].im;
+    }
+    out[2 * idx] = re;
+    out[2 * idx + 1] = im;
+  }
+}
+
 // real (part 0) or imaginary (part 1) part of a complex128 column into an FP64 basis column
 __global__ void extract_kernel(int n, int part, const double* src, double* dst) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -1023,13 +1041,19 @@ int mor_irka_reset(mor_t h) {
   return MOR_OK;
 }
 
-int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, mor_reduced* rom_out,
-                  mor_irka_stats* st_out) {
+// One IRKA iteration; btil/ctil == nullptr: SISO (input and output column
+// 0), otherwise tangential with r x m / r x q directions (row-major, in and out).
+static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil, int r, const mor_solve_opts* opts,
+                          mor_reduced* rom_out, mor_irka_stats* st_out) {
   if (!h) return MOR_EINVAL;
   if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
   if (h->order != 1) return mor_fail(h, MOR_EINVAL, "IRKA of second-order systems is not available");
   if (r < 1 || r > MOR_MAX_R || !shifts) return mor_fail(h, MOR_EINVAL, "bad r");
-  if (h->m != 1 || h->q != 1) return mor_fail(h, MOR_EINVAL, "mor_irka_step supports SISO systems (m = q = 1)");
+  const bool tang = btil != nullptr;
+  if (!tang && (h->m != 1 || h->q != 1))
+    return mor_fail(h, MOR_EINVAL, "mor_irka_step is the SISO form (m = q = 1); use mor_irka_step_tangential");
+  if (tang && !ctil) return mor_fail(h, MOR_EINVAL, "tangential directions missing");
+  const int m = h->m, q = h->q;
   if (h->seg.nseg != 1) return mor_fail(h, MOR_EINVAL, "mor_irka_step needs a single system, not a batch");
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
@@ -1040,22 +1064,29 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
   mor_irka_stats st;
   std::memset(&st, 0, sizeof st);
   // sort (Re, |Im|, -Im) and check conjugate closure
-  std::vector<mor_c64> s(shifts, shifts + r);
-  for (auto& x : s) if (!std::isfinite(x.re) || !std::isfinite(x.im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
-  std::sort(s.begin(), s.end(), [](mor_c64 a, mor_c64 b) {
+  for (int i = 0; i < r; ++i)
+    if (!std::isfinite(shifts[i].re) || !std::isfinite(shifts[i].im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
+  std::vector<int> perm(r);
+  for (int i = 0; i < r; ++i) perm[i] = i;
+  std::stable_sort(perm.begin(), perm.end(), [&](int ia, int ib) {
+    const mor_c64 a = shifts[ia], b = shifts[ib];
     if (a.re != b.re) return a.re < b.re;
     if (std::fabs(a.im) != std::fabs(b.im)) return std::fabs(a.im) < std::fabs(b.im);
     return -a.im < -b.im;
   });
-  std::vector<mor_c64> sol;
+  std::vector<mor_c64> s(r);
+  for (int i = 0; i < r; ++i) s[i] = shifts[perm[i]];
+  std::vector<mor_c64> sol, bsol, csol;     // solved shifts and (tangential) their directions
   for (int i = 0; i < r; ++i) {
-    if (s[i].im > 0) {
-      if (i + 1 >= r || s[i + 1].re != s[i].re || s[i + 1].im != -s[i].im)
-        return mor_fail(h, MOR_EINVAL, "shift set not closed under conjugation");
-      sol.push_back(s[i]);
-      ++i;
-    } else if (s[i].im == 0) sol.push_back(s[i]);
-    else return mor_fail(h, MOR_EINVAL, "shift set not closed under conjugation");
+    if (s[i].im < 0) return mor_fail(h, MOR_EINVAL, "shift set not closed under conjugation");
+    if (s[i].im > 0 && (i + 1 >= r || s[i + 1].re != s[i].re || s[i + 1].im != -s[i].im))
+      return mor_fail(h, MOR_EINVAL, "shift set not closed under conjugation");
+    sol.push_back(s[i]);
+    if (tang) {
+      for (int j = 0; j < m; ++j) bsol.push_back(btil[(size_t)perm[i] * m + j]);
+      for (int j = 0; j < q; ++j) csol.push_back(ctil[(size_t)perm[i] * q + j]);
+    }
+    if (s[i].im > 0) ++i;
   }
   const int l = (int)sol.size();
   st.nsolve = l;
@@ -1098,6 +1129,24 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
     OpData& X = h->op(t);
     if (o.precond == 0) cplx |= chain_cplx(X, Ls[t]);
   }
+  for (const mor_c64& z : bsol) cplx |= (z.im != 0.0);
+  for (const mor_c64& z : csol) cplx |= (z.im != 0.0);
+  // tangential right-hand sides B b_i (primal) and C c_i (transposed), n x l complex128
+  DBuf rhs[2], dcoef;
+  if (tang) {
+    const int g = (int)std::min<int64_t>((n * l + 255) / 256, h->grid_cap);
+    MOR_CK(h, dcoef.alloc(sizeof(mor_c64) * (size_t)l * (m + q)));
+    MOR_CK(h, cudaMemcpyAsync(dcoef.p, bsol.data(), sizeof(mor_c64) * l * m, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(dcoef.as<mor_c64>() + (size_t)l * m, csol.data(), sizeof(mor_c64) * l * q,
+                              cudaMemcpyHostToDevice, h->stream));
+    for (int t = 0; t < 2; ++t) {
+      MOR_CK(h, rhs[t].alloc(sizeof(mor_c64) * (size_t)n * l));
+      combine_kernel<<<g, 256, 0, h->stream>>>(n, t == 0 ? m : q, l, (t == 0 ? h->B : h->C).as<double>(),
+                                               dcoef.as<mor_c64>() + (t == 0 ? 0 : (size_t)l * m), rhs[t].as<double>());
+      mor_count_launches(1);
+    }
+    MOR_CK(h, cudaGetLastError());
+  }
   DBuf xs[2];                       // solutions, n x l complex128 column-major (device)
   std::vector<mor_solve_stats> ss(l);
   int solve_status = MOR_OK;
@@ -1111,12 +1160,13 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
         MOR_TRY(build_factor(h, t, sol[i], sol[i], false, o.precision));
         st.builds_spai++;
         std::vector<int> L1(1, 1);
-        int s3 = solve_many(h, &sol[i], 1, t, o, L1, cplx, nullptr, true, X + (size_t)n * i, &ss[i]);
+        const mor_c64* Ri = tang ? rhs[t].as<mor_c64>() + (size_t)n * i : nullptr;
+        int s3 = solve_many(h, &sol[i], 1, t, o, L1, cplx, Ri, true, X + (size_t)n * i, &ss[i]);
         if (s3 != MOR_OK && s3 != MOR_ENOCONV && s3 != MOR_EBREAKDOWN) return s3;
         if (s3 != MOR_OK) s2 = s3;
       }
     } else {
-      s2 = solve_many(h, sol.data(), l, t, o, Ls[t], cplx, nullptr, true, X, ss.data());
+      s2 = solve_many(h, sol.data(), l, t, o, Ls[t], cplx, tang ? rhs[t].as<mor_c64>() : nullptr, true, X, ss.data());
       if (s2 != MOR_OK && s2 != MOR_ENOCONV && s2 != MOR_EBREAKDOWN) return s2;
     }
     if (s2 != MOR_OK) solve_status = s2;
@@ -1153,8 +1203,54 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
   cudaEventRecord(ev[3], h->stream);
   mor_reduced rom;
   MOR_TRY(project_device(h, Vb, Wb, r, &rom));
-  std::vector<mor_c64> news(r);
-  MOR_TRY(poles_device(h, &rom, nullptr, news.data()));
+  std::vector<mor_c64> news(r), lam(r);
+  MOR_TRY(poles_device(h, &rom, lam.data(), news.data()));
+  std::vector<mor_c64> bnew, cnew;
+  if (tang) {
+    // the pole behind each new shift (the sort permutes mirror images exactly)
+    std::vector<double> lsorted(2 * r);
+    std::vector<char> used(r, 0);
+    for (int i = 0; i < r; ++i) {
+      int e = -1;
+      for (int k = 0; k < r && e < 0; ++k)
+        if (!used[k] && std::fabs(lam[k].re) == news[i].re && -lam[k].im == news[i].im) e = k;
+      if (e < 0) return mor_fail(h, MOR_ESINGULAR, "internal: shift without its pole");
+      used[e] = 1;
+      lsorted[2 * i] = lam[e].re;
+      lsorted[2 * i + 1] = lam[e].im;
+    }
+    DBuf tw;
+    const size_t nout = 2 * (size_t)r * (m + q) + 1;
+    const size_t nw = dense_tangent_work(r, m);
+    MOR_CK(h, tw.alloc(sizeof(double) * ((size_t)r * (m + q) + 2 * r + nout + nw) + sizeof(int) * (size_t)r * (r + 1)));
+    double* dB = tw.as<double>();
+    double* dC = dB + (size_t)r * m;
+    double* dl = dC + (size_t)r * q;
+    double* dout = dl + 2 * r;
+    double* dwork = dout + nout;
+    int* diwork = (int*)(dwork + nw);
+    const double* dAr = h->ws_rom.as<double>();
+    const double* dEr = dAr + MOR_MAX_R * MOR_MAX_R;
+    MOR_CK(h, cudaMemcpyAsync(dB, rom.Br, sizeof(double) * r * m, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(dC, rom.Cr, sizeof(double) * r * q, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(dl, lsorted.data(), sizeof(double) * 2 * r, cudaMemcpyHostToDevice, h->stream));
+    MOR_CKI(h, dense_launch_tangent(r, m, q, dAr, dEr, dB, dC, dl, dout, dwork, diwork, h->stream));
+    std::vector<double> ho(nout);
+    MOR_CK(h, cudaMemcpyAsync(ho.data(), dout, sizeof(double) * nout, cudaMemcpyDeviceToHost, h->stream));
+    MOR_CK(h, cudaStreamSynchronize(h->stream));
+    if (ho[nout - 1] != 0.0) return mor_fail(h, MOR_ESINGULAR, "E_r is singular");
+    bnew.resize((size_t)r * m);
+    cnew.resize((size_t)r * q);
+    for (size_t i = 0; i < (size_t)r * m; ++i) bnew[i] = mor_c64{ho[2 * i], ho[2 * i + 1]};
+    for (size_t i = 0; i < (size_t)r * q; ++i) cnew[i] = mor_c64{ho[2 * r * m + 2 * i], ho[2 * r * m + 2 * i + 1]};
+    // the -Im member of a conjugate pair takes the conjugate directions
+    for (int i = 0; i + 1 < r; ++i)
+      if (news[i].im > 0) {
+        for (int j = 0; j < m; ++j) bnew[(size_t)(i + 1) * m + j] = mor_c64{bnew[(size_t)i * m + j].re, -bnew[(size_t)i * m + j].im};
+        for (int j = 0; j < q; ++j) cnew[(size_t)(i + 1) * q + j] = mor_c64{cnew[(size_t)i * q + j].re, -cnew[(size_t)i * q + j].im};
+        ++i;
+      }
+  }
   cudaEventRecord(ev[4], h->stream);
   cudaEventSynchronize(ev[4]);
   float ms;
@@ -1173,10 +1269,27 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, m
   st.z = h->irka_z;
   st.status = solve_status;
   for (int i = 0; i < r; ++i) shifts[i] = news[i];
+  if (tang) {
+    std::copy(bnew.begin(), bnew.end(), btil);
+    std::copy(cnew.begin(), cnew.end(), ctil);
+  }
   if (rom_out) *rom_out = rom;
   if (st_out) *st_out = st;
   if (solve_status != MOR_OK) return mor_fail(h, solve_status, "a shifted solve did not converge");
   return MOR_OK;
+}
+
+int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, mor_reduced* rom_out,
+                  mor_irka_stats* st_out) {
+  if (!h) return MOR_EINVAL;
+  return irka_step_impl(h, shifts, nullptr, nullptr, r, opts, rom_out, st_out);
+}
+
+int mor_irka_step_tangential(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil, int r,
+                             const mor_solve_opts* opts, mor_reduced* rom_out, mor_irka_stats* st_out) {
+  if (!h) return MOR_EINVAL;
+  if (!btil || !ctil) return mor_fail(h, MOR_EINVAL, "tangential directions required");
+  return irka_step_impl(h, shifts, btil, ctil, r, opts, rom_out, st_out);
 }
 
 int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precision, int reps, double* ms) {
