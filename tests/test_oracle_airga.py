@@ -1,0 +1,110 @@
+"""Pins of the second-order reduction oracle (AIRGA iteration, Algorithm 1
+with zeroth moments; the point update is a stated reading)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import airga, operator as op
+
+
+def _small2(nx=4, ny=3, nz=3, m=2, seed=3):
+    return W.config3(nx=nx, ny=ny, nz=nz, seed=seed, m=m)
+
+
+def _H(wl, s):
+    return airga.transfer_function_2nd(wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C, [s])[0]
+
+
+def test_moment_matching_at_every_point_every_iteration():
+    """One-sided Galerkin with the block solves in span(V) interpolates the
+    whole transfer matrix at every solved point (and its conjugate)."""
+    wl = _small2(nx=5, ny=4, nz=3)
+    pts = np.array([0.3 + 0.2j, 0.3 - 0.2j, 1.5])
+    sched = airga.ReuseSchedule2(wl.K, wl.M_diag, wl.alpha, wl.beta)
+    p = pts
+    for z in range(1, 4):
+        p_new, rom, _, _, solved = airga.airga_step(wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C, p, sched, z,
+                                                    solver="dense")
+        Mr, Dr, Kr, Fr, Cr = rom
+        assert Mr.shape[0] == wl.F.shape[1] * len(p)
+        for s in list(solved) + [np.conj(x) for x in solved if x.imag != 0]:
+            H = _H(wl, s)
+            Hr = airga.transfer_function_2nd_reduced(Mr, Dr, Kr, Fr, Cr, [s])[0]
+            assert np.linalg.norm(Hr - H) <= 1e-9 * np.linalg.norm(H)
+        np.testing.assert_allclose(Dr, wl.alpha * Mr + wl.beta * Kr)
+        p = p_new
+
+
+def test_qep_eigenvalues_closed_form_and_residual():
+    """One degree of freedom: lambda = (-d +- sqrt(d^2 - 4 m k)) / (2 m);
+    in general every eigenvalue makes lambda^2 M + lambda D + K singular."""
+    lam = airga.qep_eigenvalues(np.array([[2.0]]), np.array([[0.6]]), np.array([[5.0]]))
+    ref = (-0.6 + np.array([1, -1]) * np.sqrt(complex(0.36 - 40.0))) / 4.0
+    for z in ref:
+        assert np.min(np.abs(lam - z)) <= 1e-12 * abs(z)
+    rng = np.random.default_rng(2)
+    r = 7
+    X = rng.standard_normal((r, r))
+    Mr = X @ X.T + r * np.eye(r)
+    Y = rng.standard_normal((r, r))
+    Kr = Y @ Y.T + np.eye(r)
+    Dr = 0.01 * Mr + 0.02 * Kr
+    lam = airga.qep_eigenvalues(Mr, Dr, Kr)
+    assert lam.shape == (2 * r,)
+    for z in lam:
+        Q = z * z * Mr + z * Dr + Kr
+        sv = np.linalg.svd(Q, compute_uv=False)
+        assert sv[-1] <= 1e-10 * sv[0]
+
+
+def test_select_points_rule():
+    lam = np.array([-1.0 + 3.0j, -1.0 - 3.0j, -0.5, -2.0 + 0.5j, -2.0 - 0.5j, -10.0, -0.2 + 40j, -0.2 - 40j])
+    # |lam|: 3.16 (pair), 0.5 (real), 2.06 (pair), 10 (real), 40 (pair)
+    p3 = airga.select_points(lam, 3)
+    np.testing.assert_allclose(p3, [0.5, 2.0 + 0.5j, 2.0 - 0.5j])
+    p4 = airga.select_points(lam, 4)       # 0.5, pair 2.06, pair 3.16 does not fit -> real 10
+    np.testing.assert_allclose(p4, [0.5, 2.0 + 0.5j, 2.0 - 0.5j, 10.0])
+    only_pairs = np.array([-1.0 + 1.0j, -1.0 - 1.0j, -3.0 + 4.0j, -3.0 - 4.0j])
+    p3 = airga.select_points(only_pairs, 3)   # pair, then one place: |lambda| of the next pair
+    np.testing.assert_allclose(p3, [1.0 + 1.0j, 1.0 - 1.0j, 5.0])
+    unstable = np.array([0.7 + 2.0j, 0.7 - 2.0j])
+    np.testing.assert_allclose(airga.select_points(unstable, 2), [0.7 + 2.0j, 0.7 - 2.0j])
+
+
+def test_full_order_reproduces_H():
+    """r = n: V spans R^n, so H_r == H at any frequency."""
+    wl = _small2(nx=2, ny=2, nz=2, m=2)       # n = 8
+    pts = np.array([0.5 + 0.5j, 0.5 - 0.5j, 2.0 + 1.0j, 2.0 - 1.0j])    # r = 2 * 4 = 8
+    res, _ = airga.airga(wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C, pts, iters=1, solver="dense")
+    Mr, Kr = res.Er, res.Ar
+    Dr = wl.alpha * Mr + wl.beta * Kr
+    w = 1j * np.logspace(-2, 2, 9)
+    H = airga.transfer_function_2nd(wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C, w)
+    Hr = airga.transfer_function_2nd_reduced(Mr, Dr, Kr, res.Br, res.Cr, w)
+    np.testing.assert_allclose(Hr, H, rtol=1e-9, atol=1e-12 * np.max(np.abs(H)))
+
+
+def test_iterative_matches_dense():
+    """BiCGSTAB with the reused SPAI chain to 1e-8 reproduces the exact
+    iteration: the expansion points and the 2r reduced QEP eigenvalues to
+    1e-6, and the moments H_r(s_i) = H(s_i) at the solved points to 1e-6.
+    (H_r on a frequency grid is not the measure here: with damping ratios of
+    ~5e-4, a pole moved by 1e-8 of its modulus moves H_r near the resonance
+    by ~1e-8 / 5e-4 = 2e-5 of the peak.)"""
+    wl = _small2(nx=7, ny=6, nz=5, m=3)
+    pts = np.array([0.2 + 0.1j, 0.2 - 0.1j, 1.0])
+    rd, sd = airga.airga(wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C, pts, iters=3, solver="dense")
+    ri, si = airga.airga(wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C, pts, iters=3, solver="bicgstab")
+    for a, b in zip(ri.shifts_history, rd.shifts_history):
+        assert np.max(np.abs(a - b) / np.abs(b)) <= 1e-6
+    for (s_i, rom_i), (s_d, rom_d) in zip(si, sd):
+        li = airga.qep_eigenvalues(*rom_i[:3])
+        ld = airga.qep_eigenvalues(*rom_d[:3])
+        for z in ld:
+            assert np.min(np.abs(li - z)) <= 1e-6 * abs(z)
+        for s in s_i:
+            H = _H(wl, s)
+            Hr = airga.transfer_function_2nd_reduced(*rom_i, [s])[0]
+            assert np.linalg.norm(Hr - H) <= 1e-6 * np.linalg.norm(H)
+    assert all(len(p) == 3 for p in rd.shifts_history)
