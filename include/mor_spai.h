@@ -334,6 +334,45 @@ int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts,
 int mor_irka_step_tangential(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil, int r,
                              const mor_solve_opts* opts, mor_reduced* rom, mor_irka_stats* st);
 
+/* Reduced second-order system (caller-allocated, fixed capacity): M_r =
+ * V^T M V and K_r = V^T K V (r x r, column-major), D_r = alpha M_r + beta K_r,
+ * F_r = V^T F (r x m), C_r = V^T C (r x q). */
+#define MOR_MAX_R2 32
+typedef struct {
+    int    r, m, q;
+    double alpha, beta;
+    double Mr[MOR_MAX_R2 * MOR_MAX_R2];
+    double Kr[MOR_MAX_R2 * MOR_MAX_R2];
+    double Fr[MOR_MAX_R2 * MOR_MAX_IO];
+    double Cr[MOR_MAX_R2 * MOR_MAX_IO];
+} mor_reduced2;
+
+/* One iteration of the second-order reduction (AIRGA, Algorithm 1 with
+ * zeroth moments) of a system set by mor_set_system_2nd, with the reuse
+ * schedule of mor_irka_step on s^2 M + s D + K: block solves
+ * X(s_i) = (s_i^2 M + s_i D + K)^{-1} F at the points with Im >= 0 (one
+ * lock-step column per (point, input)), V = CGS2 of [Re X, Im X],
+ * Galerkin M_r, K_r, D_r, F_r, C_r (Sec. II), and the point update, which
+ * the paper leaves unstated (line 11), read as: the mirror images
+ * |Re lambda| - i Im lambda of the eigenvalues of the reduced quadratic
+ * eigenproblem (companion pencil, FP64 on the GPU) of smallest modulus, as
+ * many as before, closed under conjugation (a pair only when two places are
+ * left; a last single place with only pairs to come takes the real point
+ * |lambda| of the first pair that did not fit).
+ *   points  in: l expansion points (closed under conjugation); out: the next
+ *           l points, sorted (Re, |Im|, -Im).
+ *   r = m l must not exceed MOR_MAX_R2.  rom, st: out (may be NULL);
+ *   st->iters_V sums the block solves' iterations.
+ * MOR_EINVAL for a first-order system, a batch, r > MOR_MAX_R2 or
+ * precond = 1; otherwise errors as mor_irka_step. */
+int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts,
+                   mor_reduced2* rom, mor_irka_stats* st);
+
+/* H_r(i omega_w) = C_r^T ((i w)^2 M_r + i w D_r + K_r)^{-1} F_r of a reduced
+ * second-order system for nw frequencies; layout and flags as mor_eval_tf. */
+int mor_eval_tf2(mor_t h, const mor_reduced2* rom, const double* omega, int nw,
+                 mor_c64* H, unsigned flags);
+
 /* Restart the reuse schedule (the next mor_irka_step is iteration 1). */
 int mor_irka_reset(mor_t h);
 

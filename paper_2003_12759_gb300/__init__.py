@@ -56,6 +56,24 @@ class mor_solve_opts(C.Structure):
                 ("graph_chunk", C.c_int), ("precond", C.c_int), ("max_chain", C.c_int), ("restart", C.c_int)]
 
 
+MOR_MAX_R2 = 32
+
+
+class mor_reduced2(C.Structure):
+    _fields_ = [("r", C.c_int), ("m", C.c_int), ("q", C.c_int), ("alpha", C.c_double), ("beta", C.c_double),
+                ("Mr", C.c_double * (MOR_MAX_R2 * MOR_MAX_R2)), ("Kr", C.c_double * (MOR_MAX_R2 * MOR_MAX_R2)),
+                ("Fr", C.c_double * (MOR_MAX_R2 * MOR_MAX_IO)), ("Cr", C.c_double * (MOR_MAX_R2 * MOR_MAX_IO))]
+
+    def arrays(self):
+        """(M_r, D_r, K_r, F_r, C_r) as NumPy arrays (D_r = alpha M_r + beta K_r)."""
+        r, m, q = self.r, self.m, self.q
+        Mr = np.ctypeslib.as_array(self.Mr)[: r * r].reshape(r, r, order="F").copy()
+        Kr = np.ctypeslib.as_array(self.Kr)[: r * r].reshape(r, r, order="F").copy()
+        Fr = np.ctypeslib.as_array(self.Fr)[: r * m].reshape(r, m, order="F").copy()
+        Cr = np.ctypeslib.as_array(self.Cr)[: r * q].reshape(r, q, order="F").copy()
+        return Mr, self.alpha * Mr + self.beta * Kr, Kr, Fr, Cr
+
+
 class mor_solve_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("relres", C.c_double), ("status", C.c_int)]
 
@@ -117,6 +135,9 @@ SIGNATURES = {
     "mor_irka_step_tangential": (C.c_int, [_P, _P, _P, _P, C.c_int, C.POINTER(mor_solve_opts), C.POINTER(mor_reduced),
                                             C.POINTER(mor_irka_stats)]),
     "mor_irka_reset": (C.c_int, [_P]),
+    "mor_airga_step": (C.c_int, [_P, _P, C.c_int, C.POINTER(mor_solve_opts), C.POINTER(mor_reduced2),
+                                 C.POINTER(mor_irka_stats)]),
+    "mor_eval_tf2": (C.c_int, [_P, C.POINTER(mor_reduced2), _P, C.c_int, _P, C.c_uint]),
     "mor_eval_tf": (C.c_int, [_P, C.POINTER(mor_reduced), _P, C.c_int, _P, C.c_uint]),
     "mor_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
     "mor_time_kernel": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
@@ -454,6 +475,29 @@ def mor_irka_step_tangential(h, shifts, btil, ctil, opts: Optional[mor_solve_opt
                                         ct.ctypes.data_as(C.c_void_p), r, C.byref(o), C.byref(rom), C.byref(st))
     _check(h, code, allow)
     return s, bt, ct, rom, st.as_dict()
+
+
+def mor_airga_step(h, points, opts: Optional[mor_solve_opts] = None, allow=()):
+    """One second-order reduction iteration (mor_set_system_2nd systems).
+    Returns (new points, mor_reduced2, stats dict)."""
+    lib = load_library()
+    p = np.ascontiguousarray(np.asarray(points, dtype=np.complex128).ravel()).copy()
+    rom = mor_reduced2()
+    st = mor_irka_stats()
+    o = opts if opts is not None else mor_default_opts()
+    code = lib.mor_airga_step(h, p.ctypes.data_as(C.c_void_p), p.shape[0], C.byref(o), C.byref(rom), C.byref(st))
+    _check(h, code, allow)
+    return p, rom, st.as_dict()
+
+
+def mor_eval_tf2(h, rom: mor_reduced2, omega):
+    """H_r(i omega) of a reduced second-order system: nw x q x m (complex128)."""
+    lib = load_library()
+    w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64).ravel())
+    nw = w.shape[0]
+    H = np.empty(nw * rom.q * rom.m, dtype=np.complex128)
+    _check(h, lib.mor_eval_tf2(h, C.byref(rom), w.ctypes.data_as(C.c_void_p), nw, H.ctypes.data_as(C.c_void_p), 0))
+    return H.reshape((nw, rom.q, rom.m), order="F")
 
 
 def mor_irka_reset(h):

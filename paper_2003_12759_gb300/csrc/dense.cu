@@ -12,6 +12,7 @@
 #include "mor_types.cuh"
 #include "small_eig.cuh"
 #include "small_tangent.cuh"
+#include "small_qep.cuh"
 
 namespace {
 
@@ -130,11 +131,38 @@ __global__ void tangent_kernel(int r, int m, int q, const double* Ar, const doub
   tangent_dirs(r, m, q, M, F, Cr, tz_c(lam[2 * t], lam[2 * t + 1]), K, iwork + r + t * r, x, y, bt, ct);
 }
 
+// Second-order point update (one thread): the companion pencil of the
+// reduced QEP, its 2r eigenvalues (small_eig) and `count` new points
+// (qep_select).  out: 2r eigenvalues (re, im), count points (re, im), status
+// (0; 1 singular M_r; 2 QR did not converge; 3 too few eigenvalues).
+__global__ void qep_kernel(int r, int count, const double* Kr, const double* Mr, double alpha, double beta,
+                           double* out, double* work, int* iwork) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int n2 = 2 * r;
+  double* A2 = work;
+  double* E2 = A2 + (size_t)n2 * n2;
+  double* W1 = E2 + (size_t)n2 * n2;
+  double* W2 = W1 + (size_t)n2 * n2;
+  double* wr = W2 + (size_t)n2 * n2;
+  double* wi = wr + n2;
+  double* sel = wi + n2;
+  double* pr = sel + 3 * n2;
+  double* pi = pr + count;
+  qep_pencil(r, Mr, Kr, alpha, beta, A2, E2);
+  int st = small_eig(n2, A2, E2, W1, W2, iwork, wr, wi);
+  if (st == 0 && qep_select(n2, wr, wi, count, pr, pi, sel) != 0) st = 3;
+  for (int i = 0; i < n2; ++i) { out[2 * i] = wr[i]; out[2 * i + 1] = wi[i]; }
+  for (int i = 0; i < count; ++i) { out[2 * n2 + 2 * i] = (st == 0) ? pr[i] : 0.0; out[2 * n2 + 2 * i + 1] = (st == 0) ? pi[i] : 0.0; }
+  out[2 * n2 + 2 * count] = (double)st;
+}
+
 // one block per frequency; (i w E_r - A_r) X = B_r by LU with partial
 // pivoting in shared memory, then H = C_r^T X.
+// order 1: (i w E_r - A_r); order 2 (A_r = K_r, E_r = M_r): s^2 M_r + s D_r + K_r
+// at s = i w, i.e. (K_r - w^2 M_r) + i w (alpha M_r + beta K_r).
 __global__ void tf_kernel(int r, int m, int q, const double* __restrict__ Ar, const double* __restrict__ Er,
                           const double* __restrict__ Br, const double* __restrict__ Cr, const double* __restrict__ omega,
-                          int nw, cdouble* __restrict__ H) {
+                          int nw, cdouble* __restrict__ H, int order, double alpha, double beta) {
   extern __shared__ __align__(16) unsigned char sm[];
   cdouble* K = (cdouble*)sm;                 // r x r, column-major
   cdouble* X = K + r * r;                    // r x m
@@ -142,7 +170,8 @@ __global__ void tf_kernel(int r, int m, int q, const double* __restrict__ Ar, co
   const int w = blockIdx.x;
   if (w >= nw) return;
   const double om = omega[w];
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) K[t] = cdouble(-Ar[t], om * Er[t]);
+  for (int t = threadIdx.x; t < r * r; t += blockDim.x)
+    K[t] = (order == 2) ? cdouble(Ar[t] - om * om * Er[t], om * (alpha * Er[t] + beta * Ar[t])) : cdouble(-Ar[t], om * Er[t]);
   for (int t = threadIdx.x; t < r * m; t += blockDim.x) X[t] = cdouble(Br[t], 0.0);
   __syncthreads();
   for (int kk = 0; kk < r; ++kk) {
@@ -244,6 +273,15 @@ int dense_launch_eig(int r, const double* Ar, const double* Er, double* out, cud
   return (int)cudaGetLastError();
 }
 
+size_t dense_qep_work(int r, int count) { return (size_t)4 * (2 * r) * (2 * r) + (size_t)5 * (2 * r) + 2 * (size_t)count; }
+
+int dense_launch_qep(int r, int count, const double* Kr, const double* Mr, double alpha, double beta, double* out,
+                     double* work, int* iwork, cudaStream_t s) {
+  qep_kernel<<<1, 32, 0, s>>>(r, count, Kr, Mr, alpha, beta, out, work, iwork);
+  mor_count_launches(1);
+  return (int)cudaGetLastError();
+}
+
 size_t dense_tangent_work(int r, int m) { return (size_t)2 * r * r + (size_t)r * m + (size_t)r * (2 * r * r + 4 * r); }
 
 int dense_launch_tangent(int r, int m, int q, const double* Ar, const double* Er, const double* Br, const double* Cr,
@@ -255,13 +293,13 @@ int dense_launch_tangent(int r, int m, int q, const double* Ar, const double* Er
 }
 
 int dense_launch_tf(int r, int m, int q, const double* Ar, const double* Er, const double* Br, const double* Cr,
-                    const double* omega, int nw, double* H, cudaStream_t s) {
+                    const double* omega, int nw, double* H, cudaStream_t s, int order, double alpha, double beta) {
   size_t sm = sizeof(cdouble) * ((size_t)r * r + (size_t)r * m);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(tf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
   }
-  tf_kernel<<<nw, 128, sm, s>>>(r, m, q, Ar, Er, Br, Cr, omega, nw, (cdouble*)H);
+  tf_kernel<<<nw, 128, sm, s>>>(r, m, q, Ar, Er, Br, Cr, omega, nw, (cdouble*)H, order, alpha, beta);
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }

@@ -223,8 +223,15 @@ int dense_launch_eig(int r, const double* Ar, const double* Er, double* out /*wr
 size_t dense_tangent_work(int r, int m);
 int dense_launch_tangent(int r, int m, int q, const double* Ar, const double* Er, const double* Br, const double* Cr,
                          const double* lam, double* out, double* work, int* iwork, cudaStream_t s);
+// second-order point update: out gets 2r eigenvalues, count points (complex
+// as re, im) and a status; work dense_qep_work doubles, iwork 2r ints
+size_t dense_qep_work(int r, int count);
+int dense_launch_qep(int r, int count, const double* Kr, const double* Mr, double alpha, double beta, double* out,
+                     double* work, int* iwork, cudaStream_t s);
+// H(i w) per frequency; order 2 reads (A_r, E_r) as (K_r, M_r) with D_r = alpha M_r + beta K_r
 int dense_launch_tf(int r, int m, int q, const double* Ar, const double* Er, const double* Br,
-                    const double* Cr, const double* omega, int nw, double* H, cudaStream_t s);
+                    const double* Cr, const double* omega, int nw, double* H, cudaStream_t s, int order = 1,
+                    double alpha = 0.0, double beta = 0.0);
 int dense_launch_diag_mul(int n, int k, const double* d, const double* X, double* Y,
                           cudaStream_t s);
 

@@ -1041,6 +1041,42 @@ int mor_irka_reset(mor_t h) {
   return MOR_OK;
 }
 
+// Reuse schedule of Algorithm 4 for the solved shifts `sol` of one iteration
+// on the primal operator and, with nops == 2, the transposed one: on the
+// first iteration (or when the chain is rebuilt) a full SPAI at sol[0], else
+// a vertical Q from the previous first shift; then a horizontal Q for every
+// further shift.  Ls[t][i] = chain prefix length of shift i (0 without a
+// preconditioner; precond 1 builds per shift at solve time).
+static int schedule_chains(mor_t h, const std::vector<mor_c64>& sol, const mor_solve_opts& o, int nops,
+                           std::vector<int>* Ls, mor_irka_stats& st) {
+  const int l = (int)sol.size();
+  for (int t = 0; t < nops; ++t) {
+    OpData& X = h->op(t);
+    std::vector<int>& L = Ls[t];
+    L.assign(l, 0);
+    if (o.precond == 2 || o.precond == 1) continue;
+    const bool rebuild = (h->irka_z == 0) || X.chain.empty() || X.chain_prec != o.precision ||
+                         (o.max_chain > 0 && h->vlen[t] + 1 > o.max_chain);
+    if (!rebuild) { X.chain.resize(h->vlen[t]); }
+    if (rebuild) {
+      MOR_TRY(build_factor(h, t, sol[0], sol[0], false, o.precision));
+      h->vlen[t] = 1;
+      st.builds_spai++;
+    } else {
+      MOR_TRY(build_factor(h, t, X.chain.back().to, sol[0], true, o.precision));
+      h->vlen[t] += 1;
+      st.builds_reuse++;
+    }
+    for (int i = 1; i < l; ++i) {
+      MOR_TRY(build_factor(h, t, sol[i - 1], sol[i], true, o.precision));
+      st.builds_reuse++;
+    }
+    for (int i = 0; i < l; ++i) L[i] = h->vlen[t] + i;
+    st.chain_len = std::max(st.chain_len, L[l - 1]);
+  }
+  return MOR_OK;
+}
+
 // One IRKA iteration; btil/ctil == nullptr: SISO (input and output column
 // 0), otherwise tangential with r x m / r x q directions (row-major, in and out).
 static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil, int r, const mor_solve_opts* opts,
@@ -1093,32 +1129,7 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
   cudaEventRecord(ev[0], h->stream);
   // reuse schedule (Algorithm 4) for the primal and, unless symmetric, the transposed operator
   std::vector<int> Ls[2];
-  const int nops = h->sym ? 1 : 2;
-  for (int t = 0; t < nops; ++t) {
-    OpData& X = h->op(t);
-    std::vector<int>& L = Ls[t];
-    L.assign(l, 0);
-    if (o.precond == 2) continue;
-    if (o.precond == 1) continue;   // fresh SPAI per shift: built below, one solve at a time
-    const bool rebuild = (h->irka_z == 0) || X.chain.empty() || X.chain_prec != o.precision ||
-                         (o.max_chain > 0 && h->vlen[t] + 1 > o.max_chain);
-    if (!rebuild) { X.chain.resize(h->vlen[t]); }
-    if (rebuild) {
-      MOR_TRY(build_factor(h, t, sol[0], sol[0], false, o.precision));
-      h->vlen[t] = 1;
-      st.builds_spai++;
-    } else {
-      MOR_TRY(build_factor(h, t, X.chain.back().to, sol[0], true, o.precision));
-      h->vlen[t] += 1;
-      st.builds_reuse++;
-    }
-    for (int i = 1; i < l; ++i) {
-      MOR_TRY(build_factor(h, t, sol[i - 1], sol[i], true, o.precision));
-      st.builds_reuse++;
-    }
-    for (int i = 0; i < l; ++i) L[i] = h->vlen[t] + i;
-    st.chain_len = std::max(st.chain_len, L[l - 1]);
-  }
+  MOR_TRY(schedule_chains(h, sol, o, h->sym ? 1 : 2, Ls, st));
   if (h->sym) Ls[1] = Ls[0];
   cudaEventRecord(ev[1], h->stream);
   // solves: V (primal, rhs B) and W (transposed, rhs C)
@@ -1290,6 +1301,181 @@ int mor_irka_step_tangential(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* c
   if (!h) return MOR_EINVAL;
   if (!btil || !ctil) return mor_fail(h, MOR_EINVAL, "tangential directions required");
   return irka_step_impl(h, shifts, btil, ctil, r, opts, rom_out, st_out);
+}
+
+int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, mor_reduced2* rom_out,
+                   mor_irka_stats* st_out) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (h->order != 2) return mor_fail(h, MOR_EINVAL, "mor_airga_step needs a second-order system (mor_set_system_2nd)");
+  if (h->seg.nseg != 1) return mor_fail(h, MOR_EINVAL, "mor_airga_step needs a single system, not a batch");
+  const int m = h->m, q = h->q;
+  if (!points || l < 1 || m * l > MOR_MAX_R2) return mor_fail(h, MOR_EINVAL, "bad points: need 1 <= m l <= %d", MOR_MAX_R2);
+  mor_solve_opts o;
+  if (opts) o = *opts; else mor_default_opts(&o);
+  if (o.precond == 1) return mor_fail(h, MOR_EINVAL, "mor_airga_step supports precond 0 (reuse) and 2 (none)");
+  cudaSetDevice(h->dev);
+  cudaEvent_t ev[5];
+  for (auto& e : ev) cudaEventCreate(&e);
+  struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]); } } eg{ev};
+  mor_irka_stats st;
+  std::memset(&st, 0, sizeof st);
+  for (int i = 0; i < l; ++i)
+    if (!std::isfinite(points[i].re) || !std::isfinite(points[i].im)) return mor_fail(h, MOR_EINVAL, "non-finite point");
+  std::vector<mor_c64> s(points, points + l);
+  std::stable_sort(s.begin(), s.end(), [](mor_c64 a, mor_c64 b) {
+    if (a.re != b.re) return a.re < b.re;
+    if (std::fabs(a.im) != std::fabs(b.im)) return std::fabs(a.im) < std::fabs(b.im);
+    return -a.im < -b.im;
+  });
+  std::vector<mor_c64> sol;
+  for (int i = 0; i < l; ++i) {
+    if (s[i].im < 0 || (s[i].im > 0 && (i + 1 >= l || s[i + 1].re != s[i].re || s[i + 1].im != -s[i].im)))
+      return mor_fail(h, MOR_EINVAL, "point set not closed under conjugation");
+    sol.push_back(s[i]);
+    if (s[i].im > 0) ++i;
+  }
+  const int ls = (int)sol.size();
+  const int r = m * l;
+  st.nsolve = ls * m;
+  cudaEventRecord(ev[0], h->stream);
+  std::vector<int> Ls[2];
+  MOR_TRY(schedule_chains(h, sol, o, 1, Ls, st));
+  cudaEventRecord(ev[1], h->stream);
+  // block solves: column c = (point c / m, input c % m)
+  const int k = ls * m;
+  const int64_t n = h->n;
+  std::vector<mor_c64> sig(k), unit((size_t)k * m, mor_c64{0.0, 0.0});
+  std::vector<int> L(k);
+  bool cplx = false;
+  for (int c = 0; c < k; ++c) {
+    sig[c] = sol[c / m];
+    L[c] = Ls[0][c / m];
+    unit[(size_t)c * m + c % m] = mor_c64{1.0, 0.0};
+    cplx |= (sig[c].im != 0.0);
+  }
+  if (o.precond == 0) cplx |= chain_cplx(h->op(0), Ls[0]);
+  DBuf rhs, dcoef, xs;
+  MOR_CK(h, dcoef.alloc(sizeof(mor_c64) * unit.size()));
+  MOR_CK(h, cudaMemcpyAsync(dcoef.p, unit.data(), sizeof(mor_c64) * unit.size(), cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, rhs.alloc(sizeof(mor_c64) * (size_t)n * k));
+  MOR_CK(h, xs.alloc(sizeof(mor_c64) * (size_t)n * k));
+  const int g = (int)std::min<int64_t>((n * k + 255) / 256, h->grid_cap);
+  combine_kernel<<<g, 256, 0, h->stream>>>(n, m, k, h->B.as<double>(), dcoef.as<mor_c64>(), rhs.as<double>());
+  mor_count_launches(1);
+  MOR_CK(h, cudaGetLastError());
+  std::vector<mor_solve_stats> ss(k);
+  const int solve_status = solve_many(h, sig.data(), k, 0, o, L, cplx, rhs.as<mor_c64>(), true, xs.as<mor_c64>(),
+                                      ss.data());
+  if (solve_status != MOR_OK && solve_status != MOR_ENOCONV && solve_status != MOR_EBREAKDOWN) return solve_status;
+  for (int c = 0; c < k; ++c) {
+    st.iters_V += ss[c].iters;
+    st.max_relres = std::max(st.max_relres, ss[c].relres);
+  }
+  cudaEventRecord(ev[2], h->stream);
+  // real basis [Re X_i, Im X_i] per solved point, CGS2, Galerkin projection (W = V)
+  DBuf basis;
+  MOR_CK(h, basis.alloc(sizeof(double) * (size_t)n * r));
+  double* Vb = basis.as<double>();
+  const int ge = (int)std::min<int64_t>((n + 255) / 256, h->grid_cap);
+  int col = 0;
+  for (int i = 0; i < ls; ++i)
+    for (int part = 0; part < (sol[i].im != 0.0 ? 2 : 1); ++part)
+      for (int j = 0; j < m; ++j) {
+        const double* src = (const double*)(xs.as<mor_c64>() + (size_t)n * (i * m + j));
+        extract_kernel<<<ge, 256, 0, h->stream>>>((int)n, part, src, Vb + (size_t)n * col++);
+        mor_count_launches(1);
+      }
+  MOR_CK(h, cudaGetLastError());
+  int dep = 0;
+  MOR_TRY(orth_device(h, Vb, n, r, &dep));
+  if (dep) return mor_fail(h, MOR_ESINGULAR, "projection basis is numerically rank deficient");
+  cudaEventRecord(ev[3], h->stream);
+  mor_reduced rom;
+  MOR_TRY(project_device(h, Vb, Vb, r, &rom));        // Ar = K_r, Er = M_r, Br = F_r, Cr = C_r
+  // reduced QEP and the next points (device, one thread)
+  DBuf qw;
+  const size_t nout = 2 * (size_t)(2 * r) + 2 * (size_t)l + 1;
+  const size_t nw = dense_qep_work(r, l);
+  MOR_CK(h, qw.alloc(sizeof(double) * (nout + nw) + sizeof(int) * 2 * (size_t)r));
+  double* dout = qw.as<double>();
+  double* dwork = dout + nout;
+  int* diwork = (int*)(dwork + nw);
+  const double* dKr = h->ws_rom.as<double>();
+  const double* dMr = dKr + MOR_MAX_R * MOR_MAX_R;
+  MOR_CKI(h, dense_launch_qep(r, l, dKr, dMr, h->alpha, h->beta, dout, dwork, diwork, h->stream));
+  std::vector<double> ho(nout);
+  MOR_CK(h, cudaMemcpyAsync(ho.data(), dout, sizeof(double) * nout, cudaMemcpyDeviceToHost, h->stream));
+  cudaEventRecord(ev[4], h->stream);
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  const int qst = (int)ho[nout - 1];
+  if (qst != 0)
+    return mor_fail(h, MOR_ESINGULAR, qst == 1 ? "M_r is singular" : qst == 2 ? "QR iteration did not converge"
+                                                                          : "too few eigenvalues for the points");
+  float ms;
+  cudaEventElapsedTime(&ms, ev[0], ev[1]); st.ms_precond = ms;
+  cudaEventElapsedTime(&ms, ev[1], ev[2]); st.ms_solve = ms;
+  cudaEventElapsedTime(&ms, ev[2], ev[3]); st.ms_orth = ms;
+  cudaEventElapsedTime(&ms, ev[3], ev[4]); st.ms_reduce = ms;
+  double chg = 0.0;
+  std::vector<mor_c64> news(l);
+  for (int i = 0; i < l; ++i) {
+    news[i] = mor_c64{ho[4 * r + 2 * i], ho[4 * r + 2 * i + 1]};
+    const double a = std::hypot(news[i].re, news[i].im);
+    chg = std::max(chg, std::hypot(news[i].re - s[i].re, news[i].im - s[i].im) / (a > 0 ? a : 1.0));
+  }
+  st.shift_change = chg;
+  h->irka_z += 1;
+  st.z = h->irka_z;
+  st.status = solve_status;
+  for (int i = 0; i < l; ++i) points[i] = news[i];
+  if (rom_out) {
+    rom_out->r = r;
+    rom_out->m = m;
+    rom_out->q = q;
+    rom_out->alpha = h->alpha;
+    rom_out->beta = h->beta;
+    std::memcpy(rom_out->Mr, rom.Er, sizeof(double) * r * r);
+    std::memcpy(rom_out->Kr, rom.Ar, sizeof(double) * r * r);
+    std::memcpy(rom_out->Fr, rom.Br, sizeof(double) * r * m);
+    std::memcpy(rom_out->Cr, rom.Cr, sizeof(double) * r * q);
+  }
+  if (st_out) *st_out = st;
+  if (solve_status != MOR_OK) return mor_fail(h, solve_status, "a shifted solve did not converge");
+  return MOR_OK;
+}
+
+int mor_eval_tf2(mor_t h, const mor_reduced2* rom, const double* omega, int nw, mor_c64* H, unsigned flags) {
+  if (!h || !rom || !omega || !H) return MOR_EINVAL;
+  if (rom->r < 1 || rom->r > MOR_MAX_R2 || rom->m < 1 || rom->m > MOR_MAX_IO || rom->q < 1 || rom->q > MOR_MAX_IO ||
+      nw < 1)
+    return mor_fail(h, MOR_EINVAL, "bad reduced system or nw");
+  cudaSetDevice(h->dev);
+  const int r = rom->r, m = rom->m, q = rom->q;
+  DBuf d;
+  const size_t nrom = (size_t)2 * r * r + (size_t)r * m + (size_t)r * q;
+  MOR_CK(h, d.alloc(sizeof(double) * (nrom + nw) + sizeof(mor_c64) * (size_t)nw * m * q));
+  double* dK = d.as<double>();
+  double* dM = dK + r * r;
+  double* dF = dM + r * r;
+  double* dC = dF + r * m;
+  double* dw = dC + r * q;
+  mor_c64* dH = (mor_c64*)(dw + nw);
+  MOR_CK(h, cudaMemcpyAsync(dK, rom->Kr, sizeof(double) * r * r, cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(dM, rom->Mr, sizeof(double) * r * r, cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(dF, rom->Fr, sizeof(double) * r * m, cudaMemcpyHostToDevice, h->stream));
+  MOR_CK(h, cudaMemcpyAsync(dC, rom->Cr, sizeof(double) * r * q, cudaMemcpyHostToDevice, h->stream));
+  const bool dev = flags & MOR_DEVICE_PTRS;
+  const double* w = omega;
+  if (!dev) {
+    MOR_CK(h, cudaMemcpyAsync(dw, omega, sizeof(double) * nw, cudaMemcpyHostToDevice, h->stream));
+    w = dw;
+  }
+  mor_c64* out = dev ? H : dH;
+  MOR_CKI(h, dense_launch_tf(r, m, q, dK, dM, dF, dC, w, nw, (double*)out, h->stream, 2, rom->alpha, rom->beta));
+  if (!dev) MOR_CK(h, cudaMemcpyAsync(H, dH, sizeof(mor_c64) * (size_t)nw * m * q, cudaMemcpyDeviceToHost, h->stream));
+  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  return MOR_OK;
 }
 
 int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precision, int reps, double* ms) {

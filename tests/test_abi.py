@@ -71,14 +71,16 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mor_spai.h"\n'
-                   'int main(void) { printf("%zu %zu %zu %zu %zu\\n", sizeof(mor_solve_opts), '
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mor_solve_opts), '
                    'offsetof(mor_solve_opts, restart), offsetof(mor_solve_opts, max_chain), '
-                   'sizeof(mor_solve_stats), sizeof(mor_reduced)); return 0; }\n')
+                   'sizeof(mor_solve_stats), sizeof(mor_reduced), sizeof(mor_reduced2), '
+                   'offsetof(mor_reduced2, Kr)); return 0; }\n')
     exe = tmp_path / "layout"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(mor.mor_solve_opts), mor.mor_solve_opts.restart.offset, mor.mor_solve_opts.max_chain.offset,
-            ctypes.sizeof(mor.mor_solve_stats), ctypes.sizeof(mor.mor_reduced)]
+            ctypes.sizeof(mor.mor_solve_stats), ctypes.sizeof(mor.mor_reduced), ctypes.sizeof(mor.mor_reduced2),
+            mor.mor_reduced2.Kr.offset]
     assert got == want
 
 

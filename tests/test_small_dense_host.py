@@ -111,3 +111,66 @@ def test_tangential_directions_match_oracle(harness, seed, r, m, q):
     Hr = Cr.T @ np.linalg.solve(s * Er - Ar, Br)
     Hres = sum(np.outer(ct[i], bt[i]) / (s - lam[i]) for i in range(r))
     np.testing.assert_allclose(Hres, Hr, rtol=1e-7, atol=1e-9 * np.linalg.norm(Hr))
+
+
+QEP_HARNESS = r"""
+#define __host__
+#define __device__
+#include <cstdio>
+#include <vector>
+#include "small_qep.cuh"
+int main() {
+  int r, count;
+  double alpha, beta;
+  if (scanf("%d %d %lf %lf", &r, &count, &alpha, &beta) != 4) return 1;
+  std::vector<double> M(r * r), K(r * r);
+  for (double& x : M) if (scanf("%lf", &x) != 1) return 1;
+  for (double& x : K) if (scanf("%lf", &x) != 1) return 1;
+  const int n2 = 2 * r;
+  std::vector<double> A2(n2 * n2), E2(n2 * n2), W1(n2 * n2), W2(n2 * n2), wr(n2), wi(n2), pr(count), pi(count), w(3 * n2);
+  std::vector<int> piv(n2);
+  qep_pencil(r, M.data(), K.data(), alpha, beta, A2.data(), E2.data());
+  int st = small_eig(n2, A2.data(), E2.data(), W1.data(), W2.data(), piv.data(), wr.data(), wi.data());
+  printf("%d\n", st);
+  for (int i = 0; i < n2; ++i) printf("%.17g %.17g\n", wr[i], wi[i]);
+  int s2 = qep_select(n2, wr.data(), wi.data(), count, pr.data(), pi.data(), w.data());
+  printf("%d\n", s2);
+  for (int i = 0; i < count; ++i) printf("%.17g %.17g\n", pr[i], pi[i]);
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def qep_harness(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("small_qep")
+    src = d / "q.cpp"
+    src.write_text(QEP_HARNESS)
+    exe = d / "q"
+    subprocess.run([cxx, "-O2", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+@pytest.mark.parametrize("seed,r,count", [(1, 3, 3), (2, 6, 3), (3, 12, 3), (4, 12, 4), (5, 20, 5)])
+def test_qep_poles_and_point_update_match_oracle(qep_harness, seed, r, count):
+    from oracle import airga
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((r, r))
+    Mr = X @ X.T + r * np.eye(r)
+    Y = rng.standard_normal((r, r))
+    Kr = Y @ Y.T + 0.1 * np.eye(r)
+    alpha, beta = 1e-3 * (1 + seed), 1e-4 * seed
+    data = "%d %d %.17g %.17g\n" % (r, count, alpha, beta) + " ".join(
+        "%.17g" % v for A in (Mr, Kr) for v in A.ravel(order="F"))
+    out = subprocess.run([qep_harness], input=data, capture_output=True, text=True, check=True).stdout.split("\n")
+    assert int(out[0]) == 0
+    lam = np.array([complex(*map(float, out[1 + i].split())) for i in range(2 * r)])
+    ref = airga.qep_eigenvalues(Mr, alpha * Mr + beta * Kr, Kr)
+    for z in ref:
+        assert np.min(np.abs(lam - z)) <= 1e-9 * abs(z)
+    assert int(out[1 + 2 * r]) == 0
+    pts = np.array([complex(*map(float, out[2 + 2 * r + i].split())) for i in range(count)])
+    np.testing.assert_allclose(pts, airga.select_points(ref, count), rtol=1e-9)
