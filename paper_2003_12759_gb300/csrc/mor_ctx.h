@@ -42,7 +42,7 @@ struct OpData {
   DBuf rowptr, col;                      // CSR (device)
   DBuf sptr, scol;                       // SELL-32 layout (device)
   DBuf a64, a32, e64, e32;               // values in layout order
-  DBuf ca64, ce64;                       // values in CSR order (column data for the other op's SPAI)
+  DBuf ca64, ce64, ca32, ce32;           // values in CSR order (column data for the other op's SPAI)
   DBuf outpos;                           // int64 per column-entry: position in this op's layout
   DBuf iptr_b, iidx_b;                   // shadow sets (owned)
   const int64_t* iptr = nullptr;         // shadow sets (may point into the other op's buffers)

@@ -197,6 +197,9 @@ struct SpaiArgs {
   const double* ca;         // A values of those entries (FP64)
   const double* ce;         // E values (EK_CSR) or nullptr
   const double* ediag;      // E diagonal (EK_DIAG) or nullptr
+  const float* ca32;        // FP32 copies, read when the factor is FP32 / complex64
+  const float* ce32;
+  const float* ediag32;
   int ekind;
   const int64_t* outpos;    // layout position of each column entry in this operator
   const int64_t* iptr;      // shadow sets I_j

@@ -308,14 +308,16 @@ int build_op(mor_t h, OpData& op, const HostCSR& S, const std::vector<double>& s
   MOR_TRY(upload(h, op.a64, la));
   MOR_TRY(upload(h, op.a32, la32));
   MOR_TRY(upload(h, op.ca64, sa));
+  MOR_TRY(upload(h, op.ca32, std::vector<float>(sa.begin(), sa.end())));
   if (has_e) {
     std::vector<double> le = permute_to_layout(se, op.h_lay, op.nlay);
     std::vector<float> le32(le.begin(), le.end());
     MOR_TRY(upload(h, op.e64, le));
     MOR_TRY(upload(h, op.e32, le32));
     MOR_TRY(upload(h, op.ce64, se));
+    MOR_TRY(upload(h, op.ce32, std::vector<float>(se.begin(), se.end())));
   } else {
-    op.e64.release(); op.e32.release(); op.ce64.release();
+    op.e64.release(); op.e32.release(); op.ce64.release(); op.ce32.release();
   }
   return MOR_OK;
 }

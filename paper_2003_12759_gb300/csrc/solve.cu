@@ -100,6 +100,9 @@ static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bo
   a.ca = Y.ca64.as<double>();
   a.ce = Y.ce64.as<double>();
   a.ediag = h->ediag64.as<double>();
+  a.ca32 = Y.ca32.as<float>();
+  a.ce32 = Y.ce32.as<float>();
+  a.ediag32 = h->ediag32.as<float>();
   a.ekind = h->ekind;
   a.outpos = X.outpos.as<int64_t>();
   a.iptr = X.iptr;

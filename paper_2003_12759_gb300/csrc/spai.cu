@@ -8,23 +8,23 @@
 // I_j reached by the columns J_j enter the problem (the others add a
 // constant), so each column is a dense |I_j| x |J_j| least-squares problem.
 //
-// GB300 mapping: one warp per column.  The warp gathers the block
-// G = A(s_new)(I_j, J_j) straight from the stored sparse columns (the shifted
-// matrix is never formed: each entry is sE e + sA a), stages it in shared
-// memory column-major (lane l owns rows l, l + 32, ...), factors it by
-// Householder QR with warp-shuffle reductions, applies Q^H to the right-hand
-// side and back-substitutes.  The solution is scattered straight into the
-// factor's value array in the operator's storage layout.
+// GB300 mapping: one group of LPC lanes per column (LPC = 4 ... 32 so that a
+// lane owns at most four rows; 32 / LPC columns per warp).  A group gathers
+// the block G = A(s_new)(I_j, J_j) straight from the stored sparse columns
+// (the shifted matrix is never formed: each entry is sE e + sA a), stages it
+// in shared memory column-major, factors it by Householder QR with
+// group-shuffle reductions, applies Q^H to the right-hand side and
+// back-substitutes.  The solution is scattered straight into the factor's
+// value array in the operator's storage layout.  A warp per column, with 25
+// rows on 32 lanes and five-step reductions, spent 5.2k warp instructions
+// per column of the 7-point stencil and kept the FP64 pipe half busy forming
+// the entries in FP64; FP32 / complex64 factors now gather from FP32 copies.
 #include "mor_internal.h"
 #include "mor_types.cuh"
 
-namespace {
+#include <algorithm>
 
-template <typename S> __device__ __forceinline__ S from_cd(cdouble z);
-template <> __device__ __forceinline__ float from_cd<float>(cdouble z) { return (float)z.re; }
-template <> __device__ __forceinline__ double from_cd<double>(cdouble z) { return z.re; }
-template <> __device__ __forceinline__ cfloat from_cd<cfloat>(cdouble z) { return cfloat((float)z.re, (float)z.im); }
-template <> __device__ __forceinline__ cdouble from_cd<cdouble>(cdouble z) { return z; }
+namespace {
 
 __device__ __forceinline__ float div_s(float a, float b) { return a / b; }
 __device__ __forceinline__ double div_s(double a, double b) { return a / b; }
@@ -33,14 +33,29 @@ template <typename R> __device__ __forceinline__ cplx<R> div_s(cplx<R> a, cplx<R
   return cplx<R>((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
 }
 
-// A(s) entry of column `kc` at column-entry q (row = colidx[q])
-__device__ __forceinline__ cdouble entry(const SpaiArgs& a, const Coef& cf, int64_t q, int row, int kc) {
-  double ev = 0.0;
-  if (a.ekind == EK_CSR) ev = a.ce[q];
-  else if (row == kc) ev = (a.ekind == EK_DIAG) ? a.ediag[kc] : 1.0;
-  const double av = a.ca[q];
-  return cdouble(cf.sEr * ev + cf.sAr * av, cf.sEi * ev + cf.sAi * av);
+// A(s) entry of column `kc` at column-entry q (row = colidx[q]), in the
+// precision V of the column data (FP32 for FP32 / complex64 factors: the
+// FP64 pipe of this GPU is narrow, and the factor is rounded to FP32 anyway)
+template <typename V> struct ColData {
+  const V* ca;
+  const V* ce;
+  const V* ediag;
+};
+template <typename V>
+__device__ __forceinline__ cplx<V> entry(const ColData<V>& d, int ekind, const cplx<V> (&cf)[2], int64_t q, int row,
+                                         int kc) {
+  V ev = V(0);
+  if (ekind == EK_CSR) ev = d.ce[q];
+  else if (row == kc) ev = (ekind == EK_DIAG) ? d.ediag[kc] : V(1);
+  const V av = d.ca[q];
+  return cplx<V>(cf[0].re * ev + cf[1].re * av, cf[0].im * ev + cf[1].im * av);
 }
+
+template <typename S, typename V> __device__ __forceinline__ S to_s(cplx<V> z);
+template <> __device__ __forceinline__ float to_s<float, float>(cplx<float> z) { return z.re; }
+template <> __device__ __forceinline__ cfloat to_s<cfloat, float>(cplx<float> z) { return z; }
+template <> __device__ __forceinline__ double to_s<double, double>(cplx<double> z) { return z.re; }
+template <> __device__ __forceinline__ cdouble to_s<cdouble, double>(cplx<double> z) { return z; }
 
 __device__ __forceinline__ int find_row(const int* Il, int nI, int row) {
   int lo = 0, hi = nI - 1;
@@ -51,96 +66,142 @@ __device__ __forceinline__ int find_row(const int* Il, int nI, int row) {
   return lo;   // I_j contains every row of the gathered columns by construction
 }
 
+// shared memory of one column's problem
 template <typename S>
-__host__ __device__ inline size_t warp_bytes(int nImax, int nJmax) {
+__host__ __device__ inline size_t col_bytes(int nImax, int nJmax) {
   size_t b = ((size_t)nImax * nJmax + nImax + 2 * nJmax) * sizeof(S) + (size_t)nImax * sizeof(int);
   return (b + 15) & ~(size_t)15;
 }
 
-template <typename S>
-__global__ void __launch_bounds__(256) spai_kernel(SpaiArgs a, S* __restrict__ out) {
+// sum over the LPC lanes of a column group (xor offsets below LPC stay inside the group)
+template <int LPC, typename T> __device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = LPC >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <int LPC, typename R> __device__ __forceinline__ cplx<R> group_sum(cplx<R> v) {
+#pragma unroll
+  for (int o = LPC >> 1; o > 0; o >>= 1) {
+    v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+    v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+  }
+  return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One column per group of LPC lanes, 32 / LPC columns per warp: each group
+// gathers G = A(s_new)(I_j, J_j) into shared memory (column-major, lane l of
+// the group owns rows l, l + LPC, ...), factors it by Householder QR with
+// group reductions, applies Q^H to the right-hand side and back-substitutes.
+// Loop bounds are the maxima over the warp's groups (a group past its own
+// sizes computes nothing), so every shuffle runs with the whole warp.
+template <typename S, typename V, int LPC>
+__global__ void __launch_bounds__(256) spai_kernel(SpaiArgs a, ColData<V> cd, S* __restrict__ out) {
   typedef typename real_of<S>::type R;
+  constexpr int CPW = 32 / LPC;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned char* base = smem + (size_t)wid * warp_bytes<S>(a.nImax, a.nJmax);
+  const int grp = lane / LPC, gl = lane % LPC;
+  unsigned char* base = smem + ((size_t)wid * CPW + grp) * col_bytes<S>(a.nImax, a.nJmax);
   S* G = (S*)base;                                   // nJmax columns of nImax rows
   S* rhs = G + (size_t)a.nImax * a.nJmax;
   S* Rd = rhs + a.nImax;                             // diagonal of R
   S* qv = Rd + a.nJmax;                              // solution
   int* Il = (int*)(qv + a.nJmax);
   const int ld = a.nImax;
+  const cplx<V> cnew[2] = {cplx<V>((V)a.cnew.sEr, (V)a.cnew.sEi), cplx<V>((V)a.cnew.sAr, (V)a.cnew.sAi)};
+  const cplx<V> cold[2] = {cplx<V>((V)a.cold.sEr, (V)a.cold.sEi), cplx<V>((V)a.cold.sAr, (V)a.cold.sAi)};
 
-  for (int j = blockIdx.x * nw + wid; j < a.n; j += gridDim.x * nw) {
-    const int64_t i0 = a.iptr[j];
-    const int nI = (int)(a.iptr[j + 1] - i0);
-    const int c0 = a.colptr[j];
-    const int nJ = a.colptr[j + 1] - c0;
-    for (int t = lane; t < nI; t += 32) Il[t] = a.iidx[i0 + t];
-    for (int t = lane; t < nJ * ld; t += 32) G[t] = S(0);
-    for (int t = lane; t < nI; t += 32) rhs[t] = S(0);
+  for (int j0 = (blockIdx.x * nw + wid) * CPW; j0 < a.n; j0 += gridDim.x * nw * CPW) {
+    const int j = j0 + grp;
+    const bool valid = j < a.n;
+    int64_t i0 = 0;
+    int nI = 0, c0 = 0, nJ = 0;
+    if (valid) {
+      i0 = a.iptr[j];
+      nI = (int)(a.iptr[j + 1] - i0);
+      c0 = a.colptr[j];
+      nJ = a.colptr[j + 1] - c0;
+    }
+    const int nJw = warp_max(nJ);
+    for (int t = gl; t < nI; t += LPC) Il[t] = a.iidx[i0 + t];
+    for (int t = gl; t < nJ * ld; t += LPC) G[t] = S(0);
+    for (int t = gl; t < nI; t += LPC) rhs[t] = S(0);
     __syncwarp();
     // gather G = A(s_new)(I_j, J_j) column by column
     for (int t = 0; t < nJ; ++t) {
       const int kc = a.colidx[c0 + t];
       const int q0 = a.colptr[kc], q1 = a.colptr[kc + 1];
-      for (int q = q0 + lane; q < q1; q += 32) {
+      for (int q = q0 + gl; q < q1; q += LPC) {
         const int row = a.colidx[q];
-        G[t * ld + find_row(Il, nI, row)] = from_cd<S>(entry(a, a.cnew, q, row, kc));
+        G[t * ld + find_row(Il, nI, row)] = to_s<S, V>(entry(cd, a.ekind, cnew, q, row, kc));
       }
     }
     // right-hand side restricted to I_j
-    if (!a.update) {
-      if (lane == 0) rhs[find_row(Il, nI, j)] = S(1);
-    } else {
-      for (int q = c0 + lane; q < c0 + nJ; q += 32) {
-        const int row = a.colidx[q];
-        rhs[find_row(Il, nI, row)] = from_cd<S>(entry(a, a.cold, q, row, j));
+    if (valid) {
+      if (!a.update) {
+        if (gl == 0) rhs[find_row(Il, nI, j)] = S(1);
+      } else {
+        for (int q = c0 + gl; q < c0 + nJ; q += LPC) {
+          const int row = a.colidx[q];
+          rhs[find_row(Il, nI, row)] = to_s<S, V>(entry(cd, a.ekind, cold, q, row, j));
+        }
       }
     }
     __syncwarp();
-    // Householder QR, lane l owns rows l, l+32, ...
+    // Householder QR, lane gl of the group owns rows gl, gl + LPC, ...
     bool singular = false;
-    for (int c = 0; c < nJ; ++c) {
+    for (int c = 0; c < nJw; ++c) {
+      const bool act = c < nJ;
       S* gc = G + c * ld;
       R s2 = R(0);
-      for (int rr = lane; rr < nI; rr += 32) if (rr >= c) s2 += abs2_(gc[rr]);
-      s2 = warp_sum(s2);
-      const S x0 = gc[c];
+      if (act)
+        for (int rr = gl; rr < nI; rr += LPC) if (rr >= c) s2 += abs2_(gc[rr]);
+      s2 = group_sum<LPC>(s2);
+      const S x0 = act ? gc[c] : S(0);
       __syncwarp();
       const R alpha = sqrt(s2);
-      if (!(alpha > R(0))) {
+      const bool ok = act && (alpha > R(0));
+      if (act && !ok) {
         singular = true;
-        if (lane == 0) Rd[c] = S(0);
-        __syncwarp();
-        continue;
+        if (gl == 0) Rd[c] = S(0);
       }
       const R ax0 = sqrt(abs2_(x0));
       const S ph = (ax0 > R(0)) ? x0 * (R(1) / ax0) : S(1);
       const S v0 = x0 + ph * alpha;
       const R vn2 = s2 - ax0 * ax0 + abs2_(v0);
-      const R beta = R(2) / vn2;
-      if (lane == (c & 31)) gc[c] = v0;
-      if (lane == 0) Rd[c] = -(ph * alpha);
+      const R beta = ok ? R(2) / vn2 : R(0);
+      if (ok && gl == (c % LPC)) gc[c] = v0;
+      if (ok && gl == 0) Rd[c] = -(ph * alpha);
       __syncwarp();
-      for (int c2 = c + 1; c2 < nJ; ++c2) {
+      for (int c2 = c + 1; c2 < nJw; ++c2) {
+        const bool act2 = ok && c2 < nJ;
         S* g2 = G + c2 * ld;
         S w = S(0);
-        for (int rr = lane; rr < nI; rr += 32) if (rr >= c) fma_s(w, conj_(gc[rr]), g2[rr]);
-        w = warp_sum(w);
+        if (act2)
+          for (int rr = gl; rr < nI; rr += LPC) if (rr >= c) fma_s(w, conj_(gc[rr]), g2[rr]);
+        w = group_sum<LPC>(w);
         const S bw = w * beta;
-        for (int rr = lane; rr < nI; rr += 32) if (rr >= c) g2[rr] -= gc[rr] * bw;
+        if (act2)
+          for (int rr = gl; rr < nI; rr += LPC) if (rr >= c) g2[rr] -= gc[rr] * bw;
       }
       {
         S w = S(0);
-        for (int rr = lane; rr < nI; rr += 32) if (rr >= c) fma_s(w, conj_(gc[rr]), rhs[rr]);
-        w = warp_sum(w);
+        if (ok)
+          for (int rr = gl; rr < nI; rr += LPC) if (rr >= c) fma_s(w, conj_(gc[rr]), rhs[rr]);
+        w = group_sum<LPC>(w);
         const S bw = w * beta;
-        for (int rr = lane; rr < nI; rr += 32) if (rr >= c) rhs[rr] -= gc[rr] * bw;
+        if (ok)
+          for (int rr = gl; rr < nI; rr += LPC) if (rr >= c) rhs[rr] -= gc[rr] * bw;
       }
       __syncwarp();
     }
-    // back substitution R q = (Q^H rhs)(0:nJ)  (lane 0), then scatter
-    if (lane == 0) {
+    // back substitution R q = (Q^H rhs)(0:nJ) (lane 0 of the group), then scatter
+    if (valid && gl == 0) {
       if (singular) {
         for (int c = 0; c < nJ; ++c) qv[c] = S(0);
         atomicAdd(a.nsingular, 1);
@@ -153,35 +214,54 @@ __global__ void __launch_bounds__(256) spai_kernel(SpaiArgs a, S* __restrict__ o
       }
     }
     __syncwarp();
-    for (int t = lane; t < nJ; t += 32) out[a.outpos[c0 + t]] = qv[t];
+    for (int t = gl; t < nJ; t += LPC) out[a.outpos[c0 + t]] = qv[t];
     __syncwarp();
   }
 }
 
-template <typename S>
-int spai_dispatch(const SpaiArgs& a, void* out, cudaStream_t s) {
-  const size_t wb = warp_bytes<S>(a.nImax, a.nJmax);
+template <typename S, typename V, int LPC>
+int spai_launch(const SpaiArgs& a, const ColData<V>& cd, void* out, cudaStream_t s) {
+  constexpr int CPW = 32 / LPC;
+  const size_t wb = col_bytes<S>(a.nImax, a.nJmax) * CPW;     // per warp
   int nw = 8;
-  while (nw > 1 && wb * nw > 100 * 1024) nw >>= 1;
+  while (nw > 1 && wb * nw > 48 * 1024) nw >>= 1;
   if (wb * nw > 200 * 1024) return (int)cudaErrorInvalidValue;
   const size_t sm = wb * nw;
-  cudaError_t e = cudaFuncSetAttribute(spai_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(spai_kernel<S, V, LPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return (int)e;
-  int64_t blocks = ((int64_t)a.n + nw - 1) / nw;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  spai_kernel<S><<<(unsigned)blocks, nw * 32, sm, s>>>(a, (S*)out);
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spai_kernel<S, V, LPC>, nw * 32, sm);
+  if (e != cudaSuccess || occ < 1) occ = 1;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t per_block = (int64_t)nw * CPW;
+  int64_t blocks = ((int64_t)a.n + per_block - 1) / per_block;
+  blocks = std::min<int64_t>(blocks, (int64_t)sms * occ);
+  spai_kernel<S, V, LPC><<<(unsigned)std::max<int64_t>(blocks, 1), nw * 32, sm, s>>>(a, cd, (S*)out);
   mor_count_launches(1);
   return (int)cudaGetLastError();
+}
+
+// lanes per column: each lane owns at most 4 rows of the |I_j| x |J_j| block
+template <typename S, typename V>
+int spai_dispatch(const SpaiArgs& a, const ColData<V>& cd, void* out, cudaStream_t s) {
+  if (a.nImax <= 16) return spai_launch<S, V, 4>(a, cd, out, s);
+  if (a.nImax <= 32) return spai_launch<S, V, 8>(a, cd, out, s);
+  if (a.nImax <= 64) return spai_launch<S, V, 16>(a, cd, out, s);
+  return spai_launch<S, V, 32>(a, cd, out, s);
 }
 
 }  // namespace
 
 int launch_spai(int st, const SpaiArgs& a, void* out, cudaStream_t s) {
+  const ColData<float> c32{a.ca32, a.ce32, a.ediag32};
+  const ColData<double> c64{a.ca, a.ce, a.ediag};
   switch (st) {
-    case ST_F32: return spai_dispatch<float>(a, out, s);
-    case ST_F64: return spai_dispatch<double>(a, out, s);
-    case ST_C32: return spai_dispatch<cfloat>(a, out, s);
-    case ST_C64: return spai_dispatch<cdouble>(a, out, s);
+    case ST_F32: return spai_dispatch<float, float>(a, c32, out, s);
+    case ST_F64: return spai_dispatch<double, double>(a, c64, out, s);
+    case ST_C32: return spai_dispatch<cfloat, float>(a, c32, out, s);
+    case ST_C64: return spai_dispatch<cdouble, double>(a, c64, out, s);
   }
   return (int)cudaErrorInvalidValue;
 }
