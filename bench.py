@@ -21,6 +21,7 @@ max-reduced over ranks on the CPU (gloo).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import multiprocessing as mp
 import os
@@ -122,6 +123,27 @@ def _oracle_sample(q, grid, iters_per_solve, ncols, nits):
     per_solve = t_cols / len(cols) * n + iters_per_solve * t_it
     q.put({"per_solve_s": per_solve, "t_col": t_cols / len(cols), "t_iter": t_it, "ncols": len(cols),
            "nits": nits})
+
+
+def profiled_traffic(kernel, k, fmt, grid):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    `kernel` from its committed ncu summary under profiles/, when that capture
+    was taken on this launch shape (grid, k columns, storage format) and the
+    SpMV source has not changed since; None otherwise."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
+                        "%s_%s_convdiff3d_n1M_k%d.md" % (kernel, fmt, k))
+    if grid != 100 or not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("|", "#", " ")):
+            key, _, val = line.partition(":")
+            fields[key.strip()] = val.strip()
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2003_12759_gb300", "csrc", "spmv.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if fields.get("spmv_source_sha256_16") != sha or "traffic_bytes_per_launch" not in fields:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
 
 
 def cpu_baseline(grid, iters_per_solve, ncols=40000, nits=20):
@@ -249,7 +271,8 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False)
     ms_dom, b_dom = (ms_fac, bytes_fac) if dom == "factor_spmv" else (ms_op, bytes_op)
     ach = b_dom / (ms_dom * 1e-3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-            "frac": ach / peak, "peak_kind": "burst, " + peak_kind, "traffic": None,
+            "frac": ach / peak, "peak_kind": "burst, " + peak_kind,
+            "traffic": profiled_traffic(dom, k, {1: "csr", 2: "sell"}.get(info["format"], "?"), args.grid),
             "ms_per_launch": ms_dom, "algorithmic_bytes_per_launch": int(b_dom), "k_columns": k,
             "format": {1: "csr", 2: "sell-32"}.get(info["format"], info["format"])}
     other = {"op_spmv": {"ms": ms_op, "bytes": int(bytes_op), "GBs": bytes_op / (ms_op * 1e-3) / 1e9},
