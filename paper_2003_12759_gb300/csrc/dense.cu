@@ -14,6 +14,8 @@
 #include "small_tangent.cuh"
 #include "small_qep.cuh"
 
+#include <algorithm>
+
 namespace {
 
 constexpr int GRAM_TR = 32;      // rows per tile
@@ -71,6 +73,68 @@ __global__ void __launch_bounds__(256) gram_kernel(int n, int a, int b, const do
   }
   __syncthreads();
   if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Tall-skinny form of gram for b <= 2 (the Gram-Schmidt coefficients and
+// norms): out[i + a j] = X(:, i)^T Y(:, j), i < a <= 64.  One pass over the
+// rows in registers (eight columns of X per blockIdx.y, the b columns of Y
+// read once per row), per-block partials, and a fixed-order sum by the last
+// block of each column group (ticket counters[blockIdx.y]).  The tiled gram
+// kernel above staged 32-row tiles with two barriers each and ran ~10x
+// below the bandwidth of this access pattern.
+template <int B>
+__global__ void __launch_bounds__(256) gram_skinny_kernel(int64_t n, int a, const double* __restrict__ X, int64_t ldx,
+                                                          const double* __restrict__ Y, int64_t ldy,
+                                                          double* __restrict__ out, double* part, unsigned* counters) {
+  constexpr int CW = 8;
+  constexpr int NV = CW * B;
+  const int i0 = blockIdx.y * CW;
+  double acc[CW][B];
+#pragma unroll
+  for (int c = 0; c < CW; ++c)
+#pragma unroll
+    for (int j = 0; j < B; ++j) acc[c][j] = 0.0;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x) {
+    double y[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) y[j] = Y[row + j * ldy];
+#pragma unroll
+    for (int c = 0; c < CW; ++c)
+      if (i0 + c < a) {
+        const double x = X[row + (int64_t)(i0 + c) * ldx];
+#pragma unroll
+        for (int j = 0; j < B; ++j) acc[c][j] = fma(x, y[j], acc[c][j]);
+      }
+  }
+  __shared__ double sh[8][NV];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double t = warp_sum(acc[v / B][v % B]);
+    if (lane == 0) sh[wid][v] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w][threadIdx.x];
+    part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * NV + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(counters + blockIdx.y, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  if (threadIdx.x < NV) {
+    const volatile double* vp = part;
+    double t = 0.0;
+    for (int blk = 0; blk < (int)gridDim.x; ++blk) t += vp[((size_t)blockIdx.y * gridDim.x + blk) * NV + threadIdx.x];
+    const int c = threadIdx.x / B, j = threadIdx.x % B;
+    if (i0 + c < a) out[(i0 + c) + (size_t)a * j] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) counters[blockIdx.y] = 0u;
 }
 
 __global__ void gs_update_kernel(int n, int j, const double* __restrict__ V, int64_t ldv,
@@ -238,6 +302,14 @@ inline int grid_for(int64_t n, int cap) {
 int dense_launch_gram(int n, int a, int b, const double* X, int64_t ldx, const double* Y, int64_t ldy,
                       double* out, double* part, unsigned* counter, int grid_cap, cudaStream_t s) {
   if (a < 1 || b < 1 || a + b > GRAM_MAXC || a * b > 1024) return (int)cudaErrorInvalidValue;
+  if (b <= 2 && a <= 64) {
+    // counter[0 .. ceil(a / 8) - 1] are the column groups' tickets
+    dim3 g((unsigned)std::max(1, std::min(grid_cap / 2, (n + 255) / 256)), (unsigned)((a + 7) / 8));
+    if (b == 1) gram_skinny_kernel<1><<<g, 256, 0, s>>>(n, a, X, ldx, Y, ldy, out, part, counter);
+    else gram_skinny_kernel<2><<<g, 256, 0, s>>>(n, a, X, ldx, Y, ldy, out, part, counter);
+    mor_count_launches(1);
+    return (int)cudaGetLastError();
+  }
   int blocks = (n + GRAM_TR - 1) / GRAM_TR;
   if (blocks > grid_cap) blocks = grid_cap;
   if (blocks < 1) blocks = 1;

@@ -7,7 +7,7 @@
 // code that must not pay cudaMalloc / cudaFree's implicit device
 // synchronisation.  This file serves them with a handle-free entry point
 // whose scratch (the per-block partial sums of the Gram kernel, the
-// Gram-Schmidt coefficients and the block counter) lives in one file-scope
+// Gram-Schmidt coefficients and the block counters) lives in one file-scope
 // __device__ array of fixed size, reserved when the library is loaded and
 // held by every GPU that loads it until the process exits.
 #include "mor_spai.h"
@@ -21,7 +21,7 @@ constexpr int NA_GRID = 608;             // Gram-kernel blocks (4 per SM on 152 
 constexpr size_t NA_H = 0;                               // Gram-Schmidt coefficients (64)
 constexpr size_t NA_NORMS = 64;                          // per-column norms (2 x 64)
 constexpr size_t NA_PART = NA_NORMS + 2 * NA_MAXK;       // block partials (NA_GRID x 64)
-constexpr size_t NA_CNT = NA_PART + (size_t)NA_GRID * NA_MAXK;   // block counter (one word)
+constexpr size_t NA_CNT = NA_PART + (size_t)NA_GRID * NA_MAXK;   // block counters (8 words used)
 constexpr size_t NA_DOUBLES = NA_CNT + 32;               // 311,808 bytes in total
 
 __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
@@ -50,8 +50,9 @@ extern "C" int mor_orthonormalize_noalloc(double* X, int64_t n, int k, void* str
   double* norms = base + NA_NORMS;
   double* part = base + NA_PART;
   unsigned* counter = (unsigned*)(base + NA_CNT);
-  // the array keeps whatever the previous call left: the counter must start at zero
-  if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) return MOR_ECUDA;
+  // the array keeps whatever the previous call left: the counters (one per
+  // group of eight columns of the Gram kernel) must start at zero
+  if (cudaMemsetAsync(counter, 0, 8 * sizeof(unsigned), s) != cudaSuccess) return MOR_ECUDA;
   for (int j = 0; j < k; ++j) {
     double* v = X + (size_t)j * n;
     for (int pass = 0; pass < 2 && j > 0; ++pass) {
