@@ -359,6 +359,105 @@ def run_batch(args, ws, rank, local):
             "max_relres": rel}
 
 
+def _timed(args, ws, local, stream, step):
+    """W untimed steps, then K steps between barriers and CUDA events (max over ranks)."""
+    import torch
+    import paper_2003_12759_gb300 as mor
+    for _ in range(args.warmup):
+        step()
+    clk = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    l0 = mor.mor_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clk.start()
+    e0.record(stream)
+    outs = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier(ws)
+    t = max_over_ranks(ws, e0.elapsed_time(e1) / 1000.0)
+    return t, outs, mor.mor_launch_count() - l0, clocks
+
+
+def run_mimo(args, ws, rank, local):
+    """MIMO sweep on the 3D convection-diffusion system (N^3, 7-point), m = q
+    = 8: 48 real shifts logspace(0, 4, 48), each solved for the whole input
+    block B (primal) and output block C (transposed): 768 solves per step,
+    FP32 in FP64 refinement, right-hand sides and solutions in device memory.
+    The preconditioner is a fresh SPAI per shift (the paper's "SPAI case"):
+    Algorithm 4's horizontal chain would be 48 factors deep for the last
+    shift of this sweep."""
+    import torch
+    import paper_2003_12759_gb300 as mor
+    import workloads as W
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    wl = W.config4(N=args.grid_mimo, m=8)
+    h = mor.mor_create(local, stream)
+    fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
+    mor.mor_set_system(h, wl.A, wl.B, wl.C, fmt=fmt)
+    n, m = wl.A.shape[0], wl.B.shape[1]
+    dev = torch.device("cuda", local)
+    # column-major n x 8 complex128 blocks on the device (the ABI's layout): (8, n) rows, transposed view
+    RB = torch.from_numpy(np.ascontiguousarray(wl.B.T)).to(dev).to(torch.complex128).T
+    RC = torch.from_numpy(np.ascontiguousarray(wl.C.T)).to(dev).to(torch.complex128).T
+    shifts = list(wl.shifts)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64 if args.precision == "fp64" else mor.MOR_MIXED, precond=1)
+
+    def step():
+        its, rel = [], 0.0
+        for t, R in ((0, RB), (1, RC)):
+            for z in shifts:
+                X, st, _ = mor.mor_solve_shifts(h, [z] * m, t, opts, R=R)
+                its += [x["iters"] for x in st]
+                rel = max(rel, max(x["relres"] for x in st))
+        return its, rel
+
+    t, outs, launches, clocks = _timed(args, ws, local, stream, step)
+    info = mor.mor_get_info(h)
+    mor.mor_destroy(h)
+    its = [i for o in outs for i in o[0]]
+    return {"t": t, "value": args.steps * 2 * len(shifts) * m * ws / t, "launches": launches, "clocks": clocks,
+            "n": n, "nnz": info["nnz"], "iters_mean": float(np.mean(its)), "max_relres": max(o[1] for o in outs)}
+
+
+def run_second(args, ws, rank, local):
+    """Second-order reduction on the 27-point structural-like system
+    (110 x 110 x 99, n = 1,197,900; M diagonal, Rayleigh damping): one step
+    is one AIRGA iteration (mor_airga_step) with 3 expansion points (a
+    conjugate pair and a real point) times the m = 4 input block: 8 solves
+    (2 points x 4 inputs, the conjugate one is implied), r = 12, reuse
+    schedule, FP64 Krylov: from the second iteration on, the points are
+    mirror images of lightly damped reduced poles (0.0005 +- 0.196 i), where
+    s^2 M + s D + K is nearly singular and indefinite; FP64 BiCGSTAB needs
+    750-1500 iterations there and FP32 inner solves stall at 1e-4 .. 1e-2."""
+    import torch
+    import paper_2003_12759_gb300 as mor
+    import workloads as W
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    wl = W.config3()
+    h = mor.mor_create(local, stream)
+    mor.mor_set_system_2nd(h, wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C)
+    pts = [np.array([0.2 + 0.1j, 0.2 - 0.1j, 1.0])]
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64)
+
+    def step():
+        p, rom, st = mor.mor_airga_step(h, pts[0], opts)
+        pts[0] = p
+        return st
+
+    t, outs, launches, clocks = _timed(args, ws, local, stream, step)
+    info = mor.mor_get_info(h)
+    mor.mor_destroy(h)
+    solves = sum(st["nsolve"] for st in outs)
+    return {"t": t, "value": solves * ws / t, "launches": launches, "clocks": clocks, "n": info["n"],
+            "nnz": info["nnz"], "stats": outs, "points": [complex(z) for z in pts[0]]}
+
+
 def kernels_only(args):
     """Short run for profilers: the hot-loop kernels on the full-size workload."""
     import paper_2003_12759_gb300 as mor
@@ -394,7 +493,8 @@ def main():
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip timing the plain FP64 one-shift-per-launch form next to the default")
     ap.add_argument("--fmt", default="auto", choices=["auto", "csr", "sell"])
-    ap.add_argument("--workload", default="convdiff", choices=["convdiff", "batch"],
+    ap.add_argument("--grid-mimo", type=int, default=200, help="grid points per axis of the MIMO workload")
+    ap.add_argument("--workload", default="convdiff", choices=["convdiff", "batch", "mimo", "second"],
                     help="convdiff: IRKA sweeps on the 3D convection-diffusion system (default); "
                          "batch: 256 uneven independent systems x 8 shifts")
     ap.add_argument("--nsys", type=int, default=256)
@@ -450,6 +550,34 @@ def main():
                     "clocks": r["clocks"], "gpu_launches": int(r["launches"]),
                     "batch": {"iters_mean": r["iters_mean"], "iters_max": r["iters_max"],
                               "max_relres": r["max_relres"]}}
+            print(json.dumps(line))
+        return
+    if args.workload in ("mimo", "second"):
+        dt = "f32 inner / f64 refinement" if args.precision == "mixed" else "f64"
+        if args.workload == "mimo":
+            r = run_mimo(args, ws, rank, local)
+            cfg_w = {"workload": "mimo_convdiff3d_%d^3_n%d_48shifts_m8_q8" % (args.grid_mimo, r["n"]),
+                     "nnz": r["nnz"], "shifts": "logspace(0,4,48), real", "rhs": "B (n x 8), C (n x 8), device",
+                     "precond": "fresh SPAI per shift", "tol": 1e-8, "l2": "inputs larger than L2"}
+            extra = {"mimo": {"iters_mean": r["iters_mean"], "max_relres": r["max_relres"]}}
+        else:
+            r = run_second(args, ws, rank, local)
+            cfg_w = {"workload": "second_order_stencil27_110x110x99_n%d_m4_r12" % r["n"], "nnz": r["nnz"],
+                     "points": "3 (conjugate pair + real), AIRGA zeroth moments, reuse schedule", "tol": 1e-8,
+                     "l2": "inputs larger than L2"}
+            dt = "c128"
+            extra = {"airga": {"iters_per_solve": float(np.mean([st["iters_V"] / st["nsolve"] for st in r["stats"]])),
+                               "chain_len": [st["chain_len"] for st in r["stats"]],
+                               "max_relres": max(st["max_relres"] for st in r["stats"]),
+                               "ms_precond": float(np.mean([st["ms_precond"] for st in r["stats"]])),
+                               "ms_solve": float(np.mean([st["ms_solve"] for st in r["stats"]])),
+                               "points": [[z.real, z.imag] for z in r["points"]]}}
+        if rank == 0:
+            line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                    "warmup": args.warmup, "ms_per_step": 1000 * r["t"] / args.steps, "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None, "dtype": dt, "data": "synthetic", "config": cfg_w,
+                    "clocks": r["clocks"], "gpu_launches": int(r["launches"])}
+            line.update(extra)
             print(json.dumps(line))
         return
     r = run_ours(args, ws, rank, local)

@@ -1210,6 +1210,7 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
     }
     MOR_CK(h, cudaGetLastError());
   }
+  if (!std::isfinite(st.max_relres)) return mor_fail(h, MOR_EBREAKDOWN, "a shifted solve broke down");
   int dep = 0, dep2 = 0;
   MOR_TRY(orth_device(h, Vb, n, r, &dep));
   MOR_TRY(orth_device(h, Wb, n, r, &dep2));
@@ -1375,6 +1376,8 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
     st.iters_V += ss[c].iters;
     st.max_relres = std::max(st.max_relres, ss[c].relres);
   }
+  // a solve that broke down (non-finite residual) leaves no basis to project on: report it as such
+  if (!std::isfinite(st.max_relres)) return mor_fail(h, MOR_EBREAKDOWN, "a block solve broke down");
   cudaEventRecord(ev[2], h->stream);
   // real basis [Re X_i, Im X_i] per solved point, CGS2, Galerkin projection (W = V)
   DBuf basis;
