@@ -321,6 +321,10 @@ SegView fit_grid(const SegView& sg, const void* kern, int tpr) {
     std::lock_guard<std::mutex> lk(mu);
     occ_cache[kern] = occ;
   }
+  // one resident wave (measured faster than 2 or 4 waves of smaller blocks);
+  // 256-thread blocks give occ <= 8, so grids stay within sms * 8 blocks,
+  // the size every per-block partial buffer is allocated for
+  if (occ > 8) occ = 8;
   const int64_t pass = 256 / tpr;
   const int64_t passes = (sg.nrows + pass - 1) / pass;
   int64_t grid = std::min<int64_t>((int64_t)sg.sms * occ, std::max<int64_t>(passes, 1));

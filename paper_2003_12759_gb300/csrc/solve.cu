@@ -74,6 +74,12 @@ int get_small(mor_t h, Small& s) {
 // forward
 static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bool update, int precision);
 
+// blocks a per-block partial buffer must hold: the segment table's grid (a
+// batch) or one resident wave of up to 8 blocks per SM (fit_grid)
+static size_t part_blocks(const mor_t h) {
+  return std::max<size_t>({(size_t)h->seg.nblocks, (size_t)h->sm_count * 8, (size_t)2048});
+}
+
 // ---------------------------------------------------------------------------
 // preconditioner chain
 // ---------------------------------------------------------------------------
@@ -167,7 +173,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
        *t = vec(7), *ph = vec(8), *sh = vec(9), *tmp0 = vec(10), *tmp1 = vec(11);
   MOR_CK(h, h->ws_r64.alloc(es64 * (size_t)n * ld));
   void* r64 = h->ws_r64.p;
-  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * (size_t)std::max(sg.nblocks, 2048)));
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * part_blocks(h)));
   Small sm;
   MOR_TRY(get_small(h, sm));
   const size_t ksb = krylov_state_bytes(st_in);
@@ -1508,7 +1514,7 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
   MOR_CK(h, cudaMemsetAsync(w.p, 0, st_size(st) * (size_t)n * ld, h->stream));
   Small sm;
   MOR_TRY(get_small(h, sm));
-  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * (size_t)std::max(h->seg.nblocks, 2048)));
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * part_blocks(h)));
   std::vector<int> ones(MOR_KMAX, 1);
   MOR_CK(h, cudaMemcpyAsync(sm.masks, ones.data(), sizeof(int) * MOR_KMAX, cudaMemcpyHostToDevice, h->stream));
   Coef cf[MOR_LDMAX];
