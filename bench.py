@@ -212,8 +212,8 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False)
     prec_name = precision or args.precision
     one = args.one_shift if one_shift is None else one_shift
     opts = mor.mor_default_opts(precision=mor.MOR_FP64 if prec_name == "fp64" else mor.MOR_MIXED,
-                                batch=0 if one else 1, use_graph=0 if one else 1,
-                                max_chain=args.max_chain)
+                                batch=0 if one else 1, use_graph=0 if (one or args.no_graph) else 1,
+                                max_chain=args.max_chain, graph_chunk=args.graph_chunk)
     omega = np.logspace(0, 5, 1000)
     shifts = wl.shifts.copy()
 
@@ -495,6 +495,8 @@ def main():
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip timing the plain FP64 one-shift-per-launch form next to the default")
     ap.add_argument("--fmt", default="auto", choices=["auto", "csr", "sell"])
+    ap.add_argument("--graph-chunk", type=int, default=16, help="Krylov iterations per CUDA-graph replay")
+    ap.add_argument("--no-graph", action="store_true", help="launch the Krylov iterations one by one")
     ap.add_argument("--grid-mimo", type=int, default=200, help="grid points per axis of the MIMO workload")
     ap.add_argument("--workload", default="convdiff", choices=["convdiff", "batch", "mimo", "second"],
                     help="convdiff: IRKA sweeps on the 3D convection-diffusion system (default); "

@@ -210,8 +210,17 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   void* dd = d;
   void *rr = r, *rh = rhat, *pp = p, *vv = v, *ssv = sv, *tt = t, *pph = ph, *ssh = sh, *t0 = tmp0, *t1 = tmp1;
   Coef cfc[MOR_LDMAX];
+  // Lcur: the longest chain prefix among the columns still in the batch.
+  // The high shifts carry the longest horizontal prefixes and converge
+  // first, so after compaction the chain is applied only as far as the
+  // remaining columns need (no copy-through launches for the dropped ones).
+  int Lcur = Lmax;
   auto upload_masks = [&]() -> int {
     if (Lmax == 0) return 0;
+    int lc = 0;
+    for (int c = 0; c < ldc; ++c)
+      if (cmap[c] >= 0 && cmap[c] < k) lc = std::max(lc, io.L[cmap[c]]);
+    Lcur = lc > 0 ? lc : Lmax;
     std::vector<int> mk((size_t)Lmax * MOR_KMAX, 0);
     for (int f = 0; f < Lmax; ++f)
       for (int c = 0; c < ldc; ++c) {
@@ -223,8 +232,8 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   auto chain_apply_d = [&](void* src, void* dst, const int* dn) -> int {
     if (Lmax == 0) return 0;
     void* s = src;
-    for (int f = 0; f < Lmax; ++f) {
-      void* dd2 = (f == Lmax - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
+    for (int f = 0; f < Lcur; ++f) {
+      void* dd2 = (f == Lcur - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
       const Factor& F = op.chain[f];
       int e = launch_factor_spmv(st_in, st_is_cplx(F.st), sg, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
                                  dd2, dn, h->stream);

@@ -50,8 +50,11 @@ template <typename S, int CPT> constexpr int op_chunk() { return narrow_slice<S,
 template <typename S, int CPT> constexpr int min_blocks() {
   return narrow_slice<S, CPT>() ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1) ? 6 : 8) : 1;
 }
+#ifndef MOR_OP_MINB
+#define MOR_OP_MINB 8
+#endif
 template <typename S, int CPT> constexpr int op_min_blocks() {
-  return narrow_slice<S, CPT>() ? (sizeof(typename real_of<S>::type) == 8 ? 5 : 8) : 1;
+  return narrow_slice<S, CPT>() ? (sizeof(typename real_of<S>::type) == 8 ? 5 : MOR_OP_MINB) : 1;
 }
 
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
@@ -62,7 +65,7 @@ template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
 // columns sub * CPT ... sub * CPT + CPT - 1 of the n x ld blocks.  The
 // coefficients are read from shared memory where they are used and row
 // indices are 32-bit, to hold the register bound of op_min_blocks.
-template <typename S, int TPR, int CPT>
+template <typename S, int TPR, int CPT, bool ECSR>
 __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(SegView sg, PatView pv, OpVals ov,
                                                                                 CoefS<S> cf, int ld,
                                                                                 const S* __restrict__ x, S* __restrict__ y,
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
   chunk_rows(sg, seg, blockIdx.x, rb64, re64);
   const int re = (int)re64;
   const bool sell = pv.fmt == FMT_SELL;
-  const int ekind = ov.ekind;
+  const int ekind = ECSR ? EK_CSR : ov.ekind;   // E a general sparse matrix: compile-time branch
   constexpr int GCH = op_chunk<S, CPT>();
   if (act) {
     for (int r = (int)rb64 + (int)threadIdx.x / TPR; r < re; r += rpb) {
@@ -115,7 +118,8 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
         for (int u = 0; u < GCH; ++u) {
           cc[u] = __ldg(pv.col + pc + u * step);
           av[u] = __ldg(a + pc + u * step);
-          ev[u] = ekind == EK_CSR ? __ldg(e + pc + u * step) : R(0);
+          if constexpr (ECSR) ev[u] = __ldg(e + pc + u * step);
+          else ev[u] = R(0);
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
@@ -125,22 +129,24 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
 #pragma unroll
           for (int j = 0; j < CPT; ++j) {
             fma_r(accA[j], av[u], xv[u].v[j]);
-            if (ekind == EK_CSR) fma_r(accE[j], ev[u], xv[u].v[j]);
+            if constexpr (ECSR) fma_r(accE[j], ev[u], xv[u].v[j]);
           }
       }
       for (; pc < p1; pc += step) {
         const int cc = __ldg(pv.col + pc);
         const R av = __ldg(a + pc);
-        const R ev = ekind == EK_CSR ? __ldg(e + pc) : R(0);
         const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+        if constexpr (ECSR) {
+          const R ev = __ldg(e + pc);
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-          fma_r(accA[j], av, xv.v[j]);
-          if (ekind == EK_CSR) fma_r(accE[j], ev, xv.v[j]);
+          for (int j = 0; j < CPT; ++j) { fma_r(accA[j], av, xv.v[j]); fma_r(accE[j], ev, xv.v[j]); }
+        } else {
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) fma_r(accA[j], av, xv.v[j]);
         }
       }
       const int64_t q = (int64_t)r * ld + c0;
-      if (ekind != EK_CSR) {
+      if constexpr (!ECSR) {
         const Pack<S, CPT> xr = ldp<S, CPT>(x + q);
         const R d = (ekind == EK_DIAG) ? __ldg(ed + r) : R(1);
 #pragma unroll
@@ -281,8 +287,15 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
         cf.sA[c] = (S)q.sAr;
       }
     }
-    const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT>, TPR);
-    op_spmv_kernel<S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y, (const S*)b, ra);
+    if (ov.ekind == EK_CSR) {
+      const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT, true>, TPR);
+      op_spmv_kernel<S, TPR, CPT, true><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y,
+                                                                  (const S*)b, ra);
+    } else {
+      const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT, false>, TPR);
+      op_spmv_kernel<S, TPR, CPT, false><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y,
+                                                                   (const S*)b, ra);
+    }
     return 0;
   });
   if (e) return e;
