@@ -432,7 +432,9 @@ def run_second(args, ws, rank, local):
     is one AIRGA iteration (mor_airga_step) with 3 expansion points (a
     conjugate pair and a real point) times the m = 4 input block: 8 solves
     (2 points x 4 inputs, the conjugate one is implied), r = 12, reuse
-    schedule, FP64 Krylov: from the second iteration on, the points are
+    schedule, FP64 Krylov with FP32 / complex64 SPAI and reuse factors
+    (FP64 least squares on the 27-point pattern take seconds on this GPU's
+    narrow FP64 pipe): from the second iteration on, the points are
     mirror images of lightly damped reduced poles (0.0005 +- 0.196 i), where
     s^2 M + s D + K is nearly singular and indefinite; FP64 BiCGSTAB needs
     750-1500 iterations there and FP32 inner solves stall at 1e-4 .. 1e-2."""
@@ -445,7 +447,7 @@ def run_second(args, ws, rank, local):
     h = mor.mor_create(local, stream)
     mor.mor_set_system_2nd(h, wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C)
     pts = [np.array([0.2 + 0.1j, 0.2 - 0.1j, 1.0])]
-    opts = mor.mor_default_opts(precision=mor.MOR_FP64)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64, precond_precision=mor.MOR_MIXED)
 
     def step():
         p, rom, st = mor.mor_airga_step(h, pts[0], opts)
@@ -569,7 +571,7 @@ def main():
             cfg_w = {"workload": "second_order_stencil27_110x110x99_n%d_m4_r12" % r["n"], "nnz": r["nnz"],
                      "points": "3 (conjugate pair + real), AIRGA zeroth moments, reuse schedule", "tol": 1e-8,
                      "l2": "inputs larger than L2"}
-            dt = "c128"
+            dt = "c128 Krylov / c64 preconditioner factors"
             extra = {"airga": {"iters_per_solve": float(np.mean([st["iters_V"] / st["nsolve"] for st in r["stats"]])),
                                "chain_len": [st["chain_len"] for st in r["stats"]],
                                "max_relres": max(st["max_relres"] for st in r["stats"]),

@@ -118,6 +118,13 @@ typedef struct {
                             exceed this many factors; 0 = unlimited (default)        */
     int    restart;      /* MOR_GMRES: Krylov basis size m per cycle, 1..64,
                             default 50                                               */
+    int    precond_precision; /* precision of the SPAI / reuse factors that
+                            mor_irka_step, mor_airga_step and precond = 1 build:
+                            -1 (default) = precision; MOR_MIXED = FP32 / complex64
+                            factors, which also serve MOR_FP64 solves (widened on
+                            load; the preconditioner's precision does not limit
+                            the solve's accuracy, and FP64 least squares are slow
+                            on GPUs with a narrow FP64 pipe)                        */
 } mor_solve_opts;
 
 /* Per-column statistics of a solve. */

@@ -144,7 +144,8 @@ int gmres_launch_solve_y(int ld, int m, void* state, const void* H, void* ycoef,
 // Launchers (spmv.cu).  x, y, w, b: n x ld row-major blocks of type st.
 int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
                    const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s);
-int launch_factor_spmv(int st, bool fcplx, const SegView& sg, const PatView& pv, const void* fvals,
+// fst: scalar type of the factor values (FP32 factors may serve FP64 vectors)
+int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals,
                        const int* apply, int ld, const void* x, void* y, const int* done,
                        cudaStream_t s);
 

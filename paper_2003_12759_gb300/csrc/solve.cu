@@ -74,6 +74,12 @@ int get_small(mor_t h, Small& s) {
 // forward
 static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bool update, int precision);
 
+// precision of the factors the schedule builds: opts.precond_precision, or
+// opts.precision when that is negative (the default)
+static int factor_precision(const mor_solve_opts& o) {
+  return o.precond_precision >= 0 ? o.precond_precision : o.precision;
+}
+
 // blocks a per-block partial buffer must hold: the segment table's grid (a
 // batch) or one resident wave of up to 8 blocks per SM (fit_grid)
 static size_t part_blocks(const mor_t h) {
@@ -160,8 +166,8 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   if (Lmax > MAX_FACTORS - 4) return mor_fail(h, MOR_EINVAL, "chain too long");
   for (int f = 0; f < Lmax; ++f) {
     const Factor& F = op.chain[f];
-    if (st_is_f32(F.st) != st_is_f32(st_in))
-      return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from the solve precision");
+    if (!st_is_f32(F.st) && st_is_f32(st_in))
+      return mor_fail(h, MOR_ESTATE, "an FP64 preconditioner chain cannot serve an FP32 inner solve");
     if (st_is_cplx(F.st) && !st_is_cplx(st_in)) return mor_fail(h, MOR_EINVAL, "internal: complex factor, real vectors");
   }
   // workspace: 12 inner vectors of n x ld
@@ -235,7 +241,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     for (int f = 0; f < Lcur; ++f) {
       void* dd2 = (f == Lcur - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
       const Factor& F = op.chain[f];
-      int e = launch_factor_spmv(st_in, st_is_cplx(F.st), sg, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
+      int e = launch_factor_spmv(st_in, F.st, sg, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
                                  dd2, dn, h->stream);
       if (e) return e;
       s = dd2;
@@ -905,7 +911,7 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   char* s = a;
   char* d = b;
   for (int f = 0; f < Lmax; ++f) {
-    MOR_CKI(h, launch_factor_spmv(st, st_is_cplx(op.chain[f].st), h->seg, op.view(), op.chain[f].vals->p,
+    MOR_CKI(h, launch_factor_spmv(st, op.chain[f].st, h->seg, op.view(), op.chain[f].vals->p,
                                   sm.masks + (size_t)f * MOR_KMAX, ld, s, d, nullptr, h->stream));
     std::swap(s, d);
   }
@@ -927,6 +933,10 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
   if (o.precision != MOR_FP64 && o.precision != MOR_MIXED) return mor_fail(h, MOR_EINVAL, "bad precision");
+  if (o.precond_precision != -1 && o.precond_precision != MOR_FP64 && o.precond_precision != MOR_MIXED)
+    return mor_fail(h, MOR_EINVAL, "bad precond_precision");
+  if (o.precision == MOR_MIXED && o.precond_precision == MOR_FP64)
+    return mor_fail(h, MOR_EINVAL, "FP64 factors cannot serve a mixed-precision solve");
   if (!(o.tol > 0) || o.maxit < 0) return mor_fail(h, MOR_EINVAL, "bad tolerance or maxit");
   for (int c = 0; c < k; ++c)
     if (!std::isfinite(sigma[c].re) || !std::isfinite(sigma[c].im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
@@ -945,7 +955,7 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
     // a new SPAI per shift: one column at a time
     int ret = MOR_OK;
     for (int c = 0; c < k; ++c) {
-      MOR_TRY(build_factor(h, transpose, sigma[c], sigma[c], false, o.precision));
+      MOR_TRY(build_factor(h, transpose, sigma[c], sigma[c], false, factor_precision(o)));
       std::vector<int> L(1, 1);
       bool cc = anyc || chain_cplx(op, L);
       int s = solve_many(h, sigma + c, 1, transpose, o, L, cc, R ? R + (size_t)h->n * c : nullptr, dev,
@@ -956,8 +966,9 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
     return ret;
   }
   std::vector<int> L = (o.precond == 2) ? std::vector<int>(k, 0) : prefix_lengths(op, sigma, k);
-  if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision)
-    return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from opts.precision");
+  if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision &&
+      !(op.chain_prec == MOR_MIXED && o.precision == MOR_FP64))
+    return mor_fail(h, MOR_ESTATE, "an FP64 preconditioner chain cannot serve a mixed-precision solve");
   bool cc = anyc || chain_cplx(op, L);
   const int nseg = h->seg.nseg;
   if (nseg == 1 || !stats) return solve_many(h, sigma, k, transpose, o, L, cc, R, dev, X, stats);
@@ -986,6 +997,10 @@ int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const m
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
   if (o.precision != MOR_FP64 && o.precision != MOR_MIXED) return mor_fail(h, MOR_EINVAL, "bad precision");
+  if (o.precond_precision != -1 && o.precond_precision != MOR_FP64 && o.precond_precision != MOR_MIXED)
+    return mor_fail(h, MOR_EINVAL, "bad precond_precision");
+  if (o.precision == MOR_MIXED && o.precond_precision == MOR_FP64)
+    return mor_fail(h, MOR_EINVAL, "FP64 factors cannot serve a mixed-precision solve");
   if (!(o.tol > 0) || o.maxit < 0) return mor_fail(h, MOR_EINVAL, "bad tolerance or maxit");
   if (o.precond == 1) return mor_fail(h, MOR_EINVAL, "mor_batch_solve: build the preconditioner with mor_build_precond");
   for (int c = 0; c < k; ++c)
@@ -993,8 +1008,9 @@ int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const m
   cudaSetDevice(h->dev);
   OpData& op = h->op(transpose);
   std::vector<int> L = (o.precond == 2) ? std::vector<int>(k, 0) : prefix_lengths(op, sigma, k);
-  if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision)
-    return mor_fail(h, MOR_ESTATE, "preconditioner chain precision differs from opts.precision");
+  if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision &&
+      !(op.chain_prec == MOR_MIXED && o.precision == MOR_FP64))
+    return mor_fail(h, MOR_ESTATE, "an FP64 preconditioner chain cannot serve a mixed-precision solve");
   bool cc = chain_cplx(op, L);
   for (int c = 0; c < k; ++c) cc |= !is_real_shift(sigma[c]);
   std::vector<mor_solve_stats> all((size_t)h->seg.nseg * k);
@@ -1073,20 +1089,21 @@ static int schedule_chains(mor_t h, const std::vector<mor_c64>& sol, const mor_s
     std::vector<int>& L = Ls[t];
     L.assign(l, 0);
     if (o.precond == 2 || o.precond == 1) continue;
-    const bool rebuild = (h->irka_z == 0) || X.chain.empty() || X.chain_prec != o.precision ||
+    const int fp = factor_precision(o);
+    const bool rebuild = (h->irka_z == 0) || X.chain.empty() || X.chain_prec != fp ||
                          (o.max_chain > 0 && h->vlen[t] + 1 > o.max_chain);
     if (!rebuild) { X.chain.resize(h->vlen[t]); }
     if (rebuild) {
-      MOR_TRY(build_factor(h, t, sol[0], sol[0], false, o.precision));
+      MOR_TRY(build_factor(h, t, sol[0], sol[0], false, fp));
       h->vlen[t] = 1;
       st.builds_spai++;
     } else {
-      MOR_TRY(build_factor(h, t, X.chain.back().to, sol[0], true, o.precision));
+      MOR_TRY(build_factor(h, t, X.chain.back().to, sol[0], true, fp));
       h->vlen[t] += 1;
       st.builds_reuse++;
     }
     for (int i = 1; i < l; ++i) {
-      MOR_TRY(build_factor(h, t, sol[i - 1], sol[i], true, o.precision));
+      MOR_TRY(build_factor(h, t, sol[i - 1], sol[i], true, fp));
       st.builds_reuse++;
     }
     for (int i = 0; i < l; ++i) L[i] = h->vlen[t] + i;
@@ -1111,6 +1128,10 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
   if (h->seg.nseg != 1) return mor_fail(h, MOR_EINVAL, "mor_irka_step needs a single system, not a batch");
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
+  if ((o.precision != MOR_FP64 && o.precision != MOR_MIXED) ||
+      (o.precond_precision != -1 && o.precond_precision != MOR_FP64 && o.precond_precision != MOR_MIXED) ||
+      (o.precision == MOR_MIXED && o.precond_precision == MOR_FP64))
+    return mor_fail(h, MOR_EINVAL, "bad precision / precond_precision");
   cudaSetDevice(h->dev);
   cudaEvent_t ev[5];
   for (auto& e : ev) cudaEventCreate(&e);
@@ -1186,7 +1207,7 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
     if (o.precond == 1) {
       s2 = MOR_OK;
       for (int i = 0; i < l; ++i) {
-        MOR_TRY(build_factor(h, t, sol[i], sol[i], false, o.precision));
+        MOR_TRY(build_factor(h, t, sol[i], sol[i], false, factor_precision(o)));
         st.builds_spai++;
         std::vector<int> L1(1, 1);
         const mor_c64* Ri = tang ? rhs[t].as<mor_c64>() + (size_t)n * i : nullptr;
@@ -1333,6 +1354,10 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
   if (o.precond == 1) return mor_fail(h, MOR_EINVAL, "mor_airga_step supports precond 0 (reuse) and 2 (none)");
+  if ((o.precision != MOR_FP64 && o.precision != MOR_MIXED) ||
+      (o.precond_precision != -1 && o.precond_precision != MOR_FP64 && o.precond_precision != MOR_MIXED) ||
+      (o.precision == MOR_MIXED && o.precond_precision == MOR_FP64))
+    return mor_fail(h, MOR_EINVAL, "bad precision / precond_precision");
   cudaSetDevice(h->dev);
   cudaEvent_t ev[5];
   for (auto& e : ev) cudaEventCreate(&e);
@@ -1534,7 +1559,7 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
   RedArgs ra{RED_DOT_W, w.p, h->ws_part.p, nullptr, FIN_NONE, nullptr, h->ws_sums.p, nullptr};
   auto launch = [&]() -> int {
     if (which == 0) return launch_op_spmv(st, h->seg, pv, ov, cf, ld, x.p, y.p, nullptr, &ra, h->stream);
-    return launch_factor_spmv(st, st_is_cplx(op.chain.back().st), h->seg, pv, op.chain.back().vals->p, sm.masks, ld,
+    return launch_factor_spmv(st, op.chain.back().st, h->seg, pv, op.chain.back().vals->p, sm.masks, ld,
                               x.p, y.p, nullptr, h->stream);
   };
   for (int i = 0; i < 3; ++i) MOR_CKI(h, launch());

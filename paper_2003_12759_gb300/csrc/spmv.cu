@@ -22,6 +22,8 @@
 
 #include "shape_dispatch.cuh"
 
+#include <type_traits>
+
 namespace {
 
 template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
@@ -190,6 +192,8 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
                                                           const S* __restrict__ x, S* __restrict__ y,
                                                           const int* done) {
   if (done && *done) return;
+  typedef typename real_of<S>::type RS;
+  typedef typename std::conditional<is_cplx<V>::value, cplx<RS>, RS>::type W;
   const int sub = threadIdx.x % TPR;
   const int c0 = sub * CPT;
   if (c0 >= ld) return;
@@ -222,16 +226,17 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
       // chunks of GCH nonzeros: indices and values first, then every gather in flight
       // whole chunks of GCH nonzeros (indices and values first, then every
       // gather in flight), then the remainder one by one; the sum runs in
-      // storage order either way
+      // storage order either way.  FP32 factor values under FP64 vectors are
+      // widened on load (W).
       constexpr int GCH = factor_chunk<S, CPT>();
       int pc = p0;
       for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
         int cc[GCH];
-        V fv[GCH];
+        W fv[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
           cc[u] = __ldg(pv.col + pc + u * step);
-          fv[u] = f[pc + u * step];
+          fv[u] = cvt_<W, V>::f(f[pc + u * step]);
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
       }
       for (; pc < p1; pc += step) {
         const int cc = __ldg(pv.col + pc);
-        const V fv = f[pc];
+        const W fv = cvt_<W, V>::f(f[pc]);
         const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
@@ -303,26 +308,30 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
   return (int)cudaGetLastError();
 }
 
-int launch_factor_spmv(int st, bool fcplx, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
+int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
                        int ld, const void* x, void* y, const int* done, cudaStream_t s) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
+  const bool fc = st_is_cplx(fst), f32 = st_is_f32(fst);
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
     typedef typename real_of<S>::type R;
+    auto go = [&]<typename V>() {
+      const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, V, TPR, CPT>, TPR);
+      factor_spmv_kernel<S, V, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const V*)fvals, apply, ld, (const S*)x,
+                                                                   (S*)y, done);
+    };
+    if (sizeof(R) == 4 && !f32) return (int)cudaErrorInvalidValue;     // FP64 factors under FP32 vectors
     if constexpr (is_cplx<S>::value) {
-      if (fcplx) {
-        const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, S, TPR, CPT>, TPR);
-        factor_spmv_kernel<S, S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const S*)fvals, apply, ld,
-                                                                     (const S*)x, (S*)y, done);
+      if (fc) {
+        if (f32 && sizeof(R) == 8) go.template operator()<cfloat>();
+        else go.template operator()<S>();
       } else {
-        const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, R, TPR, CPT>, TPR);
-        factor_spmv_kernel<S, R, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const R*)fvals, apply, ld,
-                                                                     (const S*)x, (S*)y, done);
+        if (f32 && sizeof(R) == 8) go.template operator()<float>();
+        else go.template operator()<R>();
       }
     } else {
-      if (fcplx) return (int)cudaErrorInvalidValue;
-      const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, S, TPR, CPT>, TPR);
-      factor_spmv_kernel<S, S, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const S*)fvals, apply, ld,
-                                                                   (const S*)x, (S*)y, done);
+      if (fc) return (int)cudaErrorInvalidValue;
+      if (f32 && sizeof(R) == 8) go.template operator()<float>();
+      else go.template operator()<S>();
     }
     return 0;
   });

@@ -88,4 +88,4 @@ def test_default_options(lib):
     """mor_default_opts fills host memory only (no GPU call)."""
     o = mor.mor_default_opts()
     assert o.solver == mor.MOR_BICGSTAB and o.precision == mor.MOR_MIXED and o.restart == 50
-    assert o.tol == 1e-8 and o.precond == 0 and o.max_chain == 0
+    assert o.tol == 1e-8 and o.precond == 0 and o.max_chain == 0 and o.precond_precision == -1

@@ -214,3 +214,51 @@ def test_mimo_block_rhs_many_columns(h):
     for c in range(len(sig)):
         M = oop.A_sigma(wl.A, wl.E, sig[c])
         assert np.linalg.norm(R[:, c] - M @ X[:, c]) / np.linalg.norm(R[:, c]) <= 1.001e-8
+
+
+@pytest.mark.parametrize("name", ["convdiff3d_n3375", "rand_csrE_n1500"])
+def test_fp32_factors_under_fp64_solves(h, name):
+    """precond_precision = MOR_MIXED: FP32 / complex64 SPAI and reuse factors
+    applied (widened on load) inside FP64 BiCGSTAB; every solve still reaches
+    the FP64 residual 1e-8, and the iteration counts stay within the FP64
+    chain's (the factors differ by FP32 rounding only)."""
+    wl = CASES[name]()
+    _set(h, wl)
+    shifts = [30.0, 45.0 + 20.0j, 90.0 + 5.0j]
+    b = wl.B[:, 0]
+    its = {}
+    for fp in (mor.MOR_FP64, mor.MOR_MIXED):
+        mor.mor_build_precond(h, shifts[0], 0, fp)
+        for s in shifts[1:]:
+            mor.mor_update_precond(h, s, 0)
+        opts = mor.mor_default_opts(precision=mor.MOR_FP64)
+        X, stats, code = mor.mor_solve_shifts(h, shifts, 0, opts)
+        assert code == mor.MOR_OK
+        for c, s in enumerate(shifts):
+            assert _relres(wl, s, X[:, c], b) <= 1.001e-8
+        its[fp] = [x["iters"] for x in stats]
+    for a, o in zip(its[mor.MOR_MIXED], its[mor.MOR_FP64]):
+        assert abs(a - o) <= max(3, 0.25 * o), (its)
+    # FP64 factors cannot serve a mixed-precision solve
+    mor.mor_build_precond(h, shifts[0], 0, mor.MOR_FP64)
+    with pytest.raises(RuntimeError):
+        mor.mor_solve_shifts(h, shifts[:1], 0, mor.mor_default_opts(precision=mor.MOR_MIXED))
+
+
+def test_irka_step_with_fp32_factors_under_fp64(h):
+    """The IRKA schedule builds FP32 factors for FP64 solves when asked; the
+    reduced model matches the all-FP64 step's H_r."""
+    wl = W.config1(N=12)
+    _set(h, wl)
+    mor.mor_irka_reset(h)
+    s1, rom1, st1 = mor.mor_irka_step(h, wl.shifts, mor.mor_default_opts(precision=mor.MOR_FP64))
+    _set(h, wl)
+    mor.mor_irka_reset(h)
+    s2, rom2, st2 = mor.mor_irka_step(h, wl.shifts, mor.mor_default_opts(precision=mor.MOR_FP64,
+                                                                         precond_precision=mor.MOR_MIXED))
+    assert st2["max_relres"] <= 1.001e-8
+    w = np.logspace(0, 5, 200)
+    H1 = mor.mor_eval_tf(h, rom1, w)
+    H2 = mor.mor_eval_tf(h, rom2, w)
+    H = oop.transfer_function(wl.A, wl.E, wl.B, wl.C, 1j * w)
+    assert np.max(np.abs(H1 - H2) / np.abs(H)) <= 1e-6
