@@ -63,6 +63,26 @@ struct OpData {
   }
 };
 
+// Everything one batch solve needs besides the system and its chains: a
+// stream, the Krylov / refinement / GMRES workspaces, the per-(segment)
+// reduction tickets and live counter, small device state and a pinned
+// staging buffer.  Lane 0 runs on the handle's stream; lane 1 (its own
+// non-blocking stream) lets the transposed sweep of an IRKA step run
+// concurrently with the primal one.
+struct SolveLane {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DBuf ws_vec, ws_x64, ws_r64, ws_b64, ws_part, ws_small, ws_kstate, ws_segarr, ws_sums, ws_io;
+  DBuf ws_gm_vec, ws_gm_small, ws_gm_part;
+  DBuf seg_counters, seg_live;
+  int seg_alloc = 0;                 // segments the counters were zeroed for
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  SolveLane() {}
+  SolveLane(const SolveLane&) = delete;
+  SolveLane& operator=(const SolveLane&) = delete;
+};
+
 struct mor_ctx {
   int dev = 0;
   int sm_count = 152;
@@ -91,7 +111,7 @@ struct mor_ctx {
   SegView seg{};
   std::vector<int64_t> seg_rows_h;   // nseg + 1 row offsets (host)
   DBuf ws_kstate, ws_segarr, ws_sums;
-  DBuf ws_gm_vec, ws_gm_small, ws_gm_part;   // GMRES(m): basis, scalars, reduction partials
+  SolveLane lanes[2];                        // batch-solve state per stream (lane 0: `stream`)
   // IRKA reuse schedule
   int irka_z = 0;
   int vlen[2] = {0, 0};
@@ -99,6 +119,8 @@ struct mor_ctx {
 };
 
 int mor_fail(mor_t h, int code, const char* fmt, ...);
+// lane i ready (stream, pinned buffer); lane 0 uses the handle's stream
+int mor_lane(mor_t h, int i, SolveLane** out);
 
 #define MOR_CK(h, call)                                                                     \
   do {                                                                                      \

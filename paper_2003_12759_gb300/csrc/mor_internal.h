@@ -241,3 +241,5 @@ int dense_launch_diag_mul(int n, int k, const double* d, const double* X, double
 
 // process-wide count of executed kernels (see mor_launch_count)
 void mor_count_launches(int64_t n);
+// on = 1 while this thread records a CUDA graph (its launches are counted per replay)
+void mor_capture_mark(int on);

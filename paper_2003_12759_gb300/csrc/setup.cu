@@ -19,9 +19,14 @@
 #include <cstdlib>
 #include <thread>
 #include <atomic>
+#include <mutex>
+#include <map>
 
 static std::atomic<long long> g_launches{0};
-void mor_count_launches(int64_t n) { g_launches += n; }
+// launches recorded into a CUDA graph are counted when the graph is replayed
+static thread_local int t_capturing = 0;
+void mor_count_launches(int64_t n) { if (!t_capturing) g_launches += n; }
+void mor_capture_mark(int on) { t_capturing = on; }
 
 int mor_fail(mor_t h, int code, const char* fmt, ...) {
   if (h) {
@@ -30,9 +35,32 @@ int mor_fail(mor_t h, int code, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
+    static std::mutex mu;                 // two lanes may fail at once
+    std::lock_guard<std::mutex> lk(mu);
     h->err = buf;
   }
   return code;
+}
+
+int mor_lane(mor_t h, int i, SolveLane** out) {
+  SolveLane& L = h->lanes[i];
+  if (!L.stream) {
+    if (i == 0) L.stream = h->stream;
+    else {
+      if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess)
+        return mor_fail(h, MOR_ECUDA, "cannot create the second solve stream");
+      L.own_stream = true;
+    }
+  }
+  if (!L.pinned) {
+    L.pinned_bytes = 1 << 21;
+    if (cudaHostAlloc(&L.pinned, L.pinned_bytes, cudaHostAllocDefault) != cudaSuccess) {
+      L.pinned = nullptr;
+      return mor_fail(h, MOR_ENOMEM, "cannot allocate pinned host memory");
+    }
+  }
+  *out = &L;
+  return MOR_OK;
 }
 
 Coef mor_coef(const mor_ctx* h, mor_c64 s) {
@@ -275,6 +303,49 @@ std::vector<T> permute_to_layout(const std::vector<T>& csrv, const std::vector<i
   return out;
 }
 
+// Autotuner cache: the timed CSR / SELL choice of a matrix is kept for the
+// process, keyed by its signature (device, rows, stored entries, kind of E,
+// and an FNV-1a hash of the row pointers and column indices), so that a
+// pattern set again -- a new handle, a rebuilt system, the next job on the
+// same model -- skips the timing runs.
+struct PatternKey {
+  int dev;
+  int64_t n, nnz;
+  int ekind;
+  uint64_t hash;
+  bool operator<(const PatternKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (n != o.n) return n < o.n;
+    if (nnz != o.nnz) return nnz < o.nnz;
+    if (ekind != o.ekind) return ekind < o.ekind;
+    return hash < o.hash;
+  }
+};
+std::mutex g_fmt_mu;
+std::map<PatternKey, int> g_fmt_cache;
+
+uint64_t fnv1a(const void* p, size_t bytes, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* c = (const unsigned char*)p;
+  for (size_t i = 0; i < bytes; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+  return h;
+}
+PatternKey pattern_key(mor_t h, const HostCSR& S, int ekind) {
+  uint64_t hs = fnv1a(S.rowptr.data(), S.rowptr.size() * sizeof(int32_t));
+  hs = fnv1a(S.col.data(), S.col.size() * sizeof(int32_t), hs);
+  return PatternKey{h->dev, S.n, (int64_t)S.col.size(), ekind, hs};
+}
+bool cached_format(const PatternKey& k, int* fmt) {
+  std::lock_guard<std::mutex> lk(g_fmt_mu);
+  auto it = g_fmt_cache.find(k);
+  if (it == g_fmt_cache.end()) return false;
+  *fmt = it->second;
+  return true;
+}
+void store_format(const PatternKey& k, int fmt) {
+  std::lock_guard<std::mutex> lk(g_fmt_mu);
+  g_fmt_cache[k] = fmt;
+}
+
 // upload one operator in a given format
 int build_op(mor_t h, OpData& op, const HostCSR& S, const std::vector<double>& sa, const std::vector<double>& se,
              int fmt, bool has_e) {
@@ -395,7 +466,10 @@ int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std:
   MOR_TRY(mor_build_segments(h, seg_rows ? *seg_rows : std::vector<int64_t>{0, n}));
   // layout / autotune
   int fmt = format;
-  if (fmt == MOR_FMT_AUTO) {
+  const PatternKey key = pattern_key(h, S, h->ekind);
+  if (fmt == MOR_FMT_AUTO && cached_format(key, &fmt)) {
+    MOR_TRY(build_op(h, h->P, S, sa, se, fmt, Ecsr != nullptr));
+  } else if (fmt == MOR_FMT_AUTO) {
     int st1 = 0, st2 = 0;
     MOR_TRY(build_op(h, h->P, S, sa, se, FMT_CSR, Ecsr != nullptr));
     double tc = time_op(h, h->P, st1);
@@ -404,6 +478,7 @@ int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std:
     if (st1 != MOR_OK || st2 != MOR_OK) return mor_fail(h, MOR_ECUDA, "format autotuning failed");
     fmt = (ts <= tc) ? FMT_SELL : FMT_CSR;
     if (fmt == FMT_CSR) MOR_TRY(build_op(h, h->P, S, sa, se, FMT_CSR, Ecsr != nullptr));
+    store_format(key, fmt);
   } else {
     MOR_TRY(build_op(h, h->P, S, sa, se, fmt, Ecsr != nullptr));
   }
@@ -512,6 +587,10 @@ int mor_destroy(mor_t h) {
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
   if (h->pinned) cudaFreeHost(h->pinned);
+  for (SolveLane& L : h->lanes) {
+    if (L.own_stream) { cudaStreamSynchronize(L.stream); cudaStreamDestroy(L.stream); }
+    if (L.pinned) cudaFreeHost(L.pinned);
+  }
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
   return MOR_OK;

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <thread>
 
 namespace {
 
@@ -52,10 +53,24 @@ struct Small {
 };
 const int MAX_FACTORS = 4096;
 
-int get_small(mor_t h, Small& s) {
+// kernel launches recorded in a captured graph (counted once per replay)
+int64_t kernel_nodes(cudaGraph_t g) {
+  size_t nn = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess || nn == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (cudaGraphGetNodes(g, nodes.data(), &nn) != cudaSuccess) return 0;
+  int64_t k = 0;
+  for (size_t i = 0; i < nn; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+int get_small(mor_t h, DBuf& buf, Small& s) {
   const size_t bytes = 64 * 1024 + 4096 + (size_t)MAX_FACTORS * MOR_KMAX * sizeof(int);
-  MOR_CK(h, h->ws_small.alloc(bytes));
-  char* b = h->ws_small.as<char>();
+  MOR_CK(h, buf.alloc(bytes));
+  char* b = buf.as<char>();
   s.done = (int*)(b + 0);
   s.nsing = (int*)(b + 64);
   s.kstate = (void*)(b + 256);                          // 16 * 112 B
@@ -103,7 +118,7 @@ static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bo
   MOR_CK(h, f.vals->alloc(st_size(st) * (size_t)X.nlay));
   MOR_CK(h, cudaMemsetAsync(f.vals->p, 0, st_size(st) * (size_t)X.nlay, h->stream));
   Small sm;
-  MOR_TRY(get_small(h, sm));
+  MOR_TRY(get_small(h, h->ws_small, sm));
   MOR_CK(h, cudaMemsetAsync(sm.nsing, 0, sizeof(int), h->stream));
   SpaiArgs a;
   a.n = (int)X.n;
@@ -148,11 +163,21 @@ struct BatchIO {
   void* x64;            // row-major n x k, st64 (out)
 };
 
-static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cplx, const BatchIO& io,
+static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_opts& o, bool cplx, const BatchIO& io,
                        mor_solve_stats* stats) {
   OpData& op = h->op(transpose);
-  const SegView& sg = h->seg;
+  // the system's segment table with this lane's tickets and live counter
+  SegView sg = h->seg;
   const int nseg = sg.nseg;
+  if (ln.seg_alloc < nseg) {
+    MOR_CK(h, ln.seg_counters.alloc(sizeof(unsigned) * nseg));
+    MOR_CK(h, ln.seg_live.alloc(sizeof(int) * 2));
+    MOR_CK(h, cudaMemsetAsync(ln.seg_counters.p, 0, sizeof(unsigned) * nseg, ln.stream));
+    MOR_CK(h, cudaMemsetAsync(ln.seg_live.p, 0, sizeof(int) * 2, ln.stream));
+    ln.seg_alloc = nseg;
+  }
+  sg.counters = ln.seg_counters.as<unsigned>();
+  sg.live = ln.seg_live.as<int>();
   const int k = io.k;
   const int64_t n = op.n;
   const int prec = o.precision;
@@ -172,28 +197,28 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   }
   // workspace: 12 inner vectors of n x ld
   const size_t vbytes = ((es * (size_t)n * ld) + 255) / 256 * 256;
-  MOR_CK(h, h->ws_vec.alloc(vbytes * 12));
-  char* vb = h->ws_vec.as<char>();
+  MOR_CK(h, ln.ws_vec.alloc(vbytes * 12));
+  char* vb = ln.ws_vec.as<char>();
   auto vec = [&](int i) { return (void*)(vb + vbytes * i); };
   void *rhs = vec(0), *d = vec(1), *r = vec(2), *rhat = vec(3), *p = vec(4), *v = vec(5), *sv = vec(6),
        *t = vec(7), *ph = vec(8), *sh = vec(9), *tmp0 = vec(10), *tmp1 = vec(11);
-  MOR_CK(h, h->ws_r64.alloc(es64 * (size_t)n * ld));
-  void* r64 = h->ws_r64.p;
-  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * part_blocks(h)));
+  MOR_CK(h, ln.ws_r64.alloc(es64 * (size_t)n * ld));
+  void* r64 = ln.ws_r64.p;
+  MOR_CK(h, ln.ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * part_blocks(h)));
   Small sm;
-  MOR_TRY(get_small(h, sm));
+  MOR_TRY(get_small(h, ln.ws_small, sm));
   const size_t ksb = krylov_state_bytes(st_in);
   const size_t nsc = (size_t)nseg * ld;                 // (segment, column) slots
-  MOR_CK(h, h->ws_kstate.alloc(ksb * (size_t)nseg * MOR_LDMAX));
-  void* kstate = h->ws_kstate.p;
-  MOR_CK(h, h->ws_segarr.alloc((sizeof(double) * 2 + sizeof(int) * 2) * (size_t)nseg * MOR_LDMAX));
-  double* d_target = h->ws_segarr.as<double>();
+  MOR_CK(h, ln.ws_kstate.alloc(ksb * (size_t)nseg * MOR_LDMAX));
+  void* kstate = ln.ws_kstate.p;
+  MOR_CK(h, ln.ws_segarr.alloc((sizeof(double) * 2 + sizeof(int) * 2) * (size_t)nseg * MOR_LDMAX));
+  double* d_target = ln.ws_segarr.as<double>();
   double* d_nrm2 = d_target + (size_t)nseg * MOR_LDMAX;
   int* d_maxit = (int*)(d_nrm2 + (size_t)nseg * MOR_LDMAX);
   int* d_active = d_maxit + (size_t)nseg * MOR_LDMAX;
-  MOR_CK(h, h->ws_sums.alloc(sizeof(cdouble) * 2 * (size_t)nseg * MOR_LDMAX));
-  cdouble* d_sums = h->ws_sums.as<cdouble>();
-  if ((sizeof(cdouble) * 2 + 64) * nsc > h->pinned_bytes / 2) return mor_fail(h, MOR_EINVAL, "too many systems");
+  MOR_CK(h, ln.ws_sums.alloc(sizeof(cdouble) * 2 * (size_t)nseg * MOR_LDMAX));
+  cdouble* d_sums = ln.ws_sums.as<cdouble>();
+  if ((sizeof(cdouble) * 2 + 64) * nsc > ln.pinned_bytes / 2) return mor_fail(h, MOR_EINVAL, "too many systems");
   // coefficients (dummy columns reuse column 0's)
   Coef cf[MOR_LDMAX], ncf[MOR_LDMAX];
   for (int c = 0; c < ld; ++c) {
@@ -203,7 +228,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   PatView pv = op.view();
   OpVals ov_in = op_vals(h, op, st_is_f32(st_in));
   OpVals ov64 = op_vals(h, op, false);
-  MOR_CK(h, cudaMemsetAsync(io.x64, 0, es64 * (size_t)n * ld, h->stream));
+  MOR_CK(h, cudaMemsetAsync(io.x64, 0, es64 * (size_t)n * ld, ln.stream));
 
   // Current geometry of the batch.  When enough columns have converged that
   // the live ones fit a narrower stride, the converged columns are flushed
@@ -233,7 +258,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
         const int oc = cmap[c];
         mk[(size_t)f * MOR_KMAX + c] = (oc < 0 || oc >= k || f < io.L[oc]) ? 1 : 0;
       }
-    return (int)cudaMemcpyAsync(sm.masks, mk.data(), sizeof(int) * mk.size(), cudaMemcpyHostToDevice, h->stream);
+    return (int)cudaMemcpyAsync(sm.masks, mk.data(), sizeof(int) * mk.size(), cudaMemcpyHostToDevice, ln.stream);
   };
   auto chain_apply_d = [&](void* src, void* dst, const int* dn) -> int {
     if (Lmax == 0) return 0;
@@ -242,7 +267,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
       void* dd2 = (f == Lcur - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
       const Factor& F = op.chain[f];
       int e = launch_factor_spmv(st_in, F.st, sg, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
-                                 dd2, dn, h->stream);
+                                 dd2, dn, ln.stream);
       if (e) return e;
       s = dd2;
     }
@@ -253,16 +278,16 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     int e;
     void* phat = (Lmax == 0) ? pp : pph;
     void* shat = (Lmax == 0) ? ssv : ssh;
-    if ((e = krylov_launch_update_p(st_in, sg, ldc, rr, pp, vv, kstate, sm.done, h->stream))) return e;
+    if ((e = krylov_launch_update_p(st_in, sg, ldc, rr, pp, vv, kstate, sm.done, ln.stream))) return e;
     if ((e = chain_apply(pp, pph))) return e;
-    RedArgs ra{RED_DOT_W, rh, h->ws_part.p, nullptr, FIN_ALPHA, kstate, nullptr, sm.done};
-    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, phat, vv, nullptr, &ra, h->stream))) return e;
-    if ((e = krylov_launch_update_s(st_in, sg, ldc, rr, vv, ssv, kstate, sm.done, h->stream))) return e;
+    RedArgs ra{RED_DOT_W, rh, ln.ws_part.p, nullptr, FIN_ALPHA, kstate, nullptr, sm.done};
+    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, phat, vv, nullptr, &ra, ln.stream))) return e;
+    if ((e = krylov_launch_update_s(st_in, sg, ldc, rr, vv, ssv, kstate, sm.done, ln.stream))) return e;
     if ((e = chain_apply(ssv, ssh))) return e;
-    RedArgs rb{RED_DOT_TT, ssv, h->ws_part.p, nullptr, FIN_OMEGA, kstate, nullptr, sm.done};
-    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, shat, tt, nullptr, &rb, h->stream))) return e;
-    if ((e = krylov_launch_update_xr(st_in, sg, ldc, dd, rr, phat, shat, ssv, tt, rh, h->ws_part.p, kstate, sm.done,
-                                     h->stream)))
+    RedArgs rb{RED_DOT_TT, ssv, ln.ws_part.p, nullptr, FIN_OMEGA, kstate, nullptr, sm.done};
+    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, shat, tt, nullptr, &rb, ln.stream))) return e;
+    if ((e = krylov_launch_update_xr(st_in, sg, ldc, dd, rr, phat, shat, ssv, tt, rh, ln.ws_part.p, kstate, sm.done,
+                                     ln.stream)))
       return e;
     return 0;
   };
@@ -275,15 +300,13 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     drop_graph();
     if (!o.use_graph) return MOR_OK;
     cudaGraph_t g = nullptr;
-    int64_t c0 = 0, c1 = 0;
-    mor_launch_count(&c0);
-    MOR_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    MOR_CK(h, cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
+    mor_capture_mark(1);
     int e = 0;
     for (int it = 0; it < chunk && !e; ++it) e = one_iter();
-    cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
-    mor_launch_count(&c1);
-    graph_nodes = c1 - c0;
-    mor_count_launches(-graph_nodes);   // captured, not executed
+    mor_capture_mark(0);
+    cudaError_t ce = cudaStreamEndCapture(ln.stream, &g);
+    graph_nodes = (ce == cudaSuccess && g) ? kernel_nodes(g) : 0;
     if (e) { if (g) cudaGraphDestroy(g); return mor_fail(h, MOR_ECUDA, "kernel launch failed during capture: %s", cudaGetErrorString((cudaError_t)e)); }
     MOR_CK(h, ce);
     ce = cudaGraphInstantiate(&gexec, g, 0);
@@ -296,7 +319,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
   const size_t NK = (size_t)nseg * k;                  // (segment, real column) pairs
   std::vector<double> bnorm(NK, 0.0), relres(NK, 0.0), rn2(NK, 0.0);
   std::vector<int> iters(NK, 0), refs(NK, 0), status(NK, MOR_OK), act(NK, 0);
-  double* hp = (double*)h->pinned;
+  double* hp = (double*)ln.pinned;
   cdouble* h_sums = (cdouble*)hp;                                  // 2 ld per segment
   double* tg = hp + 4 * nsc;
   double* nr = tg + nsc;
@@ -312,8 +335,8 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     const int m = o.restart;
     if (m < 1 || m > GM_MMAX) return mor_fail(h, MOR_EINVAL, "GMRES restart %d outside 1..%d", m, GM_MMAX);
     const int64_t vst = (int64_t)(vbytes / es);
-    MOR_CK(h, h->ws_gm_vec.alloc(vbytes * (size_t)(m + 4)));
-    char* gb = h->ws_gm_vec.as<char>();
+    MOR_CK(h, ln.ws_gm_vec.alloc(vbytes * (size_t)(m + 4)));
+    char* gb = ln.ws_gm_vec.as<char>();
     auto V = [&](int i) { return (void*)(gb + vbytes * (size_t)i); };
     void* W = V(m + 1);
     void* Z = V(m + 2);
@@ -324,28 +347,28 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     const size_t o_st = take(gmres_state_bytes() * ld);
     const size_t o_H = take(sizeof(cdouble) * (size_t)ld * (m + 1) * m);
     const size_t o_h1 = take(hb), o_h2 = take(hb), o_y = take(hb), o_fl = take(64);
-    MOR_CK(h, h->ws_gm_small.alloc(off));
-    char* sb = h->ws_gm_small.as<char>();
+    MOR_CK(h, ln.ws_gm_small.alloc(off));
+    char* sb = ln.ws_gm_small.as<char>();
     void* gst = sb + o_st;
     void* Hm = sb + o_H;
     void *h1 = sb + o_h1, *h2 = sb + o_h2, *yc = sb + o_y;
     unsigned* gcnt = (unsigned*)(sb + o_fl);
     int* done_cycle = (int*)(sb + o_fl + 16);
     int* done_all = (int*)(sb + o_fl + 32);
-    MOR_CK(h, cudaMemsetAsync(sb, 0, off, h->stream));
-    MOR_CK(h, h->ws_gm_part.alloc(sizeof(double) * 2 * (size_t)(m + 1) * ld * (size_t)(h->sm_count * 8)));
-    double* gpart = h->ws_gm_part.as<double>();
-    MOR_CK(h, cudaMemsetAsync(gb, 0, vbytes * (size_t)(m + 4), h->stream));   // no stale values in the basis
-    MOR_CK(h, cudaMemsetAsync(xin, 0, vbytes, h->stream));
-    RedArgs rn{RED_NORM, nullptr, h->ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
+    MOR_CK(h, cudaMemsetAsync(sb, 0, off, ln.stream));
+    MOR_CK(h, ln.ws_gm_part.alloc(sizeof(double) * 2 * (size_t)(m + 1) * ld * (size_t)(h->sm_count * 8)));
+    double* gpart = ln.ws_gm_part.as<double>();
+    MOR_CK(h, cudaMemsetAsync(gb, 0, vbytes * (size_t)(m + 4), ln.stream));   // no stale values in the basis
+    MOR_CK(h, cudaMemsetAsync(xin, 0, vbytes, ln.stream));
+    RedArgs rn{RED_NORM, nullptr, ln.ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
     RedArgs none{RED_NONE, nullptr, nullptr, nullptr, 0, nullptr, nullptr, done_cycle};
     auto start_cycle = [&](int first) -> int {
       int e;
-      if ((e = launch_op_spmv(st_in, sg, pv, ov_in, ncf, ld, xin, W, rhs, &rn, h->stream))) return e;
+      if ((e = launch_op_spmv(st_in, sg, pv, ov_in, ncf, ld, xin, W, rhs, &rn, ln.stream))) return e;
       if ((e = gmres_launch_begin(ld, d_sums, gst, d_target, d_maxit, d_active, first, done_cycle, done_all,
-                                  h->stream)))
+                                  ln.stream)))
         return e;
-      return gmres_launch_scale(st_in, sg, ld, W, V(0), gst, 1, done_cycle, h->stream);
+      return gmres_launch_scale(st_in, sg, ld, W, V(0), gst, 1, done_cycle, ln.stream);
     };
     auto cycle = [&]() -> int {
       int e;
@@ -355,27 +378,27 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
           if ((e = chain_apply_d(V(j), Z, done_cycle))) return e;
           src = Z;
         }
-        if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cf, ld, src, W, nullptr, &none, h->stream))) return e;
-        if ((e = gmres_launch_dot(st_in, sg, ld, V(0), vst, j + 1, W, gpart, gcnt, h1, done_cycle, h->stream))) return e;
+        if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cf, ld, src, W, nullptr, &none, ln.stream))) return e;
+        if ((e = gmres_launch_dot(st_in, sg, ld, V(0), vst, j + 1, W, gpart, gcnt, h1, done_cycle, ln.stream))) return e;
         if ((e = gmres_launch_axpy(st_in, sg, ld, V(0), vst, j + 1, h1, W, 0, 0, gpart, gcnt, gst, Hm, m, h1, h2,
-                                   done_cycle, h->stream)))
+                                   done_cycle, ln.stream)))
           return e;
-        if ((e = gmres_launch_dot(st_in, sg, ld, V(0), vst, j + 1, W, gpart, gcnt, h2, done_cycle, h->stream))) return e;
+        if ((e = gmres_launch_dot(st_in, sg, ld, V(0), vst, j + 1, W, gpart, gcnt, h2, done_cycle, ln.stream))) return e;
         if ((e = gmres_launch_axpy(st_in, sg, ld, V(0), vst, j + 1, h2, W, 0, 1, gpart, gcnt, gst, Hm, m, h1, h2,
-                                   done_cycle, h->stream)))
+                                   done_cycle, ln.stream)))
           return e;
-        if ((e = gmres_launch_scale(st_in, sg, ld, W, V(j + 1), gst, 1, done_cycle, h->stream))) return e;
+        if ((e = gmres_launch_scale(st_in, sg, ld, W, V(j + 1), gst, 1, done_cycle, ln.stream))) return e;
       }
-      if ((e = gmres_launch_solve_y(ld, m, gst, Hm, yc, h->stream))) return e;
+      if ((e = gmres_launch_solve_y(ld, m, gst, Hm, yc, ln.stream))) return e;
       if ((e = gmres_launch_axpy(st_in, sg, ld, V(0), vst, m, yc, U, 1, 0, gpart, gcnt, gst, Hm, m, h1, h2, nullptr,
-                                 h->stream)))
+                                 ln.stream)))
         return e;
       void* upd = U;
       if (Lmax > 0) {
         if ((e = chain_apply_d(U, Z, nullptr))) return e;
         upd = Z;
       }
-      if ((e = gmres_launch_add(st_in, sg, ld, xin, upd, h->stream))) return e;
+      if ((e = gmres_launch_add(st_in, sg, ld, xin, upd, ln.stream))) return e;
       return start_cycle(0);
     };
     MOR_CKI(h, start_cycle(1));
@@ -384,14 +407,12 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     int64_t gnodes = 0;
     if (o.use_graph) {
       cudaGraph_t g = nullptr;
-      int64_t c0 = 0, c1 = 0;
-      mor_launch_count(&c0);
-      MOR_CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      MOR_CK(h, cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
+      mor_capture_mark(1);
       const int e = cycle();
-      const cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
-      mor_launch_count(&c1);
-      gnodes = c1 - c0;
-      mor_count_launches(-gnodes);
+      mor_capture_mark(0);
+      const cudaError_t ce = cudaStreamEndCapture(ln.stream, &g);
+      gnodes = (ce == cudaSuccess && g) ? kernel_nodes(g) : 0;
       if (e) { if (g) cudaGraphDestroy(g); return mor_fail(h, MOR_ECUDA, "launch failed during capture: %s", cudaGetErrorString((cudaError_t)e)); }
       MOR_CK(h, ce);
       const cudaError_t ie = cudaGraphInstantiate(&gx, g, 0);
@@ -402,19 +423,19 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
     for (int c = 0; c < ld; ++c) maxrem = std::max(maxrem, mi[c]);
     int* hd = (int*)(ac + nsc);
     for (int cyc = 0; cyc <= maxrem; ++cyc) {
-      MOR_CK(h, cudaMemcpyAsync(hd, done_all, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-      MOR_CK(h, cudaStreamSynchronize(h->stream));
+      MOR_CK(h, cudaMemcpyAsync(hd, done_all, sizeof(int), cudaMemcpyDeviceToHost, ln.stream));
+      MOR_CK(h, cudaStreamSynchronize(ln.stream));
       if (*hd) break;
       if (gx) {
-        MOR_CK(h, cudaGraphLaunch(gx, h->stream));
+        MOR_CK(h, cudaGraphLaunch(gx, ln.stream));
         mor_count_launches(gnodes);
       } else {
         MOR_CKI(h, cycle());
       }
     }
     std::vector<unsigned char> gs(gmres_state_bytes() * ld);
-    MOR_CK(h, cudaMemcpyAsync(gs.data(), gst, gs.size(), cudaMemcpyDeviceToHost, h->stream));
-    MOR_CK(h, cudaStreamSynchronize(h->stream));
+    MOR_CK(h, cudaMemcpyAsync(gs.data(), gst, gs.size(), cudaMemcpyDeviceToHost, ln.stream));
+    MOR_CK(h, cudaStreamSynchronize(ln.stream));
     for (int c = 0; c < k; ++c) {
       const void* e = gs.data() + gmres_state_bytes() * c;
       kit_out[c] = gmres_state_iters(e);
@@ -426,10 +447,10 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
 
   for (int pass = 0;; ++pass) {
     // true residual r64 = b - A(sigma) x64 in FP64 with fused norms, per (system, column)
-    RedArgs rn{RED_NORM, nullptr, h->ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
-    MOR_CKI(h, launch_op_spmv(st64, sg, pv, ov64, ncf, ld, io.x64, r64, io.b64, &rn, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(h_sums, d_sums, sizeof(cdouble) * 2 * nsc, cudaMemcpyDeviceToHost, h->stream));
-    MOR_CK(h, cudaStreamSynchronize(h->stream));
+    RedArgs rn{RED_NORM, nullptr, ln.ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
+    MOR_CKI(h, launch_op_spmv(st64, sg, pv, ov64, ncf, ld, io.x64, r64, io.b64, &rn, ln.stream));
+    MOR_CK(h, cudaMemcpyAsync(h_sums, d_sums, sizeof(cdouble) * 2 * nsc, cudaMemcpyDeviceToHost, ln.stream));
+    MOR_CK(h, cudaStreamSynchronize(ln.stream));
     int nact = 0;
     for (int sgi = 0; sgi < nseg; ++sgi)
       for (int c = 0; c < k; ++c) {
@@ -462,24 +483,24 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
         nr[z] = rn2[q];
         if (act[q]) refs[q] += 1;
       }
-    MOR_CK(h, cudaMemcpyAsync(d_target, tg, sizeof(double) * nsc, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(d_maxit, mi, sizeof(int) * nsc, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(d_active, ac, sizeof(int) * nsc, cudaMemcpyHostToDevice, h->stream));
-    MOR_CK(h, cudaMemcpyAsync(d_nrm2, nr, sizeof(double) * nsc, cudaMemcpyHostToDevice, h->stream));
+    MOR_CK(h, cudaMemcpyAsync(d_target, tg, sizeof(double) * nsc, cudaMemcpyHostToDevice, ln.stream));
+    MOR_CK(h, cudaMemcpyAsync(d_maxit, mi, sizeof(int) * nsc, cudaMemcpyHostToDevice, ln.stream));
+    MOR_CK(h, cudaMemcpyAsync(d_active, ac, sizeof(int) * nsc, cudaMemcpyHostToDevice, ln.stream));
+    MOR_CK(h, cudaMemcpyAsync(d_nrm2, nr, sizeof(double) * nsc, cudaMemcpyHostToDevice, ln.stream));
     // full geometry for this inner solve
     ldc = ld;
     for (int c = 0; c < ld; ++c) { cmap[c] = c < k ? c : -1; cfc[c] = cf[c]; }
     dd = d; rr = r; rh = rhat; pp = p; vv = v; ssv = sv; tt = t; pph = ph; ssh = sh; t0 = tmp0; t1 = tmp1;
     bool compacted = false;
     MOR_CKI(h, upload_masks());
-    MOR_CKI(h, refine_launch_scale_cast(st_in, sg, ld, r64, d_nrm2, d_active, rhs, h->stream));
+    MOR_CKI(h, refine_launch_scale_cast(st_in, sg, ld, r64, d_nrm2, d_active, rhs, ln.stream));
     std::vector<int> kit(NK, 0), kstat(NK, KST_OK);
     void* dres = dd;
     if (o.solver == MOR_GMRES) {
       MOR_TRY(gmres_inner(dd, kit, kstat));
     } else {
-      MOR_CKI(h, krylov_launch_init(st_in, sg, ld, rhs, dd, rr, rh, pp, vv, h->ws_part.p, kstate, d_target, d_maxit,
-                                    sm.done, h->stream));
+      MOR_CKI(h, krylov_launch_init(st_in, sg, ld, rhs, dd, rr, rh, pp, vv, ln.ws_part.p, kstate, d_target, d_maxit,
+                                    sm.done, ln.stream));
       MOR_TRY(capture());
       int maxrem = 0;
       for (size_t z = 0; z < nsc; ++z) maxrem = std::max(maxrem, mi[z]);
@@ -487,7 +508,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
       int* hd = (int*)(ac + nsc);
       while (it < maxrem) {
         if (gexec) {
-          MOR_CK(h, cudaGraphLaunch(gexec, h->stream));
+          MOR_CK(h, cudaGraphLaunch(gexec, ln.stream));
           mor_count_launches(graph_nodes);
           it += chunk;
         } else {
@@ -496,12 +517,12 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
           if ((it % chunk) != 0 && it < maxrem) continue;
         }
         if (nseg > 1) {
-          MOR_CK(h, cudaMemcpyAsync(hd, sm.done, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-          MOR_CK(h, cudaStreamSynchronize(h->stream));
+          MOR_CK(h, cudaMemcpyAsync(hd, sm.done, sizeof(int), cudaMemcpyDeviceToHost, ln.stream));
+          MOR_CK(h, cudaStreamSynchronize(ln.stream));
           if (*hd) break;
           continue;
         }
-        MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, ldc, h->stream));
+        MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, ldc, ln.stream));
         int nlive = 0;
         for (int c = 0; c < ldc; ++c) nlive += krylov_state_active(kst_host.data() + ksb * c) ? 1 : 0;
         if (nlive == 0) break;
@@ -524,15 +545,15 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
         std::vector<int> maps(3 * MOR_LDMAX, 0);
         for (size_t i = 0; i < drop_src.size(); ++i) { maps[i] = drop_src[i]; maps[MOR_LDMAX + i] = drop_dst[i]; }
         for (size_t i = 0; i < live.size(); ++i) maps[2 * MOR_LDMAX + i] = live[i];
-        MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, h->stream));
+        MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, ln.stream));
         if (!drop_src.empty())
           MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, (int)drop_src.size(), dmaps, dmaps + MOR_LDMAX, dd,
-                                              d_full, h->stream));
+                                              d_full, ln.stream));
         const int* gmap = dmaps + 2 * MOR_LDMAX;
         void* src[5] = {dd, rr, rh, pp, vv};
         void* dst[5] = {ssv, tt, pph, ssh, t0};
         for (int q = 0; q < 5; ++q)
-          MOR_CKI(h, conv_launch_gather_cols(st_in, n, ldc, ld_new, (int)live.size(), gmap, src[q], dst[q], h->stream));
+          MOR_CKI(h, conv_launch_gather_cols(st_in, n, ldc, ld_new, (int)live.size(), gmap, src[q], dst[q], ln.stream));
         // the old state vectors become the scratch set
         dd = dst[0]; rr = dst[1]; rh = dst[2]; pp = dst[3]; vv = dst[4];
         ssv = src[0]; tt = src[1]; pph = src[2]; ssh = src[3]; t0 = src[4];
@@ -549,13 +570,13 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
         }
         cmap = nmap;
         ldc = ld_new;
-        MOR_CKI(h, krylov_write_state(kst_new.data(), kstate, ldc, h->stream));
+        MOR_CKI(h, krylov_write_state(kst_new.data(), kstate, ldc, ln.stream));
         MOR_CKI(h, upload_masks());
         compacted = true;
         MOR_TRY(capture());
       }
       // final per-(system, column) state of this inner solve
-      MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, nseg * ldc, h->stream));
+      MOR_CKI(h, krylov_read_states(kst_host.data(), kstate, nseg * ldc, ln.stream));
       for (int sgi = 0; sgi < nseg; ++sgi)
         for (int c = 0; c < ldc; ++c) {
           const int oc = cmap[c];
@@ -572,9 +593,9 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
         for (int c = 0; c < ldc; ++c)
           if (cmap[c] >= 0 && cmap[c] < k) { maps[nrem] = c; maps[MOR_LDMAX + nrem] = cmap[c]; ++nrem; }
         int* dmaps = sm.masks + (size_t)MAX_FACTORS * MOR_KMAX - 3 * MOR_LDMAX;
-        MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, h->stream));
+        MOR_CK(h, cudaMemcpyAsync(dmaps, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice, ln.stream));
         if (nrem > 0)
-          MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, nrem, dmaps, dmaps + MOR_LDMAX, dd, d_full, h->stream));
+          MOR_CKI(h, conv_launch_scatter_cols(st_in, n, ldc, ld, nrem, dmaps, dmaps + MOR_LDMAX, dd, d_full, ln.stream));
         dres = d_full;
       }
     }
@@ -583,7 +604,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
       iters[q] += kit[q];
       if (kstat[q] == KST_BREAKDOWN && pass + 1 >= max_outer) status[q] = MOR_EBREAKDOWN;
     }
-    MOR_CKI(h, refine_launch_update(st_in, sg, ld, io.x64, dres, d_nrm2, d_active, h->stream));
+    MOR_CKI(h, refine_launch_update(st_in, sg, ld, io.x64, dres, d_nrm2, d_active, ln.stream));
   }
   // per-column statistics: with several systems, stats has nseg x k entries
   if (stats)
@@ -602,7 +623,7 @@ static int solve_batch(mor_t h, int transpose, const mor_solve_opts& o, bool cpl
 
 // Solve k shifts (any k), batching by 16.  rhs: either R (col-major c128, host or
 // device) or the system's B/C column 0.  X out col-major c128 (host or device).
-static int solve_many(mor_t h, const mor_c64* sig, int k, int transpose, const mor_solve_opts& o,
+static int solve_many(mor_t h, SolveLane& ln, const mor_c64* sig, int k, int transpose, const mor_solve_opts& o,
                       const std::vector<int>& L, bool cplx, const mor_c64* R, bool dev, mor_c64* X,
                       mor_solve_stats* stats) {
   const int64_t n = h->n;
@@ -614,27 +635,27 @@ static int solve_many(mor_t h, const mor_c64* sig, int k, int transpose, const m
   for (int c0 = 0; c0 < k; c0 += bmax) {
     const int kc = std::min(bmax, k - c0);
     const int ld = row_stride(st_in, kc);
-    MOR_CK(h, h->ws_b64.alloc(es64 * (size_t)n * ld));
-    MOR_CK(h, h->ws_x64.alloc(es64 * (size_t)n * ld));
-    void* xrow = h->ws_x64.p;
-    if (ld > kc) MOR_CK(h, cudaMemsetAsync(h->ws_b64.p, 0, es64 * (size_t)n * ld, h->stream));
+    MOR_CK(h, ln.ws_b64.alloc(es64 * (size_t)n * ld));
+    MOR_CK(h, ln.ws_x64.alloc(es64 * (size_t)n * ld));
+    void* xrow = ln.ws_x64.p;
+    if (ld > kc) MOR_CK(h, cudaMemsetAsync(ln.ws_b64.p, 0, es64 * (size_t)n * ld, ln.stream));
     if (R) {
       const mor_c64* Rc = R + (size_t)n * c0;
       const void* src = Rc;
       if (!dev) {
-        MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * kc));
-        MOR_CK(h, cudaMemcpyAsync(h->ws_io.p, Rc, sizeof(mor_c64) * (size_t)n * kc, cudaMemcpyHostToDevice, h->stream));
-        src = h->ws_io.p;
+        MOR_CK(h, ln.ws_io.alloc(sizeof(mor_c64) * (size_t)n * kc));
+        MOR_CK(h, cudaMemcpyAsync(ln.ws_io.p, Rc, sizeof(mor_c64) * (size_t)n * kc, cudaMemcpyHostToDevice, ln.stream));
+        src = ln.ws_io.p;
       }
-      MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st64, (int)n, kc, ld, src, h->ws_b64.p, h->stream));
+      MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st64, (int)n, kc, ld, src, ln.ws_b64.p, ln.stream));
     } else {
       const double* col0 = transpose ? h->C.as<double>() : h->B.as<double>();
-      MOR_CKI(h, conv_launch_real_col_to_rowmajor(st64, (int)n, kc, ld, col0, 0, h->ws_b64.p, h->stream));
+      MOR_CKI(h, conv_launch_real_col_to_rowmajor(st64, (int)n, kc, ld, col0, 0, ln.ws_b64.p, ln.stream));
     }
-    BatchIO io{sig + c0, kc, ld, L.data() + c0, h->ws_b64.p, xrow};
+    BatchIO io{sig + c0, kc, ld, L.data() + c0, ln.ws_b64.p, xrow};
     const int nseg = h->seg.nseg;
     std::vector<mor_solve_stats> sb((size_t)nseg * kc);
-    int s = solve_batch(h, transpose, o, cplx, io, sb.data());
+    int s = solve_batch(h, ln, transpose, o, cplx, io, sb.data());
     if (stats)   // stats has nseg x k entries: [seg * k + c]
       for (int sgi = 0; sgi < nseg; ++sgi)
         for (int c = 0; c < kc; ++c) stats[(size_t)sgi * k + c0 + c] = sb[(size_t)sgi * kc + c];
@@ -643,15 +664,15 @@ static int solve_many(mor_t h, const mor_c64* sig, int k, int transpose, const m
     if (X) {
       mor_c64* Xc = X + (size_t)n * c0;
       if (dev) {
-        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, ld, xrow, Xc, h->stream));
+        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, ld, xrow, Xc, ln.stream));
       } else {
-        MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * kc));
-        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, ld, xrow, h->ws_io.p, h->stream));
-        MOR_CK(h, cudaMemcpyAsync(Xc, h->ws_io.p, sizeof(mor_c64) * (size_t)n * kc, cudaMemcpyDeviceToHost, h->stream));
+        MOR_CK(h, ln.ws_io.alloc(sizeof(mor_c64) * (size_t)n * kc));
+        MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st64, (int)n, kc, ld, xrow, ln.ws_io.p, ln.stream));
+        MOR_CK(h, cudaMemcpyAsync(Xc, ln.ws_io.p, sizeof(mor_c64) * (size_t)n * kc, cudaMemcpyDeviceToHost, ln.stream));
       }
     }
   }
-  MOR_CK(h, cudaStreamSynchronize(h->stream));
+  MOR_CK(h, cudaStreamSynchronize(ln.stream));
   return ret;
 }
 
@@ -903,7 +924,7 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   if (ld > k) MOR_CK(h, cudaMemsetAsync(a, 0, st_size(st) * (size_t)n * ld, h->stream));
   MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(st, (int)n, k, ld, src, a, h->stream));
   Small sm;
-  MOR_TRY(get_small(h, sm));
+  MOR_TRY(get_small(h, h->ws_small, sm));
   std::vector<int> masks((size_t)std::max(Lmax, 1) * MOR_KMAX, 0);
   for (int f = 0; f < Lmax; ++f)
     for (int c = 0; c < ld; ++c) masks[(size_t)f * MOR_KMAX + c] = (c >= k || f < L[c]) ? 1 : 0;
@@ -941,6 +962,8 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
   for (int c = 0; c < k; ++c)
     if (!std::isfinite(sigma[c].re) || !std::isfinite(sigma[c].im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
   cudaSetDevice(h->dev);
+  SolveLane* lane0 = nullptr;
+  MOR_TRY(mor_lane(h, 0, &lane0));
   const bool dev = flags & MOR_DEVICE_PTRS;
   OpData& op = h->op(transpose);
   bool rc = false;
@@ -958,7 +981,7 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
       MOR_TRY(build_factor(h, transpose, sigma[c], sigma[c], false, factor_precision(o)));
       std::vector<int> L(1, 1);
       bool cc = anyc || chain_cplx(op, L);
-      int s = solve_many(h, sigma + c, 1, transpose, o, L, cc, R ? R + (size_t)h->n * c : nullptr, dev,
+      int s = solve_many(h, *lane0, sigma + c, 1, transpose, o, L, cc, R ? R + (size_t)h->n * c : nullptr, dev,
                          X + (size_t)h->n * c, stats ? stats + c : nullptr);
       if (s != MOR_OK && s != MOR_ENOCONV && s != MOR_EBREAKDOWN) return s;
       if (s != MOR_OK) ret = s;
@@ -971,10 +994,10 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
     return mor_fail(h, MOR_ESTATE, "an FP64 preconditioner chain cannot serve a mixed-precision solve");
   bool cc = anyc || chain_cplx(op, L);
   const int nseg = h->seg.nseg;
-  if (nseg == 1 || !stats) return solve_many(h, sigma, k, transpose, o, L, cc, R, dev, X, stats);
+  if (nseg == 1 || !stats) return solve_many(h, *lane0, sigma, k, transpose, o, L, cc, R, dev, X, stats);
   // several systems: report, per shift, the worst over the systems
   std::vector<mor_solve_stats> all((size_t)nseg * k);
-  int ret = solve_many(h, sigma, k, transpose, o, L, cc, R, dev, X, all.data());
+  int ret = solve_many(h, *lane0, sigma, k, transpose, o, L, cc, R, dev, X, all.data());
   for (int c = 0; c < k; ++c) {
     mor_solve_stats a = all[c];
     for (int sgi = 1; sgi < nseg; ++sgi) {
@@ -1006,6 +1029,8 @@ int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const m
   for (int c = 0; c < k; ++c)
     if (!std::isfinite(sigma[c].re) || !std::isfinite(sigma[c].im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
   cudaSetDevice(h->dev);
+  SolveLane* lane0 = nullptr;
+  MOR_TRY(mor_lane(h, 0, &lane0));
   OpData& op = h->op(transpose);
   std::vector<int> L = (o.precond == 2) ? std::vector<int>(k, 0) : prefix_lengths(op, sigma, k);
   if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision &&
@@ -1014,7 +1039,8 @@ int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const m
   bool cc = chain_cplx(op, L);
   for (int c = 0; c < k; ++c) cc |= !is_real_shift(sigma[c]);
   std::vector<mor_solve_stats> all((size_t)h->seg.nseg * k);
-  int ret = solve_many(h, sigma, k, transpose, o, L, cc, nullptr, (flags & MOR_DEVICE_PTRS) != 0, X, all.data());
+  int ret = solve_many(h, *lane0, sigma, k, transpose, o, L, cc, nullptr, (flags & MOR_DEVICE_PTRS) != 0, X,
+                       all.data());
   if (stats) std::memcpy(stats, all.data(), sizeof(mor_solve_stats) * all.size());
   return ret;
 }
@@ -1198,31 +1224,60 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
     MOR_CK(h, cudaGetLastError());
   }
   DBuf xs[2];                       // solutions, n x l complex128 column-major (device)
-  std::vector<mor_solve_stats> ss(l);
-  int solve_status = MOR_OK;
+  std::vector<mor_solve_stats> ss[2];
+  int s2v[2] = {MOR_OK, MOR_OK};
   for (int t = 0; t < 2; ++t) {
     MOR_CK(h, xs[t].alloc(sizeof(mor_c64) * (size_t)n * l));
-    mor_c64* X = xs[t].as<mor_c64>();
-    int s2;
-    if (o.precond == 1) {
-      s2 = MOR_OK;
+    ss[t].resize(l);
+  }
+  SolveLane* lane[2];
+  MOR_TRY(mor_lane(h, 0, &lane[0]));
+  MOR_TRY(mor_lane(h, 1, &lane[1]));
+  if (o.precond == 1) {
+    // a fresh SPAI per shift: factor builds and solves alternate on the handle's stream
+    for (int t = 0; t < 2; ++t)
       for (int i = 0; i < l; ++i) {
         MOR_TRY(build_factor(h, t, sol[i], sol[i], false, factor_precision(o)));
         st.builds_spai++;
         std::vector<int> L1(1, 1);
         const mor_c64* Ri = tang ? rhs[t].as<mor_c64>() + (size_t)n * i : nullptr;
-        int s3 = solve_many(h, &sol[i], 1, t, o, L1, cplx, Ri, true, X + (size_t)n * i, &ss[i]);
+        int s3 = solve_many(h, *lane[0], &sol[i], 1, t, o, L1, cplx, Ri, true, xs[t].as<mor_c64>() + (size_t)n * i,
+                            &ss[t][i]);
         if (s3 != MOR_OK && s3 != MOR_ENOCONV && s3 != MOR_EBREAKDOWN) return s3;
-        if (s3 != MOR_OK) s2 = s3;
+        if (s3 != MOR_OK) s2v[t] = s3;
       }
-    } else {
-      s2 = solve_many(h, sol.data(), l, t, o, Ls[t], cplx, tang ? rhs[t].as<mor_c64>() : nullptr, true, X, ss.data());
-      if (s2 != MOR_OK && s2 != MOR_ENOCONV && s2 != MOR_EBREAKDOWN) return s2;
-    }
-    if (s2 != MOR_OK) solve_status = s2;
+  } else {
+    // the primal (V) and transposed (W) sweeps are independent: V on the
+    // handle's stream, W on lane 1's stream from a second host thread, both
+    // after the factor builds queued so far
+    cudaEvent_t built;
+    MOR_CK(h, cudaEventCreateWithFlags(&built, cudaEventDisableTiming));
+    struct EvG { cudaEvent_t e; ~EvG() { cudaEventDestroy(e); } } evg{built};
+    MOR_CK(h, cudaEventRecord(built, h->stream));
+    MOR_CK(h, cudaStreamWaitEvent(lane[1]->stream, built, 0));
+    auto sweep = [&](int t) {
+      cudaSetDevice(h->dev);
+      s2v[t] = solve_many(h, *lane[t], sol.data(), l, t, o, Ls[t], cplx, tang ? rhs[t].as<mor_c64>() : nullptr, true,
+                          xs[t].as<mor_c64>(), ss[t].data());
+    };
+    std::thread tw(sweep, 1);
+    sweep(0);
+    tw.join();
+    // solve_many leaves its stream synchronised; order lane 1 before the handle's later work
+    cudaEvent_t wdone;
+    MOR_CK(h, cudaEventCreateWithFlags(&wdone, cudaEventDisableTiming));
+    struct EvG2 { cudaEvent_t e; ~EvG2() { cudaEventDestroy(e); } } evg2{wdone};
+    MOR_CK(h, cudaEventRecord(wdone, lane[1]->stream));
+    MOR_CK(h, cudaStreamWaitEvent(h->stream, wdone, 0));
+    for (int t = 0; t < 2; ++t)
+      if (s2v[t] != MOR_OK && s2v[t] != MOR_ENOCONV && s2v[t] != MOR_EBREAKDOWN) return s2v[t];
+  }
+  int solve_status = MOR_OK;
+  for (int t = 0; t < 2; ++t) {
+    if (s2v[t] != MOR_OK) solve_status = s2v[t];
     for (int i = 0; i < l; ++i) {
-      (t == 0 ? st.iters_V : st.iters_W) += ss[i].iters;
-      st.max_relres = std::max(st.max_relres, ss[i].relres);
+      (t == 0 ? st.iters_V : st.iters_W) += ss[t][i].iters;
+      st.max_relres = std::max(st.max_relres, ss[t][i].relres);
     }
   }
   cudaEventRecord(ev[2], h->stream);
@@ -1409,7 +1464,9 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
   mor_count_launches(1);
   MOR_CK(h, cudaGetLastError());
   std::vector<mor_solve_stats> ss(k);
-  const int solve_status = solve_many(h, sig.data(), k, 0, o, L, cplx, rhs.as<mor_c64>(), true, xs.as<mor_c64>(),
+  SolveLane* lane0 = nullptr;
+  MOR_TRY(mor_lane(h, 0, &lane0));
+  const int solve_status = solve_many(h, *lane0, sig.data(), k, 0, o, L, cplx, rhs.as<mor_c64>(), true, xs.as<mor_c64>(),
                                       ss.data());
   if (solve_status != MOR_OK && solve_status != MOR_ENOCONV && solve_status != MOR_EBREAKDOWN) return solve_status;
   for (int c = 0; c < k; ++c) {
@@ -1547,7 +1604,7 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
   MOR_CK(h, cudaMemsetAsync(x.p, 0, st_size(st) * (size_t)n * ld, h->stream));
   MOR_CK(h, cudaMemsetAsync(w.p, 0, st_size(st) * (size_t)n * ld, h->stream));
   Small sm;
-  MOR_TRY(get_small(h, sm));
+  MOR_TRY(get_small(h, h->ws_small, sm));
   MOR_CK(h, h->ws_part.alloc(sizeof(double) * 2 * 2 * MOR_LDMAX * part_blocks(h)));
   std::vector<int> ones(MOR_KMAX, 1);
   MOR_CK(h, cudaMemcpyAsync(sm.masks, ones.data(), sizeof(int) * MOR_KMAX, cudaMemcpyHostToDevice, h->stream));
