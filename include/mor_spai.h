@@ -90,7 +90,9 @@ enum mor_solver {
 
 /* sparse storage of the operator and of every preconditioner factor */
 enum mor_format {
-    MOR_FMT_AUTO = 0,  /* timed choice at mor_set_system (the autotuner) */
+    MOR_FMT_AUTO = 0,  /* timed choice at mor_set_system (the autotuner); the
+                          choice is kept for the process by pattern signature
+                          (device, n, nnz, kind of E, hash of the pattern) */
     MOR_FMT_CSR = 1,   /* compressed sparse row, one thread per row      */
     MOR_FMT_SELL = 2   /* SELL-C-sigma with C = 32, sigma = 1 (slices of 32 rows,
                           column-major inside a slice: coalesced loads)   */
