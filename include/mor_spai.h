@@ -127,6 +127,12 @@ typedef struct {
                             load; the preconditioner's precision does not limit
                             the solve's accuracy, and FP64 least squares are slow
                             on GPUs with a narrow FP64 pipe)                        */
+    int    fp64_fallback; /* MOR_MIXED: 1 (default) = a column whose mixed-precision
+                            solve fails before maxit (FP32 breakdown, an inner solve
+                            that stops improving, or a refinement step that cuts
+                            the FP64 residual by less than 10%) is
+                            solved again from zero with FP64 Krylov iterations and
+                            the same preconditioner; 0 = report the failure      */
 } mor_solve_opts;
 
 /* Per-column statistics of a solve. */
@@ -135,6 +141,9 @@ typedef struct {
     int    refinements;  /* FP64 outer steps taken                          */
     double relres;       /* final true relative residual, FP64              */
     int    status;       /* mor_status of this column                       */
+    int    fallback;     /* 1: solved again in FP64 after a failed mixed-
+                            precision solve (iters counts both solves,
+                            refinements the FP64 one)                      */
 } mor_solve_stats;
 
 #define MOR_MAX_R 64
@@ -163,6 +172,7 @@ typedef struct {
     double shift_change;   /* max_i |s_new - s_old| / |s_new|                  */
     double ms_precond, ms_solve, ms_orth, ms_reduce;  /* stage times (CUDA events) */
     int    status;
+    int    fallbacks;      /* columns solved again in FP64 (fp64_fallback)     */
 } mor_irka_stats;
 
 /* ------------------------------------------------------------------------ */

@@ -54,7 +54,7 @@ class mor_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("batch", C.c_int), ("use_graph", C.c_int),
                 ("graph_chunk", C.c_int), ("precond", C.c_int), ("max_chain", C.c_int), ("restart", C.c_int),
-                ("precond_precision", C.c_int)]
+                ("precond_precision", C.c_int), ("fp64_fallback", C.c_int)]
 
 
 MOR_MAX_R2 = 32
@@ -76,7 +76,8 @@ class mor_reduced2(C.Structure):
 
 
 class mor_solve_stats(C.Structure):
-    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("relres", C.c_double), ("status", C.c_int)]
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("relres", C.c_double), ("status", C.c_int),
+                ("fallback", C.c_int)]
 
 
 class mor_reduced(C.Structure):
@@ -98,7 +99,7 @@ class mor_irka_stats(C.Structure):
     _fields_ = [("z", C.c_int), ("nsolve", C.c_int), ("builds_spai", C.c_int), ("builds_reuse", C.c_int),
                 ("chain_len", C.c_int), ("iters_V", C.c_int), ("iters_W", C.c_int), ("max_relres", C.c_double),
                 ("shift_change", C.c_double), ("ms_precond", C.c_double), ("ms_solve", C.c_double),
-                ("ms_orth", C.c_double), ("ms_reduce", C.c_double), ("status", C.c_int)]
+                ("ms_orth", C.c_double), ("ms_reduce", C.c_double), ("status", C.c_int), ("fallbacks", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -403,7 +404,8 @@ def mor_solve_shifts(h, sigma, transpose: int = 0, opts: Optional[mor_solve_opts
     st = (mor_solve_stats * k)()
     code = lib.mor_solve_shifts(h, sp_, k, int(transpose), C.byref(o), Rp, Xp, st, MOR_DEVICE_PTRS if dev else 0)
     _check(h, code, allow)
-    stats = [{"iters": x.iters, "refinements": x.refinements, "relres": x.relres, "status": x.status} for x in st]
+    stats = [{"iters": x.iters, "refinements": x.refinements, "relres": x.relres, "status": x.status,
+              "fallback": x.fallback} for x in st]
     if dev:
         X = X.T
     return X, stats, code
@@ -592,6 +594,7 @@ def mor_batch_solve(h, sigma, transpose: int = 0, opts: Optional[mor_solve_opts]
     code = lib.mor_batch_solve(h, sp_, k, int(transpose), C.byref(o), X.ctypes.data_as(C.c_void_p), st, 0)
     _check(h, code, allow)
     stats = [[{"iters": st[i * k + c].iters, "refinements": st[i * k + c].refinements,
-               "relres": st[i * k + c].relres, "status": st[i * k + c].status} for c in range(k)]
+               "relres": st[i * k + c].relres, "status": st[i * k + c].status,
+               "fallback": st[i * k + c].fallback} for c in range(k)]
              for i in range(nsys)]
     return X, stats, code

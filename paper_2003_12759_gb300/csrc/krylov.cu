@@ -174,10 +174,11 @@ __global__ void __launch_bounds__(256) init_kernel(SegView sg, int ld, const S* 
   col_reduce_finalize<S, TPR, CPT>(v0, v1, ld, sg, seg, blockIdx.x, part, FIN_INIT, st, nullptr, done);
 }
 
-__global__ void set_targets_kernel(int count, KState* st, const double* target, const int* maxit) {
+__global__ void set_targets_kernel(int count, KState* st, const double* target, const int* maxit, int stag) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < count; c += gridDim.x * blockDim.x) {
     st[c].target2 = target[c] * target[c];
     st[c].maxit = maxit[c];
+    st[c].stag = stag;
   }
 }
 __global__ void set_done_kernel(const int* live, int* done) { *done = (*live == 0) ? 1 : 0; }
@@ -374,10 +375,10 @@ int krylov_launch_update_xr(int st, const SegView& sg, int ld, void* x, void* r,
 }
 
 int krylov_launch_init(int st, const SegView& sg, int ld, const void* rhs, void* x, void* r, void* rhat, void* p,
-                       void* v, void* part, void* state, const double* target, const int* maxit, int* done,
+                       void* v, void* part, void* state, const double* target, const int* maxit, int stag, int* done,
                        cudaStream_t s) {
   const int count = sg.nseg * ld;
-  set_targets_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, (KState*)state, target, maxit);
+  set_targets_kernel<<<(count + 255) / 256, 256, 0, s>>>(count, (KState*)state, target, maxit, stag);
   mor_count_launches(1);
   cudaError_t ce = cudaMemsetAsync(sg.live, 0, sizeof(int), s);
   if (ce != cudaSuccess) return (int)ce;
@@ -497,6 +498,7 @@ int krylov_read_states(void* host_states, const void* state_dev, int k, cudaStre
 int krylov_state_active(const void* host_state) { return ((const KState*)host_state)->active; }
 int krylov_state_iters(const void* host_state) { return ((const KState*)host_state)->iters; }
 int krylov_state_status(const void* host_state) { return ((const KState*)host_state)->status; }
+int krylov_status_stagnated(int status) { return status == KST_STAGNATED; }
 void krylov_state_make_dummy(void* host_state) {
   KState* k = (KState*)host_state;
   memset(k, 0, sizeof(KState));

@@ -25,12 +25,18 @@ enum {
   FIN_RHO = 4      // sums: (r_hat, r), ||r||^2         -> convergence, beta
 };
 
-enum { KST_OK = 0, KST_NOCONV = 4, KST_BREAKDOWN = 5 };
+enum { KST_OK = 0, KST_NOCONV = 4, KST_BREAKDOWN = 5, KST_STAGNATED = 6 };
 
+// stag > 0: a column whose best residual has not dropped by 0.1% for
+// max(stag, iterations it took to reach that best) iterations stops with
+// KST_STAGNATED (an FP32 inner solve that has reached its working accuracy;
+// the FP64 refinement restarts it from the true residual).  The window grows
+// with the solve, so that the long plateaus of BiCGSTAB on hard shifts (a few
+// hundred iterations after a few hundred of progress) do not stop it.
 struct KState {
   cdouble rho, rho_old, alpha, omega, beta;
-  double rnorm2, target2;
-  int active, iters, maxit, status;
+  double rnorm2, target2, best2;
+  int active, iters, maxit, status, best_it, stag;
 };
 
 // sums[c*2 + q] for column c, reduction q
@@ -45,6 +51,8 @@ __device__ inline int krylov_finalize(int stage, int k, const cdouble* sums, KSt
       S.omega = cdouble(1.0);
       S.beta = cdouble(0.0);
       S.rnorm2 = sums[2 * c + 1].re;
+      S.best2 = S.rnorm2;
+      S.best_it = 0;
       S.iters = 0;
       S.status = KST_OK;
       S.active = (S.rnorm2 > S.target2 && S.maxit > 0) ? 1 : 0;
@@ -64,8 +72,10 @@ __device__ inline int krylov_finalize(int stage, int k, const cdouble* sums, KSt
     } else if (stage == FIN_RHO) {
       S.iters += 1;
       S.rnorm2 = sums[2 * c + 1].re;
+      if (S.rnorm2 < 0.999 * S.best2) { S.best2 = S.rnorm2; S.best_it = S.iters; }
       if (S.rnorm2 <= S.target2) { S.active = 0; S.status = KST_OK; }
       else if (S.iters >= S.maxit) { S.active = 0; S.status = KST_NOCONV; }
+      else if (S.stag > 0 && S.iters - S.best_it >= max(S.stag, S.best_it)) { S.active = 0; S.status = KST_STAGNATED; }
       else if (!(S.rnorm2 == S.rnorm2)) { S.active = 0; S.status = KST_BREAKDOWN; }   // NaN
       else {
         S.rho_old = S.rho;

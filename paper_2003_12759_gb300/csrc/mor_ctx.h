@@ -74,6 +74,7 @@ struct SolveLane {
   bool own_stream = false;
   DBuf ws_vec, ws_x64, ws_r64, ws_b64, ws_part, ws_small, ws_kstate, ws_segarr, ws_sums, ws_io;
   DBuf ws_gm_vec, ws_gm_small, ws_gm_part;
+  DBuf ws_fb;                        // FP64 re-solve of failed mixed columns: maps, b, x
   DBuf seg_counters, seg_live;
   int seg_alloc = 0;                 // segments the counters were zeroed for
   void* pinned = nullptr;

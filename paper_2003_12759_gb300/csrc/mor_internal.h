@@ -157,9 +157,12 @@ int krylov_launch_update_s(int st, const SegView& sg, int ld, const void* r, con
 int krylov_launch_update_xr(int st, const SegView& sg, int ld, void* x, void* r, const void* phat,
                             const void* shat, const void* sv, const void* t, const void* rhat,
                             void* part, void* state, int* done, cudaStream_t s);
+// stag: iterations without a 0.1% drop of the best residual after which a
+// column stops as stagnated (0: never)
 int krylov_launch_init(int st, const SegView& sg, int ld, const void* rhs, void* x, void* r, void* rhat,
                        void* p, void* v, void* part, void* state, const double* target, const int* maxit,
-                       int* done, cudaStream_t s);
+                       int stag, int* done, cudaStream_t s);
+int krylov_status_stagnated(int status);
 size_t krylov_state_bytes(int st);
 int krylov_read_state(int st, const void* state_dev, int k, int* iters, int* status,
                       cudaStream_t s);

@@ -163,6 +163,21 @@ struct BatchIO {
   void* x64;            // row-major n x k, st64 (out)
 };
 
+// minimum stagnation window of a mixed-precision inner BiCGSTAB solve (iterations
+// without a 0.1% drop of its best residual; 0 = no stagnation test)
+#ifndef MOR_MIXED_STAG
+#define MOR_MIXED_STAG 200
+#endif
+// refinement passes in a row, each cutting the FP64 residual by less than 10%, after
+// which a mixed-precision column is given up (and solved again in FP64).  Measured on
+// GB300: one pass (with the 200-iteration window) gives the shortest times on the
+// uneven batch, on near-resonant second-order shifts and on mixed AIRGA iterations --
+// a column that needs longer FP32 solves than the rest of its batch finishes sooner
+// in FP64 than by more refinement passes.
+#ifndef MOR_MIXED_POOR
+#define MOR_MIXED_POOR 1
+#endif
+
 static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_opts& o, bool cplx, const BatchIO& io,
                        mor_solve_stats* stats) {
   OpData& op = h->op(transpose);
@@ -317,8 +332,8 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
 
   const int max_outer = (prec == MOR_FP64) ? 4 : std::max(1, o.max_refine);
   const size_t NK = (size_t)nseg * k;                  // (segment, real column) pairs
-  std::vector<double> bnorm(NK, 0.0), relres(NK, 0.0), rn2(NK, 0.0);
-  std::vector<int> iters(NK, 0), refs(NK, 0), status(NK, MOR_OK), act(NK, 0);
+  std::vector<double> bnorm(NK, 0.0), relres(NK, 0.0), rn2(NK, 0.0), prevrel(NK, 0.0);
+  std::vector<int> iters(NK, 0), refs(NK, 0), status(NK, MOR_OK), act(NK, 0), poor(NK, 0);
   double* hp = (double*)ln.pinned;
   cdouble* h_sums = (cdouble*)hp;                                  // 2 ld per segment
   double* tg = hp + 4 * nsc;
@@ -458,6 +473,14 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
         rn2[q] = h_sums[(size_t)sgi * 2 * ld + 2 * c].re;
         if (pass == 0) bnorm[q] = std::sqrt(rn2[q]);
         relres[q] = bnorm[q] > 0 ? std::sqrt(rn2[q]) / bnorm[q] : 0.0;
+        // mixed precision: MOR_MIXED_POOR refinement passes in a row that each cut the FP64
+        // residual by less than 10% (FP32 inner solves that break down or stagnate) end the
+        // column
+        if (prec == MOR_MIXED && pass > 0 && refs[q] > 0 && status[q] == MOR_OK && relres[q] > o.tol) {
+          poor[q] = (relres[q] > 0.9 * prevrel[q]) ? poor[q] + 1 : 0;
+          if (poor[q] >= MOR_MIXED_POOR) status[q] = MOR_ENOCONV;
+        }
+        prevrel[q] = relres[q];
         act[q] = (bnorm[q] > 0 && relres[q] > o.tol && status[q] == MOR_OK && iters[q] < o.maxit &&
                   std::isfinite(relres[q])) ? 1 : 0;
         nact += act[q];
@@ -499,8 +522,10 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
     if (o.solver == MOR_GMRES) {
       MOR_TRY(gmres_inner(dd, kit, kstat));
     } else {
+      // mixed precision: an FP32 inner solve that stops improving hands back to the refinement
+      const int stag = (prec == MOR_MIXED) ? MOR_MIXED_STAG : 0;
       MOR_CKI(h, krylov_launch_init(st_in, sg, ld, rhs, dd, rr, rh, pp, vv, ln.ws_part.p, kstate, d_target, d_maxit,
-                                    sm.done, ln.stream));
+                                    stag, sm.done, ln.stream));
       MOR_TRY(capture());
       int maxrem = 0;
       for (size_t z = 0; z < nsc; ++z) maxrem = std::max(maxrem, mi[z]);
@@ -613,6 +638,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
       stats[q].refinements = refs[q];
       stats[q].relres = relres[q];
       stats[q].status = status[q];
+      stats[q].fallback = 0;
     }
   int worst = MOR_OK;
   for (size_t q = 0; q < NK; ++q)
@@ -656,6 +682,56 @@ static int solve_many(mor_t h, SolveLane& ln, const mor_c64* sig, int k, int tra
     const int nseg = h->seg.nseg;
     std::vector<mor_solve_stats> sb((size_t)nseg * kc);
     int s = solve_batch(h, ln, transpose, o, cplx, io, sb.data());
+    if ((s == MOR_ENOCONV || s == MOR_EBREAKDOWN) && o.precision == MOR_MIXED && o.fp64_fallback) {
+      // columns that failed in mixed precision before maxit: solve them again from zero with
+      // FP64 Krylov iterations (same chain prefix), then put them back in place
+      std::vector<int> redo;
+      for (int c = 0; c < kc; ++c) {
+        bool bad = false;
+        for (int sgi = 0; sgi < nseg; ++sgi) {
+          const mor_solve_stats& x = sb[(size_t)sgi * kc + c];
+          if (x.status != MOR_OK && x.iters < o.maxit) bad = true;
+        }
+        if (bad) redo.push_back(c);
+      }
+      if (!redo.empty()) {
+        const int nr = (int)redo.size();
+        mor_solve_opts o64 = o;
+        o64.precision = MOR_FP64;
+        const int ld2 = row_stride(st_of(MOR_FP64, cplx), nr);
+        const size_t vb = es64 * (size_t)n * ld2;
+        MOR_CK(h, ln.ws_fb.alloc(256 + 2 * vb));
+        int* dmap = ln.ws_fb.as<int>();                   // [redo columns | 0 .. nr-1]
+        void* b2 = ln.ws_fb.as<char>() + 256;
+        void* x2 = (char*)b2 + vb;
+        std::vector<int> hmap(2 * nr);
+        for (int i = 0; i < nr; ++i) { hmap[i] = redo[i]; hmap[nr + i] = i; }
+        MOR_CK(h, cudaMemcpyAsync(dmap, hmap.data(), sizeof(int) * 2 * nr, cudaMemcpyHostToDevice, ln.stream));
+        MOR_CK(h, cudaStreamSynchronize(ln.stream));
+        MOR_CKI(h, conv_launch_gather_cols(st64, n, ld, ld2, nr, dmap, ln.ws_b64.p, b2, ln.stream));
+        std::vector<mor_c64> s2(nr);
+        std::vector<int> L2(nr);
+        for (int i = 0; i < nr; ++i) { s2[i] = sig[c0 + redo[i]]; L2[i] = L[c0 + redo[i]]; }
+        BatchIO io2{s2.data(), nr, ld2, L2.data(), b2, x2};
+        std::vector<mor_solve_stats> sb2((size_t)nseg * nr);
+        const int s2r = solve_batch(h, ln, transpose, o64, cplx, io2, sb2.data());
+        if (s2r != MOR_OK && s2r != MOR_ENOCONV && s2r != MOR_EBREAKDOWN) return s2r;
+        MOR_CKI(h, conv_launch_scatter_cols(st64, n, ld2, ld, nr, dmap + nr, dmap, x2, xrow, ln.stream));
+        s = MOR_OK;
+        for (int sgi = 0; sgi < nseg; ++sgi)
+          for (int i = 0; i < nr; ++i) {
+            mor_solve_stats& a = sb[(size_t)sgi * kc + redo[i]];
+            const mor_solve_stats& b = sb2[(size_t)sgi * nr + i];
+            a.iters += b.iters;
+            a.refinements = b.refinements;
+            a.relres = b.relres;
+            a.status = b.status;
+            a.fallback = 1;
+          }
+        for (const mor_solve_stats& a : sb)
+          if (a.status != MOR_OK) s = (s == MOR_OK || a.status == MOR_EBREAKDOWN) ? a.status : s;
+      }
+    }
     if (stats)   // stats has nseg x k entries: [seg * k + c]
       for (int sgi = 0; sgi < nseg; ++sgi)
         for (int c = 0; c < kc; ++c) stats[(size_t)sgi * k + c0 + c] = sb[(size_t)sgi * kc + c];
@@ -1005,6 +1081,7 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
       a.iters = std::max(a.iters, b.iters);
       a.refinements = std::max(a.refinements, b.refinements);
       a.relres = std::max(a.relres, b.relres);
+      a.fallback = std::max(a.fallback, b.fallback);
       if (b.status != MOR_OK) a.status = b.status;
     }
     stats[c] = a;
@@ -1278,6 +1355,7 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
     for (int i = 0; i < l; ++i) {
       (t == 0 ? st.iters_V : st.iters_W) += ss[t][i].iters;
       st.max_relres = std::max(st.max_relres, ss[t][i].relres);
+      st.fallbacks += ss[t][i].fallback;
     }
   }
   cudaEventRecord(ev[2], h->stream);
@@ -1472,6 +1550,7 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
   for (int c = 0; c < k; ++c) {
     st.iters_V += ss[c].iters;
     st.max_relres = std::max(st.max_relres, ss[c].relres);
+    st.fallbacks += ss[c].fallback;
   }
   // a solve that broke down (non-finite residual) leaves no basis to project on: report it as such
   if (!std::isfinite(st.max_relres)) return mor_fail(h, MOR_EBREAKDOWN, "a block solve broke down");

@@ -82,3 +82,26 @@ def test_batch_unpreconditioned_and_single_system_equivalence(h):
     assert cb == cs == mor.MOR_OK
     assert [x["iters"] for x in sb[0]] == [x["iters"] for x in ss]
     np.testing.assert_allclose(Xb, Xs, rtol=1e-12, atol=1e-14 * np.abs(Xs).max())
+
+
+def test_batch_failed_mixed_columns_fall_back_to_fp64(h):
+    """In a batch of systems a column (shift) that fails in mixed precision in
+    any system is solved again in FP64 for every system; all reach 1e-8."""
+    sysl = _batch()
+    mor.mor_set_batch(h, [w.A for w in sysl], [w.B[:, 0] for w in sysl], [w.C[:, 0] for w in sysl])
+    nsys, off = mor.mor_batch_info(h)
+    shifts = [1.0, 10.0, 100.0]
+    mor.mor_build_precond(h, shifts[0], 0, mor.MOR_MIXED)
+    for s in shifts[1:]:
+        mor.mor_update_precond(h, s, 0)
+    weak = dict(max_refine=1, inner_tol=1e-3)
+    _, st0, code0 = mor.mor_batch_solve(h, shifts, 0, mor.mor_default_opts(fp64_fallback=0, **weak))
+    assert code0 == mor.MOR_ENOCONV
+    X, st1, code1 = mor.mor_batch_solve(h, shifts, 0, mor.mor_default_opts(**weak))
+    assert code1 == mor.MOR_OK
+    for i, w in enumerate(sysl):
+        b = w.B[:, 0]
+        for c, s in enumerate(shifts):
+            assert st1[i][c]["fallback"] == 1 and st1[i][c]["status"] == mor.MOR_OK
+            rel = np.linalg.norm(b - oop.A_sigma(w.A, w.E, s) @ X[off[i]:off[i + 1], c]) / np.linalg.norm(b)
+            assert rel <= 1.001e-8, (i, c, rel)

@@ -262,3 +262,38 @@ def test_irka_step_with_fp32_factors_under_fp64(h):
     H2 = mor.mor_eval_tf(h, rom2, w)
     H = oop.transfer_function(wl.A, wl.E, wl.B, wl.C, 1j * w)
     assert np.max(np.abs(H1 - H2) / np.abs(H)) <= 1e-6
+
+
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_failed_mixed_columns_fall_back_to_fp64(h, transpose):
+    """A mixed solve allowed one refinement step of 1e-3 cannot reach 1e-8:
+    with fp64_fallback = 0 it reports MOR_ENOCONV per column; with the default
+    the failed columns are solved again from zero in FP64 and reach 1e-8.  A
+    zero right-hand side converges at once and is not solved again."""
+    wl = CASES["convdiff3d_n3375"]()
+    _set(h, wl)
+    shifts = [30.0, 45.0 + 20.0j, 90.0 + 5.0j, 200.0]
+    mor.mor_build_precond(h, shifts[0], transpose, mor.MOR_MIXED)
+    for s in shifts[1:]:
+        mor.mor_update_precond(h, s, transpose)
+    rng = np.random.default_rng(11)
+    R = rng.standard_normal((wl.n, 4)) + 1j * rng.standard_normal((wl.n, 4))
+    R[:, 2] = 0.0
+    weak = dict(max_refine=1, inner_tol=1e-3)
+    X0, st0, code0 = mor.mor_solve_shifts(h, shifts, transpose, mor.mor_default_opts(fp64_fallback=0, **weak), R=R)
+    assert code0 == mor.MOR_ENOCONV
+    X1, st1, code1 = mor.mor_solve_shifts(h, shifts, transpose, mor.mor_default_opts(**weak), R=R)
+    assert code1 == mor.MOR_OK
+    for c, s in enumerate(shifts):
+        assert st0[c]["fallback"] == 0
+        if c == 2:
+            assert st0[c]["status"] == st1[c]["status"] == mor.MOR_OK and st1[c]["fallback"] == 0
+            assert not np.any(X1[:, c])
+            continue
+        assert st0[c]["status"] == mor.MOR_ENOCONV and st0[c]["refinements"] == 1
+        assert st1[c]["fallback"] == 1 and st1[c]["status"] == mor.MOR_OK
+        assert st1[c]["iters"] > st0[c]["iters"]
+        M = oop.A_sigma(wl.A, wl.E, s, transpose=bool(transpose))
+        rel = np.linalg.norm(R[:, c] - M @ X1[:, c]) / np.linalg.norm(R[:, c])
+        assert rel <= 1.001e-8, (c, rel)
+        assert abs(st1[c]["relres"] - rel) <= 1e-3 * rel + 1e-15
