@@ -125,11 +125,21 @@ def _oracle_sample(q, grid, iters_per_solve, ncols, nits):
            "nits": nits})
 
 
+def spmv_source_sha():
+    """First 16 hex digits of the SHA-256 over the sources the SpMV kernels are
+    compiled from (spmv.cu and the headers it includes), in a fixed order."""
+    d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2003_12759_gb300", "csrc")
+    hs = hashlib.sha256()
+    for f in ("spmv.cu", "krylov_state.cuh", "mor_internal.h", "shape_dispatch.cuh", "mor_types.cuh"):
+        hs.update(open(os.path.join(d, f), "rb").read())
+    return hs.hexdigest()[:16]
+
+
 def profiled_traffic(kernel, k, fmt, grid):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
     `kernel` from its committed ncu summary under profiles/, when that capture
     was taken on this launch shape (grid, k columns, storage format) and the
-    SpMV source has not changed since; None otherwise."""
+    SpMV sources have not changed since; None otherwise."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
                         "%s_%s_convdiff3d_n1M_k%d.md" % (kernel, fmt, k))
     if grid != 100 or not os.path.exists(path):
@@ -139,8 +149,7 @@ def profiled_traffic(kernel, k, fmt, grid):
         if ":" in line and not line.startswith(("|", "#", " ")):
             key, _, val = line.partition(":")
             fields[key.strip()] = val.strip()
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2003_12759_gb300", "csrc", "spmv.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = spmv_source_sha()
     if fields.get("spmv_source_sha256_16") != sha or "traffic_bytes_per_launch" not in fields:
         return None
     return int(fields["traffic_bytes_per_launch"])
@@ -213,7 +222,8 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False)
     one = args.one_shift if one_shift is None else one_shift
     opts = mor.mor_default_opts(precision=mor.MOR_FP64 if prec_name == "fp64" else mor.MOR_MIXED,
                                 batch=0 if one else 1, use_graph=0 if (one or args.no_graph) else 1,
-                                max_chain=args.max_chain, graph_chunk=args.graph_chunk)
+                                max_chain=args.max_chain, graph_chunk=args.graph_chunk,
+                                concurrent_sweeps=0 if args.serial_sweeps else 1)
     omega = np.logspace(0, 5, 1000)
     shifts = wl.shifts.copy()
 
@@ -499,6 +509,9 @@ def main():
     ap.add_argument("--fmt", default="auto", choices=["auto", "csr", "sell"])
     ap.add_argument("--graph-chunk", type=int, default=16, help="Krylov iterations per CUDA-graph replay")
     ap.add_argument("--no-graph", action="store_true", help="launch the Krylov iterations one by one")
+    ap.add_argument("--serial-sweeps", action="store_true",
+                    help="run an IRKA step's V and W sweeps one after the other from one host thread "
+                         "(the same kernels; for profilers that follow one thread)")
     ap.add_argument("--grid-mimo", type=int, default=200, help="grid points per axis of the MIMO workload")
     ap.add_argument("--workload", default="convdiff", choices=["convdiff", "batch", "mimo", "second"],
                     help="convdiff: IRKA sweeps on the 3D convection-diffusion system (default); "
@@ -513,6 +526,7 @@ def main():
            "grid": args.grid, "shifts": "5 conjugate pairs a_k(1 +- 0.5i), a_k = logspace(1,4,5)",
            "precision": "fp32/c64 Krylov in fp64 refinement" if args.precision == "mixed" else "fp64",
            "batch": "one shift per launch" if args.one_shift else "all shifts lock-step, CUDA graph",
+           "sweeps": "V then W, one host thread" if args.serial_sweeps else "V and W concurrent on two streams",
            "max_chain": args.max_chain or "unlimited",
            "tol": 1e-8, "l2": "inputs larger than L2 (matrix + 12 Krylov vectors of n x 5 complex64 ~ 0.5 GB)"}
     if args.impl == "reference":

@@ -133,6 +133,11 @@ typedef struct {
                             the FP64 residual by less than 10%) is
                             solved again from zero with FP64 Krylov iterations and
                             the same preconditioner; 0 = report the failure      */
+    int    concurrent_sweeps; /* mor_irka_step(_tangential): 1 (default) = the
+                            primal (V) and transposed (W) sweeps run at the same
+                            time on two streams, W from a second host thread;
+                            0 = one after the other from the calling thread
+                            (same kernels; for tools that follow one host thread) */
 } mor_solve_opts;
 
 /* Per-column statistics of a solve. */

@@ -54,7 +54,7 @@ class mor_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("batch", C.c_int), ("use_graph", C.c_int),
                 ("graph_chunk", C.c_int), ("precond", C.c_int), ("max_chain", C.c_int), ("restart", C.c_int),
-                ("precond_precision", C.c_int), ("fp64_fallback", C.c_int)]
+                ("precond_precision", C.c_int), ("fp64_fallback", C.c_int), ("concurrent_sweeps", C.c_int)]
 
 
 MOR_MAX_R2 = 32

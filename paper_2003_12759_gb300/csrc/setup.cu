@@ -547,6 +547,7 @@ void mor_default_opts(mor_solve_opts* o) {
   o->restart = 50;
   o->precond_precision = -1;
   o->fp64_fallback = 1;
+  o->concurrent_sweeps = 1;
   o->tol = 1e-8;
   o->maxit = 20000;
   o->inner_tol = 1e-4;

@@ -1337,9 +1337,14 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
       s2v[t] = solve_many(h, *lane[t], sol.data(), l, t, o, Ls[t], cplx, tang ? rhs[t].as<mor_c64>() : nullptr, true,
                           xs[t].as<mor_c64>(), ss[t].data());
     };
-    std::thread tw(sweep, 1);
-    sweep(0);
-    tw.join();
+    if (o.concurrent_sweeps) {
+      std::thread tw(sweep, 1);
+      sweep(0);
+      tw.join();
+    } else {
+      sweep(0);
+      sweep(1);
+    }
     // solve_many leaves its stream synchronised; order lane 1 before the handle's later work
     cudaEvent_t wdone;
     MOR_CK(h, cudaEventCreateWithFlags(&wdone, cudaEventDisableTiming));
