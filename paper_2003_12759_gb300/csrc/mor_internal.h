@@ -144,10 +144,13 @@ int gmres_launch_solve_y(int ld, int m, void* state, const void* H, void* ycoef,
 // Launchers (spmv.cu).  x, y, w, b: n x ld row-major blocks of type st.
 int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
                    const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s);
-// fst: scalar type of the factor values (FP32 factors may serve FP64 vectors)
+// fst: scalar type of the factor values (FP32 factors may serve FP64 vectors).
+// kstate (nullable): the per-(segment, column) Krylov states of the solve the
+// factor is applied in; lanes whose columns have all stopped skip their rows
+// (their rows of y are left as they were).
 int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals,
                        const int* apply, int ld, const void* x, void* y, const int* done,
-                       cudaStream_t s);
+                       const void* kstate, cudaStream_t s);
 
 // Krylov helpers (krylov.cu)
 int krylov_launch_update_p(int st, const SegView& sg, int ld, const void* r, void* p, const void* v,

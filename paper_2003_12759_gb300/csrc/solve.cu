@@ -275,20 +275,21 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
       }
     return (int)cudaMemcpyAsync(sm.masks, mk.data(), sizeof(int) * mk.size(), cudaMemcpyHostToDevice, ln.stream);
   };
-  auto chain_apply_d = [&](void* src, void* dst, const int* dn) -> int {
+  auto chain_apply_d = [&](void* src, void* dst, const int* dn, const void* ks = nullptr) -> int {
     if (Lmax == 0) return 0;
     void* s = src;
     for (int f = 0; f < Lcur; ++f) {
       void* dd2 = (f == Lcur - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
       const Factor& F = op.chain[f];
       int e = launch_factor_spmv(st_in, F.st, sg, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
-                                 dd2, dn, ln.stream);
+                                 dd2, dn, ks, ln.stream);
       if (e) return e;
       s = dd2;
     }
     return 0;
   };
-  auto chain_apply = [&](void* src, void* dst) -> int { return chain_apply_d(src, dst, sm.done); };
+  // BiCGSTAB: stopped columns (and finished systems of a batch) skip the chain
+  auto chain_apply = [&](void* src, void* dst) -> int { return chain_apply_d(src, dst, sm.done, kstate); };
   auto one_iter = [&]() -> int {
     int e;
     void* phat = (Lmax == 0) ? pp : pph;
@@ -1009,7 +1010,7 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   char* d = b;
   for (int f = 0; f < Lmax; ++f) {
     MOR_CKI(h, launch_factor_spmv(st, op.chain[f].st, h->seg, op.view(), op.chain[f].vals->p,
-                                  sm.masks + (size_t)f * MOR_KMAX, ld, s, d, nullptr, h->stream));
+                                  sm.masks + (size_t)f * MOR_KMAX, ld, s, d, nullptr, nullptr, h->stream));
     std::swap(s, d);
   }
   if (dev) {
@@ -1701,7 +1702,7 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
   auto launch = [&]() -> int {
     if (which == 0) return launch_op_spmv(st, h->seg, pv, ov, cf, ld, x.p, y.p, nullptr, &ra, h->stream);
     return launch_factor_spmv(st, op.chain.back().st, h->seg, pv, op.chain.back().vals->p, sm.masks, ld,
-                              x.p, y.p, nullptr, h->stream);
+                              x.p, y.p, nullptr, nullptr, h->stream);
   };
   for (int i = 0; i < 3; ++i) MOR_CKI(h, launch());
   cudaEvent_t e0, e1;

@@ -83,12 +83,22 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
   const S* __restrict__ w = (const S*)red.w;
   const int sub = threadIdx.x % TPR;
   const int c0 = sub * CPT;
-  const bool act = c0 < ld;
+  const int seg = seg_of_chunk(sg, blockIdx.x);
+  // inside a Krylov iteration, a lane whose columns of this segment have all stopped
+  // (converged, or every column of a finished system of a batch) has no work: its
+  // rows of y are read only by stopped columns, and its reduction terms stay zero
+  bool act = c0 < ld;
+  if (act && red.state && red.fin >= FIN_ALPHA) {
+    const KState* ks = (const KState*)red.state + (size_t)seg * ld + c0;
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) any |= (ks[j].active != 0);
+    act = any;
+  }
   S v0[CPT], v1[CPT];
 #pragma unroll
   for (int j = 0; j < CPT; ++j) { v0[j] = zero_<S>(); v1[j] = zero_<S>(); }
   const int rpb = blockDim.x / TPR;
-  const int seg = seg_of_chunk(sg, blockIdx.x);
   int64_t rb64, re64;
   chunk_rows(sg, seg, blockIdx.x, rb64, re64);
   const int re = (int)re64;
@@ -183,6 +193,8 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
 }
 
 // Y(:, c) = F X(:, c) where the factor applies to column c, else Y(:, c) = X(:, c).
+// With Krylov states (kst), lanes whose columns of the block's segment have all
+// stopped leave their rows of Y as they were.
 // Kept lean (32-bit row indices, a column bit mask, the copy-through value
 // loaded only at the end) so that the register bound of min_blocks holds
 // without spills.
@@ -190,7 +202,7 @@ template <typename S, typename V, int TPR, int CPT>
 __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(SegView sg, PatView pv, const V* __restrict__ f,
                                                           const int* __restrict__ apply, int ld,
                                                           const S* __restrict__ x, S* __restrict__ y,
-                                                          const int* done) {
+                                                          const int* done, const KState* __restrict__ kst) {
   if (done && *done) return;
   typedef typename real_of<S>::type RS;
   typedef typename std::conditional<is_cplx<V>::value, cplx<RS>, RS>::type W;
@@ -200,9 +212,20 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
   unsigned mask = 0;
 #pragma unroll
   for (int j = 0; j < CPT; ++j) mask |= (apply[c0 + j] != 0 ? 1u : 0u) << j;
-  const int rpb = blockDim.x / TPR;
   int64_t rb64, re64;
-  chunk_rows(sg, seg_of_chunk(sg, blockIdx.x), blockIdx.x, rb64, re64);
+  {
+    const int seg = seg_of_chunk(sg, blockIdx.x);
+    if (kst) {
+      // inside a Krylov iteration: lanes whose columns of this segment have all stopped skip
+      const KState* ks = kst + (size_t)seg * ld + c0;
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) any |= (ks[j].active != 0);
+      if (!any) return;
+    }
+    chunk_rows(sg, seg, blockIdx.x, rb64, re64);
+  }
+  const int rpb = blockDim.x / TPR;
   const int re = (int)re64;
   const bool sell = pv.fmt == FMT_SELL;
   for (int r = (int)rb64 + (int)threadIdx.x / TPR; r < re; r += rpb) {
@@ -309,7 +332,7 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
 }
 
 int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
-                       int ld, const void* x, void* y, const int* done, cudaStream_t s) {
+                       int ld, const void* x, void* y, const int* done, const void* kstate, cudaStream_t s) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
   const bool fc = st_is_cplx(fst), f32 = st_is_f32(fst);
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
@@ -317,7 +340,7 @@ int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, co
     auto go = [&]<typename V>() {
       const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, V, TPR, CPT>, TPR);
       factor_spmv_kernel<S, V, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const V*)fvals, apply, ld, (const S*)x,
-                                                                   (S*)y, done);
+                                                                   (S*)y, done, (const KState*)kstate);
     };
     if (sizeof(R) == 4 && !f32) return (int)cudaErrorInvalidValue;     // FP64 factors under FP32 vectors
     if constexpr (is_cplx<S>::value) {
