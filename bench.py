@@ -106,7 +106,7 @@ def _oracle_sample(q, grid, iters_per_solve, ncols, nits):
     import numpy as np  # noqa
     import workloads as W
     from oracle import operator as oop, spai as ospai, krylov as okry
-    wl = W.config1(N=grid)
+    wl = W.convdiff3d_siso(N=grid)
     s1 = wl.shifts[0]
     M = oop.A_sigma(wl.A, wl.E, s1)
     S = ospai.spai_pattern(wl.A, wl.E)
@@ -212,7 +212,7 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False)
 
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    wl = W.config1(N=args.grid)
+    wl = W.convdiff3d_siso(N=args.grid)
     n = wl.n
     h = mor.mor_create(local, stream)
     fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
@@ -331,7 +331,7 @@ def run_batch(args, ws, rank, local):
     import workloads as W
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    sysl = W.config2(num_systems=args.nsys)
+    sysl = W.uneven_laplace2d_batch(num_systems=args.nsys)
     h = mor.mor_create(local, stream)
     fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
     mor.mor_set_batch(h, [w.A for w in sysl], [w.B[:, 0] for w in sysl], [w.C[:, 0] for w in sysl], fmt=fmt)
@@ -407,7 +407,7 @@ def run_mimo(args, ws, rank, local):
     import workloads as W
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    wl = W.config4(N=args.grid_mimo, m=8)
+    wl = W.convdiff3d_mimo(N=args.grid_mimo, m=8)
     h = mor.mor_create(local, stream)
     fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
     mor.mor_set_system(h, wl.A, wl.B, wl.C, fmt=fmt)
@@ -453,7 +453,7 @@ def run_second(args, ws, rank, local):
     import workloads as W
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    wl = W.config3()
+    wl = W.stencil27_second_order()
     h = mor.mor_create(local, stream)
     mor.mor_set_system_2nd(h, wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C)
     pts = [np.array([0.2 + 0.1j, 0.2 - 0.1j, 1.0])]
@@ -476,7 +476,7 @@ def kernels_only(args):
     """Short run for profilers: the hot-loop kernels on the full-size workload."""
     import paper_2003_12759_gb300 as mor
     import workloads as W
-    wl = W.config1(N=args.grid)
+    wl = W.convdiff3d_siso(N=args.grid)
     h = mor.mor_create(0)
     fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
     mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E, fmt=fmt)
@@ -609,7 +609,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1000 * r["t"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 inner / c128 refinement" if args.precision == "mixed" else "c128",
-            "data": "synthetic (seeded stencil system, BASELINE config shape)", "config": cfg,
+            "data": "synthetic (seeded 3D convection-diffusion stencil system)", "config": cfg,
             "clocks": r["clocks"], "gpu_launches": int(r["launches"]), "roofline": r["roofline"],
             "kernels": r["kernels"],
             "irka": {"iters_per_solve": float(iters_per_solve),

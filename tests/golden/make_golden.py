@@ -3,9 +3,9 @@
 Everything here is computed by the CPU oracle (oracle/) from the seeded
 workloads (workloads/); nothing comes from the CUDA library.
 
-    python tests/golden/make_golden.py            # writes irka_cfg0.json
+    python tests/golden/make_golden.py            # writes irka_laplace2d_n10000.json
 
-irka_cfg0.json: the 2D-Laplacian IRKA workload (n = 10,000, E = I, SISO,
+irka_laplace2d_n10000.json: the 2D-Laplacian IRKA workload (n = 10,000, E = I, SISO,
 r = 6, initial shifts logspace(1, 4, 6)), 20 IRKA iterations with the reuse
 schedule of Algorithm 4, right-preconditioned BiCGSTAB to 1e-8: the shift
 history, BiCGSTAB iteration counts per solve, the final reduced system, and
@@ -35,7 +35,7 @@ def c2l(z):
 
 def main():
     t0 = time.time()
-    wl = W.config0()
+    wl = W.laplace2d_siso()
     res = irka.irka(wl.A, wl.E, wl.B, wl.C, wl.shifts, iters=wl.irka_iters, mode="reuse", solver="bicgstab",
                     tol=1e-8)
     s = 1j * OMEGA
@@ -53,7 +53,7 @@ def main():
         "H": c2l(H),
         "oracle_seconds": time.time() - t0,
     }
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "irka_cfg0.json")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "irka_laplace2d_n10000.json")
     with open(path, "w") as f:
         json.dump(out, f)
     print("wrote", path, "in %.1f s" % (time.time() - t0))

@@ -48,7 +48,7 @@ def _H(wl, s):
 @pytest.mark.parametrize("dims", [(9, 8, 7, 3), (6, 7, 5, 4)])
 def test_airga_matches_oracle(h, precision, dims):
     nx, ny, nz, m = dims
-    wl = W.config3(nx=nx, ny=ny, nz=nz, m=m)
+    wl = W.stencil27_second_order(nx=nx, ny=ny, nz=nz, m=m)
     iters = 3
     a, sa = airga.airga(wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C, POINTS, iters=iters, tol=1e-8)
     b, sb = airga.airga(wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C, POINTS, iters=iters, tol=1e-10)
@@ -81,7 +81,7 @@ def test_airga_matches_oracle(h, precision, dims):
 
 
 def test_eval_tf2_matches_dense_evaluation(h):
-    wl = W.config3(nx=6, ny=5, nz=4, m=2)
+    wl = W.stencil27_second_order(nx=6, ny=5, nz=4, m=2)
     _set(h, wl)
     p, rom, _ = mor.mor_airga_step(h, POINTS, mor.mor_default_opts(precision=mor.MOR_FP64))
     w = np.logspace(-2, 1, 300)
@@ -91,13 +91,13 @@ def test_eval_tf2_matches_dense_evaluation(h):
 
 
 def test_airga_argument_errors(h):
-    wl = W.config3(nx=5, ny=4, nz=4, m=4)
+    wl = W.stencil27_second_order(nx=5, ny=4, nz=4, m=4)
     _set(h, wl)
     with pytest.raises(RuntimeError):                 # r = 4 * 9 > 32
         mor.mor_airga_step(h, np.linspace(0.1, 1.0, 9), mor.mor_default_opts())
     with pytest.raises(RuntimeError):                 # not closed under conjugation
         mor.mor_airga_step(h, np.array([0.2 + 0.1j, 1.0]), mor.mor_default_opts())
-    first = W.config1(N=5)
+    first = W.convdiff3d_siso(N=5)
     mor.mor_set_system(h, first.A, first.B, first.C, E_diag=first.E)
     with pytest.raises(RuntimeError):
         mor.mor_airga_step(h, POINTS, mor.mor_default_opts())

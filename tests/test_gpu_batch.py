@@ -30,7 +30,7 @@ def h():
 
 def _batch(nsys=6, seed=7):
     # the uneven-batch generator at small sizes (n_s in [300, 2500])
-    return W.config2(num_systems=nsys, n_lo=300, n_hi=2500, seed=seed)
+    return W.uneven_laplace2d_batch(num_systems=nsys, n_lo=300, n_hi=2500, seed=seed)
 
 
 @pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])

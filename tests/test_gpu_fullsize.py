@@ -36,8 +36,8 @@ def h():
 
 
 @pytest.fixture(scope="module")
-def cfg1(h):
-    wl = W.config1()
+def convdiff(h):
+    wl = W.convdiff3d_siso()
     mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E)
     return wl
 
@@ -48,8 +48,8 @@ def _sample_rows(n, rng, count=2000):
 
 
 @pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
-def test_operator_rows_full_size(h, cfg1, precision):
-    wl = cfg1
+def test_operator_rows_full_size(h, convdiff, precision):
+    wl = convdiff
     rng = np.random.default_rng(11)
     sig = np.array([30.0, 45.0 + 20.0j, 90.0 + 5.0j, 200.0, 400.0 + 400.0j, 1e3 + 500j, 1e4])
     X = rng.standard_normal((wl.n, 7)) + 1j * rng.standard_normal((wl.n, 7))
@@ -64,8 +64,8 @@ def test_operator_rows_full_size(h, cfg1, precision):
 
 
 @pytest.mark.parametrize("transpose", [0, 1])
-def test_spai_and_reuse_columns_full_size(h, cfg1, transpose):
-    wl = cfg1
+def test_spai_and_reuse_columns_full_size(h, convdiff, transpose):
+    wl = convdiff
     s1, s2 = 12.0 + 3.0j, 20.0 - 1.0j
     mor.mor_build_precond(h, s1, transpose, mor.MOR_MIXED)
     mor.mor_update_precond(h, s2, transpose)
@@ -87,8 +87,8 @@ def test_spai_and_reuse_columns_full_size(h, cfg1, transpose):
             assert np.linalg.norm(a - b) <= 2e-4 * np.linalg.norm(b), (idx, j)
 
 
-def test_irka_step_full_size_solves_and_hermite(h, cfg1):
-    wl = cfg1
+def test_irka_step_full_size_solves_and_hermite(h, convdiff):
+    wl = convdiff
     mor.mor_irka_reset(h)
     opts = mor.mor_default_opts()
     s0 = wl.shifts.copy()
@@ -123,7 +123,7 @@ def test_irka_step_full_size_solves_and_hermite(h, cfg1):
 
 
 def test_batch_full_size_sampled_systems(h):
-    sysl = W.config2()
+    sysl = W.uneven_laplace2d_batch()
     mor.mor_set_batch(h, [w.A for w in sysl], [w.B[:, 0] for w in sysl], [w.C[:, 0] for w in sysl])
     nsys, off = mor.mor_batch_info(h)
     assert nsys == 256 and off[-1] == sum(w.n for w in sysl)

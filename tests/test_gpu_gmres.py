@@ -43,8 +43,8 @@ def _chain(wl, shifts, transpose):
 
 
 CASES = {
-    "convdiff3d_n3375": lambda: W.config1(N=15),
-    "laplace2d_n4900": lambda: W.config0(N=70),
+    "convdiff3d_n3375": lambda: W.convdiff3d_siso(N=15),
+    "laplace2d_n4900": lambda: W.laplace2d_siso(N=70),
     "rand_csrE_n1500": lambda: W.random_sparse_system(1500, 0.004, seed=8, e_kind="csr"),
 }
 
@@ -122,7 +122,7 @@ def test_gmres_unpreconditioned_noconv_and_zero_rhs(h):
     """Unpreconditioned GMRES on a hard shift stops at maxit with MOR_ENOCONV
     (Sec. IV: plain GMRES fails on the paper's models); a zero right-hand
     side takes no iteration and returns x = 0."""
-    wl = W.config0(N=60)
+    wl = W.laplace2d_siso(N=60)
     _set(h, wl)
     opts = mor.mor_default_opts(precision=mor.MOR_FP64, precond=2, maxit=12, tol=1e-12, solver=mor.MOR_GMRES,
                                 restart=5)
@@ -130,7 +130,7 @@ def test_gmres_unpreconditioned_noconv_and_zero_rhs(h):
     assert code == mor.MOR_ENOCONV
     assert stats[0]["status"] == mor.MOR_ENOCONV and stats[0]["iters"] == 12
     assert np.all(np.isfinite(X))
-    wl = W.config1(N=6)
+    wl = W.convdiff3d_siso(N=6)
     _set(h, wl)
     X, stats, code = mor.mor_solve_shifts(h, [5.0], 0, mor.mor_default_opts(precond=2, solver=mor.MOR_GMRES),
                                           R=np.zeros((wl.n, 1), dtype=complex))
@@ -161,7 +161,7 @@ def test_gmres_rejects_batches_and_bad_restart(h):
     opts = mor.mor_default_opts(solver=mor.MOR_GMRES, precond=2)
     with pytest.raises(RuntimeError):
         mor.mor_batch_solve(h, [1.0], 0, opts)
-    wl = W.config1(N=6)
+    wl = W.convdiff3d_siso(N=6)
     _set(h, wl)
     with pytest.raises(RuntimeError):
         mor.mor_solve_shifts(h, [5.0], 0, mor.mor_default_opts(precond=2, solver=mor.MOR_GMRES, restart=65))

@@ -2,7 +2,7 @@
 
   * the 2D-Laplacian IRKA workload at full size (n = 10,000, 20 iterations,
     FP64): H_r on 1000 log-spaced frequencies within 1e-6 of the oracle's,
-    relative to |H| (stored oracle values, tests/golden/irka_cfg0.json),
+    relative to |H| (stored oracle values, tests/golden/irka_laplace2d_n10000.json),
     BiCGSTAB iterations per IRKA iteration within 10% of the oracle's, and
     the shift history within 1e-3 relative.  The IRKA fixed-point iteration
     amplifies solve-level differences: the oracle itself, run with solve
@@ -27,7 +27,7 @@ from oracle import irka as oirka, operator as oop
 
 pytestmark = pytest.mark.gpu
 
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "irka_cfg0.json")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "irka_laplace2d_n10000.json")
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +70,7 @@ def _run(h, wl, iters, opts):
 @pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
 def test_irka_laplace2d_full_size_vs_stored_oracle(h, precision):
     gold = json.load(open(GOLDEN))
-    wl = W.config0()
+    wl = W.laplace2d_siso()
     opts = mor.mor_default_opts(precision=precision)
     hist, rom, stats = _run(h, wl, gold["iters"], opts)
     w = np.logspace(0, 5, 1000)
@@ -93,7 +93,7 @@ def test_irka_laplace2d_full_size_vs_stored_oracle(h, precision):
 
 
 def test_irka_nonsymmetric_complex_vs_live_oracle(h):
-    wl = W.config1(N=9)
+    wl = W.convdiff3d_siso(N=9)
     opts = mor.mor_default_opts(precision=mor.MOR_FP64)
     hist, rom, stats = _run(h, wl, 3, opts)
     ref = oirka.irka(wl.A, wl.E, wl.B, wl.C, wl.shifts, iters=3, hermite=True)
@@ -120,7 +120,7 @@ def test_irka_nonsymmetric_complex_vs_live_oracle(h):
 def test_irka_one_shift_and_fresh_modes_vs_live_oracle(h, mode):
     """The plain FP64 one-shift-per-launch form (no batching, no graphs) and
     the fresh-SPAI-per-shift form reach the oracle's H_r too."""
-    wl = W.config1(N=9)
+    wl = W.convdiff3d_siso(N=9)
     if mode == "one_shift":
         opts = mor.mor_default_opts(precision=mor.MOR_FP64, batch=0, use_graph=0)
         ref, bar = _shift_bar(wl, 3)
@@ -139,7 +139,7 @@ def test_irka_one_shift_and_fresh_modes_vs_live_oracle(h, mode):
 
 
 def test_irka_mixed_with_chain_cap(h):
-    wl = W.config1(N=9)
+    wl = W.convdiff3d_siso(N=9)
     opts = mor.mor_default_opts(precision=mor.MOR_MIXED, max_chain=2)
     hist, rom, stats = _run(h, wl, 4, opts)
     assert [st["builds_spai"] for st in stats] == [2, 0, 2, 0]
@@ -153,7 +153,7 @@ def test_irka_mixed_with_chain_cap(h):
 
 
 def test_irka_rejects_non_conjugate_closed_shifts(h):
-    wl = W.config1(N=5)
+    wl = W.convdiff3d_siso(N=5)
     mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E)
     with pytest.raises(mor.MorError) as e:
         mor.mor_irka_step(h, np.array([1.0 + 1j, 2.0]), mor.mor_default_opts())
@@ -165,7 +165,7 @@ def test_irka_serial_and_concurrent_sweeps_agree(h):
     same kernels on the same per-sweep streams as the default concurrent form,
     whose reductions are fixed-order: shifts, reduced system and statistics
     agree."""
-    wl = W.config1(N=12)
+    wl = W.convdiff3d_siso(N=12)
     out = []
     for conc in (1, 0):
         opts = mor.mor_default_opts(precision=mor.MOR_MIXED, concurrent_sweeps=conc)

@@ -53,7 +53,7 @@ def _start(m, q, seed=7):
 CASES = {
     "rand_diagE_m3_q2": lambda: W.random_sparse_system(700, 0.006, seed=41, e_kind="diag", m=3, q=2),
     "rand_csrE_m2_q3": lambda: W.random_sparse_system(500, 0.008, seed=42, e_kind="csr", m=2, q=3),
-    "convdiff_n512_m4": lambda: W.config4(N=8, m=4),
+    "convdiff_n512_m4": lambda: W.convdiff3d_mimo(N=8, m=4),
 }
 
 
@@ -113,7 +113,7 @@ def test_tangential_irka_mixed_precision(h):
 
 
 def test_tangential_with_one_input_output_reproduces_siso_step(h):
-    wl = W.config1(N=10)
+    wl = W.convdiff3d_siso(N=10)
     r = len(wl.shifts)
     opts = mor.mor_default_opts(precision=mor.MOR_FP64)
     _set(h, wl)

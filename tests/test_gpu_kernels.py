@@ -44,8 +44,8 @@ def _E_abs(wl):
 
 SYSTEMS = {
     # ragged sizes: not multiples of 32 or 256, several thread blocks
-    "laplace2d_n1369": lambda: W.config0(N=37),
-    "convdiff3d_n2197": lambda: W.config1(N=13),
+    "laplace2d_n1369": lambda: W.laplace2d_siso(N=37),
+    "convdiff3d_n2197": lambda: W.convdiff3d_siso(N=13),
     "rand_csrE_n700": lambda: W.random_sparse_system(700, 0.01, seed=3, e_kind="csr"),
     "rand_diagE_n33": lambda: W.random_sparse_system(33, 0.2, seed=4, e_kind="diag"),
 }
@@ -86,7 +86,7 @@ def test_operator_spmv(h, name, fmt, transpose, precision):
 
 def test_operator_second_order(h):
     """(s^2 + alpha s) M + (1 + beta s) K applied on the fly (27-point K)."""
-    wl = W.config3(nx=9, ny=8, nz=7)
+    wl = W.stencil27_second_order(nx=9, ny=8, nz=7)
     mor.mor_set_system_2nd(h, wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C)
     sig = np.array([0.3 + 0.2j, 2.0])
     rng = np.random.default_rng(1)

@@ -63,8 +63,8 @@ def _oracle_chain_solves(wl, shifts, transpose):
 
 
 CASES = {
-    "convdiff3d_n3375": lambda: W.config1(N=15),
-    "laplace2d_n4900": lambda: W.config0(N=70),
+    "convdiff3d_n3375": lambda: W.convdiff3d_siso(N=15),
+    "laplace2d_n4900": lambda: W.laplace2d_siso(N=70),
     "rand_csrE_n1500": lambda: W.random_sparse_system(1500, 0.004, seed=8, e_kind="csr"),
 }
 
@@ -139,7 +139,7 @@ def test_unpreconditioned_hits_maxit_with_status(h):
     """Unpreconditioned Krylov on a hard shift stops at maxit with
     MOR_ENOCONV and a finite best iterate (Sec. IV: unpreconditioned GMRES
     fails on the paper's models)."""
-    wl = W.config0(N=60)
+    wl = W.laplace2d_siso(N=60)
     _set(h, wl)
     opts = mor.mor_default_opts(precision=mor.MOR_FP64, precond=2, maxit=10, tol=1e-12)
     X, stats, code = mor.mor_solve_shifts(h, [1e-3], 0, opts)
@@ -165,7 +165,7 @@ def test_tiny_and_zero_rhs(h):
     mor.mor_set_system(h, A, np.ones((1, 1)), np.ones((1, 1)))
     X, stats, code = mor.mor_solve_shifts(h, [3.0], 0, mor.mor_default_opts(precond=2))
     assert code == mor.MOR_OK and abs(X[0, 0] - 1.0 / 5.0) < 1e-12
-    wl = W.config1(N=6)
+    wl = W.convdiff3d_siso(N=6)
     _set(h, wl)
     X, stats, code = mor.mor_solve_shifts(h, [5.0], 0, mor.mor_default_opts(precond=2),
                                           R=np.zeros((wl.n, 1), dtype=complex))
@@ -177,7 +177,7 @@ def test_second_order_solves_match_oracle(h, precision):
     """s^2 M + s D + K with Rayleigh damping (27-point K), applied on the fly;
     SPAI and reuse factors on the pattern of K (Algorithm 1's matrices,
     Algorithm 4's reuse)."""
-    wl = W.config3(nx=11, ny=10, nz=9)
+    wl = W.stencil27_second_order(nx=11, ny=10, nz=9)
     mor.mor_set_system_2nd(h, wl.K, wl.M_diag, wl.alpha, wl.beta, wl.F, wl.C)
     shifts = [0.3 + 0.15j, 1.0 + 0.5j, 3.0]
     mor.mor_build_precond(h, shifts[0], 0, precision)
@@ -201,7 +201,7 @@ def test_second_order_solves_match_oracle(h, precision):
 def test_mimo_block_rhs_many_columns(h):
     """MIMO sweep shape: several shifts x an m-column block of right-hand
     sides as (shift, column) pairs, more than one 16-column batch."""
-    wl = W.config4(N=12, m=4)
+    wl = W.convdiff3d_mimo(N=12, m=4)
     _set(h, wl)
     shifts = np.logspace(0, 4, 6)
     mor.mor_build_precond(h, shifts[0], 0, mor.MOR_MIXED)
@@ -248,7 +248,7 @@ def test_fp32_factors_under_fp64_solves(h, name):
 def test_irka_step_with_fp32_factors_under_fp64(h):
     """The IRKA schedule builds FP32 factors for FP64 solves when asked; the
     reduced model matches the all-FP64 step's H_r."""
-    wl = W.config1(N=12)
+    wl = W.convdiff3d_siso(N=12)
     _set(h, wl)
     mor.mor_irka_reset(h)
     s1, rom1, st1 = mor.mor_irka_step(h, wl.shifts, mor.mor_default_opts(precision=mor.MOR_FP64))

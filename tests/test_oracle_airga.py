@@ -9,7 +9,7 @@ from oracle import airga, operator as op
 
 
 def _small2(nx=4, ny=3, nz=3, m=2, seed=3):
-    return W.config3(nx=nx, ny=ny, nz=nz, seed=seed, m=m)
+    return W.stencil27_second_order(nx=nx, ny=ny, nz=nz, seed=seed, m=m)
 
 
 def _H(wl, s):

@@ -57,7 +57,7 @@ def _dense_run(wl, iters, mode="reuse"):
 def test_hermite_interpolation_every_iteration(which):
     """Petrov-Galerkin with V, W from the shifted solves interpolates H and
     H' at every shift, at every iteration (Sec. II)."""
-    wl = W.config0(N=9) if which == "sym" else W.config1(N=5)
+    wl = W.laplace2d_siso(N=9) if which == "sym" else W.convdiff3d_siso(N=5)
     res = _dense_run(wl, 4)
     for h in res.hermite:
         np.testing.assert_allclose(h["Hr"], h["H"], rtol=1e-9)
@@ -93,7 +93,7 @@ def test_irka_fixed_point_is_mirrored_reduced_poles():
 def test_iterative_irka_matches_dense_irka():
     """BiCGSTAB with reused SPAI (Algorithm 4) to 1e-8 reproduces the exact
     (dense LU) IRKA's H_r to 1e-6 on log-spaced frequencies."""
-    wl = W.config1(N=8)
+    wl = W.convdiff3d_siso(N=8)
     rd = _dense_run(wl, 3)
     ri = irka.irka(wl.A, wl.E, wl.B, wl.C, wl.shifts, iters=3, solver="bicgstab")
     w = 1j * np.logspace(0, 5, 200)
@@ -104,7 +104,7 @@ def test_iterative_irka_matches_dense_irka():
 
 
 def test_reuse_schedule_follows_algorithm4():
-    wl = W.config1(N=5)
+    wl = W.convdiff3d_siso(N=5)
     res = irka.irka(wl.A, wl.E, wl.B, wl.C, wl.shifts, iters=3, solver="dense")
     prim = [b for b in res.builds[: len(res.builds) // 2]]
     # z = 1: full SPAI for i = 1, horizontal for i > 1
@@ -116,7 +116,7 @@ def test_reuse_schedule_follows_algorithm4():
 def test_reuse_vs_fresh_vs_none_same_rom():
     """The preconditioner changes iteration counts, never the solution:
     reuse, fresh-SPAI and unpreconditioned IRKA give the same H_r."""
-    wl = W.config0(N=12)
+    wl = W.laplace2d_siso(N=12)
     w = 1j * np.logspace(0, 5, 50)
     Hs = []
     for mode in ("reuse", "fresh", "none"):
@@ -220,7 +220,7 @@ def test_tangential_with_one_input_output_is_siso_irka():
     to 1e-6 only: the scalar directions change the bases (not their spans),
     and the poles of this non-normal reduced pencil move by ~1e-7 under
     that change of basis while H_r does not."""
-    wl = W.config1(N=5)
+    wl = W.convdiff3d_siso(N=5)
     res_s = irka.irka(wl.A, wl.E, wl.B, wl.C, wl.shifts, iters=3, solver="dense")
     r = len(wl.shifts)
     res_t, _ = irka.irka_tangential(wl.A, wl.E, wl.B, wl.C, wl.shifts, np.ones((r, 1)), np.ones((r, 1)), iters=3,

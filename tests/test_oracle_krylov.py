@@ -11,7 +11,7 @@ from oracle import spai, krylov
 
 
 def _problem(sigma, N=14):
-    wl = W.config1(N=N)                        # nonsymmetric, E diagonal
+    wl = W.convdiff3d_siso(N=N)                        # nonsymmetric, E diagonal
     M = op.A_sigma(wl.A, wl.E, sigma)
     b = wl.B[:, 0].astype(M.dtype)
     return wl, M, b
@@ -51,7 +51,7 @@ def test_preconditioner_reduces_iterations():
 
 def test_symmetric_case_matches_cg():
     """Laplacian (SPD sigma I + L): BiCGSTAB and scipy CG agree."""
-    wl = W.config0(N=20)
+    wl = W.laplace2d_siso(N=20)
     M = op.A_sigma(wl.A, wl.E, 25.0)
     b = wl.B[:, 0]
     x, it, rel, st = krylov.bicgstab(lambda v: M @ v, None, b, tol=1e-10)

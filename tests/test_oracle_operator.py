@@ -19,7 +19,7 @@ def test_laplacian_eigenpair_closed_form(sigma):
     """For A = -L2, E = I: (sigma I - A) u = (sigma + lambda) u with the
     closed-form sine eigenpairs of the Dirichlet 5-point Laplacian."""
     N = 13
-    wl = W.config0(N=N)
+    wl = W.laplace2d_siso(N=N)
     for (j, k) in [(1, 1), (2, 5), (13, 7)]:
         uj, lj = _sine_mode(N, j)
         uk, lk = _sine_mode(N, k)
@@ -34,7 +34,7 @@ def test_convdiff_interior_rowsums_and_diag_E():
     (diffusion and the one-sided difference both annihilate constants), so
     (sigma E - A) 1 = sigma e at interior rows; boundary rows are larger."""
     N = 7
-    wl = W.config1(N=N)
+    wl = W.convdiff3d_siso(N=N)
     sigma = 2.0 + 1.0j
     y = op.A_sigma(wl.A, wl.E, sigma) @ np.ones(wl.n)
     idx = np.arange(wl.n)

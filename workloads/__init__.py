@@ -10,11 +10,15 @@ The paper's own test models (disk brakes from Grabner et al.) are not
 available; the generators here stand in for them with stencil systems of the
 same size and sparsity class:
 
-  * config 0  2D 5-point Laplacian, n = 10,000, E = I, SISO
-  * config 1  3D 7-point upwind convection-diffusion, n = 1,000,000, E diagonal
-  * config 2  256 uneven 2D Laplacian-plus-diagonal systems, n_s in [2000, 60000]
-  * config 3  3D 27-point SPD stencil, second order, Rayleigh damping, n = 1,197,900
-  * config 4  3D 7-point convection-diffusion, n = 8,000,000, MIMO m = q = 8
+  * laplace2d_siso          2D 5-point Laplacian, n = 10,000, E = I, SISO
+  * convdiff3d_siso         3D 7-point upwind convection-diffusion, n = 1,000,000,
+                            E diagonal
+  * uneven_laplace2d_batch  256 uneven 2D Laplacian-plus-diagonal systems,
+                            n_s in [2000, 60000]
+  * stencil27_second_order  3D 27-point SPD stencil, second order, Rayleigh
+                            damping, n = 1,197,900
+  * convdiff3d_mimo         3D 7-point convection-diffusion, n = 8,000,000,
+                            MIMO m = q = 8
 """
 from .generators import (  # noqa: F401
     Workload,
@@ -22,11 +26,11 @@ from .generators import (  # noqa: F401
     laplacian_2d,
     convection_diffusion_3d,
     stencil27_3d,
-    config0,
-    config1,
-    config2,
-    config3,
-    config4,
+    laplace2d_siso,
+    convdiff3d_siso,
+    uneven_laplace2d_batch,
+    stencil27_second_order,
+    convdiff3d_mimo,
     csr_arrays,
     random_sparse_system,
 )

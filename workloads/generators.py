@@ -148,7 +148,7 @@ def conj_pairs(a: np.ndarray, ratio: float = 0.5) -> np.ndarray:
 # --------------------------------------------------------------------------
 # the five configurations
 # --------------------------------------------------------------------------
-def config0(N: int = 100, seed: int = 0) -> Workload:
+def laplace2d_siso(N: int = 100, seed: int = 0) -> Workload:
     """Plain FP64 IRKA, SISO: A = -L2 (5-point Laplacian, N x N grid,
     h = 1/(N+1), scaled), E = I, B, C ~ N(0,1) (drawn in that order),
     r = 6, initial real shifts logspace(1, 4, 6), 20 IRKA iterations."""
@@ -158,11 +158,11 @@ def config0(N: int = 100, seed: int = 0) -> Workload:
     B = rng.standard_normal((n, 1))
     C = rng.standard_normal((n, 1))
     shifts = np.logspace(1, 4, 6).astype(np.complex128)
-    return Workload("cfg0_laplace2d_n%d" % n, A, None, B, C, shifts, r=6,
+    return Workload("laplace2d_n%d" % n, A, None, B, C, shifts, r=6,
                     irka_iters=20, meta={"grid": (N, N), "seed": seed})
 
 
-def config1(N: int = 100, seed: int = 1) -> Workload:
+def convdiff3d_siso(N: int = 100, seed: int = 1) -> Workload:
     """Nonsymmetric 3D convection-diffusion (7-point, Peclet 10, upwind) on
     N^3, A = -L, E = diag(U[0.5, 1.5]); draws B, C ~ N(0,1) then E's
     diagonal.  r = 10 complex shifts: 5 conjugate pairs a_k (1 +- 0.5 i),
@@ -174,12 +174,12 @@ def config1(N: int = 100, seed: int = 1) -> Workload:
     C = rng.standard_normal((n, 1))
     Ed = rng.uniform(0.5, 1.5, n)
     shifts = conj_pairs(np.logspace(1, 4, 5))
-    return Workload("cfg1_convdiff3d_n%d" % n, A, Ed, B, C, shifts, r=10,
+    return Workload("convdiff3d_n%d" % n, A, Ed, B, C, shifts, r=10,
                     meta={"grid": (N, N, N), "seed": seed, "peclet": 10.0})
 
 
-def config2(num_systems: int = 256, n_lo: int = 2000, n_hi: int = 60000,
-            seed: int = 2) -> List[Workload]:
+def uneven_laplace2d_batch(num_systems: int = 256, n_lo: int = 2000, n_hi: int = 60000,
+                           seed: int = 2) -> List[Workload]:
     """256 independent systems.  Draw order: all sizes n_s ~ U{n_lo..n_hi},
     then per system B, C ~ N(0,1) and the diagonal U[0,1].  nx = ceil(sqrt
     n_s); A_s = -(L2(nx x nx, h = 1/(nx+1)) + diag(U[0,1])) restricted to its
@@ -197,13 +197,13 @@ def config2(num_systems: int = 256, n_lo: int = 2000, n_hi: int = 60000,
         d = rng.uniform(0.0, 1.0, ns)
         A = _canon(-(L + sp.diags(d)))
         shifts = np.logspace(0, 4, 8).astype(np.complex128)
-        out.append(Workload("cfg2_sys%03d_n%d" % (s, ns), A, None, B, C,
+        out.append(Workload("uneven_batch_sys%03d_n%d" % (s, ns), A, None, B, C,
                             shifts, r=8, meta={"nx": nx, "seed": seed}))
     return out
 
 
-def config3(nx: int = 110, ny: int = 110, nz: int = 99, seed: int = 3,
-            m: int = 4) -> SecondOrderWorkload:
+def stencil27_second_order(nx: int = 110, ny: int = 110, nz: int = 99, seed: int = 3,
+                           m: int = 4) -> SecondOrderWorkload:
     """Second-order structural-like system: K = 27-point SPD stencil on
     nx x ny x nz, M = diag(U[1, 2]), D = 1e-3 M + 1e-4 K.  Draw order:
     F, C ~ N(0,1) (n x m each), then M's diagonal.  Shifts: 6 conjugate
@@ -215,12 +215,12 @@ def config3(nx: int = 110, ny: int = 110, nz: int = 99, seed: int = 3,
     C = rng.standard_normal((n, m))
     Md = rng.uniform(1.0, 2.0, n)
     shifts = conj_pairs(np.logspace(-1, 1, 6))
-    return SecondOrderWorkload("cfg3_stencil27_n%d" % n, K, Md, 1e-3, 1e-4, F, C,
+    return SecondOrderWorkload("stencil27_second_order_n%d" % n, K, Md, 1e-3, 1e-4, F, C,
                                shifts, r=12, meta={"grid": (nx, ny, nz), "seed": seed})
 
 
-def config4(N: int = 200, seed: int = 4, m: int = 8) -> Workload:
-    """MIMO 3D convection-diffusion on N^3 (config-1 operator, h = 1/(N+1)),
+def convdiff3d_mimo(N: int = 200, seed: int = 4, m: int = 8) -> Workload:
+    """MIMO 3D convection-diffusion on N^3 (the operator of convdiff3d_siso, h = 1/(N+1)),
     E = I, B, C ~ N(0,1) n x m (drawn in that order); the timed sweep is 48
     real shifts logspace(0, 4, 48) times the full m-column block; r = 16."""
     A = _canon(-convection_diffusion_3d(N))
@@ -229,7 +229,7 @@ def config4(N: int = 200, seed: int = 4, m: int = 8) -> Workload:
     B = rng.standard_normal((n, m))
     C = rng.standard_normal((n, m))
     shifts = np.logspace(0, 4, 48).astype(np.complex128)
-    return Workload("cfg4_convdiff3d_n%d" % n, A, None, B, C, shifts, r=16,
+    return Workload("convdiff3d_mimo_n%d" % n, A, None, B, C, shifts, r=16,
                     meta={"grid": (N, N, N), "seed": seed})
 
 
