@@ -2,15 +2,21 @@
 test infrastructure only).  Shares no code with the CUDA library.
 
 Systems  M x'' + D x' + K x = F u,  y = C^T x,  D = alpha M + beta K
-(Eq. linear-non-para), M diagonal.  One AIRGA iteration (Algorithm 1 with
-the zeroth moments only, i.e. its inner loop not entered):
-  lines 3-5  X(s_i) = (s_i^2 M + s_i D + K)^{-1} F at the expansion points
+(Eq. linear-non-para), M diagonal.  One AIRGA iteration (Algorithm 1):
+  lines 3-5  X^(0)(s_i) = (s_i^2 M + s_i D + K)^{-1} F at the expansion points
              (one solve per column of F, right-preconditioned, with the reuse
              schedule of Algorithm 4 on s^2 M + s D + K);
-  Galerkin   V = orth([Re X(s_i), Im X(s_i)]) by CGS2 (the normalisation of
-             line 5 does not change the span), M_r = V^T M V, K_r = V^T K V,
-             D_r = alpha M_r + beta K_r, F_r = V^T F, C_r = V^T C (Sec. II);
+  lines 7-12 the inner moment loop, here run for a fixed number J of moments
+             per point (``moments``; J = 1 skips it): V_j = X^(j-1) / ||X^(j-1)||_F
+             and X^(j)(s_i) = -(s_i^2 M + s_i D + K)^{-1} M V_j, solved with the
+             same matrix and the same (reused) preconditioner as X^(0)(s_i);
+  Galerkin   V = orth([Re X^(j)(s_i), Im X^(j)(s_i)]) by CGS2 (the Frobenius
+             normalisations do not change the span), M_r = V^T M V,
+             K_r = V^T K V, D_r = alpha M_r + beta K_r, F_r = V^T F, C_r = V^T C
+             (Sec. II);
   line 11    "all expansion points are updated": the rule is not stated.
+The inner loop's own stopping test (an H2 change, Sec. IV) and an adaptive r
+are not taken: J is an input.
 Reading taken for line 11: the new points are the mirror images
 sigma = |Re lambda| - i Im lambda of the eigenvalues lambda of the reduced
 quadratic eigenproblem (lambda^2 M_r + lambda D_r + K_r) x = 0 of smallest
@@ -19,8 +25,8 @@ order of increasing |lambda| (ties by Re, then Im), a conjugate pair only
 when two places are left; if one place is left and no real eigenvalue comes
 before the candidates run out, that place gets the real point |lambda| of the
 first pair that did not fit.  Only the point with Im >= 0 of a conjugate
-pair is solved; it contributes 2m real basis columns, a real point m, so
-r = m * (number of points).
+pair is solved; it contributes 2 m J real basis columns, a real point m J,
+so r = m J (number of points).
 """
 from __future__ import annotations
 
@@ -127,10 +133,12 @@ def real_block_basis(blocks, points) -> np.ndarray:
 
 
 def airga_step(K, M_diag, alpha, beta, F, C, points, sched: ReuseSchedule2, z: int, solver: str = "bicgstab",
-               tol: float = 1e-8, maxit: int = 20000):
-    """One iteration (module docstring).  Returns (new points,
-    (M_r, D_r, K_r, F_r, C_r), iteration counts, true relative residuals,
-    solved points)."""
+               tol: float = 1e-8, maxit: int = 20000, moments: int = 1):
+    """One iteration (module docstring) with ``moments`` = J blocks per
+    solved point.  Returns (new points, (M_r, D_r, K_r, F_r, C_r), iteration
+    counts, true relative residuals, solved points)."""
+    if moments < 1:
+        raise ValueError("moments must be >= 1")
     s_solve = solve_shifts_of(points)
     chains = sched.chains(z, s_solve)
     if solver == "dense":
@@ -142,18 +150,30 @@ def airga_step(K, M_diag, alpha, beta, F, C, points, sched: ReuseSchedule2, z: i
 
         def krylov(apply_A, apply_P, b, tol=tol, maxit=maxit, M=None):
             return base(apply_A, apply_P, b, tol=tol, maxit=maxit)
-    blocks, its, rr = [], [], []
+    blocks, bpts, its, rr = [], [], [], []
     for s, ch in zip(s_solve, chains):
         M = A_sigma_2nd(K, M_diag, alpha, beta, s)
-        X = np.zeros((K.shape[0], F.shape[1]), dtype=np.complex128)
-        for j in range(F.shape[1]):
-            x, it, rel, _ = krylov(lambda v, M=M: M @ v, (lambda v, f=ch: chain_apply(f, v)) if ch else None,
-                                   F[:, j].astype(M.dtype), M=M)
-            X[:, j] = x
-            its.append(it)
-            rr.append(rel)
+
+        def block_solve(R):
+            X = np.zeros((K.shape[0], R.shape[1]), dtype=np.complex128)
+            for j in range(R.shape[1]):
+                rhs = R[:, j] if np.iscomplexobj(R) and M.dtype.kind == "c" else np.real(R[:, j])
+                x, it, rel, _ = krylov(lambda v, M=M: M @ v, (lambda v, f=ch: chain_apply(f, v)) if ch else None,
+                                       rhs.astype(M.dtype), M=M)
+                X[:, j] = x
+                its.append(it)
+                rr.append(rel)
+            return X
+
+        X = block_solve(F)                                   # X^(0)(s)
         blocks.append(X)
-    V, _ = cgs2(real_block_basis(blocks, s_solve))
+        bpts.append(s)
+        for _ in range(1, moments):
+            Vj = X / np.linalg.norm(X, "fro")                # V_j = X^(j-1) / ||X^(j-1)||_F
+            X = block_solve(-(M_diag[:, None] * Vj))         # X^(j) = -A(s)^{-1} M V_j
+            blocks.append(X)
+            bpts.append(s)
+    V, _ = cgs2(real_block_basis(blocks, bpts))
     Mr = V.T @ (M_diag[:, None] * V)
     Kr = V.T @ (K @ V)
     Dr = alpha * Mr + beta * Kr
@@ -163,16 +183,17 @@ def airga_step(K, M_diag, alpha, beta, F, C, points, sched: ReuseSchedule2, z: i
 
 
 def airga(K, M_diag, alpha, beta, F, C, points, iters: int, mode: str = "reuse", solver: str = "bicgstab",
-          tol: float = 1e-8, maxit: int = 20000, max_chain: Optional[int] = None):
-    """``iters`` iterations from the initial expansion points.  The result's
-    (Ar, Er, Br, Cr) slots hold (K_r, M_r, F_r, C_r); D_r = alpha M_r + beta K_r."""
+          tol: float = 1e-8, maxit: int = 20000, max_chain: Optional[int] = None, moments: int = 1):
+    """``iters`` iterations from the initial expansion points, ``moments``
+    blocks per point.  The result's (Ar, Er, Br, Cr) slots hold (K_r, M_r,
+    F_r, C_r); D_r = alpha M_r + beta K_r."""
     sched = ReuseSchedule2(K, M_diag, alpha, beta, mode=mode, max_chain=max_chain)
     p = sort_shifts(points)
     res = IrkaResult([p], None, None, None, None)
     solved = []
     for z in range(1, iters + 1):
         p, rom, its, rr, s_solve = airga_step(K, M_diag, alpha, beta, F, C, p, sched, z, solver=solver, tol=tol,
-                                              maxit=maxit)
+                                              maxit=maxit, moments=moments)
         res.shifts_history.append(p)
         res.Ar, res.Er, res.Br, res.Cr = rom[2], rom[0], rom[3], rom[4]
         res.iters.append(its)
