@@ -42,7 +42,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 from .operator import A_sigma, E_matrix, transfer_function_reduced
-from .spai import spai, reuse_factor, spai_pattern, chain_apply
+from .spai import spai, reuse_factor, spai_pattern, chain_apply, frobenius_ratios
 from .krylov import bicgstab, gmres, STATUS_OK
 
 
@@ -142,10 +142,15 @@ class ReuseSchedule:
     operator (primal or transposed) and returns, for the shifts of the
     current iteration, the factor chain of every shift.
 
-    mode: 'reuse' (Algorithm 4), 'fresh' (a new SPAI per shift, the paper's
-    "SPAI case"), or 'none' (unpreconditioned).  ``max_chain`` (default: no
-    limit, as in the paper) rebuilds P_1 from scratch when the vertical chain
-    would grow beyond it."""
+    mode: 'reuse' (Algorithm 4: the second approach of Table II, P_i = Q_i
+    P_{i-1}), 'first' (the first approach of Table II along the shifts of an
+    iteration: P_i = Q_i P_1 with Q_i from min ||A_1 - A_i Q||_F, so every
+    chain is the vertical chain plus one factor), 'auto' (Algorithm 4 with
+    the reuse decision read from the Frobenius ratios the paper tabulates,
+    see ``reuse_ok``), 'fresh' (a new SPAI per shift, the paper's "SPAI
+    case"), or 'none' (unpreconditioned).  ``max_chain`` (default: no limit,
+    as in the paper) rebuilds P_1 from scratch when the vertical chain would
+    grow beyond it."""
 
     def __init__(self, A, E, transpose: bool, mode: str = "reuse",
                  max_chain: Optional[int] = None):
@@ -160,6 +165,15 @@ class ReuseSchedule:
     def _Asig(self, s):
         return A_sigma(self.A, self.E, s, transpose=self.transpose)
 
+    def reuse_ok(self, s_old, s_new) -> bool:
+        """Reading of the paper's reuse criterion (Sec. IV, the discussion
+        of its Frobenius-ratio table): reuse pays when ||I - A_new||_F /
+        ||I||_F is large and ||A_old - A_new||_F / ||A_old||_F is small; the
+        paper fixes no thresholds, so 'small' is read as below 1 and below
+        the first ratio.  Otherwise a fresh SPAI is built for the new shift."""
+        std, change = frobenius_ratios(self._Asig(s_old), self._Asig(s_new))
+        return change < min(1.0, std)
+
     def chains(self, z: int, solve_shifts: np.ndarray):
         if self.mode == "none":
             return [[] for _ in solve_shifts]
@@ -171,6 +185,8 @@ class ReuseSchedule:
             return out
         s1 = solve_shifts[0]
         rebuild = (not self.vertical) or (self.max_chain is not None and len(self.vertical) + 1 > self.max_chain)
+        if not rebuild and self.mode == "auto":
+            rebuild = not self.reuse_ok(self.sigma1_prev, s1)
         if rebuild:
             self.vertical = [spai(self._Asig(s1), self.S)]
             self.builds.append((z, 1, "spai"))
@@ -180,9 +196,17 @@ class ReuseSchedule:
         self.sigma1_prev = s1
         out = [list(self.vertical)]
         for i in range(1, len(solve_shifts)):
-            Q = reuse_factor(self._Asig(solve_shifts[i - 1]), self._Asig(solve_shifts[i]), self.S)
-            self.builds.append((z, i + 1, "horizontal"))
-            out.append(out[-1] + [Q])
+            if self.mode == "first":
+                Q = reuse_factor(self._Asig(s1), self._Asig(solve_shifts[i]), self.S)
+                self.builds.append((z, i + 1, "first"))
+                out.append(list(self.vertical) + [Q])
+            elif self.mode == "auto" and not self.reuse_ok(solve_shifts[i - 1], solve_shifts[i]):
+                self.builds.append((z, i + 1, "spai"))
+                out.append([spai(self._Asig(solve_shifts[i]), self.S)])
+            else:
+                Q = reuse_factor(self._Asig(solve_shifts[i - 1]), self._Asig(solve_shifts[i]), self.S)
+                self.builds.append((z, i + 1, "horizontal"))
+                out.append(out[-1] + [Q])
         return out
 
 

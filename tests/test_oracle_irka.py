@@ -113,13 +113,64 @@ def test_reuse_schedule_follows_algorithm4():
     assert [k for (z, i, k) in prim if i == 1] == ["spai", "vertical", "vertical"]
 
 
+def test_first_approach_chains_and_full_pattern_inverse():
+    """Table II's first approach along the shifts: every shift i > 1 gets the
+    vertical chain plus one factor Q_i fitted from A_1 (min ||A_1 - A_i Q||_F).
+    With a full pattern Q_i = A_i^{-1} A_1 and P_1 = A_1^{-1}, so every chain
+    is exactly A_i^{-1}: A_i Q_i P_1 = A_1 P_1 = I (Table II, first column)."""
+    wl = W.convdiff3d_siso(N=3)                      # n = 27
+    n = wl.A.shape[0]
+    s = irka.ReuseSchedule(wl.A, wl.E, transpose=False, mode="first")
+    s.S = sp.csr_matrix(np.ones((n, n)))             # full pattern
+    shifts = np.array([20.0 + 5.0j, 35.0 + 2.0j, 60.0, 90.0 + 30.0j])
+    ch = s.chains(1, shifts)
+    assert [len(c) for c in ch] == [1, 2, 2, 2]
+    assert [k for (_, _, k) in s.builds] == ["spai", "first", "first", "first"]
+    for c, x in zip(ch, shifts):
+        M = op.A_sigma(wl.A, wl.E, x).toarray()
+        P = np.eye(n, dtype=complex)
+        for F in c:
+            P = F.toarray() @ P
+        assert np.linalg.norm(M @ P - np.eye(n)) <= 1e-9
+    ch2 = s.chains(2, shifts * 1.01)                  # second iteration: vertical factor + Q_i
+    assert [len(c) for c in ch2] == [2, 3, 3, 3]
+    assert all(c[:2] == ch2[0] for c in ch2[1:])
+
+
+def test_auto_policy_reads_the_frobenius_ratios():
+    """The reuse decision (reading of the paper's ratio discussion): close
+    shifts (change ratio far below 1 and below ||I - A||_F / ||I||_F) reuse,
+    a jump whose change ratio exceeds 1 builds a fresh SPAI, which then
+    starts the horizontal chain again; the decision agrees with ratios
+    recomputed by brute force on the dense matrices."""
+    wl = W.laplace2d_siso(N=8)
+    n = wl.A.shape[0]
+    s = irka.ReuseSchedule(wl.A, wl.E, transpose=False, mode="auto")
+    shifts = np.array([100.0, 110.0, 5000.0, 5100.0])
+    ch = s.chains(1, shifts)
+    kinds = [k for (_, _, k) in s.builds]
+    assert kinds == ["spai", "horizontal", "spai", "horizontal"]
+    assert [len(c) for c in ch] == [1, 2, 1, 2]
+    for a, b, want in ((100.0, 110.0, True), (110.0, 5000.0, False), (5000.0, 5100.0, True)):
+        Ma = op.A_sigma(wl.A, wl.E, a).toarray()
+        Mb = op.A_sigma(wl.A, wl.E, b).toarray()
+        std = np.linalg.norm(np.eye(n) - Mb) / np.sqrt(n)
+        change = np.linalg.norm(Ma - Mb) / np.linalg.norm(Ma)
+        assert (change < min(1.0, std)) == want == s.reuse_ok(a, b)
+    s.chains(2, shifts * 1.02)                        # small vertical move: reused
+    assert s.builds[4] == (2, 1, "vertical")
+    s.chains(3, shifts * 40.0)                        # large vertical move: rebuilt
+    assert s.builds[8] == (3, 1, "spai")
+
+
 def test_reuse_vs_fresh_vs_none_same_rom():
     """The preconditioner changes iteration counts, never the solution:
-    reuse, fresh-SPAI and unpreconditioned IRKA give the same H_r."""
+    reuse, first-approach, ratio-policy, fresh-SPAI and unpreconditioned
+    IRKA give the same H_r."""
     wl = W.laplace2d_siso(N=12)
     w = 1j * np.logspace(0, 5, 50)
     Hs = []
-    for mode in ("reuse", "fresh", "none"):
+    for mode in ("reuse", "first", "auto", "fresh", "none"):
         r = irka.irka(wl.A, wl.E, wl.B, wl.C, wl.shifts, iters=2, mode=mode)
         Hs.append(op.transfer_function_reduced(r.Ar, r.Er, r.Br, r.Cr, w)[:, 0, 0])
     H = op.transfer_function(wl.A, wl.E, wl.B, wl.C, w)[:, 0, 0]
