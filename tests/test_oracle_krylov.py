@@ -88,3 +88,57 @@ def test_identity_preconditioned_by_exact_inverse_one_iteration():
     b = rng.standard_normal(n)
     x, it, rel, st = krylov.bicgstab(lambda v: M @ v, lambda v: Minv @ v, b, tol=1e-10)
     assert it == 1 and st == krylov.STATUS_OK
+
+
+# ----------------------------------------------------------------------------
+# block GMRES (several right-hand sides sharing one block Krylov space)
+# ----------------------------------------------------------------------------
+def _block_problem(sigma, p=3, N=9, seed=4):
+    wl = W.convdiff3d_siso(N=N)
+    M = op.A_sigma(wl.A, wl.E, sigma)
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((M.shape[0], p)).astype(M.dtype)
+    return wl, M, B
+
+
+@pytest.mark.parametrize("sigma", [10.0, 30.0 + 15.0j])
+@pytest.mark.parametrize("precond", [False, True])
+def test_block_gmres_matches_dense_lu(sigma, precond):
+    wl, M, B = _block_problem(sigma)
+    P = None
+    if precond:
+        Pm = spai.spai(M, spai.spai_pattern(wl.A, wl.E))
+        P = lambda x: Pm @ x  # noqa: E731
+    X, it, rel, st = krylov.block_gmres(lambda v: M @ v, P, B, tol=1e-10, m=12)
+    assert st == krylov.STATUS_OK and np.all(rel <= 1e-10)
+    Md = M.toarray()
+    Xd = np.linalg.solve(Md, B)
+    kappa = np.linalg.cond(Md)
+    for c in range(B.shape[1]):
+        assert np.linalg.norm(X[:, c] - Xd[:, c]) <= kappa * 2e-10 * np.linalg.norm(Xd[:, c])
+        # the true residual is recomputed here, not taken from the solver
+        assert np.linalg.norm(B[:, c] - Md @ X[:, c]) <= 1.001e-10 * np.linalg.norm(B[:, c])
+
+
+def test_block_gmres_one_column_is_gmres():
+    """p = 1: the block method is GMRES (QR of a single column = normalisation,
+    the block least squares = the Givens least squares)."""
+    wl, M, B = _block_problem(20.0 + 5.0j, p=1)
+    X, itb, relb, _ = krylov.block_gmres(lambda v: M @ v, None, B, tol=1e-9, m=15)
+    x, itg, relg, _ = krylov.gmres(lambda v: M @ v, None, B[:, 0], tol=1e-9, m=15)
+    assert abs(itb - itg) <= 1
+    np.testing.assert_allclose(X[:, 0], x, rtol=0, atol=1e-8 * np.linalg.norm(x))
+
+
+def test_block_space_contains_each_columns_space():
+    """Without restarts the block Krylov space of degree j contains every
+    column's own Krylov space of degree j, so block GMRES needs no more
+    iterations than the slowest column's GMRES, and (exact arithmetic) ends
+    within ceil(n / p) block steps."""
+    wl, M, B = _block_problem(5.0 + 2.0j, p=4, N=4)          # n = 64
+    n, p = B.shape
+    X, itb, rel, st = krylov.block_gmres(lambda v: M @ v, None, B, tol=1e-12, m=n)
+    single = [krylov.gmres(lambda v: M @ v, None, B[:, c], tol=1e-12, m=n)[1] for c in range(p)]
+    assert st == krylov.STATUS_OK
+    assert itb <= max(single)
+    assert itb <= -(-n // p)
