@@ -532,7 +532,10 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        ref_iters = 150
+        # iterations per solve of the FP64 method on this workload: 57, as the FP64 one-shift
+        # form of the GPU path measured (56.6), whose FP64 iteration counts match the oracle's
+        # within 10% in the parity tests
+        ref_iters = 57
         per = []
         for _ in range(args.warmup + args.steps):
             r = cpu_baseline(args.grid, ref_iters, ncols=20000, nits=10)
