@@ -258,13 +258,16 @@ int mor_build_precond(mor_t h, mor_c64 sigma, int transpose, int precision);
  * Errors: MOR_ESTATE when no P was built for this operator/precision. */
 int mor_update_precond(mor_t h, mor_c64 sigma_new, int transpose);
 
-/* Keep only the first `length` factors of the chain (0 clears it). */
+/* Keep only the first `length` factors of the chain (0 clears it): the
+ * chain Q_L ... Q_2 P_1 of Sec. III.B cut back to Q_length ... P_1. */
 int mor_truncate_precond(mor_t h, int transpose, int length);
 
-/* Number of factors and precision of the chain of one operator. */
+/* Number of factors and precision of the chain (Sec. III.B, P_i = Q_i
+ * P_{i-1} kept as its factors) of one operator. */
 int mor_chain_info(mor_t h, int transpose, int* length, int* precision);
 
-/* Copy factor `index` (0 = P) of a chain to the caller: values (complex128,
+/* Copy factor `index` (0 = P, the SPAI of Eq. gen-precond; later ones the
+ * reuse factors Q of Table II) of a chain to the caller: values (complex128,
  * nnz entries in the CSR order of the pattern returned by mor_get_pattern)
  * and the shifts it maps between (sigma_from = sigma_to for a full SPAI). */
 int mor_get_factor(mor_t h, int transpose, int index, mor_c64* vals,
@@ -279,7 +282,10 @@ int mor_get_pattern(mor_t h, int transpose, int32_t* rowptr, int32_t* col);
 /* ------------------------------------------------------------------------ */
 
 /* Y(:, c) = A(sigma_c) X(:, c), c = 0..k-1 (or the transposed operator),
- * without forming A(sigma_c).  X, Y: n x k complex128, column-major.
+ * without forming A(sigma_c): sigma E - A for first-order systems (the
+ * shifted matrix of the solves of Algorithm 2, lines 4-5), (s^2 + alpha s) M
+ * + (1 + beta s) K for second-order ones (Algorithm 1, line 4, with Rayleigh
+ * damping D = alpha M + beta K).  X, Y: n x k complex128, column-major.
  * precision MOR_MIXED computes in FP32/complex64 (inputs rounded), MOR_FP64
  * in FP64.  1 <= k <= 16. */
 int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int precision,
@@ -287,7 +293,8 @@ int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int 
 
 /* Y(:, c) = P(sigma_c) X(:, c): the chain prefix that ends at the last
  * factor built for sigma_c (the whole chain when none was), applied factor
- * by factor in the chain's precision.  Shapes as mor_apply_operator. */
+ * by factor in the chain's precision (Sec. III.B: Q_i ... Q_2 P_1 is applied
+ * as successive mat-vecs, never formed; Algorithm 4).  Shapes as mor_apply_operator. */
 int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose,
                       const mor_c64* X, mor_c64* Y, unsigned flags);
 
@@ -393,15 +400,18 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts,
                    mor_reduced2* rom, mor_irka_stats* st);
 
 /* H_r(i omega_w) = C_r^T ((i w)^2 M_r + i w D_r + K_r)^{-1} F_r of a reduced
- * second-order system for nw frequencies; layout and flags as mor_eval_tf. */
+ * second-order system (the reduced system of Sec. II's Galerkin projection)
+ * for nw frequencies; layout and flags as mor_eval_tf. */
 int mor_eval_tf2(mor_t h, const mor_reduced2* rom, const double* omega, int nw,
                  mor_c64* H, unsigned flags);
 
-/* Restart the reuse schedule (the next mor_irka_step is iteration 1). */
+/* Restart the reuse schedule (the next mor_irka_step is iteration 1 of
+ * Algorithm 4: a full SPAI at the first shift). */
 int mor_irka_reset(mor_t h);
 
 /* H_r(i omega_w) = C_r^T (i omega_w E_r - A_r)^{-1} B_r for nw frequencies
- * (on the GPU, one block per frequency, FP64 complex LU with partial
+ * (the reduced transfer function whose error Sec. IV plots over s = i omega,
+ * Fig. 3; on the GPU, one block per frequency, FP64 complex LU with partial
  * pivoting).  H: nw x q x m complex128, H[w + nw*(iq + q*im)].  omega and H are
  * host arrays unless flags has MOR_DEVICE_PTRS. */
 int mor_eval_tf(mor_t h, const mor_reduced* rom, const double* omega, int nw,
@@ -425,13 +435,15 @@ int mor_eval_tf(mor_t h, const mor_reduced* rom, const double* omega, int nw,
 int mor_set_batch(mor_t h, int nsys, const mor_csr* A, const double* const* E_diag,
                   const double* const* B, const double* const* C, int format, unsigned flags);
 
-/* Number of systems of the batch and its row offsets (nsys + 1 entries;
+/* Number of systems of the batch (independent problems of the solve
+ * sequence of Sec. III.A, one segment each) and its row offsets (nsys + 1 entries;
  * system s owns rows offsets[s] .. offsets[s+1]-1 of the batch). */
 int mor_batch_info(mor_t h, int* nsys, int64_t* offsets);
 
 /* Solve A_s(sigma_c) x_{s,c} = b_s (transpose = 0) or A_s(sigma_c)^T
  * x_{s,c} = c_s (transpose = 1) for every system s of the batch and every
- * shift c = 0..k-1, all in the same lock-step launches (the shift columns of
+ * shift c = 0..k-1 (the right-preconditioned solves of Sec. III.A, each
+ * system with its own chain factors of Sec. III.B), all in the same lock-step launches (the shift columns of
  * all systems advance together; each (system, shift) pair converges on its
  * own relative residual).  Preconditioning, precision and options as in
  * mor_solve_shifts.  X: N x k complex128 column-major over the batch rows
@@ -464,7 +476,8 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
 /* allocation-free entry point (no counterpart in the paper)                */
 /* ------------------------------------------------------------------------ */
 
-/* The same two-pass Gram-Schmidt as mor_orthonormalize, for callers that
+/* The same two-pass Gram-Schmidt as mor_orthonormalize (orth of Algorithm 2,
+ * line 6), for callers that
  * cannot let a library allocate device memory: frameworks whose own caching
  * allocator holds the whole device budget, real-time or embedded loops that
  * must keep a fixed memory map, and code that must not pay the implicit
