@@ -12,6 +12,7 @@
 // All host work is O(nnz) or O(sum |I_j|), multi-threaded where it matters.
 #include "mor_ctx.h"
 #include "mor_types.cuh"
+#include "host_pattern.h"
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -120,11 +121,11 @@ int mor_build_segments(mor_t h, const std::vector<int64_t>& rows) {
 
 namespace {
 
-struct HostCSR {
-  int64_t n = 0;
-  std::vector<int32_t> rowptr, col;
-  std::vector<double> val;
-};
+using mor_host::HostCSR;
+using mor_host::merge_pattern;
+using mor_host::transpose_pattern;
+using mor_host::shadow_sets;
+using mor_host::sell_layout;
 
 int fetch_csr(mor_t h, const mor_csr* M, bool dev, const char* name, HostCSR& out) {
   if (!M || M->n <= 0 || M->nnz < 0 || !M->rowptr || (M->nnz > 0 && (!M->col || !M->val)))
@@ -155,138 +156,6 @@ int fetch_csr(mor_t h, const mor_csr* M, bool dev, const char* name, HostCSR& ou
     }
   }
   return MOR_OK;
-}
-
-// merged pattern of A (+ E) + diagonal, values aligned
-void merge_pattern(const HostCSR& A, const HostCSR* E, HostCSR& S, std::vector<double>& sa, std::vector<double>& se) {
-  const int64_t n = A.n;
-  S.n = n;
-  S.rowptr.assign(n + 1, 0);
-  S.col.clear();
-  sa.clear();
-  se.clear();
-  S.col.reserve(A.col.size() + n + (E ? E->col.size() : 0));
-  sa.reserve(S.col.capacity());
-  if (E) se.reserve(S.col.capacity());
-  for (int64_t i = 0; i < n; ++i) {
-    int32_t pa = A.rowptr[i], ea = A.rowptr[i + 1];
-    int32_t pe = E ? E->rowptr[i] : 0, ee = E ? E->rowptr[i + 1] : 0;
-    bool diag_done = false;
-    while (pa < ea || pe < ee || !diag_done) {
-      int64_t ca = pa < ea ? A.col[pa] : INT64_MAX;
-      int64_t ce = pe < ee ? E->col[pe] : INT64_MAX;
-      int64_t cd = diag_done ? INT64_MAX : i;
-      int64_t c = std::min(ca, std::min(ce, cd));
-      double va = 0.0, ve = 0.0;
-      if (ca == c) { va = A.val[pa]; ++pa; }
-      if (ce == c) { ve = E->val[pe]; ++pe; }
-      if (cd == c) diag_done = true;
-      S.col.push_back((int32_t)c);
-      sa.push_back(va);
-      if (E) se.push_back(ve);
-    }
-    S.rowptr[i + 1] = (int32_t)S.col.size();
-  }
-}
-
-// transpose pattern; t2p[t] = position in S of the entry at T position t
-void transpose_pattern(const HostCSR& S, HostCSR& T, std::vector<int64_t>& t2p) {
-  const int64_t n = S.n, nnz = (int64_t)S.col.size();
-  T.n = n;
-  T.rowptr.assign(n + 1, 0);
-  for (int64_t p = 0; p < nnz; ++p) T.rowptr[S.col[p] + 1]++;
-  for (int64_t i = 0; i < n; ++i) T.rowptr[i + 1] += T.rowptr[i];
-  T.col.resize(nnz);
-  t2p.resize(nnz);
-  std::vector<int32_t> next(T.rowptr.begin(), T.rowptr.end() - 1);
-  for (int64_t i = 0; i < n; ++i)
-    for (int32_t p = S.rowptr[i]; p < S.rowptr[i + 1]; ++p) {
-      const int32_t t = next[S.col[p]]++;
-      T.col[t] = (int32_t)i;
-      t2p[t] = p;
-    }
-}
-
-// shadow sets: for column j of the operator whose columns are the rows of
-// `cols` (a CSR whose row j lists J_j), I_j = union over k in J_j of row k.
-void shadow_sets(const HostCSR& cols, std::vector<int64_t>& iptr, std::vector<int32_t>& iidx, int& nImax, int& nJmax) {
-  const int64_t n = cols.n;
-  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-  if (n < 20000) nt = 1;
-  std::vector<std::vector<int32_t>> parts(nt);
-  std::vector<std::vector<int32_t>> counts(nt);
-  std::vector<int> maxI(nt, 0);
-  auto work = [&](unsigned t) {
-    const int64_t j0 = n * t / nt, j1 = n * (t + 1) / nt;
-    std::vector<int64_t> stamp(n, -1);
-    std::vector<int32_t> buf;
-    auto& out = parts[t];
-    auto& cnt = counts[t];
-    cnt.reserve(j1 - j0);
-    for (int64_t j = j0; j < j1; ++j) {
-      buf.clear();
-      for (int32_t p = cols.rowptr[j]; p < cols.rowptr[j + 1]; ++p) {
-        const int32_t k = cols.col[p];
-        for (int32_t q = cols.rowptr[k]; q < cols.rowptr[k + 1]; ++q) {
-          const int32_t i = cols.col[q];
-          if (stamp[i] != j) { stamp[i] = j; buf.push_back(i); }
-        }
-      }
-      std::sort(buf.begin(), buf.end());
-      out.insert(out.end(), buf.begin(), buf.end());
-      cnt.push_back((int32_t)buf.size());
-      maxI[t] = std::max(maxI[t], (int)buf.size());
-    }
-  };
-  std::vector<std::thread> th;
-  for (unsigned t = 1; t < nt; ++t) th.emplace_back(work, t);
-  work(0);
-  for (auto& x : th) x.join();
-  iptr.assign(n + 1, 0);
-  int64_t j = 0;
-  for (unsigned t = 0; t < nt; ++t)
-    for (int32_t c : counts[t]) { iptr[j + 1] = iptr[j] + c; ++j; }
-  iidx.resize(iptr[n]);
-  int64_t off = 0;
-  for (unsigned t = 0; t < nt; ++t) {
-    std::memcpy(iidx.data() + off, parts[t].data(), parts[t].size() * sizeof(int32_t));
-    off += (int64_t)parts[t].size();
-  }
-  nImax = 0;
-  for (int x : maxI) nImax = std::max(nImax, x);
-  nJmax = 0;
-  for (int64_t jj = 0; jj < n; ++jj) nJmax = std::max(nJmax, cols.rowptr[jj + 1] - cols.rowptr[jj]);
-}
-
-// SELL-32 (sigma = 1) layout of a CSR pattern: slice offsets, padded columns,
-// and the map CSR position -> layout position.
-void sell_layout(const HostCSR& S, std::vector<int64_t>& sptr, std::vector<int32_t>& scol, std::vector<int64_t>& lay) {
-  const int64_t n = S.n;
-  const int64_t ns = (n + 31) / 32;
-  sptr.assign(ns + 1, 0);
-  for (int64_t s = 0; s < ns; ++s) {
-    int w = 0;
-    for (int64_t r = s * 32; r < std::min(n, s * 32 + 32); ++r) w = std::max(w, S.rowptr[r + 1] - S.rowptr[r]);
-    sptr[s + 1] = sptr[s] + 32LL * w;
-  }
-  scol.assign(sptr[ns], 0);
-  lay.resize(S.col.size());
-  for (int64_t s = 0; s < ns; ++s) {
-    const int64_t w = (sptr[s + 1] - sptr[s]) / 32;
-    for (int64_t l = 0; l < 32; ++l) {
-      const int64_t r = s * 32 + l;
-      for (int64_t t = 0; t < w; ++t) {
-        const int64_t pos = sptr[s] + 32 * t + l;
-        if (r < n && t < S.rowptr[r + 1] - S.rowptr[r]) {
-          const int64_t p = S.rowptr[r] + t;
-          scol[pos] = S.col[p];
-          lay[p] = pos;
-        } else {
-          scol[pos] = (int32_t)std::min<int64_t>(r, n - 1);   // padding: a valid index, value 0
-        }
-      }
-    }
-  }
 }
 
 template <class T>
