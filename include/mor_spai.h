@@ -73,6 +73,10 @@ enum mor_status {
 
 /* flags */
 #define MOR_DEVICE_PTRS 1u   /* array arguments of this call are device pointers */
+#define MOR_REAL_VECTORS 2u  /* mor_apply_operator / mor_apply_precond: compute
+                                in real arithmetic (FP64, or FP32 for MOR_MIXED)
+                                on the real parts of X; Y gets zero imaginary
+                                parts.  Needs real shifts (and a real chain). */
 
 /* precision of the Krylov arithmetic */
 enum mor_precision {
@@ -287,14 +291,16 @@ int mor_get_pattern(mor_t h, int transpose, int32_t* rowptr, int32_t* col);
  * + (1 + beta s) K for second-order ones (Algorithm 1, line 4, with Rayleigh
  * damping D = alpha M + beta K).  X, Y: n x k complex128, column-major.
  * precision MOR_MIXED computes in FP32/complex64 (inputs rounded), MOR_FP64
- * in FP64.  1 <= k <= 16. */
+ * in FP64 / complex128; with MOR_REAL_VECTORS in flags, real FP32 / FP64 on
+ * the real parts of X (real shifts only).  1 <= k <= 16. */
 int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int precision,
                        const mor_c64* X, mor_c64* Y, unsigned flags);
 
 /* Y(:, c) = P(sigma_c) X(:, c): the chain prefix that ends at the last
  * factor built for sigma_c (the whole chain when none was), applied factor
  * by factor in the chain's precision (Sec. III.B: Q_i ... Q_2 P_1 is applied
- * as successive mat-vecs, never formed; Algorithm 4).  Shapes as mor_apply_operator. */
+ * as successive mat-vecs, never formed; Algorithm 4).  Shapes and flags as
+ * mor_apply_operator (MOR_REAL_VECTORS needs real factors). */
 int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose,
                       const mor_c64* X, mor_c64* Y, unsigned flags);
 
@@ -460,6 +466,15 @@ int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const m
  * (graph replays count every kernel node they run).  Process-wide. */
 int mor_launch_count(int64_t* count);
 
+/* Launches of one SpMV kernel since the process started, by width:
+ *   which     0 operator SpMV, 1 preconditioner-factor SpMV;
+ *   vec_type  vector type: 0 FP32, 1 FP64, 2 complex64, 3 complex128;
+ *   counts    MOR_KMAX_COLS + 1 entries out; counts[k] = launches over k real
+ *             (non-padding) shift columns (graph replays count every
+ *             recorded launch).  Process-wide. */
+#define MOR_KMAX_COLS 16
+int mor_kernel_tally(int which, int vec_type, int64_t* counts);
+
 /* Time one hot-loop kernel of the solve exactly as the inner BiCGSTAB
  * iteration launches it, with CUDA events on the handle's stream:
  *   which = 0   operator SpMV  Y = A(sigma_c) X over k columns;
@@ -467,8 +482,10 @@ int mor_launch_count(int64_t* count);
  *               factor; requires a built preconditioner).
  * precision selects FP32/complex64 (MOR_MIXED) or FP64 vectors; complex
  * vectors are used when any sigma_c is complex.  `reps` launches are timed
- * after 3 untimed ones; *ms receives the mean duration of one launch.
- * The input vectors are resident device buffers of n x k entries. */
+ * after 3 untimed ones, each between its own pair of events and after a
+ * write of twice the L2 size (no launch finds the previous one's data in
+ * L2); *ms receives the mean duration of one launch.  The input vectors are
+ * resident device buffers of n x k entries. */
 int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precision, int reps,
                     double* ms);
 
@@ -482,7 +499,7 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
  * allocator holds the whole device budget, real-time or embedded loops that
  * must keep a fixed memory map, and code that must not pay the implicit
  * device synchronisation of cudaMalloc / cudaFree.  It needs no handle and
- * allocates nothing: its scratch is one fixed array of 311,808 bytes that
+ * allocates nothing: its scratch is one fixed array of 313,088 bytes that
  * the library reserves on every GPU that loads it, until the process exits.
  *   X       device pointer, n x k FP64, column-major, orthonormalised in
  *           place on the current CUDA device.

@@ -33,6 +33,7 @@ MOR_OK, MOR_EINVAL, MOR_ENOMEM, MOR_ECUDA, MOR_ENOCONV, MOR_EBREAKDOWN, MOR_ESIN
 STATUS_NAMES = {0: "MOR_OK", 1: "MOR_EINVAL", 2: "MOR_ENOMEM", 3: "MOR_ECUDA", 4: "MOR_ENOCONV",
                 5: "MOR_EBREAKDOWN", 6: "MOR_ESINGULAR", 7: "MOR_ETIMEOUT", 8: "MOR_ESTATE"}
 MOR_DEVICE_PTRS = 1
+MOR_REAL_VECTORS = 2
 MOR_FP64, MOR_MIXED = 0, 1
 MOR_BICGSTAB = 0
 MOR_GMRES = 1
@@ -142,6 +143,7 @@ SIGNATURES = {
     "mor_eval_tf2": (C.c_int, [_P, C.POINTER(mor_reduced2), _P, C.c_int, _P, C.c_uint]),
     "mor_eval_tf": (C.c_int, [_P, C.POINTER(mor_reduced), _P, C.c_int, _P, C.c_uint]),
     "mor_launch_count": (C.c_int, [C.POINTER(C.c_int64)]),
+    "mor_kernel_tally": (C.c_int, [C.c_int, C.c_int, _P]),
     "mor_time_kernel": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "mor_orthonormalize_noalloc": (C.c_int, [_P, C.c_int64, C.c_int, _P]),
     "mor_set_batch": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_int, C.c_uint]),
@@ -190,12 +192,43 @@ def _is_torch(x):
     return type(x).__module__.startswith("torch")
 
 
-def _ptr(x, dtype=None, fortran=True):
-    """(pointer, keep-alive object, is_device) for a NumPy array or torch tensor."""
+_HANDLE_DEVICE = {}        # handle address -> CUDA device it was created on
+
+
+def _check_cuda_tensor(x, dtype=None, rows=None, device=None):
+    """Reject a CUDA tensor whose dtype, device or layout differs from what
+    the C side will read through its raw pointer: an n x k block must be
+    column-major (stride (1, n); a single column needs only stride(0) == 1),
+    a vector contiguous."""
+    import torch
+    want = {np.dtype(np.float64): torch.float64, np.dtype(np.complex128): torch.complex128,
+            np.dtype(np.int32): torch.int32}.get(np.dtype(dtype)) if dtype is not None else None
+    if want is not None and x.dtype != want:
+        raise ValueError("device tensor has dtype %s, the library reads %s" % (x.dtype, want))
+    if device is not None and x.device.index != device:
+        raise ValueError("device tensor is on cuda:%s, the handle on cuda:%d" % (x.device.index, device))
+    if rows is not None and (x.dim() == 0 or x.shape[0] != rows):
+        raise ValueError("device tensor has %s rows, expected %d" % (tuple(x.shape)[:1], rows))
+    if x.dim() == 1:
+        if x.numel() > 1 and x.stride(0) != 1:
+            raise ValueError("device vector must be contiguous")
+    elif x.dim() == 2:
+        n, k = x.shape
+        if (n > 1 and x.stride(0) != 1) or (k > 1 and x.stride(1) != n):
+            raise ValueError("device block must be column-major n x k (stride (1, n))")
+    else:
+        raise ValueError("device tensor must be 1-D or 2-D")
+
+
+def _ptr(x, dtype=None, fortran=True, rows=None, device=None):
+    """(pointer, keep-alive object, is_device) for a NumPy array or torch tensor.
+    CUDA tensors are passed by address after a check of dtype, rows, device
+    and layout (see _check_cuda_tensor)."""
     if x is None:
         return None, None, False
     if _is_torch(x):
         if x.is_cuda:
+            _check_cuda_tensor(x, dtype, rows, device)
             return C.c_void_p(x.data_ptr()), x, True
         x = x.numpy()
     a = np.asarray(x, dtype=dtype)
@@ -252,11 +285,17 @@ def mor_create(device: int = 0, stream=None):
     code = lib.mor_create(C.byref(h), int(device), sp_)
     if code != MOR_OK:
         raise MorError(code, "mor_create failed")
+    _HANDLE_DEVICE[h.value] = int(device)
     return h
 
 
 def mor_destroy(h):
+    _HANDLE_DEVICE.pop(getattr(h, "value", None), None)
     return load_library().mor_destroy(h)
+
+
+def _hdev(h):
+    return _HANDLE_DEVICE.get(getattr(h, "value", None))
 
 
 def mor_last_error(h) -> str:
@@ -270,9 +309,11 @@ def mor_set_system(h, A, B, C_, E=None, E_diag=None, fmt: int = MOR_FMT_AUTO):
     lib = load_library()
     As, keepA = _csr_struct(A)
     Es, keepE = _csr_struct(E)
-    Bp, Bk, dev = _ptr(np.asarray(B).reshape(As.n, -1) if not _is_torch(B) else B, np.float64)
-    Cp, Ck, devc = _ptr(np.asarray(C_).reshape(As.n, -1) if not _is_torch(C_) else C_, np.float64)
-    Dp, Dk, devd = _ptr(E_diag, np.float64)
+    Bp, Bk, dev = _ptr(np.asarray(B).reshape(As.n, -1) if not _is_torch(B) else B, np.float64, rows=As.n,
+                       device=_hdev(h))
+    Cp, Ck, devc = _ptr(np.asarray(C_).reshape(As.n, -1) if not _is_torch(C_) else C_, np.float64, rows=As.n,
+                        device=_hdev(h))
+    Dp, Dk, devd = _ptr(E_diag, np.float64, rows=As.n, device=_hdev(h))
     if dev != devc or (E_diag is not None and devd != dev):
         raise ValueError("B, C and E_diag must all be host arrays or all device tensors")
     m = Bk.shape[1] if Bk.ndim == 2 else 1
@@ -355,30 +396,39 @@ def _nk_c128(X, n):
     return np.asfortranarray(X)
 
 
-def mor_apply_operator(h, sigma, X, transpose: int = 0, precision: int = MOR_FP64, Y=None):
+def mor_apply_operator(h, sigma, X, transpose: int = 0, precision: int = MOR_FP64, Y=None, real: bool = False):
     lib = load_library()
     n = mor_get_info(h)["n"]
     s, sp_ = _shifts(sigma)
     Xa = _nk_c128(X, n)
     k = Xa.shape[1]
     if Y is None:
-        Y = np.empty((n, k), dtype=np.complex128, order="F") if not _is_torch(Xa) else None
-    Xp, Xk, dev = _ptr(Xa)
-    Yp, Yk, _ = _ptr(Y) if not _is_torch(Y) else (C.c_void_p(Y.data_ptr()), Y, True)
+        if _is_torch(Xa) and Xa.is_cuda:
+            import torch
+            Y = torch.empty((k, n), dtype=torch.complex128, device=Xa.device).T    # column-major n x k
+        else:
+            Y = np.empty((n, k), dtype=np.complex128, order="F")
+    Xp, Xk, dev = _ptr(Xa, np.complex128, rows=n, device=_hdev(h))
+    Yp, Yk, devy = _ptr(Y, np.complex128, rows=n, device=_hdev(h))
+    if devy != dev:
+        raise ValueError("X and Y must both be host arrays or both device tensors")
+    if (Yk.shape[1] if Yk.ndim == 2 else 1) != k:
+        raise ValueError("Y must have k = %d columns" % k)
     _check(h, lib.mor_apply_operator(h, sp_, k, int(transpose), int(precision), Xp, Yp,
-                                     MOR_DEVICE_PTRS if dev else 0))
+                                     (MOR_DEVICE_PTRS if dev else 0) | (MOR_REAL_VECTORS if real else 0)))
     return Y if _is_torch(Y) else Yk
 
 
-def mor_apply_precond(h, sigma, X, transpose: int = 0):
+def mor_apply_precond(h, sigma, X, transpose: int = 0, real: bool = False):
     lib = load_library()
     n = mor_get_info(h)["n"]
     s, sp_ = _shifts(sigma)
     Xa = _nk_c128(X, n)
     k = Xa.shape[1]
     Y = np.empty((n, k), dtype=np.complex128, order="F")
-    Xp, Xk, dev = _ptr(Xa)
-    _check(h, lib.mor_apply_precond(h, sp_, k, int(transpose), Xp, Y.ctypes.data_as(C.c_void_p), 0))
+    Xp, Xk, dev = _ptr(Xa, np.complex128, rows=n, device=_hdev(h))
+    _check(h, lib.mor_apply_precond(h, sp_, k, int(transpose), Xp, Y.ctypes.data_as(C.c_void_p),
+                                    MOR_REAL_VECTORS if real else 0))
     return Y
 
 
@@ -393,7 +443,9 @@ def mor_solve_shifts(h, sigma, transpose: int = 0, opts: Optional[mor_solve_opts
     o = opts if opts is not None else mor_default_opts()
     Rp, Rk, dev = (None, None, False)
     if R is not None:
-        Rp, Rk, dev = _ptr(_nk_c128(R, n))
+        Rp, Rk, dev = _ptr(_nk_c128(R, n), np.complex128, rows=n, device=_hdev(h))
+        if (Rk.shape[1] if Rk.ndim == 2 else 1) != k:
+            raise ValueError("R must have k = %d columns" % k)
     if dev:
         import torch
         X = torch.empty((k, n), dtype=torch.complex128, device=R.device)   # column-major n x k
@@ -523,6 +575,19 @@ def mor_launch_count() -> int:
     return c.value
 
 
+VEC_F32, VEC_F64, VEC_C64, VEC_C128 = 0, 1, 2, 3
+
+
+def mor_kernel_tally(which: int, vec_type: int):
+    """Launches of the operator (which = 0) or factor (1) SpMV since the
+    process started, by number of real shift columns: array of 17 counts."""
+    out = np.zeros(17, dtype=np.int64)
+    code = load_library().mor_kernel_tally(int(which), int(vec_type), out.ctypes.data_as(C.c_void_p))
+    if code != MOR_OK:
+        raise MorError(code, "mor_kernel_tally")
+    return out
+
+
 def mor_time_kernel(h, which: int, sigma, precision: int = MOR_MIXED, reps: int = 20) -> float:
     """Mean duration (ms) of one hot-loop kernel launch (0 operator SpMV,
     1 preconditioner-factor SpMV) over k = len(sigma) columns, CUDA events on
@@ -540,9 +605,12 @@ def mor_orthonormalize_noalloc(X, stream=None) -> int:
     place on the current device.  Returns the status code (MOR_OK on success)."""
     if not _is_torch(X) or not X.is_cuda:
         raise ValueError("X must be a CUDA tensor")
+    import torch
+    if X.dim() != 2:
+        raise ValueError("X must be an n x k tensor")
     n, k = X.shape
-    if X.stride() != (1, n):
-        raise ValueError("X must be column-major (stride (1, n))")
+    # the C side works on the current device and reads n x k FP64, column-major
+    _check_cuda_tensor(X, np.float64, rows=n, device=torch.cuda.current_device())
     sp_ = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
     return load_library().mor_orthonormalize_noalloc(C.c_void_p(X.data_ptr()), int(n), int(k), sp_)
 

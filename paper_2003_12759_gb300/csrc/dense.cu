@@ -304,34 +304,34 @@ int dense_launch_gram(int n, int a, int b, const double* X, int64_t ldx, const d
   if (a < 1 || b < 1 || a + b > GRAM_MAXC || a * b > 1024) return (int)cudaErrorInvalidValue;
   if (b <= 2 && a <= 64) {
     // counter[0 .. ceil(a / 8) - 1] are the column groups' tickets
-    dim3 g((unsigned)std::max(1, std::min(grid_cap / 2, (n + 255) / 256)), (unsigned)((a + 7) / 8));
+    dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_cap / 2, ((int64_t)n + 255) / 256)), (unsigned)((a + 7) / 8));
     if (b == 1) gram_skinny_kernel<1><<<g, 256, 0, s>>>(n, a, X, ldx, Y, ldy, out, part, counter);
     else gram_skinny_kernel<2><<<g, 256, 0, s>>>(n, a, X, ldx, Y, ldy, out, part, counter);
     mor_count_launches(1);
     return (int)cudaGetLastError();
   }
-  int blocks = (n + GRAM_TR - 1) / GRAM_TR;
+  int64_t blocks = ((int64_t)n + GRAM_TR - 1) / GRAM_TR;
   if (blocks > grid_cap) blocks = grid_cap;
   if (blocks < 1) blocks = 1;
-  gram_kernel<<<blocks, 256, 0, s>>>(n, a, b, X, ldx, Y, ldy, out, part, counter);
+  gram_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, a, b, X, ldx, Y, ldy, out, part, counter);
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
 int dense_launch_gs_update(int n, int j, const double* V, int64_t ldv, const double* h, double* v, cudaStream_t s) {
-  gs_update_kernel<<<grid_for(n, 152 * 8), 256, 0, s>>>(n, j, V, ldv, h, v);
+  gs_update_kernel<<<grid_for(n, mor_device_sms() * 8), 256, 0, s>>>(n, j, V, ldv, h, v);
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
 int dense_launch_scale(int n, double* v, const double* nrm2, cudaStream_t s) {
-  scale_kernel<<<grid_for(n, 152 * 8), 256, 0, s>>>(n, v, nrm2);
+  scale_kernel<<<grid_for(n, mor_device_sms() * 8), 256, 0, s>>>(n, v, nrm2);
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 
 int dense_launch_diag_mul(int n, int k, const double* d, const double* X, double* Y, cudaStream_t s) {
-  diag_mul_kernel<<<grid_for((int64_t)n * k, 152 * 8), 256, 0, s>>>(n, k, d, X, Y);
+  diag_mul_kernel<<<grid_for((int64_t)n * k, mor_device_sms() * 8), 256, 0, s>>>(n, k, d, X, Y);
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }

@@ -307,6 +307,20 @@ __global__ void scatter_cols_kernel(int64_t n, int ld_src, int ld_dst, int ncols
 
 size_t krylov_state_bytes(int) { return sizeof(KState); }
 
+int mor_device_sms() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  cache[dev] = sms;
+  return sms;
+}
+
 SegView fit_grid(const SegView& sg, const void* kern, int tpr) {
   if (sg.nseg != 1) return sg;
   static std::mutex mu;
@@ -430,26 +444,26 @@ int refine_launch_update(int st_in, const SegView& sg, int ld, void* x64, const 
 }
 
 int conv_launch_colmajor_c128_to_rowmajor(int st, int n, int k, int ld, const void* src, void* dst, cudaStream_t s) {
-  const int g = grid_for((int64_t)n * k, 152 * 8);
+  const int g = grid_for((int64_t)n * k, mor_device_sms() * 8);
   ST_SWITCH(st, (c128_col_to_row_kernel<S><<<g, 256, 0, s>>>(n, k, ld, (const cdouble*)src, (S*)dst)));
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 int conv_launch_rowmajor_to_colmajor_c128(int st, int n, int k, int ld, const void* src, void* dst, cudaStream_t s) {
-  const int g = grid_for((int64_t)n * k, 152 * 8);
+  const int g = grid_for((int64_t)n * k, mor_device_sms() * 8);
   ST_SWITCH(st, (row_to_c128_col_kernel<S><<<g, 256, 0, s>>>(n, k, ld, (const S*)src, (cdouble*)dst)));
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 int conv_launch_real_col_to_rowmajor(int st, int n, int k, int ld, const double* src, int64_t lds, void* dst,
                                      cudaStream_t s) {
-  const int g = grid_for((int64_t)n * k, 152 * 8);
+  const int g = grid_for((int64_t)n * k, mor_device_sms() * 8);
   ST_SWITCH(st, (real_col_to_row_kernel<S><<<g, 256, 0, s>>>(n, k, ld, src, lds, (S*)dst)));
   mor_count_launches(1);
   return (int)cudaGetLastError();
 }
 int conv_launch_copy_cast(int st_dst, int st_src, int64_t count, const void* src, void* dst, cudaStream_t s) {
-  const int g = grid_for(count, 152 * 8);
+  const int g = grid_for(count, mor_device_sms() * 8);
   if (st_src == ST_F64 && st_dst == ST_F32) copy_cast_kernel<float, double><<<g, 256, 0, s>>>(count, (const double*)src, (float*)dst);
   else if (st_src == ST_C64 && st_dst == ST_C32) copy_cast_kernel<cfloat, cdouble><<<g, 256, 0, s>>>(count, (const cdouble*)src, (cfloat*)dst);
   else if (st_src == ST_F32 && st_dst == ST_C64) copy_cast_kernel<cdouble, float><<<g, 256, 0, s>>>(count, (const float*)src, (cdouble*)dst);
@@ -467,7 +481,7 @@ int conv_launch_copy_cast(int st_dst, int st_src, int64_t count, const void* src
 
 int conv_launch_gather_cols(int st, int64_t n, int ld_src, int ld_dst, int ncols, const int* map, const void* src,
                             void* dst, cudaStream_t s) {
-  const int g = grid_for(n * ld_dst, 152 * 8);
+  const int g = grid_for(n * ld_dst, mor_device_sms() * 8);
   const size_t es = st_size(st);
   if (es == 4) gather_cols_kernel<uint32_t><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, map, (const uint32_t*)src, (uint32_t*)dst);
   else if (es == 8) gather_cols_kernel<uint2><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, map, (const uint2*)src, (uint2*)dst);
@@ -478,7 +492,7 @@ int conv_launch_gather_cols(int st, int64_t n, int ld_src, int ld_dst, int ncols
 
 int conv_launch_scatter_cols(int st, int64_t n, int ld_src, int ld_dst, int ncols, const int* smap, const int* dmap,
                              const void* src, void* dst, cudaStream_t s) {
-  const int g = grid_for(n * ncols, 152 * 8);
+  const int g = grid_for(n * ncols, mor_device_sms() * 8);
   const size_t es = st_size(st);
   if (es == 4) scatter_cols_kernel<uint32_t><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, smap, dmap, (const uint32_t*)src, (uint32_t*)dst);
   else if (es == 8) scatter_cols_kernel<uint2><<<g, 256, 0, s>>>(n, ld_src, ld_dst, ncols, smap, dmap, (const uint2*)src, (uint2*)dst);

@@ -86,7 +86,7 @@ struct SolveLane {
 
 struct mor_ctx {
   int dev = 0;
-  int sm_count = 152;
+  int sm_count = 1;          // set from the device at mor_create
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::string err;
@@ -106,7 +106,7 @@ struct mor_ctx {
   DBuf ws_io;       // API conversions
   void* pinned = nullptr;   // small pinned host buffer
   size_t pinned_bytes = 0;
-  int grid_cap = 152 * 8;
+  int grid_cap = 8;          // sm_count * 8, set at mor_create
   // segment table: one segment per independent system (1 for mor_set_system)
   DBuf seg_blk0, seg_row0, seg_counters, seg_live;
   SegView seg{};

@@ -50,35 +50,30 @@ enum {
 };
 
 // ---------------------------------------------------------------------------
-// Row layout of the n x k blocks of a solve: row-major with a padded stride ld
-// (the k columns of one row contiguous, ld - k dummy columns kept at zero), so
-// that rows are whole 16-byte vectors.  A row is handled by `tpr` lanes, each
-// owning `cpt` consecutive columns (one 16-byte vector load when cpt * size =
-// 16).  Narrow rows (ld * size < 16) use one thread per row.
+// Row layout of the n x k blocks of a solve: row-major with stride ld (the k
+// columns of one row contiguous).  A row of at least 16 bytes is a whole
+// number of 16-byte vectors: ld = ceil(k / c) c with c = 16 / size (only FP32
+// rows of k = 5..7, 9..11, 13..15 and FP64 / complex64 rows of odd k carry
+// dummy columns, kept at zero).  Lane `sub` of the tpr lanes of a row owns the
+// cpt = c consecutive columns sub * c ... (one 16-byte load or store); tpr is
+// ld / c rounded up to a power of two so that a warp holds whole rows, and the
+// lanes past the row's last vector stay idle.  Narrow rows (k * size < 16)
+// use one thread per row.
 inline int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
 inline bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
-// Padded row stride for k columns of type st.  Rows of whole 16-byte vectors
-// over a power-of-two number of lanes when that wastes little; otherwise (k <=
-// 8) one thread per row over the unpadded row; wider rows pad to 16 bytes x
-// a power of two.
 inline int row_stride(int st, int k) {
   const int es = (int)st_size(st);
   if (k * es < 16) return k;
   const int c = 16 / es;
-  const int t = (k + c - 1) / c;
-  if (is_pow2(t)) return t * c;
-  if (k <= 8) return k;
-  return next_pow2(t) * c;
+  return (k + c - 1) / c * c;
 }
 // Lanes per row (tpr) and columns per lane (cpt) for rows of stride ld.
 inline void lane_shape(int st, int ld, int* tpr, int* cpt) {
   const int es = (int)st_size(st);
   if (ld * es < 16) { *tpr = 1; *cpt = ld; return; }
   const int c = 16 / es;
-  if (ld % c == 0 && is_pow2(ld / c)) { *cpt = c; *tpr = ld / c; return; }
-  if (ld <= 8) { *tpr = 1; *cpt = ld; return; }
-  *cpt = 1;
-  *tpr = next_pow2(ld);
+  *cpt = c;
+  *tpr = next_pow2((ld + c - 1) / c);
 }
 
 #define MOR_LDMAX 16
@@ -142,15 +137,16 @@ int gmres_launch_begin(int ld, const void* sums, void* state, const double* targ
 int gmres_launch_solve_y(int ld, int m, void* state, const void* H, void* ycoef, cudaStream_t s);
 
 // Launchers (spmv.cu).  x, y, w, b: n x ld row-major blocks of type st.
+// kreal: real (non-dummy) columns of the block, for the launch tally (-1: ld)
 int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
-                   const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s);
+                   const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s, int kreal = -1);
 // fst: scalar type of the factor values (FP32 factors may serve FP64 vectors).
 // kstate (nullable): the per-(segment, column) Krylov states of the solve the
 // factor is applied in; lanes whose columns have all stopped skip their rows
 // (their rows of y are left as they were).
 int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals,
                        const int* apply, int ld, const void* x, void* y, const int* done,
-                       const void* kstate, cudaStream_t s);
+                       const void* kstate, cudaStream_t s, int kreal = -1);
 
 // Krylov helpers (krylov.cu)
 int krylov_launch_update_p(int st, const SegView& sg, int ld, const void* r, void* p, const void* v,
@@ -245,7 +241,16 @@ int dense_launch_tf(int r, int m, int q, const double* Ar, const double* Er, con
 int dense_launch_diag_mul(int n, int k, const double* d, const double* X, double* Y,
                           cudaStream_t s);
 
+// SMs of the current CUDA device (queried once per device)
+int mor_device_sms();
+
 // process-wide count of executed kernels (see mor_launch_count)
 void mor_count_launches(int64_t n);
 // on = 1 while this thread records a CUDA graph (its launches are counted per replay)
 void mor_capture_mark(int on);
+// SpMV launch tally (see mor_kernel_tally): kernel 0 operator, 1 factor; st the
+// vector type; kreal the real (non-dummy) columns of the block
+struct ShapeTally { int64_t c[2][4][MOR_KMAX + 1] = {}; };
+void mor_tally(int kernel, int st, int kreal, int64_t n = 1);
+ShapeTally mor_capture_tally();               // what the current capture recorded
+void mor_replay_tally(const ShapeTally& t);   // one replay of a captured graph

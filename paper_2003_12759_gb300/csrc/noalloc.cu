@@ -12,17 +12,22 @@
 // held by every GPU that loads it until the process exits.
 #include "mor_spai.h"
 #include "mor_internal.h"
+#include <algorithm>
 #include <mutex>
 
 namespace {
 
 constexpr int NA_MAXK = 64;              // widest block accepted
-constexpr int NA_GRID = 608;             // Gram-kernel blocks (4 per SM on 152 SMs)
+// Gram-kernel grid cap: 4 blocks per SM of the device, at most NA_GRID (the
+// capacity of the partials region; the skinny Gram kernel uses at most
+// NA_GRID / 2 blocks per group of 8 columns, 8 groups, 8 partials each)
+constexpr int NA_GRID = 608;
 constexpr size_t NA_H = 0;                               // Gram-Schmidt coefficients (64)
 constexpr size_t NA_NORMS = 64;                          // per-column norms (2 x 64)
 constexpr size_t NA_PART = NA_NORMS + 2 * NA_MAXK;       // block partials (NA_GRID x 64)
 constexpr size_t NA_CNT = NA_PART + (size_t)NA_GRID * NA_MAXK;   // block counters (8 words used)
-constexpr size_t NA_DOUBLES = NA_CNT + 32;               // 311,808 bytes in total
+constexpr size_t NA_DOUBLES = NA_CNT + 32;               // 39,136 doubles = 313,088 bytes in total
+static_assert(NA_DOUBLES * sizeof(double) == 313088, "scratch size stated in the header");
 
 __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
 
@@ -46,6 +51,9 @@ extern "C" int mor_orthonormalize_noalloc(double* X, int64_t n, int k, void* str
     base = g_addr[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return MOR_ECUDA;
+  const int grid_cap = std::min(NA_GRID, 4 * sms);
   double* hbuf = base + NA_H;
   double* norms = base + NA_NORMS;
   double* part = base + NA_PART;
@@ -56,10 +64,10 @@ extern "C" int mor_orthonormalize_noalloc(double* X, int64_t n, int k, void* str
   for (int j = 0; j < k; ++j) {
     double* v = X + (size_t)j * n;
     for (int pass = 0; pass < 2 && j > 0; ++pass) {
-      if (dense_launch_gram((int)n, j, 1, X, n, v, n, hbuf, part, counter, NA_GRID, s)) return MOR_ECUDA;
+      if (dense_launch_gram((int)n, j, 1, X, n, v, n, hbuf, part, counter, grid_cap, s)) return MOR_ECUDA;
       if (dense_launch_gs_update((int)n, j, X, n, hbuf, v, s)) return MOR_ECUDA;
     }
-    if (dense_launch_gram((int)n, 1, 1, v, n, v, n, norms + j, part, counter, NA_GRID, s)) return MOR_ECUDA;
+    if (dense_launch_gram((int)n, 1, 1, v, n, v, n, norms + j, part, counter, grid_cap, s)) return MOR_ECUDA;
     if (dense_launch_scale((int)n, v, norms + j, s)) return MOR_ECUDA;
   }
   return MOR_OK;

@@ -27,7 +27,26 @@ static std::atomic<long long> g_launches{0};
 // launches recorded into a CUDA graph are counted when the graph is replayed
 static thread_local int t_capturing = 0;
 void mor_count_launches(int64_t n) { if (!t_capturing) g_launches += n; }
-void mor_capture_mark(int on) { t_capturing = on; }
+// SpMV launches by (kernel, vector type, real columns): process-wide, and the
+// part recorded into the graph this thread is capturing
+static std::atomic<long long> g_tally[2][4][MOR_KMAX + 1];
+static thread_local ShapeTally t_cap_tally;
+void mor_capture_mark(int on) {
+  t_capturing = on;
+  if (on) t_cap_tally = ShapeTally{};
+}
+void mor_tally(int kernel, int st, int kreal, int64_t n) {
+  if (kernel < 0 || kernel > 1 || st < 0 || st > 3 || kreal < 0 || kreal > MOR_KMAX) return;
+  if (t_capturing) t_cap_tally.c[kernel][st][kreal] += n;
+  else g_tally[kernel][st][kreal] += n;
+}
+ShapeTally mor_capture_tally() { return t_cap_tally; }
+void mor_replay_tally(const ShapeTally& t) {
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c <= MOR_KMAX; ++c)
+        if (t.c[a][b][c]) g_tally[a][b][c] += t.c[a][b][c];
+}
 
 int mor_fail(mor_t h, int code, const char* fmt, ...) {
   if (h) {
@@ -470,6 +489,12 @@ int mor_destroy(mor_t h) {
 int mor_launch_count(int64_t* count) {
   if (!count) return MOR_EINVAL;
   *count = (int64_t)g_launches.load();
+  return MOR_OK;
+}
+
+int mor_kernel_tally(int which, int vec_type, int64_t* counts) {
+  if (which < 0 || which > 1 || vec_type < 0 || vec_type > 3 || !counts) return MOR_EINVAL;
+  for (int k = 0; k <= MOR_KMAX; ++k) counts[k] = (int64_t)g_tally[which][vec_type][k].load();
   return MOR_OK;
 }
 

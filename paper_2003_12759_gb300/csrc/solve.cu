@@ -261,7 +261,10 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
   // first, so after compaction the chain is applied only as far as the
   // remaining columns need (no copy-through launches for the dropped ones).
   int Lcur = Lmax;
+  int kreal = k;                             // real columns in the current geometry (launch tally)
   auto upload_masks = [&]() -> int {
+    kreal = 0;
+    for (int c = 0; c < ldc; ++c) kreal += (cmap[c] >= 0 && cmap[c] < k) ? 1 : 0;
     if (Lmax == 0) return 0;
     int lc = 0;
     for (int c = 0; c < ldc; ++c)
@@ -282,7 +285,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
       void* dd2 = (f == Lcur - 1) ? dst : ((f % 2 == 0) ? t0 : t1);
       const Factor& F = op.chain[f];
       int e = launch_factor_spmv(st_in, F.st, sg, pv, F.vals->p, sm.masks + (size_t)f * MOR_KMAX, ldc, s,
-                                 dd2, dn, ks, ln.stream);
+                                 dd2, dn, ks, ln.stream, kreal);
       if (e) return e;
       s = dd2;
     }
@@ -297,11 +300,11 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
     if ((e = krylov_launch_update_p(st_in, sg, ldc, rr, pp, vv, kstate, sm.done, ln.stream))) return e;
     if ((e = chain_apply(pp, pph))) return e;
     RedArgs ra{RED_DOT_W, rh, ln.ws_part.p, nullptr, FIN_ALPHA, kstate, nullptr, sm.done};
-    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, phat, vv, nullptr, &ra, ln.stream))) return e;
+    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, phat, vv, nullptr, &ra, ln.stream, kreal))) return e;
     if ((e = krylov_launch_update_s(st_in, sg, ldc, rr, vv, ssv, kstate, sm.done, ln.stream))) return e;
     if ((e = chain_apply(ssv, ssh))) return e;
     RedArgs rb{RED_DOT_TT, ssv, ln.ws_part.p, nullptr, FIN_OMEGA, kstate, nullptr, sm.done};
-    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, shat, tt, nullptr, &rb, ln.stream))) return e;
+    if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cfc, ldc, shat, tt, nullptr, &rb, ln.stream, kreal))) return e;
     if ((e = krylov_launch_update_xr(st_in, sg, ldc, dd, rr, phat, shat, ssv, tt, rh, ln.ws_part.p, kstate, sm.done,
                                      ln.stream)))
       return e;
@@ -310,6 +313,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
   const int chunk = std::max(1, o.graph_chunk);
   cudaGraphExec_t gexec = nullptr;
   int64_t graph_nodes = 0;
+  ShapeTally graph_tally;
   auto drop_graph = [&]() { if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; } };
   struct GraphGuard { std::function<void()> f; ~GraphGuard() { f(); } } guard{drop_graph};
   auto capture = [&]() -> int {
@@ -320,6 +324,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
     mor_capture_mark(1);
     int e = 0;
     for (int it = 0; it < chunk && !e; ++it) e = one_iter();
+    graph_tally = mor_capture_tally();
     mor_capture_mark(0);
     cudaError_t ce = cudaStreamEndCapture(ln.stream, &g);
     graph_nodes = (ce == cudaSuccess && g) ? kernel_nodes(g) : 0;
@@ -380,7 +385,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
     RedArgs none{RED_NONE, nullptr, nullptr, nullptr, 0, nullptr, nullptr, done_cycle};
     auto start_cycle = [&](int first) -> int {
       int e;
-      if ((e = launch_op_spmv(st_in, sg, pv, ov_in, ncf, ld, xin, W, rhs, &rn, ln.stream))) return e;
+      if ((e = launch_op_spmv(st_in, sg, pv, ov_in, ncf, ld, xin, W, rhs, &rn, ln.stream, k))) return e;
       if ((e = gmres_launch_begin(ld, d_sums, gst, d_target, d_maxit, d_active, first, done_cycle, done_all,
                                   ln.stream)))
         return e;
@@ -394,7 +399,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
           if ((e = chain_apply_d(V(j), Z, done_cycle))) return e;
           src = Z;
         }
-        if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cf, ld, src, W, nullptr, &none, ln.stream))) return e;
+        if ((e = launch_op_spmv(st_in, sg, pv, ov_in, cf, ld, src, W, nullptr, &none, ln.stream, k))) return e;
         if ((e = gmres_launch_dot(st_in, sg, ld, V(0), vst, j + 1, W, gpart, gcnt, h1, done_cycle, ln.stream))) return e;
         if ((e = gmres_launch_axpy(st_in, sg, ld, V(0), vst, j + 1, h1, W, 0, 0, gpart, gcnt, gst, Hm, m, h1, h2,
                                    done_cycle, ln.stream)))
@@ -421,11 +426,13 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
     cudaGraphExec_t gx = nullptr;
     struct GxGuard { cudaGraphExec_t* g; ~GxGuard() { if (*g) cudaGraphExecDestroy(*g); } } gxg{&gx};
     int64_t gnodes = 0;
+    ShapeTally gm_tally;
     if (o.use_graph) {
       cudaGraph_t g = nullptr;
       MOR_CK(h, cudaStreamBeginCapture(ln.stream, cudaStreamCaptureModeThreadLocal));
       mor_capture_mark(1);
       const int e = cycle();
+      gm_tally = mor_capture_tally();
       mor_capture_mark(0);
       const cudaError_t ce = cudaStreamEndCapture(ln.stream, &g);
       gnodes = (ce == cudaSuccess && g) ? kernel_nodes(g) : 0;
@@ -445,6 +452,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
       if (gx) {
         MOR_CK(h, cudaGraphLaunch(gx, ln.stream));
         mor_count_launches(gnodes);
+        mor_replay_tally(gm_tally);
       } else {
         MOR_CKI(h, cycle());
       }
@@ -464,7 +472,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
   for (int pass = 0;; ++pass) {
     // true residual r64 = b - A(sigma) x64 in FP64 with fused norms, per (system, column)
     RedArgs rn{RED_NORM, nullptr, ln.ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
-    MOR_CKI(h, launch_op_spmv(st64, sg, pv, ov64, ncf, ld, io.x64, r64, io.b64, &rn, ln.stream));
+    MOR_CKI(h, launch_op_spmv(st64, sg, pv, ov64, ncf, ld, io.x64, r64, io.b64, &rn, ln.stream, k));
     MOR_CK(h, cudaMemcpyAsync(h_sums, d_sums, sizeof(cdouble) * 2 * nsc, cudaMemcpyDeviceToHost, ln.stream));
     MOR_CK(h, cudaStreamSynchronize(ln.stream));
     int nact = 0;
@@ -536,6 +544,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
         if (gexec) {
           MOR_CK(h, cudaGraphLaunch(gexec, ln.stream));
           mor_count_launches(graph_nodes);
+          mor_replay_tally(graph_tally);
           it += chunk;
         } else {
           MOR_CKI(h, one_iter());
@@ -552,8 +561,14 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
         int nlive = 0;
         for (int c = 0; c < ldc; ++c) nlive += krylov_state_active(kst_host.data() + ksb * c) ? 1 : 0;
         if (nlive == 0) break;
+        // repack when the live columns fit rows at least a quarter narrower or
+        // half as many lanes (a repack and a graph capture cost about as much
+        // as a few iterations)
         const int ld_new = row_stride(st_in, nlive);
-        if (ld_new >= ldc || it >= maxrem) continue;
+        int tpr_old = 1, tpr_new = 1, cpt_ = 1;
+        lane_shape(st_in, ldc, &tpr_old, &cpt_);
+        lane_shape(st_in, ld_new, &tpr_new, &cpt_);
+        if (ld_new >= ldc || it >= maxrem || (4 * ld_new > 3 * ldc && tpr_new >= tpr_old)) continue;
         // ---- compaction: flush dropped real columns, repack the live ones
         std::vector<int> live, drop_src, drop_dst;
         for (int c = 0; c < ldc; ++c) {
@@ -945,9 +960,13 @@ int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int 
   if (k < 1 || k > MOR_KMAX || !sigma || !X || !Y) return mor_fail(h, MOR_EINVAL, "bad arguments");
   cudaSetDevice(h->dev);
   const bool dev = flags & MOR_DEVICE_PTRS;
+  const bool real = flags & MOR_REAL_VECTORS;
+  if (real)
+    for (int c = 0; c < k; ++c)
+      if (!is_real_shift(sigma[c])) return mor_fail(h, MOR_EINVAL, "MOR_REAL_VECTORS needs real shifts");
   OpData& op = h->op(transpose);
   const int64_t n = h->n;
-  const int st = (precision == MOR_FP64) ? ST_C64 : ST_C32;
+  const int st = (precision == MOR_FP64) ? (real ? ST_F64 : ST_C64) : (real ? ST_F32 : ST_C32);
   const int ld = row_stride(st, k);
   MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * (k + 2 * ld)));
   mor_c64* io = h->ws_io.as<mor_c64>();
@@ -963,7 +982,7 @@ int mor_apply_operator(mor_t h, const mor_c64* sigma, int k, int transpose, int 
   Coef cf[MOR_LDMAX];
   for (int c = 0; c < ld; ++c) cf[c] = mor_coef(h, sigma[c < k ? c : 0]);
   MOR_CKI(h, launch_op_spmv(st, h->seg, op.view(), op_vals(h, op, precision != MOR_FP64), cf, ld, xr, yr, nullptr,
-                            nullptr, h->stream));
+                            nullptr, h->stream, k));
   if (dev) {
     MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(st, (int)n, k, ld, yr, Y, h->stream));
   } else {
@@ -983,11 +1002,15 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   if (op.chain.empty()) return mor_fail(h, MOR_ESTATE, "no preconditioner built");
   cudaSetDevice(h->dev);
   const bool dev = flags & MOR_DEVICE_PTRS;
+  const bool real = flags & MOR_REAL_VECTORS;
   const int64_t n = h->n;
-  const int st = (op.chain_prec == MOR_FP64) ? ST_C64 : ST_C32;
+  const int st = (op.chain_prec == MOR_FP64) ? (real ? ST_F64 : ST_C64) : (real ? ST_F32 : ST_C32);
   std::vector<int> L = prefix_lengths(op, sigma, k);
   int Lmax = 0;
   for (int x : L) Lmax = std::max(Lmax, x);
+  if (real)
+    for (int f = 0; f < Lmax; ++f)
+      if (st_is_cplx(op.chain[f].st)) return mor_fail(h, MOR_EINVAL, "MOR_REAL_VECTORS with a complex chain factor");
   const int ld = row_stride(st, k);
   MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * (k + 2 * ld)));
   mor_c64* io = h->ws_io.as<mor_c64>();
@@ -1010,7 +1033,7 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   char* d = b;
   for (int f = 0; f < Lmax; ++f) {
     MOR_CKI(h, launch_factor_spmv(st, op.chain[f].st, h->seg, op.view(), op.chain[f].vals->p,
-                                  sm.masks + (size_t)f * MOR_KMAX, ld, s, d, nullptr, nullptr, h->stream));
+                                  sm.masks + (size_t)f * MOR_KMAX, ld, s, d, nullptr, nullptr, h->stream, k));
     std::swap(s, d);
   }
   if (dev) {
@@ -1700,26 +1723,36 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
   MOR_CK(h, h->ws_sums.alloc(sizeof(cdouble) * 2 * (size_t)h->seg.nseg * MOR_LDMAX));
   RedArgs ra{RED_DOT_W, w.p, h->ws_part.p, nullptr, FIN_NONE, nullptr, h->ws_sums.p, nullptr};
   auto launch = [&]() -> int {
-    if (which == 0) return launch_op_spmv(st, h->seg, pv, ov, cf, ld, x.p, y.p, nullptr, &ra, h->stream);
+    if (which == 0) return launch_op_spmv(st, h->seg, pv, ov, cf, ld, x.p, y.p, nullptr, &ra, h->stream, k);
     return launch_factor_spmv(st, op.chain.back().st, h->seg, pv, op.chain.back().vals->p, sm.masks, ld,
-                              x.p, y.p, nullptr, nullptr, h->stream);
+                              x.p, y.p, nullptr, nullptr, h->stream, k);
   };
+  // L2 is flushed before every timed launch (a write of twice its size), and
+  // each launch is bracketed by its own events, so that no launch finds the
+  // previous one's matrix or vectors in L2
+  int l2 = 0;
+  MOR_CK(h, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->dev));
+  DBuf flush;
+  const size_t fbytes = std::max<size_t>((size_t)2 * (size_t)l2, (size_t)64 << 20);
+  MOR_CK(h, flush.alloc(fbytes));
   for (int i = 0; i < 3; ++i) MOR_CKI(h, launch());
-  cudaEvent_t e0, e1;
-  MOR_CK(h, cudaEventCreate(&e0));
-  MOR_CK(h, cudaEventCreate(&e1));
-  cudaEventRecord(e0, h->stream);
+  std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
+  struct EvVec { std::vector<cudaEvent_t>* v; ~EvVec() { for (auto e : *v) if (e) cudaEventDestroy(e); } } evg{&ev};
+  for (auto& e : ev) MOR_CK(h, cudaEventCreate(&e));
   for (int i = 0; i < reps; ++i) {
-    int e = launch();
-    if (e) { cudaEventDestroy(e0); cudaEventDestroy(e1); MOR_CKI(h, e); }
+    MOR_CK(h, cudaMemsetAsync(flush.p, i & 0xff, fbytes, h->stream));
+    MOR_CK(h, cudaEventRecord(ev[2 * i], h->stream));
+    MOR_CKI(h, launch());
+    MOR_CK(h, cudaEventRecord(ev[2 * i + 1], h->stream));
   }
-  cudaEventRecord(e1, h->stream);
-  cudaEventSynchronize(e1);
-  float t = 0.f;
-  cudaEventElapsedTime(&t, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  *ms = (double)t / reps;
+  MOR_CK(h, cudaEventSynchronize(ev.back()));
+  double tot = 0.0;
+  for (int i = 0; i < reps; ++i) {
+    float t = 0.f;
+    MOR_CK(h, cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+    tot += t;
+  }
+  *ms = tot / reps;
   return MOR_OK;
 }
 

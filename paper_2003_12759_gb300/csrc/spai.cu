@@ -242,9 +242,7 @@ int spai_launch(const SpaiArgs& a, const ColData<V>& cd, void* out, cudaStream_t
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spai_kernel<S, V, LPC>, nw * 32, sm);
   if (e != cudaSuccess || occ < 1) occ = 1;
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = mor_device_sms();
   const int64_t per_block = (int64_t)nw * CPW;
   int64_t blocks = ((int64_t)a.n + per_block - 1) / per_block;
   blocks = std::min<int64_t>(blocks, (int64_t)sms * occ);

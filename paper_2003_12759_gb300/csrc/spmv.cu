@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
 }  // namespace
 
 int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,
-                   const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s) {
+                   const void* x, void* y, const void* b, const RedArgs* red, cudaStream_t s, int kreal) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
   RedArgs ra;
   if (red) ra = *red;
@@ -328,11 +328,13 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
   });
   if (e) return e;
   mor_count_launches(1);
+  mor_tally(0, st, kreal < 0 ? ld : kreal);
   return (int)cudaGetLastError();
 }
 
 int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
-                       int ld, const void* x, void* y, const int* done, const void* kstate, cudaStream_t s) {
+                       int ld, const void* x, void* y, const int* done, const void* kstate, cudaStream_t s,
+                       int kreal) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
   const bool fc = st_is_cplx(fst), f32 = st_is_f32(fst);
   int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
@@ -360,5 +362,6 @@ int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, co
   });
   if (e) return e;
   mor_count_launches(1);
+  mor_tally(1, st, kreal < 0 ? ld : kreal);
   return (int)cudaGetLastError();
 }

@@ -1,10 +1,12 @@
 """The row layout rule of the lock-step blocks (csrc/mor_internal.h:
-row_stride pads k shift columns to a stride ld whose row is a whole number
-of 16-byte vectors, lane_shape spreads a row over a power-of-two number of
-lanes) compiled with g++ and checked for every scalar type and every k the
-library batches (1..16): ld >= k, ld fits the 16-column limit, padded rows
-are whole 16-byte vectors, the lanes of a row stay inside one warp and cover
-the row exactly (or one column per lane).  No GPU."""
+row_stride pads k shift columns to the next whole 16-byte vector, lane_shape
+gives each lane one 16-byte vector and a row a power-of-two number of lanes,
+the last ones idle) compiled with g++ and checked for every scalar type and
+every k the library batches (1..16): ld >= k, ld fits the 16-column limit,
+rows of 16 bytes or more are whole 16-byte vectors with less than one vector
+of padding, narrow rows are one thread per row, the lanes of a row stay
+inside one warp and cover it, and every (type, lanes, columns per lane)
+shape is instantiated in csrc/shape_dispatch.cuh.  No GPU."""
 import os
 import shutil
 import subprocess
@@ -45,9 +47,19 @@ def test_row_stride_and_lane_shape():
         rows = [tuple(map(int, l.split())) for l in subprocess.run([exe], capture_output=True, text=True,
                                                                   check=True).stdout.split("\n") if l.strip()]
     assert len(rows) == 4 * 16
+    import re
+    names = {"float": 0, "double": 1, "cfloat": 2, "cdouble": 3}
+    disp = open(os.path.join(CSRC, "shape_dispatch.cuh")).read()
+    shapes = {(int({"ST_F32": 0, "ST_F64": 1, "ST_C32": 2, "ST_C64": 3}[a]), int(c), int(d))
+              for a, b, c, d in re.findall(r"MOR_SHAPE_CASE\((ST_\w+), (\w+), (\d+), (\d+)\)", disp)}
+    assert shapes, "no shapes parsed"
     for st, es, k, ld, tpr, cpt in rows:
         assert k <= ld <= 16, (st, k, ld)
-        assert ld == k or (ld * es) % 16 == 0, (st, k, ld)          # padded rows: whole 16-byte vectors
-        assert tpr >= 1 and (tpr & (tpr - 1)) == 0 and tpr <= 32, (st, ld, tpr)
-        assert tpr * cpt == ld or (cpt == 1 and tpr >= ld), (st, ld, tpr, cpt)
-        assert cpt * es <= 16 or tpr == 1, (st, ld, tpr, cpt)       # one vector per lane unless one lane per row
+        if k * es < 16:                                             # narrow rows: one thread per row
+            assert (ld, tpr, cpt) == (k, 1, k), (st, k, ld, tpr, cpt)
+        else:
+            assert (ld * es) % 16 == 0 and (ld - k) * es < 16, (st, k, ld)   # whole vectors, < 1 vector padding
+            assert cpt * es == 16, (st, ld, cpt)                    # one 16-byte vector per lane
+            assert tpr & (tpr - 1) == 0 and tpr * cpt >= ld > (tpr // 2) * cpt, (st, ld, tpr, cpt)
+        assert tpr <= 32, (st, ld, tpr)
+        assert (st, tpr, cpt) in shapes, ("shape not instantiated", st, tpr, cpt)
