@@ -142,7 +142,29 @@ typedef struct {
                             time on two streams, W from a second host thread;
                             0 = one after the other from the calling thread
                             (same kernels; for tools that follow one host thread) */
+    int    reuse;        /* reuse variant of the schedule (precond = 0), mor_reuse:
+                            MOR_REUSE_CHAIN (default), MOR_REUSE_FIRST or
+                            MOR_REUSE_AUTO                                        */
+    int    moments;      /* mor_airga_step: moment blocks J per expansion point
+                            (Algorithm 1 lines 7-12), 1 (default) = zeroth only  */
 } mor_solve_opts;
+
+/* Reuse variants of the preconditioner schedule (Table II, Algorithm 4). */
+enum mor_reuse {
+    MOR_REUSE_CHAIN = 0,  /* second approach, Algorithm 4: P_i = Q_i P_{i-1} along
+                             the shifts of an iteration (horizontal), the first
+                             shift's chain extended across iterations (vertical)  */
+    MOR_REUSE_FIRST = 1,  /* first approach of Table II along the shifts: P_i =
+                             Q_i P_1 with Q_i minimising ||A_1 - A_i Q||_F, so every
+                             shift's chain is the vertical chain plus one factor;
+                             vertical as MOR_REUSE_CHAIN                          */
+    MOR_REUSE_AUTO = 2    /* MOR_REUSE_CHAIN with the reuse decision of the Frobenius
+                             ratios of Sec. IV (Tables III / VII): a factor from
+                             s_old to s_new is built only when ||A(s_old) - A(s_new)||_F
+                             / ||A(s_old)||_F is below 1 and below ||I - A(s_new)||_F
+                             / ||I||_F; otherwise a fresh SPAI at s_new starts a new
+                             chain (the paper states no thresholds: this reading)  */
+};
 
 /* Per-column statistics of a solve. */
 typedef struct {
@@ -479,7 +501,9 @@ int mor_kernel_tally(int which, int vec_type, int64_t* counts);
  * iteration launches it, with CUDA events on the handle's stream:
  *   which = 0   operator SpMV  Y = A(sigma_c) X over k columns;
  *   which = 1   one factor SpMV Y = F X over k columns (the chain's last
- *               factor; requires a built preconditioner).
+ *               factor of the vectors' kind: complex values when any sigma_c
+ *               is complex, else real ones, else the last factor; requires a
+ *               built preconditioner).
  * precision selects FP32/complex64 (MOR_MIXED) or FP64 vectors; complex
  * vectors are used when any sigma_c is complex.  `reps` launches are timed
  * after 3 untimed ones, each between its own pair of events and after a

@@ -38,6 +38,7 @@ MOR_FP64, MOR_MIXED = 0, 1
 MOR_BICGSTAB = 0
 MOR_GMRES = 1
 MOR_FMT_AUTO, MOR_FMT_CSR, MOR_FMT_SELL = 0, 1, 2
+MOR_REUSE_CHAIN, MOR_REUSE_FIRST, MOR_REUSE_AUTO = 0, 1, 2
 MOR_MAX_R = 64
 MOR_MAX_IO = 8
 
@@ -55,7 +56,8 @@ class mor_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("solver", C.c_int), ("tol", C.c_double), ("maxit", C.c_int),
                 ("inner_tol", C.c_double), ("max_refine", C.c_int), ("batch", C.c_int), ("use_graph", C.c_int),
                 ("graph_chunk", C.c_int), ("precond", C.c_int), ("max_chain", C.c_int), ("restart", C.c_int),
-                ("precond_precision", C.c_int), ("fp64_fallback", C.c_int), ("concurrent_sweeps", C.c_int)]
+                ("precond_precision", C.c_int), ("fp64_fallback", C.c_int), ("concurrent_sweeps", C.c_int),
+                ("reuse", C.c_int), ("moments", C.c_int)]
 
 
 MOR_MAX_R2 = 32

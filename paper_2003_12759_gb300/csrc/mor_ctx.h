@@ -2,6 +2,7 @@
 #pragma once
 #include "mor_spai.h"
 #include "mor_internal.h"
+#include "reuse_policy.h"
 #include <cstdarg>
 #include <cstdio>
 #include <memory>
@@ -113,6 +114,8 @@ struct mor_ctx {
   std::vector<int64_t> seg_rows_h;   // nseg + 1 row offsets (host)
   DBuf ws_kstate, ws_segarr, ws_sums;
   SolveLane lanes[2];                        // batch-solve state per stream (lane 0: `stream`)
+  // scalar products of the stored matrices for the Frobenius-ratio reuse decision
+  FrobScalars frob;
   // IRKA reuse schedule
   int irka_z = 0;
   int vlen[2] = {0, 0};

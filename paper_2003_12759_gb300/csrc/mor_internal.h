@@ -67,13 +67,17 @@ inline int row_stride(int st, int k) {
   const int c = 16 / es;
   return (k + c - 1) / c * c;
 }
-// Lanes per row (tpr) and columns per lane (cpt) for rows of stride ld.
+// Lanes per row (tpr) and columns per lane (cpt) for rows of stride ld.  A
+// stride chosen for another type (the FP64 refinement reuses the stride of
+// the FP32 inner solve) that does not make rows whole 16-byte vectors of this
+// type is handled one thread per row with scalar accesses: a 16-byte access
+// is only ever made at a 16-byte aligned address.
 inline void lane_shape(int st, int ld, int* tpr, int* cpt) {
   const int es = (int)st_size(st);
-  if (ld * es < 16) { *tpr = 1; *cpt = ld; return; }
   const int c = 16 / es;
+  if (ld * es < 16 || ld % c != 0) { *tpr = 1; *cpt = ld; return; }
   *cpt = c;
-  *tpr = next_pow2((ld + c - 1) / c);
+  *tpr = next_pow2(ld / c);
 }
 
 #define MOR_LDMAX 16

@@ -328,6 +328,11 @@ int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std:
   h->irka_z = 0; h->vlen[0] = h->vlen[1] = 0;
   h->n = n;
   h->ekind = Ecsr ? EK_CSR : (Ediag ? EK_DIAG : EK_IDENTITY);
+  // A(s) = c1(s) P + c2(s) Q with P = E (or M), Q = A (or K): the scalars of the
+  // reuse decision's Frobenius ratios, once per system
+  h->frob = frob_scalars(h->order, h->alpha, h->beta, n, Ediag ? Ediag->data() : nullptr,
+                         Ecsr ? Ecsr->rowptr.data() : nullptr, Ecsr ? Ecsr->col.data() : nullptr,
+                         Ecsr ? Ecsr->val.data() : nullptr, A.rowptr.data(), A.col.data(), A.val.data());
   // pattern and transpose
   HostCSR S, Tm;
   std::vector<double> sa, se, ta, te;
@@ -445,6 +450,8 @@ void mor_default_opts(mor_solve_opts* o) {
   o->graph_chunk = 16;
   o->precond = 0;
   o->max_chain = 0;
+  o->reuse = MOR_REUSE_CHAIN;
+  o->moments = 1;
 }
 
 int mor_create(mor_t* out, int device, void* stream) {

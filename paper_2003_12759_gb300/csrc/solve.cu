@@ -87,7 +87,8 @@ int get_small(mor_t h, DBuf& buf, Small& s) {
 }  // namespace
 
 // forward
-static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bool update, int precision);
+static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bool update, int precision,
+                        bool append = false);
 
 // precision of the factors the schedule builds: opts.precond_precision, or
 // opts.precision when that is negative (the default)
@@ -104,7 +105,11 @@ static size_t part_blocks(const mor_t h) {
 // ---------------------------------------------------------------------------
 // preconditioner chain
 // ---------------------------------------------------------------------------
-static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bool update, int precision) {
+// update: a reuse factor Q from s_old to s_new, appended to the chain; else a
+// SPAI at s_new that replaces the chain, or (append) starts a new chain after
+// the factors already held (the reuse decision's fresh build).
+static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bool update, int precision,
+                        bool append) {
   OpData& X = h->op(transpose);
   OpData& Y = (transpose && !h->sym) ? h->P : (h->sym ? h->P : h->T);   // column data source
   const bool cplx = !is_real_shift(s_new) || (update && !is_real_shift(s_old));
@@ -144,7 +149,7 @@ static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bo
   int nsing = 0;
   MOR_CK(h, cudaMemcpyAsync(&nsing, sm.nsing, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   MOR_CK(h, cudaStreamSynchronize(h->stream));
-  if (!update) { X.chain.clear(); }
+  if (!update && !append) { X.chain.clear(); }
   X.chain.push_back(std::move(f));
   X.chain_prec = precision;
   if (nsing > 0) return mor_fail(h, MOR_ESINGULAR, "%d rank-deficient least-squares columns", nsing);
@@ -154,11 +159,24 @@ static int build_factor(mor_t h, int transpose, mor_c64 s_old, mor_c64 s_new, bo
 // ---------------------------------------------------------------------------
 // one batch of k <= 16 columns
 // ---------------------------------------------------------------------------
+// The factors of the chain one shift column applies, in chain order: every f
+// with a <= f < b, then f = x when x >= b.  A prefix Q_L ... Q_2 P_1 (Algorithm
+// 4) is {0, L, -1}; the first approach of Table II is the vertical prefix plus
+// the shift's own factor {0, v, x}; a chain restarted by a fresh SPAI at
+// factor a is {a, b, -1}.
+struct ColChain {
+  int a = 0, b = 0, x = -1;
+  int end() const { return x >= 0 ? x + 1 : b; }
+  bool uses(int f) const { return (f >= a && f < b) || f == x; }
+  int count() const { return (b > a ? b - a : 0) + (x >= 0 ? 1 : 0); }
+};
+static ColChain prefix_chain(int L) { ColChain c; c.b = L; return c; }
+
 struct BatchIO {
   const mor_c64* sig;   // k shifts
   int k;
   int ld;               // padded row stride of the blocks
-  const int* L;         // chain prefix length per column
+  const ColChain* L;    // factors of the chain each column applies
   void* b64;            // row-major n x k, st64
   void* x64;            // row-major n x k, st64 (out)
 };
@@ -201,11 +219,14 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
   const int ld = io.ld;                              // padded row stride, columns k..ld-1 are dummies
   const size_t es = st_size(st_in), es64 = st_size(st64);
   int Lmax = 0;
-  for (int c = 0; c < k; ++c) Lmax = std::max(Lmax, io.L[c]);
+  for (int c = 0; c < k; ++c) Lmax = std::max(Lmax, io.L[c].end());
   if (Lmax > (int)op.chain.size()) return mor_fail(h, MOR_ESTATE, "chain shorter than requested prefix");
   if (Lmax > MAX_FACTORS - 4) return mor_fail(h, MOR_EINVAL, "chain too long");
   for (int f = 0; f < Lmax; ++f) {
     const Factor& F = op.chain[f];
+    bool used = false;
+    for (int c = 0; c < k; ++c) used |= io.L[c].uses(f);
+    if (!used) continue;
     if (!st_is_f32(F.st) && st_is_f32(st_in))
       return mor_fail(h, MOR_ESTATE, "an FP64 preconditioner chain cannot serve an FP32 inner solve");
     if (st_is_cplx(F.st) && !st_is_cplx(st_in)) return mor_fail(h, MOR_EINVAL, "internal: complex factor, real vectors");
@@ -268,13 +289,13 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
     if (Lmax == 0) return 0;
     int lc = 0;
     for (int c = 0; c < ldc; ++c)
-      if (cmap[c] >= 0 && cmap[c] < k) lc = std::max(lc, io.L[cmap[c]]);
+      if (cmap[c] >= 0 && cmap[c] < k) lc = std::max(lc, io.L[cmap[c]].end());
     Lcur = lc > 0 ? lc : Lmax;
     std::vector<int> mk((size_t)Lmax * MOR_KMAX, 0);
     for (int f = 0; f < Lmax; ++f)
       for (int c = 0; c < ldc; ++c) {
         const int oc = cmap[c];
-        mk[(size_t)f * MOR_KMAX + c] = (oc < 0 || oc >= k || f < io.L[oc]) ? 1 : 0;
+        mk[(size_t)f * MOR_KMAX + c] = (oc < 0 || oc >= k || io.L[oc].uses(f)) ? 1 : 0;
       }
     return (int)cudaMemcpyAsync(sm.masks, mk.data(), sizeof(int) * mk.size(), cudaMemcpyHostToDevice, ln.stream);
   };
@@ -666,7 +687,7 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
 // Solve k shifts (any k), batching by 16.  rhs: either R (col-major c128, host or
 // device) or the system's B/C column 0.  X out col-major c128 (host or device).
 static int solve_many(mor_t h, SolveLane& ln, const mor_c64* sig, int k, int transpose, const mor_solve_opts& o,
-                      const std::vector<int>& L, bool cplx, const mor_c64* R, bool dev, mor_c64* X,
+                      const std::vector<ColChain>& L, bool cplx, const mor_c64* R, bool dev, mor_c64* X,
                       mor_solve_stats* stats) {
   const int64_t n = h->n;
   const int st64 = cplx ? ST_C64 : ST_F64;
@@ -726,7 +747,7 @@ static int solve_many(mor_t h, SolveLane& ln, const mor_c64* sig, int k, int tra
         MOR_CK(h, cudaStreamSynchronize(ln.stream));
         MOR_CKI(h, conv_launch_gather_cols(st64, n, ld, ld2, nr, dmap, ln.ws_b64.p, b2, ln.stream));
         std::vector<mor_c64> s2(nr);
-        std::vector<int> L2(nr);
+        std::vector<ColChain> L2(nr);
         for (int i = 0; i < nr; ++i) { s2[i] = sig[c0 + redo[i]]; L2[i] = L[c0 + redo[i]]; }
         BatchIO io2{s2.data(), nr, ld2, L2.data(), b2, x2};
         std::vector<mor_solve_stats> sb2((size_t)nseg * nr);
@@ -768,18 +789,18 @@ static int solve_many(mor_t h, SolveLane& ln, const mor_c64* sig, int k, int tra
   return ret;
 }
 
-static std::vector<int> prefix_lengths(OpData& op, const mor_c64* sig, int k) {
-  std::vector<int> L(k, (int)op.chain.size());
+static std::vector<ColChain> prefix_lengths(OpData& op, const mor_c64* sig, int k) {
+  std::vector<ColChain> L(k, prefix_chain((int)op.chain.size()));
   for (int c = 0; c < k; ++c)
     for (int f = (int)op.chain.size() - 1; f >= 0; --f)
-      if (same_shift(op.chain[f].to, sig[c])) { L[c] = f + 1; break; }
+      if (same_shift(op.chain[f].to, sig[c])) { L[c] = prefix_chain(f + 1); break; }
   return L;
 }
 
-static bool chain_cplx(const OpData& op, const std::vector<int>& L) {
-  int Lmax = 0;
-  for (int x : L) Lmax = std::max(Lmax, x);
-  for (int f = 0; f < Lmax; ++f) if (st_is_cplx(op.chain[f].st)) return true;
+static bool chain_cplx(const OpData& op, const std::vector<ColChain>& L) {
+  for (const ColChain& c : L)
+    for (int f = 0; f < c.end(); ++f)
+      if (c.uses(f) && st_is_cplx(op.chain[f].st)) return true;
   return false;
 }
 
@@ -1005,9 +1026,9 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   const bool real = flags & MOR_REAL_VECTORS;
   const int64_t n = h->n;
   const int st = (op.chain_prec == MOR_FP64) ? (real ? ST_F64 : ST_C64) : (real ? ST_F32 : ST_C32);
-  std::vector<int> L = prefix_lengths(op, sigma, k);
+  std::vector<ColChain> L = prefix_lengths(op, sigma, k);
   int Lmax = 0;
-  for (int x : L) Lmax = std::max(Lmax, x);
+  for (const ColChain& x : L) Lmax = std::max(Lmax, x.end());
   if (real)
     for (int f = 0; f < Lmax; ++f)
       if (st_is_cplx(op.chain[f].st)) return mor_fail(h, MOR_EINVAL, "MOR_REAL_VECTORS with a complex chain factor");
@@ -1027,7 +1048,7 @@ int mor_apply_precond(mor_t h, const mor_c64* sigma, int k, int transpose, const
   MOR_TRY(get_small(h, h->ws_small, sm));
   std::vector<int> masks((size_t)std::max(Lmax, 1) * MOR_KMAX, 0);
   for (int f = 0; f < Lmax; ++f)
-    for (int c = 0; c < ld; ++c) masks[(size_t)f * MOR_KMAX + c] = (c >= k || f < L[c]) ? 1 : 0;
+    for (int c = 0; c < ld; ++c) masks[(size_t)f * MOR_KMAX + c] = (c >= k || L[c].uses(f)) ? 1 : 0;
   MOR_CK(h, cudaMemcpyAsync(sm.masks, masks.data(), sizeof(int) * masks.size(), cudaMemcpyHostToDevice, h->stream));
   char* s = a;
   char* d = b;
@@ -1079,7 +1100,7 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
     int ret = MOR_OK;
     for (int c = 0; c < k; ++c) {
       MOR_TRY(build_factor(h, transpose, sigma[c], sigma[c], false, factor_precision(o)));
-      std::vector<int> L(1, 1);
+      std::vector<ColChain> L(1, prefix_chain(1));
       bool cc = anyc || chain_cplx(op, L);
       int s = solve_many(h, *lane0, sigma + c, 1, transpose, o, L, cc, R ? R + (size_t)h->n * c : nullptr, dev,
                          X + (size_t)h->n * c, stats ? stats + c : nullptr);
@@ -1088,7 +1109,7 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
     }
     return ret;
   }
-  std::vector<int> L = (o.precond == 2) ? std::vector<int>(k, 0) : prefix_lengths(op, sigma, k);
+  std::vector<ColChain> L = (o.precond == 2) ? std::vector<ColChain>(k) : prefix_lengths(op, sigma, k);
   if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision &&
       !(op.chain_prec == MOR_MIXED && o.precision == MOR_FP64))
     return mor_fail(h, MOR_ESTATE, "an FP64 preconditioner chain cannot serve a mixed-precision solve");
@@ -1133,7 +1154,7 @@ int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const m
   SolveLane* lane0 = nullptr;
   MOR_TRY(mor_lane(h, 0, &lane0));
   OpData& op = h->op(transpose);
-  std::vector<int> L = (o.precond == 2) ? std::vector<int>(k, 0) : prefix_lengths(op, sigma, k);
+  std::vector<ColChain> L = (o.precond == 2) ? std::vector<ColChain>(k) : prefix_lengths(op, sigma, k);
   if (o.precond == 0 && !op.chain.empty() && op.chain_prec != o.precision &&
       !(op.chain_prec == MOR_MIXED && o.precision == MOR_FP64))
     return mor_fail(h, MOR_ESTATE, "an FP64 preconditioner chain cannot serve a mixed-precision solve");
@@ -1203,23 +1224,34 @@ int mor_irka_reset(mor_t h) {
 }
 
 // Reuse schedule of Algorithm 4 for the solved shifts `sol` of one iteration
-// on the primal operator and, with nops == 2, the transposed one: on the
-// first iteration (or when the chain is rebuilt) a full SPAI at sol[0], else
-// a vertical Q from the previous first shift; then a horizontal Q for every
-// further shift.  Ls[t][i] = chain prefix length of shift i (0 without a
-// preconditioner; precond 1 builds per shift at solve time).
+// on the primal operator and, with nops == 2, the transposed one.  Vertical:
+// on the first iteration (or when the chain is rebuilt) a full SPAI at
+// sol[0], else a Q from the previous first shift.  Horizontal, by opts.reuse:
+//   MOR_REUSE_CHAIN  a Q from sol[i-1] to sol[i] for every further shift
+//                    (P_i = Q_i P_{i-1}, Table II second approach);
+//   MOR_REUSE_FIRST  a Q from sol[0] to sol[i] (P_i = Q_i P_1, Table II first
+//                    approach): shift i applies the vertical chain and its Q;
+//   MOR_REUSE_AUTO   as MOR_REUSE_CHAIN, but a factor is built only when the
+//                    Frobenius ratios allow reuse (frob_reuse_ok), otherwise
+//                    a fresh SPAI at the new shift, vertically (the chain is
+//                    rebuilt) or horizontally (later shifts chain from it).
+// Ls[t][i] = the factors shift i applies (none without a preconditioner;
+// precond 1 builds per shift at solve time).
 static int schedule_chains(mor_t h, const std::vector<mor_c64>& sol, const mor_solve_opts& o, int nops,
-                           std::vector<int>* Ls, mor_irka_stats& st) {
+                           std::vector<ColChain>* Ls, mor_irka_stats& st) {
   const int l = (int)sol.size();
+  if (o.reuse < MOR_REUSE_CHAIN || o.reuse > MOR_REUSE_AUTO) return mor_fail(h, MOR_EINVAL, "unknown reuse variant");
+  auto fz = [](mor_c64 z) { return frob_z{z.re, z.im}; };
   for (int t = 0; t < nops; ++t) {
     OpData& X = h->op(t);
-    std::vector<int>& L = Ls[t];
-    L.assign(l, 0);
+    std::vector<ColChain>& L = Ls[t];
+    L.assign(l, ColChain{});
     if (o.precond == 2 || o.precond == 1) continue;
     const int fp = factor_precision(o);
-    const bool rebuild = (h->irka_z == 0) || X.chain.empty() || X.chain_prec != fp ||
-                         (o.max_chain > 0 && h->vlen[t] + 1 > o.max_chain);
+    bool rebuild = (h->irka_z == 0) || X.chain.empty() || X.chain_prec != fp ||
+                   (o.max_chain > 0 && h->vlen[t] + 1 > o.max_chain);
     if (!rebuild) { X.chain.resize(h->vlen[t]); }
+    if (!rebuild && o.reuse == MOR_REUSE_AUTO) rebuild = !frob_reuse_ok(h->frob, fz(X.chain.back().to), fz(sol[0]));
     if (rebuild) {
       MOR_TRY(build_factor(h, t, sol[0], sol[0], false, fp));
       h->vlen[t] = 1;
@@ -1229,12 +1261,25 @@ static int schedule_chains(mor_t h, const std::vector<mor_c64>& sol, const mor_s
       h->vlen[t] += 1;
       st.builds_reuse++;
     }
+    const int v = h->vlen[t];
+    L[0] = prefix_chain(v);
     for (int i = 1; i < l; ++i) {
-      MOR_TRY(build_factor(h, t, sol[i - 1], sol[i], true, fp));
-      st.builds_reuse++;
+      if (o.reuse == MOR_REUSE_FIRST) {
+        MOR_TRY(build_factor(h, t, sol[0], sol[i], true, fp));
+        L[i] = ColChain{0, v, (int)X.chain.size() - 1};
+        st.builds_reuse++;
+      } else if (o.reuse == MOR_REUSE_AUTO && !frob_reuse_ok(h->frob, fz(sol[i - 1]), fz(sol[i]))) {
+        MOR_TRY(build_factor(h, t, sol[i], sol[i], false, fp, true));
+        const int a = (int)X.chain.size() - 1;
+        L[i] = ColChain{a, a + 1, -1};
+        st.builds_spai++;
+      } else {
+        MOR_TRY(build_factor(h, t, sol[i - 1], sol[i], true, fp));
+        L[i] = ColChain{L[i - 1].a, (int)X.chain.size(), -1};
+        st.builds_reuse++;
+      }
     }
-    for (int i = 0; i < l; ++i) L[i] = h->vlen[t] + i;
-    st.chain_len = std::max(st.chain_len, L[l - 1]);
+    for (int i = 0; i < l; ++i) st.chain_len = std::max(st.chain_len, L[i].count());
   }
   return MOR_OK;
 }
@@ -1294,7 +1339,7 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
   st.nsolve = l;
   cudaEventRecord(ev[0], h->stream);
   // reuse schedule (Algorithm 4) for the primal and, unless symmetric, the transposed operator
-  std::vector<int> Ls[2];
+  std::vector<ColChain> Ls[2];
   MOR_TRY(schedule_chains(h, sol, o, h->sym ? 1 : 2, Ls, st));
   if (h->sym) Ls[1] = Ls[0];
   cudaEventRecord(ev[1], h->stream);
@@ -1340,7 +1385,7 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
       for (int i = 0; i < l; ++i) {
         MOR_TRY(build_factor(h, t, sol[i], sol[i], false, factor_precision(o)));
         st.builds_spai++;
-        std::vector<int> L1(1, 1);
+        std::vector<ColChain> L1(1, prefix_chain(1));
         const mor_c64* Ri = tang ? rhs[t].as<mor_c64>() + (size_t)n * i : nullptr;
         int s3 = solve_many(h, *lane[0], &sol[i], 1, t, o, L1, cplx, Ri, true, xs[t].as<mor_c64>() + (size_t)n * i,
                             &ss[t][i]);
@@ -1545,14 +1590,14 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
   const int r = m * l;
   st.nsolve = ls * m;
   cudaEventRecord(ev[0], h->stream);
-  std::vector<int> Ls[2];
+  std::vector<ColChain> Ls[2];
   MOR_TRY(schedule_chains(h, sol, o, 1, Ls, st));
   cudaEventRecord(ev[1], h->stream);
   // block solves: column c = (point c / m, input c % m)
   const int k = ls * m;
   const int64_t n = h->n;
   std::vector<mor_c64> sig(k), unit((size_t)k * m, mor_c64{0.0, 0.0});
-  std::vector<int> L(k);
+  std::vector<ColChain> L(k);
   bool cplx = false;
   for (int c = 0; c < k; ++c) {
     sig[c] = sol[c / m];
@@ -1698,8 +1743,13 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
   cudaSetDevice(h->dev);
   bool cplx = false;
   for (int c = 0; c < k; ++c) cplx |= !is_real_shift(sigma[c]);
+  // the factor timed: the chain's last one of the vectors' kind (complex values
+  // for complex shifts, as the solve applies them), else the last one
+  int fidx = (int)op.chain.size() - 1;
   if (which == 1) {
-    cplx |= st_is_cplx(op.chain.back().st);
+    for (int f = fidx; f >= 0; --f)
+      if (st_is_cplx(op.chain[f].st) == cplx) { fidx = f; break; }
+    cplx |= st_is_cplx(op.chain[fidx].st);
     precision = op.chain_prec;
   }
   const int st = st_of(precision, cplx);
@@ -1724,7 +1774,7 @@ int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precisi
   RedArgs ra{RED_DOT_W, w.p, h->ws_part.p, nullptr, FIN_NONE, nullptr, h->ws_sums.p, nullptr};
   auto launch = [&]() -> int {
     if (which == 0) return launch_op_spmv(st, h->seg, pv, ov, cf, ld, x.p, y.p, nullptr, &ra, h->stream, k);
-    return launch_factor_spmv(st, op.chain.back().st, h->seg, pv, op.chain.back().vals->p, sm.masks, ld,
+    return launch_factor_spmv(st, op.chain[fidx].st, h->seg, pv, op.chain[fidx].vals->p, sm.masks, ld,
                               x.p, y.p, nullptr, nullptr, h->stream, k);
   };
   // L2 is flushed before every timed launch (a write of twice its size), and

@@ -41,16 +41,20 @@ template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 // the operator kernel), where 32 registers would spill.  Wider lane slices
 // take no bound and chunk 1.
 #ifndef MOR_FACTOR_GCH
-#define MOR_FACTOR_GCH 4
+#define MOR_FACTOR_GCH 8
 #endif
 #ifndef MOR_OP_GCH
-#define MOR_OP_GCH 2
+#define MOR_OP_GCH 4
 #endif
 template <typename S, int CPT> constexpr bool narrow_slice() { return CPT * sizeof(S) <= 16; }
 template <typename S, int CPT> constexpr int factor_chunk() { return narrow_slice<S, CPT>() ? MOR_FACTOR_GCH : 1; }
 template <typename S, int CPT> constexpr int op_chunk() { return narrow_slice<S, CPT>() ? MOR_OP_GCH : 1; }
+#ifndef MOR_FACTOR_MINB
+#define MOR_FACTOR_MINB 8
+#endif
 template <typename S, int CPT> constexpr int min_blocks() {
-  return narrow_slice<S, CPT>() ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1) ? 6 : 8) : 1;
+  return narrow_slice<S, CPT>() ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1 && MOR_FACTOR_MINB > 6)
+                                       ? 6 : MOR_FACTOR_MINB) : 1;
 }
 #ifndef MOR_OP_MINB
 #define MOR_OP_MINB 8
@@ -122,20 +126,30 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
       S accA[CPT], accE[CPT];
 #pragma unroll
       for (int j = 0; j < CPT; ++j) { accA[j] = zero_<S>(); accE[j] = zero_<S>(); }
-      int pc = p0;
-      for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
+      // chunks of GCH nonzeros, the last one predicated past the row's end
+      // (see the factor kernel); the sums run in storage order
+      for (int pc = p0; pc < p1; pc += GCH * step) {
         int cc[GCH];
         R av[GCH], ev[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          cc[u] = __ldg(pv.col + pc + u * step);
-          av[u] = __ldg(a + pc + u * step);
-          if constexpr (ECSR) ev[u] = __ldg(e + pc + u * step);
+          const int q = pc + u * step;
+          const bool ok = q < p1;
+          cc[u] = ok ? __ldg(pv.col + q) : r;
+          av[u] = ok ? __ldg(a + q) : R(0);
+          if constexpr (ECSR) ev[u] = ok ? __ldg(e + q) : R(0);
           else ev[u] = R(0);
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
-        for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+        for (int u = 0; u < GCH; ++u) {
+          if (pc + u * step < p1) {
+            xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+          } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) xv[u].v[j] = zero_<S>();
+          }
+        }
 #pragma unroll
         for (int u = 0; u < GCH; ++u)
 #pragma unroll
@@ -143,19 +157,6 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
             fma_r(accA[j], av[u], xv[u].v[j]);
             if constexpr (ECSR) fma_r(accE[j], ev[u], xv[u].v[j]);
           }
-      }
-      for (; pc < p1; pc += step) {
-        const int cc = __ldg(pv.col + pc);
-        const R av = __ldg(a + pc);
-        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
-        if constexpr (ECSR) {
-          const R ev = __ldg(e + pc);
-#pragma unroll
-          for (int j = 0; j < CPT; ++j) { fma_r(accA[j], av, xv.v[j]); fma_r(accE[j], ev, xv.v[j]); }
-        } else {
-#pragma unroll
-          for (int j = 0; j < CPT; ++j) fma_r(accA[j], av, xv.v[j]);
-        }
       }
       const int64_t q = (int64_t)r * ld + c0;
       if constexpr (!ECSR) {
@@ -246,24 +247,32 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
         p1 = pv.rowptr[r + 1];
         step = 1;
       }
-      // chunks of GCH nonzeros: indices and values first, then every gather in flight
-      // whole chunks of GCH nonzeros (indices and values first, then every
-      // gather in flight), then the remainder one by one; the sum runs in
-      // storage order either way.  FP32 factor values under FP64 vectors are
-      // widened on load (W).
+      // chunks of GCH nonzeros, the last one predicated past the row's end:
+      // the chunk's indices and values first, then all its gathers in flight,
+      // so that a row of at most GCH nonzeros costs one index round trip and
+      // one gather round trip.  The sum runs in storage order.  FP32 factor
+      // values under FP64 vectors are widened on load (W).
       constexpr int GCH = factor_chunk<S, CPT>();
-      int pc = p0;
-      for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
+      for (int pc = p0; pc < p1; pc += GCH * step) {
         int cc[GCH];
         W fv[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          cc[u] = __ldg(pv.col + pc + u * step);
-          fv[u] = cvt_<W, V>::f(f[pc + u * step]);
+          const int q = pc + u * step;
+          const bool ok = q < p1;
+          cc[u] = ok ? __ldg(pv.col + q) : r;
+          fv[u] = ok ? cvt_<W, V>::f(f[q]) : W(0);
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
-        for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+        for (int u = 0; u < GCH; ++u) {
+          if (pc + u * step < p1) {
+            xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+          } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) xv[u].v[j] = zero_<S>();
+          }
+        }
 #pragma unroll
         for (int u = 0; u < GCH; ++u)
 #pragma unroll
@@ -271,16 +280,6 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
             if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
             else fma_r(acc.v[j], fv[u], xv[u].v[j]);
           }
-      }
-      for (; pc < p1; pc += step) {
-        const int cc = __ldg(pv.col + pc);
-        const W fv = cvt_<W, V>::f(f[pc]);
-        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-          if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv, xv.v[j]);
-          else fma_r(acc.v[j], fv, xv.v[j]);
-        }
       }
     }
     const int64_t q = (int64_t)r * ld + c0;

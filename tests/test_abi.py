@@ -71,12 +71,13 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mor_spai.h"\n'
-                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mor_solve_opts), '
+                   'int main(void) { printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(mor_solve_opts), '
                    'offsetof(mor_solve_opts, restart), offsetof(mor_solve_opts, max_chain), '
                    'sizeof(mor_solve_stats), sizeof(mor_reduced), sizeof(mor_reduced2), '
                    'offsetof(mor_reduced2, Kr), offsetof(mor_solve_opts, fp64_fallback), '
                    'offsetof(mor_solve_stats, fallback), sizeof(mor_irka_stats), '
-                   'offsetof(mor_irka_stats, fallbacks), offsetof(mor_solve_opts, concurrent_sweeps)); return 0; }\n')
+                   'offsetof(mor_irka_stats, fallbacks), offsetof(mor_solve_opts, concurrent_sweeps), '
+                   'offsetof(mor_solve_opts, reuse), offsetof(mor_solve_opts, moments)); return 0; }\n')
     exe = tmp_path / "layout"
     subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
@@ -84,7 +85,8 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
             ctypes.sizeof(mor.mor_solve_stats), ctypes.sizeof(mor.mor_reduced), ctypes.sizeof(mor.mor_reduced2),
             mor.mor_reduced2.Kr.offset, mor.mor_solve_opts.fp64_fallback.offset, mor.mor_solve_stats.fallback.offset,
             ctypes.sizeof(mor.mor_irka_stats), mor.mor_irka_stats.fallbacks.offset,
-            mor.mor_solve_opts.concurrent_sweeps.offset]
+            mor.mor_solve_opts.concurrent_sweeps.offset, mor.mor_solve_opts.reuse.offset,
+            mor.mor_solve_opts.moments.offset]
     assert got == want
 
 
@@ -94,3 +96,4 @@ def test_default_options(lib):
     assert o.solver == mor.MOR_BICGSTAB and o.precision == mor.MOR_MIXED and o.restart == 50
     assert o.tol == 1e-8 and o.precond == 0 and o.max_chain == 0 and o.precond_precision == -1
     assert o.fp64_fallback == 1 and o.concurrent_sweeps == 1
+    assert o.reuse == mor.MOR_REUSE_CHAIN and o.moments == 1

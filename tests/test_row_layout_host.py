@@ -28,6 +28,16 @@ int main() {
       lane_shape(st, ld, &tpr, &cpt);
       printf("%d %d %d %d %d %d\n", st, (int)st_size(st), k, ld, tpr, cpt);
     }
+  // the FP64 refinement of a solve reuses the inner solve's stride:
+  // (inner type, its wide type) = (F32, F64), (C32, C64)
+  const int wide[4] = {ST_F64, ST_F64, ST_C64, ST_C64};
+  for (int st = 0; st < 4; ++st)
+    for (int k = 1; k <= MOR_KMAX; ++k) {
+      const int ld = row_stride(st, k);
+      int tpr = 0, cpt = 0;
+      lane_shape(wide[st], ld, &tpr, &cpt);
+      printf("W %d %d %d %d %d %d\n", wide[st], (int)st_size(wide[st]), k, ld, tpr, cpt);
+    }
   return 0;
 }
 """
@@ -44,9 +54,11 @@ def test_row_stride_and_lane_shape():
         exe = os.path.join(d, "h")
         subprocess.run([cxx, "-O1", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-I", CUDA_INC,
                         src, "-o", exe], check=True)
-        rows = [tuple(map(int, l.split())) for l in subprocess.run([exe], capture_output=True, text=True,
-                                                                  check=True).stdout.split("\n") if l.strip()]
-    assert len(rows) == 4 * 16
+        lines = [l for l in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+                 if l.strip()]
+    rows = [tuple(map(int, l.split())) for l in lines if not l.startswith("W")]
+    cross = [tuple(map(int, l.split()[1:])) for l in lines if l.startswith("W")]
+    assert len(rows) == 4 * 16 and len(cross) == 4 * 16
     import re
     names = {"float": 0, "double": 1, "cfloat": 2, "cdouble": 3}
     disp = open(os.path.join(CSRC, "shape_dispatch.cuh")).read()
@@ -62,4 +74,11 @@ def test_row_stride_and_lane_shape():
             assert cpt * es == 16, (st, ld, cpt)                    # one 16-byte vector per lane
             assert tpr & (tpr - 1) == 0 and tpr * cpt >= ld > (tpr // 2) * cpt, (st, ld, tpr, cpt)
         assert tpr <= 32, (st, ld, tpr)
+        assert (st, tpr, cpt) in shapes, ("shape not instantiated", st, tpr, cpt)
+    for st, es, k, ld, tpr, cpt in cross:
+        # a stride of another type: 16-byte lanes only on whole 16-byte rows, else scalar rows
+        if cpt * es == 16:
+            assert (ld * es) % 16 == 0 and tpr * cpt >= ld, (st, k, ld, tpr, cpt)
+        else:
+            assert tpr == 1 and cpt == ld, (st, k, ld, tpr, cpt)
         assert (st, tpr, cpt) in shapes, ("shape not instantiated", st, tpr, cpt)
