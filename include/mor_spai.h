@@ -339,6 +339,29 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose,
                      const mor_solve_opts* opts, const mor_c64* R, mor_c64* X,
                      mor_solve_stats* stats, unsigned flags);
 
+/* Moment blocks with one matrix and one preconditioner per shift: the higher
+ * moments [(s_i D - K)^{-1} D]^j (s_i D - K)^{-1} F of QB-IHOMM (Algorithm 3
+ * line 4) in the first-order form of this library (D -> E, K -> A, F -> R):
+ *     X_0(s_i) = A(s_i)^{-1} R,   X_j(s_i) = A(s_i)^{-1} E X_{j-1}(s_i),
+ * j = 0 .. J-1, for the l shifts s_i (transpose = 1: A(s_i)^{-T} and E^T, the
+ * left blocks of a two-sided projection).  X_j(s_i) = (-1)^j / j! times the
+ * j-th derivative of (sE - A)^{-1} R at s_i, so projecting on the real span
+ * of the blocks matches that many derivatives of H at every shift.
+ *   R      n x m complex128 (host, or device with MOR_DEVICE_PTRS), or NULL for
+ *          B (transpose 0) / C (transpose 1); 1 <= m <= MOR_MAX_IO, l m <= 64.
+ *   X      out: n x (l J m) complex128, block (i, j) in columns
+ *          (i J + j) m ... (i J + j) m + m - 1.
+ *   stats  l J m entries in the same order (may be NULL).
+ * The l m columns of a level advance in one lock-step batch; every level of
+ * a shift is solved with the same matrix and preconditioner, which
+ * opts->precond picks: 0 = the schedule's chain along the shifts (SPAI at
+ * s_1, a reuse factor Q from s_{i-1} to s_i for each further shift), 1 = a
+ * fresh SPAI per shift, 2 = none.  Single first-order systems only
+ * (MOR_EINVAL otherwise); errors as mor_solve_shifts. */
+int mor_moment_blocks(mor_t h, const mor_c64* sigma, int l, int J, int transpose,
+                      const mor_solve_opts* opts, const mor_c64* R, int m, mor_c64* X,
+                      mor_solve_stats* stats, unsigned flags);
+
 /* In-place two-pass classical Gram-Schmidt (Algorithm 2 line 6, orth) of the
  * n x k FP64 block X (column-major), k <= MOR_MAX_R.  MOR_ESINGULAR if a
  * column is numerically dependent (its norm after both passes is below
@@ -406,11 +429,14 @@ typedef struct {
     double Cr[MOR_MAX_R2 * MOR_MAX_IO];
 } mor_reduced2;
 
-/* One iteration of the second-order reduction (AIRGA, Algorithm 1 with
- * zeroth moments) of a system set by mor_set_system_2nd, with the reuse
- * schedule of mor_irka_step on s^2 M + s D + K: block solves
- * X(s_i) = (s_i^2 M + s_i D + K)^{-1} F at the points with Im >= 0 (one
- * lock-step column per (point, input)), V = CGS2 of [Re X, Im X],
+/* One iteration of the second-order reduction (AIRGA, Algorithm 1) of a
+ * system set by mor_set_system_2nd, with the reuse schedule of mor_irka_step
+ * on s^2 M + s D + K: block solves X^(0)(s_i) = (s_i^2 M + s_i D + K)^{-1} F
+ * at the points with Im >= 0 (one lock-step column per (point, input)); then,
+ * for opts->moments = J > 1, the inner moment loop of lines 7-12 for a fixed
+ * J (its H2 stopping test is not taken): V_j = X^(j-1) / ||X^(j-1)||_F per
+ * point and X^(j) = -(s_i^2 M + s_i D + K)^{-1} M V_j with the same matrix
+ * and the same chain; V = CGS2 of [Re X^(j), Im X^(j)] (per point and block),
  * Galerkin M_r, K_r, D_r, F_r, C_r (Sec. II), and the point update, which
  * the paper leaves unstated (line 11), read as: the mirror images
  * |Re lambda| - i Im lambda of the eigenvalues of the reduced quadratic
@@ -420,8 +446,9 @@ typedef struct {
  * |lambda| of the first pair that did not fit).
  *   points  in: l expansion points (closed under conjugation); out: the next
  *           l points, sorted (Re, |Im|, -Im).
- *   r = m l must not exceed MOR_MAX_R2.  rom, st: out (may be NULL);
- *   st->iters_V sums the block solves' iterations.
+ *   r = m J l must not exceed MOR_MAX_R2.  rom, st: out (may be NULL);
+ *   st->iters_V sums the block solves' iterations, st->nsolve counts the
+ *   solved columns of all J blocks.
  * MOR_EINVAL for a first-order system, a batch, r > MOR_MAX_R2 or
  * precond = 1; otherwise errors as mor_irka_step. */
 int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts,

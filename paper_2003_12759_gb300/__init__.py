@@ -133,6 +133,8 @@ SIGNATURES = {
     "mor_solve_shifts": (C.c_int, [_P, _P, C.c_int, C.c_int, C.POINTER(mor_solve_opts), _P, _P,
                                    C.POINTER(mor_solve_stats), C.c_uint]),
     "mor_orthonormalize": (C.c_int, [_P, _P, C.c_int, C.c_uint]),
+    "mor_moment_blocks": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.POINTER(mor_solve_opts), _P, C.c_int, _P,
+                                    C.POINTER(mor_solve_stats), C.c_uint]),
     "mor_project": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(mor_reduced), C.c_uint]),
     "mor_reduced_poles": (C.c_int, [_P, C.POINTER(mor_reduced), _P, _P]),
     "mor_irka_step": (C.c_int, [_P, _P, C.c_int, C.POINTER(mor_solve_opts), C.POINTER(mor_reduced),
@@ -463,6 +465,34 @@ def mor_solve_shifts(h, sigma, transpose: int = 0, opts: Optional[mor_solve_opts
     if dev:
         X = X.T
     return X, stats, code
+
+
+def mor_moment_blocks(h, sigma, J: int, transpose: int = 0, opts: Optional[mor_solve_opts] = None, R=None,
+                      allow=(MOR_ENOCONV, MOR_EBREAKDOWN)):
+    """Moment blocks X_j(s_i) = A(s_i)^{-1} E X_{j-1}(s_i), X_0 = A(s_i)^{-1} R
+    (R = None: B, or C for transpose = 1).  Returns (blocks as a list over
+    shifts of lists over j of n x m complex128 arrays, stats, status)."""
+    lib = load_library()
+    n = mor_get_info(h)["n"]
+    s, sp_ = _shifts(sigma)
+    l = s.shape[0]
+    o = opts if opts is not None else mor_default_opts()
+    if R is None:
+        m = mor_get_io(h)[1 if transpose else 0]
+        Rp, Rk = None, None
+    else:
+        Rk = np.asfortranarray(np.asarray(R, dtype=np.complex128).reshape(n, -1))
+        m = Rk.shape[1]
+        Rp = Rk.ctypes.data_as(C.c_void_p)
+    X = np.empty((n, l * J * m), dtype=np.complex128, order="F")
+    st = (mor_solve_stats * (l * J * m))()
+    code = lib.mor_moment_blocks(h, sp_, l, int(J), int(transpose), C.byref(o), Rp, int(m),
+                                 X.ctypes.data_as(C.c_void_p), st, 0)
+    _check(h, code, allow)
+    blocks = [[X[:, (i * J + j) * m:(i * J + j + 1) * m] for j in range(J)] for i in range(l)]
+    stats = [{"iters": x.iters, "refinements": x.refinements, "relres": x.relres, "status": x.status,
+              "fallback": x.fallback} for x in st]
+    return blocks, stats, code
 
 
 def mor_orthonormalize(h, X):

@@ -913,6 +913,69 @@ __global__ void extract_kernel(int n, int part, const double* src, double* dst) 
     dst[i] = src[2 * i + part];
 }
 
+// out(:, c) = sgn * D X(:, c) / ||X(:, g c .. g c + g - 1)||_F for the group
+// of g columns containing c (nrm2: squared column norms; nullptr: no scaling);
+// D diagonal (d), or the identity (d = nullptr).  n x k complex128, column-major.
+__global__ void moment_rhs_kernel(int64_t n, int k, int g, const double* d, const cdouble* X, const double* nrm2,
+                                  double sgn, cdouble* out) {
+  const int64_t tot = n * k;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx % n;
+    const int c = (int)(idx / n);
+    double sc = sgn;
+    if (nrm2) {
+      double f = 0.0;
+      for (int j = (c / g) * g; j < (c / g) * g + g; ++j) f += nrm2[j];
+      sc = f > 0.0 ? sgn / sqrt(f) : 0.0;
+    }
+    if (d) sc *= d[row];
+    out[idx] = cdouble(sc * X[idx].re, sc * X[idx].im);
+  }
+}
+
+// squared norms of k complex128 columns (n rows each, column-major) into nrm2[0..k-1]
+static int column_norms2(mor_t h, const mor_c64* X, int64_t n, int k, double* nrm2, cudaStream_t s) {
+  if (2 * n > 0x7fffffffLL) return mor_fail(h, MOR_EINVAL, "columns too long for the norm kernel");
+  MOR_CK(h, h->ws_part.alloc(sizeof(double) * 1024 * (size_t)h->grid_cap));
+  unsigned* cnt = h->ws_counter.as<unsigned>() + 8;
+  for (int c = 0; c < k; ++c) {
+    const double* v = (const double*)(X + (size_t)n * c);
+    MOR_CKI(h, dense_launch_gram((int)(2 * n), 1, 1, v, 2 * n, v, 2 * n, nrm2 + c, h->ws_part.as<double>(), cnt,
+                                 h->grid_cap, s));
+  }
+  return MOR_OK;
+}
+
+// Y = E' X for k complex128 columns (column-major, device): E' = E (transpose
+// 0) or E^T (1) of the first-order system.  Identity and diagonal E act
+// elementwise; a general sparse E runs the operator SpMV with coefficients
+// (1, 0) on row-major batches of at most 16 columns.
+static int apply_E(mor_t h, int transpose, const mor_c64* X, mor_c64* Y, int64_t n, int k, cudaStream_t s) {
+  const int g = (int)std::min<int64_t>((n * k + 255) / 256, h->grid_cap);
+  if (h->ekind != EK_CSR) {
+    moment_rhs_kernel<<<g, 256, 0, s>>>(n, k, 1, h->ekind == EK_DIAG ? h->ediag64.as<double>() : nullptr,
+                                        (const cdouble*)X, nullptr, 1.0, (cdouble*)Y);
+    mor_count_launches(1);
+    MOR_CK(h, cudaGetLastError());
+    return MOR_OK;
+  }
+  OpData& op = h->op(transpose);
+  for (int c0 = 0; c0 < k; c0 += MOR_KMAX) {
+    const int kc = std::min(MOR_KMAX, k - c0);
+    const int ld = row_stride(ST_C64, kc);
+    MOR_CK(h, h->ws_io.alloc(sizeof(mor_c64) * (size_t)n * 2 * ld));
+    char* xr = h->ws_io.as<char>();
+    char* yr = xr + sizeof(mor_c64) * (size_t)n * ld;
+    if (ld > kc) MOR_CK(h, cudaMemsetAsync(xr, 0, sizeof(mor_c64) * (size_t)n * ld, s));
+    MOR_CKI(h, conv_launch_colmajor_c128_to_rowmajor(ST_C64, (int)n, kc, ld, X + (size_t)n * c0, xr, s));
+    Coef cf[MOR_LDMAX];
+    for (int c = 0; c < ld; ++c) cf[c] = Coef{1.0, 0.0, 0.0, 0.0};
+    MOR_CKI(h, launch_op_spmv(ST_C64, h->seg, op.view(), op_vals(h, op, false), cf, ld, xr, yr, nullptr, nullptr, s, kc));
+    MOR_CKI(h, conv_launch_rowmajor_to_colmajor_c128(ST_C64, (int)n, kc, ld, yr, Y + (size_t)n * c0, s));
+  }
+  return MOR_OK;
+}
+
 extern "C" {
 
 int mor_build_precond(mor_t h, mor_c64 sigma, int transpose, int precision) {
@@ -1537,6 +1600,114 @@ static int irka_step_impl(mor_t h, mor_c64* shifts, mor_c64* btil, mor_c64* ctil
   return MOR_OK;
 }
 
+int mor_moment_blocks(mor_t h, const mor_c64* sigma, int l, int J, int transpose, const mor_solve_opts* opts,
+                      const mor_c64* R, int m, mor_c64* X, mor_solve_stats* stats, unsigned flags) {
+  if (!h) return MOR_EINVAL;
+  if (!h->has_sys) return mor_fail(h, MOR_ESTATE, "no system set");
+  if (h->order != 1 || h->seg.nseg != 1)
+    return mor_fail(h, MOR_EINVAL, "mor_moment_blocks needs a single first-order system");
+  if (!sigma || !X || l < 1 || J < 1 || (transpose != 0 && transpose != 1))
+    return mor_fail(h, MOR_EINVAL, "bad arguments");
+  if (!R) m = transpose ? h->q : h->m;
+  if (m < 1 || m > MOR_MAX_IO) return mor_fail(h, MOR_EINVAL, "1 <= m <= %d right-hand sides", MOR_MAX_IO);
+  const int k = l * m;                     // lock-step columns: (shift c / m, right-hand side c % m)
+  if (k > 64) return mor_fail(h, MOR_EINVAL, "l m must not exceed 64");
+  mor_solve_opts o;
+  if (opts) o = *opts; else mor_default_opts(&o);
+  if ((o.precision != MOR_FP64 && o.precision != MOR_MIXED) ||
+      (o.precond_precision != -1 && o.precond_precision != MOR_FP64 && o.precond_precision != MOR_MIXED) ||
+      (o.precision == MOR_MIXED && o.precond_precision == MOR_FP64))
+    return mor_fail(h, MOR_EINVAL, "bad precision / precond_precision");
+  if (o.precond < 0 || o.precond > 2) return mor_fail(h, MOR_EINVAL, "bad precond");
+  for (int i = 0; i < l; ++i)
+    if (!std::isfinite(sigma[i].re) || !std::isfinite(sigma[i].im)) return mor_fail(h, MOR_EINVAL, "non-finite shift");
+  cudaSetDevice(h->dev);
+  const bool dev = flags & MOR_DEVICE_PTRS;
+  const int64_t n = h->n;
+  cudaStream_t s = h->stream;
+  SolveLane* lane0 = nullptr;
+  MOR_TRY(mor_lane(h, 0, &lane0));
+  // right-hand sides: R (or B / C) repeated for every shift, n x k complex128
+  DBuf rhs, lev, Rd;
+  MOR_CK(h, rhs.alloc(sizeof(mor_c64) * (size_t)n * k));
+  MOR_CK(h, lev.alloc(sizeof(mor_c64) * (size_t)n * k * J));     // level-major: block j at lev + j n k
+  if (R) {
+    const mor_c64* src = R;
+    if (!dev) {
+      MOR_CK(h, Rd.alloc(sizeof(mor_c64) * (size_t)n * m));
+      MOR_CK(h, cudaMemcpyAsync(Rd.p, R, sizeof(mor_c64) * (size_t)n * m, cudaMemcpyHostToDevice, s));
+      src = Rd.as<mor_c64>();
+    }
+    for (int i = 0; i < l; ++i)
+      MOR_CK(h, cudaMemcpyAsync(rhs.as<mor_c64>() + (size_t)n * m * i, src, sizeof(mor_c64) * (size_t)n * m,
+                                cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::vector<mor_c64> unit((size_t)k * m, mor_c64{0.0, 0.0});
+    for (int c = 0; c < k; ++c) unit[(size_t)c * m + c % m] = mor_c64{1.0, 0.0};
+    DBuf dcoef;
+    MOR_CK(h, dcoef.alloc(sizeof(mor_c64) * unit.size()));
+    MOR_CK(h, cudaMemcpyAsync(dcoef.p, unit.data(), sizeof(mor_c64) * unit.size(), cudaMemcpyHostToDevice, s));
+    const int g = (int)std::min<int64_t>((n * k + 255) / 256, h->grid_cap);
+    combine_kernel<<<g, 256, 0, s>>>(n, m, k, (transpose ? h->C : h->B).as<double>(), dcoef.as<mor_c64>(),
+                                     rhs.as<double>());
+    mor_count_launches(1);
+    MOR_CK(h, cudaGetLastError());
+    MOR_CK(h, cudaStreamSynchronize(s));
+  }
+  bool cplx = true;                        // right-hand sides may be complex; complex arithmetic throughout
+  std::vector<mor_c64> sig(k);
+  for (int c = 0; c < k; ++c) sig[c] = sigma[c / m];
+  std::vector<mor_solve_stats> sst((size_t)k * J);
+  int worst = MOR_OK;
+  auto note = [&](int st2) { if (st2 != MOR_OK) worst = (worst == MOR_OK || st2 == MOR_EBREAKDOWN) ? st2 : worst; };
+  // the J levels of the columns cs .. cs + kc - 1 (one shift's m columns, or all of them)
+  auto levels = [&](int cs, int kc, const std::vector<ColChain>& L) -> int {
+    for (int j = 0; j < J; ++j) {
+      mor_c64* Xj = lev.as<mor_c64>() + (size_t)n * k * j + (size_t)n * cs;
+      const mor_c64* Rj = rhs.as<mor_c64>() + (size_t)n * cs;
+      if (j > 0) {
+        MOR_TRY(apply_E(h, transpose, lev.as<mor_c64>() + (size_t)n * k * (j - 1) + (size_t)n * cs,
+                        rhs.as<mor_c64>() + (size_t)n * cs, n, kc, s));
+      }
+      const int st2 = solve_many(h, *lane0, sig.data() + cs, kc, transpose, o, L, cplx, Rj, true, Xj,
+                                 sst.data() + (size_t)k * j + cs);
+      if (st2 != MOR_OK && st2 != MOR_ENOCONV && st2 != MOR_EBREAKDOWN) return st2;
+      note(st2);
+    }
+    return MOR_OK;
+  };
+  const int fp = factor_precision(o);
+  if (o.precond == 1) {
+    // a fresh SPAI per shift (the matrix of a shift is fixed for its J blocks)
+    for (int i = 0; i < l; ++i) {
+      MOR_TRY(build_factor(h, transpose, sigma[i], sigma[i], false, fp));
+      MOR_TRY(levels(i * m, m, std::vector<ColChain>(m, prefix_chain(1))));
+    }
+  } else {
+    std::vector<ColChain> L(k);
+    if (o.precond == 0) {
+      // Algorithm 4 along the shifts: SPAI at the first, a reuse factor per further shift
+      MOR_TRY(build_factor(h, transpose, sigma[0], sigma[0], false, fp));
+      for (int i = 1; i < l; ++i) MOR_TRY(build_factor(h, transpose, sigma[i - 1], sigma[i], true, fp));
+      for (int c = 0; c < k; ++c) L[c] = prefix_chain(c / m + 1);
+    }
+    MOR_TRY(levels(0, k, L));
+  }
+  // out: block (i, j) at columns (i J + j) m .. (i J + j) m + m - 1
+  for (int i = 0; i < l; ++i)
+    for (int j = 0; j < J; ++j) {
+      const mor_c64* src = lev.as<mor_c64>() + (size_t)n * k * j + (size_t)n * m * i;
+      mor_c64* dst = X + (size_t)n * m * ((size_t)i * J + j);
+      MOR_CK(h, cudaMemcpyAsync(dst, src, sizeof(mor_c64) * (size_t)n * m,
+                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+      if (stats)
+        for (int c = 0; c < m; ++c) stats[((size_t)i * J + j) * m + c] = sst[(size_t)k * j + (size_t)m * i + c];
+    }
+  MOR_CK(h, cudaStreamSynchronize(s));
+  if (worst != MOR_OK) return mor_fail(h, worst, "a moment solve did not converge");
+  return MOR_OK;
+}
+
 int mor_irka_step(mor_t h, mor_c64* shifts, int r, const mor_solve_opts* opts, mor_reduced* rom_out,
                   mor_irka_stats* st_out) {
   if (!h) return MOR_EINVAL;
@@ -1557,9 +1728,12 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
   if (h->order != 2) return mor_fail(h, MOR_EINVAL, "mor_airga_step needs a second-order system (mor_set_system_2nd)");
   if (h->seg.nseg != 1) return mor_fail(h, MOR_EINVAL, "mor_airga_step needs a single system, not a batch");
   const int m = h->m, q = h->q;
-  if (!points || l < 1 || m * l > MOR_MAX_R2) return mor_fail(h, MOR_EINVAL, "bad points: need 1 <= m l <= %d", MOR_MAX_R2);
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
+  const int J = o.moments;
+  if (J < 1) return mor_fail(h, MOR_EINVAL, "moments must be >= 1");
+  if (!points || l < 1 || m * J * l > MOR_MAX_R2)
+    return mor_fail(h, MOR_EINVAL, "bad points: need 1 <= m moments l <= %d", MOR_MAX_R2);
   if (o.precond == 1) return mor_fail(h, MOR_EINVAL, "mor_airga_step supports precond 0 (reuse) and 2 (none)");
   if ((o.precision != MOR_FP64 && o.precision != MOR_MIXED) ||
       (o.precond_precision != -1 && o.precond_precision != MOR_FP64 && o.precond_precision != MOR_MIXED) ||
@@ -1587,8 +1761,8 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
     if (s[i].im > 0) ++i;
   }
   const int ls = (int)sol.size();
-  const int r = m * l;
-  st.nsolve = ls * m;
+  const int r = m * J * l;
+  st.nsolve = ls * m * J;
   cudaEventRecord(ev[0], h->stream);
   std::vector<ColChain> Ls[2];
   MOR_TRY(schedule_chains(h, sol, o, 1, Ls, st));
@@ -1610,7 +1784,8 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
   MOR_CK(h, dcoef.alloc(sizeof(mor_c64) * unit.size()));
   MOR_CK(h, cudaMemcpyAsync(dcoef.p, unit.data(), sizeof(mor_c64) * unit.size(), cudaMemcpyHostToDevice, h->stream));
   MOR_CK(h, rhs.alloc(sizeof(mor_c64) * (size_t)n * k));
-  MOR_CK(h, xs.alloc(sizeof(mor_c64) * (size_t)n * k));
+  // moment blocks X^(0), ..., X^(J-1), each n x k (block j at xs + j n k)
+  MOR_CK(h, xs.alloc(sizeof(mor_c64) * (size_t)n * k * J));
   const int g = (int)std::min<int64_t>((n * k + 255) / 256, h->grid_cap);
   combine_kernel<<<g, 256, 0, h->stream>>>(n, m, k, h->B.as<double>(), dcoef.as<mor_c64>(), rhs.as<double>());
   mor_count_launches(1);
@@ -1621,27 +1796,53 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
   const int solve_status = solve_many(h, *lane0, sig.data(), k, 0, o, L, cplx, rhs.as<mor_c64>(), true, xs.as<mor_c64>(),
                                       ss.data());
   if (solve_status != MOR_OK && solve_status != MOR_ENOCONV && solve_status != MOR_EBREAKDOWN) return solve_status;
-  for (int c = 0; c < k; ++c) {
-    st.iters_V += ss[c].iters;
-    st.max_relres = std::max(st.max_relres, ss[c].relres);
-    st.fallbacks += ss[c].fallback;
+  int solve_worst = solve_status;
+  auto add_stats = [&]() {
+    for (int c = 0; c < k; ++c) {
+      st.iters_V += ss[c].iters;
+      st.max_relres = std::max(st.max_relres, ss[c].relres);
+      st.fallbacks += ss[c].fallback;
+    }
+  };
+  add_stats();
+  // inner moment loop (Algorithm 1 lines 7-12): V_j = X^(j-1) / ||X^(j-1)||_F per
+  // point, X^(j) = -A(s)^{-1} M V_j with the same matrix and the same chain
+  if (J > 1) {
+    DBuf nrm;
+    MOR_CK(h, nrm.alloc(sizeof(double) * (size_t)k));
+    for (int j = 1; j < J && std::isfinite(st.max_relres); ++j) {
+      const mor_c64* Xp = xs.as<mor_c64>() + (size_t)n * k * (j - 1);
+      mor_c64* Xj = xs.as<mor_c64>() + (size_t)n * k * j;
+      MOR_TRY(column_norms2(h, Xp, n, k, nrm.as<double>(), h->stream));
+      moment_rhs_kernel<<<g, 256, 0, h->stream>>>(n, k, m, h->ediag64.as<double>(), (const cdouble*)Xp,
+                                                  nrm.as<double>(), -1.0, rhs.as<cdouble>());
+      mor_count_launches(1);
+      MOR_CK(h, cudaGetLastError());
+      const int sj = solve_many(h, *lane0, sig.data(), k, 0, o, L, cplx, rhs.as<mor_c64>(), true, Xj, ss.data());
+      if (sj != MOR_OK && sj != MOR_ENOCONV && sj != MOR_EBREAKDOWN) return sj;
+      if (sj != MOR_OK) solve_worst = sj;
+      add_stats();
+    }
   }
+  const int solve_status_all = solve_worst;
   // a solve that broke down (non-finite residual) leaves no basis to project on: report it as such
   if (!std::isfinite(st.max_relres)) return mor_fail(h, MOR_EBREAKDOWN, "a block solve broke down");
   cudaEventRecord(ev[2], h->stream);
-  // real basis [Re X_i, Im X_i] per solved point, CGS2, Galerkin projection (W = V)
+  // real basis: per solved point and moment block, Re X, then Im X for a complex
+  // point; CGS2, Galerkin projection (W = V)
   DBuf basis;
   MOR_CK(h, basis.alloc(sizeof(double) * (size_t)n * r));
   double* Vb = basis.as<double>();
   const int ge = (int)std::min<int64_t>((n + 255) / 256, h->grid_cap);
   int col = 0;
   for (int i = 0; i < ls; ++i)
-    for (int part = 0; part < (sol[i].im != 0.0 ? 2 : 1); ++part)
-      for (int j = 0; j < m; ++j) {
-        const double* src = (const double*)(xs.as<mor_c64>() + (size_t)n * (i * m + j));
-        extract_kernel<<<ge, 256, 0, h->stream>>>((int)n, part, src, Vb + (size_t)n * col++);
-        mor_count_launches(1);
-      }
+    for (int jm = 0; jm < J; ++jm)
+      for (int part = 0; part < (sol[i].im != 0.0 ? 2 : 1); ++part)
+        for (int j = 0; j < m; ++j) {
+          const double* src = (const double*)(xs.as<mor_c64>() + (size_t)n * k * jm + (size_t)n * (i * m + j));
+          extract_kernel<<<ge, 256, 0, h->stream>>>((int)n, part, src, Vb + (size_t)n * col++);
+          mor_count_launches(1);
+        }
   MOR_CK(h, cudaGetLastError());
   int dep = 0;
   MOR_TRY(orth_device(h, Vb, n, r, &dep));
@@ -1683,7 +1884,7 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
   st.shift_change = chg;
   h->irka_z += 1;
   st.z = h->irka_z;
-  st.status = solve_status;
+  st.status = solve_status_all;
   for (int i = 0; i < l; ++i) points[i] = news[i];
   if (rom_out) {
     rom_out->r = r;
@@ -1697,7 +1898,7 @@ int mor_airga_step(mor_t h, mor_c64* points, int l, const mor_solve_opts* opts, 
     std::memcpy(rom_out->Cr, rom.Cr, sizeof(double) * r * q);
   }
   if (st_out) *st_out = st;
-  if (solve_status != MOR_OK) return mor_fail(h, solve_status, "a shifted solve did not converge");
+  if (solve_status_all != MOR_OK) return mor_fail(h, solve_status_all, "a shifted solve did not converge");
   return MOR_OK;
 }
 
