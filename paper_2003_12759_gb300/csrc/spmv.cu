@@ -29,19 +29,22 @@ namespace {
 template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 
 // Tuning of the two SpMV kernels, measured on the 7-point 100^3 pattern with
-// seven complex64 shift columns (4 lanes x 16 B per row).  Both kernels are
-// latency-bound, so resident warps matter more than gathers in flight per
-// thread: the register allocation is held to a full SM of 256-thread blocks
-// (32 registers) for lane slices of at most 16 bytes, and a row's nonzeros
-// are gathered in whole chunks (all gathers of a chunk in flight) plus a
-// one-by-one remainder.  Factor SpMV: chunk 4 -> 52 us (8-deep chunks at 80
-// registers and 3 blocks/SM took 78 us).  Operator SpMV (with its fused
-// reduction): chunk 2 -> 96 us (chunk 1: 105 us, chunk 4: 126 us).  FP64
+// complex64 shift columns (CUDA events, L2 flushed before every launch).
+// Both kernels are latency-bound on the chain row pointer -> index -> gather,
+// so resident warps matter more than gathers in flight per thread: the
+// register allocation is held to a full SM of 256-thread blocks (32
+// registers) for lane slices of at most 16 bytes, and a row's nonzeros are
+// gathered in chunks (all gathers of a chunk in flight, the last chunk
+// predicated past the row's end).  A sweep of chunk depth x blocks per SM
+// (factor / operator SpMV, k = 7): 4 x 8 blocks 64 / 102 us, 8 x 8: 65 / 100,
+// 8 x 6: 75 / 113, 8 x 5: 76 / 109, 8 x 4: 77 / 104, 8 x 3: 94 / 132 -- at 32
+// registers the compiler keeps only a few gathers in flight whatever the
+// chunk, and fewer resident warps cost more than deeper chunks gain.  FP64
 // data keeps fewer blocks (6 in the factor kernel for two real columns, 5 in
 // the operator kernel), where 32 registers would spill.  Wider lane slices
 // take no bound and chunk 1.
 #ifndef MOR_FACTOR_GCH
-#define MOR_FACTOR_GCH 8
+#define MOR_FACTOR_GCH 4
 #endif
 #ifndef MOR_OP_GCH
 #define MOR_OP_GCH 4
