@@ -87,9 +87,15 @@ enum mor_precision {
 
 enum mor_solver {
     MOR_BICGSTAB = 0,  /* right-preconditioned BiCGSTAB (default)                  */
-    MOR_GMRES = 1      /* right-preconditioned restarted GMRES(m), m = restart: the
+    MOR_GMRES = 1,     /* right-preconditioned restarted GMRES(m), m = restart: the
                           solver of the paper's experiments (Sec. IV); one system
                           only (not mor_batch_solve)                               */
+    MOR_BGMRES = 2     /* right-preconditioned restarted block GMRES(m): the
+                          columns of a solve that share a shift (and its chain)
+                          share one block Krylov space (at most 8 columns per
+                          block; columns with different shifts form separate
+                          blocks); the MIMO form of the shifted solves of
+                          Algorithm 2 lines 4-5.  One system only              */
 };
 
 /* sparse storage of the operator and of every preconditioner factor */

@@ -1,0 +1,214 @@
+// Kernels of restarted block GMRES(m) (Saad 2003, Sec. 6.12) for the p right-
+// hand sides of one shift: the p columns of an n x ld row-major block share
+// one block Krylov space of A(sigma) P.  The basis [V_0 .. V_j] is kept
+// stacked, row-major n x ldv (row r holds V_0[r, 0..p), V_1[r, 0..p), ...),
+// so that one pass over the rows serves every block of the basis:
+//   bg_dot     H = V^H W       (K = (j+1) p basis columns against the p
+//                               columns of W; per-block partials, fixed-order
+//                               reduction by the last block)
+//   bg_update  W = W - V C     (block classical Gram-Schmidt update), or
+//              Y = V C         (Y = W R^{-1} of CholQR, x += P V y at a restart)
+//   bg_copy    copy p columns between a contiguous block and the stack.
+// The block least-squares problem and the small Cholesky factors run on the
+// host in FP64 (csrc/block_ls.h).
+#include "mor_internal.h"
+#include "krylov_state.cuh"
+
+#include <algorithm>
+
+namespace {
+
+template <typename S> __device__ __forceinline__ cdouble to_cd(S v) { return cdouble((double)real_(v), (double)imag_(v)); }
+template <typename S> __device__ __forceinline__ S from_cd(cdouble z);
+template <> __device__ __forceinline__ float from_cd<float>(cdouble z) { return (float)z.re; }
+template <> __device__ __forceinline__ double from_cd<double>(cdouble z) { return z.re; }
+template <> __device__ __forceinline__ cfloat from_cd<cfloat>(cdouble z) { return cfloat((float)z.re, (float)z.im); }
+template <> __device__ __forceinline__ cdouble from_cd<cdouble>(cdouble z) { return z; }
+
+constexpr int BG_PMAX = 8;       // right-hand sides per block
+
+// out[kk * P + b] = sum_r conj(V[r, kk]) W[r, b], kk < K, b < P.  The block's
+// threads form G = 256 / KT row groups of KT threads (KT = K rounded up to a
+// multiple of 32, at most 256); thread (g, t) owns the basis columns kk = t +
+// KT u (u < U) and all P columns of W, for the rows r0 + g, r0 + g + G, ...
+// of the block's contiguous row range.  The groups' sums meet in shared
+// memory, the blocks' partials are reduced in a fixed order by the last one.
+template <typename S, int U>
+__global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, const S* __restrict__ V, int64_t ldv,
+                                                     const S* __restrict__ W, int64_t ldw, double* part,
+                                                     unsigned* counter, cdouble* out) {
+  __shared__ double red[128 * BG_PMAX][2];
+  const int KT = K >= 256 ? 256 : ((K + 31) / 32) * 32;
+  const int G = 256 / KT;
+  const int g = threadIdx.x / KT, t = threadIdx.x % KT;
+  S acc[U][BG_PMAX];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int b = 0; b < BG_PMAX; ++b) acc[u][b] = S(0);
+  const int64_t rpb = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rpb;
+  const int64_t r1 = r0 + rpb < n ? r0 + rpb : n;
+  if (g < G) {
+    for (int64_t r = r0 + g; r < r1; r += G) {
+      S w[BG_PMAX];
+#pragma unroll
+      for (int b = 0; b < BG_PMAX; ++b) w[b] = b < P ? W[r * ldw + b] : S(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kk = t + KT * u;
+        if (kk < K) {
+          const S v = conj_(V[r * ldv + kk]);
+#pragma unroll
+          for (int b = 0; b < BG_PMAX; ++b) fma_s(acc[u][b], v, w[b]);
+        }
+      }
+    }
+  }
+  const int nout = K * P;
+  if (G > 1) {
+    // K <= 128 here: sum the G groups' accumulators in a fixed order
+    for (int gg = 0; gg < G; ++gg) {
+      if (g == gg && t < K) {
+#pragma unroll
+        for (int b = 0; b < BG_PMAX; ++b) {
+          if (b >= P) break;
+          const double re = (double)real_(acc[0][b]), im = (double)imag_(acc[0][b]);
+          if (gg == 0) { red[t * P + b][0] = re; red[t * P + b][1] = im; }
+          else { red[t * P + b][0] += re; red[t * P + b][1] += im; }
+        }
+      }
+      __syncthreads();
+    }
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      double* q = part + ((size_t)blockIdx.x * nout + o) * 2;
+      q[0] = red[o][0];
+      q[1] = red[o][1];
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int kk = t + KT * u;
+      if (kk < K) {
+#pragma unroll
+        for (int b = 0; b < BG_PMAX; ++b) {
+          if (b >= P) break;
+          double* q = part + ((size_t)blockIdx.x * nout + (size_t)kk * P + b) * 2;
+          q[0] = (double)real_(acc[u][b]);
+          q[1] = (double)imag_(acc[u][b]);
+        }
+      }
+    }
+  }
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  const volatile double* vp = part;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int blk = 0; blk < (int)gridDim.x; ++blk) {
+      re += vp[((size_t)blk * nout + o) * 2 + 0];
+      im += vp[((size_t)blk * nout + o) * 2 + 1];
+    }
+    out[o] = cdouble(re, im);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// mode 0: Y[r, b] = W[r, b] - sum_kk V[r, kk] C[kk * P + b]
+// mode 1: Y[r, b] =          sum_kk V[r, kk] C[kk * P + b]
+// Eight lanes per row (lane b < P computes column b), 32 rows per pass.
+template <typename S>
+__global__ void __launch_bounds__(256) bg_update_kernel(int64_t n, int K, int P, const S* __restrict__ V, int64_t ldv,
+                                                        const cdouble* __restrict__ C, const S* W, int64_t ldw,
+                                                        int mode, S* Y, int64_t ldy) {
+  extern __shared__ __align__(16) unsigned char bg_smem[];
+  S* cs = reinterpret_cast<S*>(bg_smem);
+  for (int t = threadIdx.x; t < K * P; t += blockDim.x) cs[t] = from_cd<S>(C[t]);
+  __syncthreads();
+  const int b = threadIdx.x & 7;
+  const int rl = threadIdx.x >> 3;
+  if (b >= P) return;
+  for (int64_t r = (int64_t)blockIdx.x * 32 + rl; r < n; r += (int64_t)gridDim.x * 32) {
+    S acc = mode == 0 ? W[r * ldw + b] : S(0);
+    const S* vr = V + r * ldv;
+    if (mode == 0) {
+      for (int kk = 0; kk < K; ++kk) acc -= vr[kk] * cs[kk * P + b];
+    } else {
+      for (int kk = 0; kk < K; ++kk) fma_s(acc, vr[kk], cs[kk * P + b]);
+    }
+    Y[r * ldy + b] = acc;
+  }
+}
+
+// dst[r * ldd + off + b] = src[r * lds + b], b < P
+template <typename S>
+__global__ void bg_copy_kernel(int64_t n, int P, const S* __restrict__ src, int64_t lds, S* __restrict__ dst,
+                               int64_t ldd, int64_t off) {
+  const int64_t tot = n * P;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / P;
+    const int b = (int)(t % P);
+    dst[r * ldd + off + b] = src[r * lds + b];
+  }
+}
+
+#define BG_ST_SWITCH(st, ...)                                 \
+  switch (st) {                                               \
+    case ST_F32: { typedef float S; __VA_ARGS__; break; }     \
+    case ST_F64: { typedef double S; __VA_ARGS__; break; }    \
+    case ST_C32: { typedef cfloat S; __VA_ARGS__; break; }    \
+    case ST_C64: { typedef cdouble S; __VA_ARGS__; break; }   \
+    default: return (int)cudaErrorInvalidValue;               \
+  }
+
+}  // namespace
+
+int bgmres_max_cols() { return BG_PMAX; }
+
+int bgmres_dot_grid() { return 2 * mor_device_sms(); }
+
+size_t bgmres_part_doubles(int K, int P) { return (size_t)2 * K * P * (size_t)bgmres_dot_grid(); }
+
+int bgmres_launch_dot(int st, int64_t n, int K, int P, const void* V, int64_t ldv, const void* W, int64_t ldw,
+                      double* part, unsigned* counter, void* out, cudaStream_t s) {
+  if (K < 1 || K > 1024 || P < 1 || P > BG_PMAX) return (int)cudaErrorInvalidValue;
+  const int grid = bgmres_dot_grid();
+  const int U = (K + 255) / 256;
+  BG_ST_SWITCH(st, {
+    if (U == 1) bg_dot_kernel<S, 1><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part, counter, (cdouble*)out);
+    else if (U == 2) bg_dot_kernel<S, 2><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part, counter, (cdouble*)out);
+    else bg_dot_kernel<S, 4><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part, counter, (cdouble*)out);
+  });
+  mor_count_launches(1);
+  return (int)cudaGetLastError();
+}
+
+int bgmres_launch_update(int st, int64_t n, int K, int P, const void* V, int64_t ldv, const void* C, const void* W,
+                         int64_t ldw, int mode, void* Y, int64_t ldy, cudaStream_t s) {
+  if (K < 1 || P < 1 || P > BG_PMAX) return (int)cudaErrorInvalidValue;
+  const size_t sm = st_size(st) * (size_t)K * P;
+  if (sm > 160 * 1024) return (int)cudaErrorInvalidValue;
+  const int grid = (int)std::min<int64_t>((n + 31) / 32, (int64_t)mor_device_sms() * 8);
+  BG_ST_SWITCH(st, {
+    cudaError_t e = cudaFuncSetAttribute(bg_update_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    bg_update_kernel<S><<<grid, 256, sm, s>>>(n, K, P, (const S*)V, ldv, (const cdouble*)C, (const S*)W, ldw, mode,
+                                              (S*)Y, ldy);
+  });
+  mor_count_launches(1);
+  return (int)cudaGetLastError();
+}
+
+int bgmres_launch_copy(int st, int64_t n, int P, const void* src, int64_t lds, void* dst, int64_t ldd, int64_t off,
+                       cudaStream_t s) {
+  const int grid = (int)std::min<int64_t>((n * P + 255) / 256, (int64_t)mor_device_sms() * 8);
+  BG_ST_SWITCH(st, (bg_copy_kernel<S><<<grid, 256, 0, s>>>(n, P, (const S*)src, lds, (S*)dst, ldd, off)));
+  mor_count_launches(1);
+  return (int)cudaGetLastError();
+}

@@ -140,6 +140,20 @@ int gmres_launch_begin(int ld, const void* sums, void* state, const double* targ
                        const int* enabled, int first, int* done_cycle, int* done_all, cudaStream_t s);
 int gmres_launch_solve_y(int ld, int m, void* state, const void* H, void* ycoef, cudaStream_t s);
 
+// Block GMRES kernels (bgmres.cu): stacked basis V (n x ldv row-major, K
+// columns used), blocks W, Y of P <= bgmres_max_cols() columns (row stride
+// ldw, ldy); out / C: K x P complex128 row-major (out[kk * P + b]).
+int bgmres_max_cols();
+int bgmres_dot_grid();
+size_t bgmres_part_doubles(int K, int P);
+int bgmres_launch_dot(int st, int64_t n, int K, int P, const void* V, int64_t ldv, const void* W, int64_t ldw,
+                      double* part, unsigned* counter, void* out, cudaStream_t s);
+// mode 0: Y = W - V C; mode 1: Y = V C (Y must not overlap V)
+int bgmres_launch_update(int st, int64_t n, int K, int P, const void* V, int64_t ldv, const void* C, const void* W,
+                         int64_t ldw, int mode, void* Y, int64_t ldy, cudaStream_t s);
+int bgmres_launch_copy(int st, int64_t n, int P, const void* src, int64_t lds, void* dst, int64_t ldd, int64_t off,
+                       cudaStream_t s);
+
 // Launchers (spmv.cu).  x, y, w, b: n x ld row-major blocks of type st.
 // kreal: real (non-dummy) columns of the block, for the launch tally (-1: ld)
 int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& ov, const Coef* coefs, int ld,

@@ -14,6 +14,7 @@
 //                  x += ||r|| d.
 #include "mor_ctx.h"
 #include "krylov_state.cuh"
+#include "block_ls.h"
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -490,6 +491,184 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
     return MOR_OK;
   };
 
+  // ---- block GMRES(m) inner solve of A P Y = rhs, x_in = P Y (single system):
+  // the k columns (one shift, one chain) share one block Krylov space of A P
+  // (Saad 2003, Sec. 6.12).  Each cycle starts from the residual block with
+  // every unconverged column scaled to unit norm (converged columns are left
+  // out as zero columns), block Arnoldi by block CGS2 over the stacked basis,
+  // each new block orthonormalised by a rank-revealing CholQR (two passes,
+  // pivoted Cholesky of the Gram matrix: dependent directions become zero
+  // basis columns), the block least-squares problem incrementally on the host
+  // (block_ls.h); a column stops iterating once its least-squares residual
+  // meets its target.  x_in += P V Y at the end of a cycle.
+  auto bgmres_inner = [&](void* xin, std::vector<int>& kit_out, std::vector<int>& kst_out) -> int {
+    typedef std::complex<double> cx;
+    if (nseg != 1) return mor_fail(h, MOR_EINVAL, "block GMRES solves one system (not a batch of systems)");
+    const int m = o.restart;
+    if (m < 1 || m > GM_MMAX) return mor_fail(h, MOR_EINVAL, "block GMRES restart %d outside 1..%d", m, GM_MMAX);
+    if (k > bgmres_max_cols()) return mor_fail(h, MOR_EINVAL, "block GMRES takes at most %d columns", bgmres_max_cols());
+    for (int c = 1; c < k; ++c)
+      if (!same_shift(io.sig[c], io.sig[0]) || io.L[c].a != io.L[0].a || io.L[c].b != io.L[0].b ||
+          io.L[c].x != io.L[0].x)
+        return mor_fail(h, MOR_EINVAL, "block GMRES needs one shift and one chain for all columns of a block");
+    const double gtol = st_is_f32(st_in) ? 1e-8 : 1e-20;
+    const int64_t ldv = (int64_t)(m + 1) * k;
+    const size_t sbytes = ((es * (size_t)n * ldv) + 255) / 256 * 256;
+    MOR_CK(h, ln.ws_gm_vec.alloc(sbytes + vbytes * 5));
+    char* gb = ln.ws_gm_vec.as<char>();
+    void* Vst = gb;
+    void* W = gb + sbytes;
+    void* Wt = (char*)W + vbytes;
+    void* Vj = (char*)Wt + vbytes;
+    void* Z = (char*)Vj + vbytes;
+    void* U = (char*)Z + vbytes;
+    const int Kmax = (m + 1) * k;
+    size_t off = 0;
+    auto take = [&](size_t b) { const size_t o2 = off; off += (b + 255) / 256 * 256; return o2; };
+    const size_t o_h1 = take(sizeof(cdouble) * Kmax * k), o_h2 = take(sizeof(cdouble) * Kmax * k);
+    const size_t o_c = take(sizeof(cdouble) * Kmax * k), o_g = take(sizeof(cdouble) * k * k), o_cnt = take(64);
+    MOR_CK(h, ln.ws_gm_small.alloc(off));
+    char* sb = ln.ws_gm_small.as<char>();
+    cdouble* h1d = (cdouble*)(sb + o_h1);
+    cdouble* h2d = (cdouble*)(sb + o_h2);
+    cdouble* cd = (cdouble*)(sb + o_c);
+    cdouble* gd = (cdouble*)(sb + o_g);
+    unsigned* bcnt = (unsigned*)(sb + o_cnt);
+    MOR_CK(h, cudaMemsetAsync(sb, 0, off, ln.stream));
+    MOR_CK(h, ln.ws_gm_part.alloc(sizeof(double) * bgmres_part_doubles(Kmax, k)));
+    double* gpart = ln.ws_gm_part.as<double>();
+    MOR_CK(h, cudaMemsetAsync(gb, 0, sbytes + vbytes * 5, ln.stream));
+    MOR_CK(h, cudaMemsetAsync(xin, 0, vbytes, ln.stream));
+    std::vector<cx> hh1((size_t)Kmax * k), hh2((size_t)Kmax * k), up((size_t)Kmax * k), hg((size_t)k * k);
+    auto dot = [&](const void* V, int64_t ldvv, int K, const void* Wp, cdouble* outd) -> int {
+      return bgmres_launch_dot(st_in, n, K, k, V, ldvv, Wp, ld, gpart, bcnt, outd, ln.stream);
+    };
+    auto fetch = [&](const cdouble* d, std::vector<cx>& hbuf, size_t cnt) -> int {
+      MOR_CK(h, cudaMemcpyAsync(hbuf.data(), d, sizeof(cdouble) * cnt, cudaMemcpyDeviceToHost, ln.stream));
+      MOR_CK(h, cudaStreamSynchronize(ln.stream));
+      return MOR_OK;
+    };
+    // Y = V C for a K x k coefficient matrix given column-major (Cm[b K + kk])
+    auto apply_coef = [&](const void* V, int64_t ldvv, int K, const std::vector<cx>& Cm, void* Y) -> int {
+      for (int kk = 0; kk < K; ++kk)
+        for (int b = 0; b < k; ++b) up[(size_t)kk * k + b] = Cm[(size_t)b * K + kk];
+      MOR_CK(h, cudaMemcpyAsync(cd, up.data(), sizeof(cdouble) * K * k, cudaMemcpyHostToDevice, ln.stream));
+      MOR_CKI(h, bgmres_launch_update(st_in, n, K, k, V, ldvv, cd, nullptr, 0, 1, Y, ld, ln.stream));
+      return MOR_OK;
+    };
+    // rank-revealing CholQR2 of the k columns of Wsrc (stride ld) into Vout; F = R factor
+    std::vector<cx> Gm((size_t)k * k), C1((size_t)k * k), F1((size_t)k * k), C2((size_t)k * k), F2((size_t)k * k);
+    auto orth = [&](const void* Wsrc, void* Vout, std::vector<cx>& F, int* rank) -> int {
+      MOR_CKI(h, dot(Wsrc, ld, k, Wsrc, gd));
+      MOR_TRY(fetch(gd, hg, (size_t)k * k));
+      for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) Gm[(size_t)b * k + a] = hg[(size_t)a * k + b];
+      const int r1 = block_orth_factor(k, Gm.data(), gtol, C1.data(), F1.data());
+      MOR_TRY(apply_coef(Wsrc, ld, k, C1, Wt));
+      MOR_CKI(h, dot(Wt, ld, k, Wt, gd));
+      MOR_TRY(fetch(gd, hg, (size_t)k * k));
+      for (int a = 0; a < k; ++a)
+        for (int b = 0; b < k; ++b) Gm[(size_t)b * k + a] = hg[(size_t)a * k + b];
+      const int r2 = block_orth_factor(k, Gm.data(), 1e-2, C2.data(), F2.data());
+      MOR_TRY(apply_coef(Wt, ld, k, C2, Vout));
+      // W = Vt F1 = Vout F2 F1
+      for (int c = 0; c < k; ++c)
+        for (int i = 0; i < k; ++i) {
+          cx s2(0.0, 0.0);
+          for (int l = 0; l < k; ++l) s2 += F2[(size_t)l * k + i] * F1[(size_t)c * k + l];
+          F[(size_t)c * k + i] = s2;
+        }
+      *rank = std::min(r1, r2);
+      return MOR_OK;
+    };
+    std::vector<int> itc(k, 0), conv(k, 0), brk(k, 0);
+    std::vector<double> tgt(k), scale(k);
+    int budget = 0;
+    for (int c = 0; c < k; ++c) { tgt[c] = tg[c]; budget = std::max(budget, mi[c]); }
+    BlockLS ls;
+    std::vector<cx> R0((size_t)k * k), Y, hcol;
+    int used = 0;
+    for (;;) {
+      // residual block of the inner system and its column norms
+      MOR_CKI(h, launch_op_spmv(st_in, sg, pv, ov_in, ncf, ld, xin, W, rhs, nullptr, ln.stream, k));
+      MOR_CKI(h, dot(W, ld, k, W, gd));
+      MOR_TRY(fetch(gd, hg, (size_t)k * k));
+      int nact = 0;
+      for (int c = 0; c < k; ++c) {
+        const double rn = std::sqrt(std::max(0.0, hg[(size_t)c * k + c].real()));
+        if (!std::isfinite(rn)) brk[c] = 1;
+        conv[c] = (std::isfinite(rn) && rn <= tgt[c]) ? 1 : 0;
+        scale[c] = (!conv[c] && !brk[c] && itc[c] < mi[c]) ? rn : 0.0;
+        nact += scale[c] > 0.0 ? 1 : 0;
+      }
+      if (nact == 0 || used >= budget) break;
+      // unit-norm unconverged columns, zero columns for the rest
+      std::vector<cx> Dm((size_t)k * k, cx(0.0, 0.0));
+      for (int c = 0; c < k; ++c) Dm[(size_t)c * k + c] = scale[c] > 0.0 ? cx(1.0 / scale[c], 0.0) : cx(0.0, 0.0);
+      MOR_TRY(apply_coef(W, ld, k, Dm, U));
+      int rank = 0;
+      MOR_TRY(orth(U, Vj, R0, &rank));
+      if (rank == 0) break;
+      ls.reset(k, m, R0.data());
+      MOR_CKI(h, bgmres_launch_copy(st_in, n, k, Vj, ld, Vst, ldv, 0, ln.stream));
+      int steps = 0;
+      for (int j = 0; j < m && used < budget; ++j) {
+        void* src = Vj;
+        if (Lmax > 0) {
+          MOR_CKI(h, chain_apply_d(Vj, Z, nullptr, nullptr));
+          src = Z;
+        }
+        MOR_CKI(h, launch_op_spmv(st_in, sg, pv, ov_in, cf, ld, src, W, nullptr, nullptr, ln.stream, k));
+        const int K = (j + 1) * k;
+        MOR_CKI(h, dot(Vst, ldv, K, W, h1d));
+        MOR_CKI(h, bgmres_launch_update(st_in, n, K, k, Vst, ldv, h1d, W, ld, 0, W, ld, ln.stream));
+        MOR_CKI(h, dot(Vst, ldv, K, W, h2d));
+        MOR_CKI(h, bgmres_launch_update(st_in, n, K, k, Vst, ldv, h2d, W, ld, 0, W, ld, ln.stream));
+        MOR_CK(h, cudaMemcpyAsync(hh1.data(), h1d, sizeof(cdouble) * K * k, cudaMemcpyDeviceToHost, ln.stream));
+        MOR_CK(h, cudaMemcpyAsync(hh2.data(), h2d, sizeof(cdouble) * K * k, cudaMemcpyDeviceToHost, ln.stream));
+        std::vector<cx> Rs((size_t)k * k);
+        int rk = 0;
+        MOR_TRY(orth(W, Vj, Rs, &rk));        // synchronises the stream (hh1/hh2 are in place)
+        const int rows = (j + 2) * k;
+        hcol.assign((size_t)rows * k, cx(0.0, 0.0));
+        for (int b = 0; b < k; ++b) {
+          for (int kk = 0; kk < K; ++kk) hcol[(size_t)b * rows + kk] = hh1[(size_t)kk * k + b] + hh2[(size_t)kk * k + b];
+          for (int i = 0; i < k; ++i) hcol[(size_t)b * rows + K + i] = Rs[(size_t)b * k + i];
+        }
+        ls.add_block(hcol.data());
+        steps = j + 1;
+        ++used;
+        bool all = true;
+        for (int c = 0; c < k; ++c) {
+          if (scale[c] == 0.0) continue;
+          if (!conv[c]) itc[c] += 1;
+          if (ls.resnorm(c) * scale[c] <= tgt[c]) conv[c] = 1;
+          all = all && (conv[c] || itc[c] >= mi[c]);
+        }
+        if (all || rk == 0) break;
+        MOR_CKI(h, bgmres_launch_copy(st_in, n, k, Vj, ld, Vst, ldv, (int64_t)(j + 1) * k, ln.stream));
+      }
+      // x_in += P V Y, Y scaled back column by column
+      Y.assign((size_t)steps * k * k, cx(0.0, 0.0));
+      ls.solve(Y.data());
+      for (int c = 0; c < k; ++c)
+        for (int kk = 0; kk < steps * k; ++kk) Y[(size_t)c * steps * k + kk] *= scale[c];
+      MOR_TRY(apply_coef(Vst, ldv, steps * k, Y, U));
+      void* upd = U;
+      if (Lmax > 0) {
+        MOR_CKI(h, chain_apply_d(U, Z, nullptr, nullptr));
+        upd = Z;
+      }
+      MOR_CKI(h, gmres_launch_add(st_in, sg, ld, xin, upd, ln.stream));
+      for (int c = 0; c < k; ++c) conv[c] = 0;       // decided again on the true residual
+    }
+    for (int c = 0; c < k; ++c) {
+      kit_out[c] = itc[c];
+      kst_out[c] = conv[c] ? KST_OK : (brk[c] ? KST_BREAKDOWN : KST_NOCONV);
+    }
+    return MOR_OK;
+  };
+
   for (int pass = 0;; ++pass) {
     // true residual r64 = b - A(sigma) x64 in FP64 with fused norms, per (system, column)
     RedArgs rn{RED_NORM, nullptr, ln.ws_part.p, nullptr, FIN_NONE, nullptr, d_sums, nullptr};
@@ -549,7 +728,9 @@ static int solve_batch(mor_t h, SolveLane& ln, int transpose, const mor_solve_op
     MOR_CKI(h, refine_launch_scale_cast(st_in, sg, ld, r64, d_nrm2, d_active, rhs, ln.stream));
     std::vector<int> kit(NK, 0), kstat(NK, KST_OK);
     void* dres = dd;
-    if (o.solver == MOR_GMRES) {
+    if (o.solver == MOR_BGMRES) {
+      MOR_TRY(bgmres_inner(dd, kit, kstat));
+    } else if (o.solver == MOR_GMRES) {
       MOR_TRY(gmres_inner(dd, kit, kstat));
     } else {
       // mixed precision: an FP32 inner solve that stops improving hands back to the refinement
@@ -695,8 +876,15 @@ static int solve_many(mor_t h, SolveLane& ln, const mor_c64* sig, int k, int tra
   const size_t es64 = st_size(st64);
   const int bmax = o.batch ? MOR_KMAX : 1;
   int ret = MOR_OK;
-  for (int c0 = 0; c0 < k; c0 += bmax) {
-    const int kc = std::min(bmax, k - c0);
+  for (int c0 = 0, kc = 0; c0 < k; c0 += kc) {
+    kc = std::min(bmax, k - c0);
+    if (o.solver == MOR_BGMRES) {
+      // a block: the consecutive columns that share the shift and the chain
+      kc = 1;
+      while (c0 + kc < k && kc < bgmres_max_cols() && same_shift(sig[c0 + kc], sig[c0]) &&
+             L[c0 + kc].a == L[c0].a && L[c0 + kc].b == L[c0].b && L[c0 + kc].x == L[c0].x)
+        ++kc;
+    }
     const int ld = row_stride(st_in, kc);
     MOR_CK(h, ln.ws_b64.alloc(es64 * (size_t)n * ld));
     MOR_CK(h, ln.ws_x64.alloc(es64 * (size_t)n * ld));
@@ -1138,6 +1326,8 @@ int mor_solve_shifts(mor_t h, const mor_c64* sigma, int k, int transpose, const 
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
   if (o.precision != MOR_FP64 && o.precision != MOR_MIXED) return mor_fail(h, MOR_EINVAL, "bad precision");
+  if (o.solver != MOR_BICGSTAB && o.solver != MOR_GMRES && o.solver != MOR_BGMRES)
+    return mor_fail(h, MOR_EINVAL, "unknown solver %d", o.solver);
   if (o.precond_precision != -1 && o.precond_precision != MOR_FP64 && o.precond_precision != MOR_MIXED)
     return mor_fail(h, MOR_EINVAL, "bad precond_precision");
   if (o.precision == MOR_MIXED && o.precond_precision == MOR_FP64)
@@ -1205,6 +1395,8 @@ int mor_batch_solve(mor_t h, const mor_c64* sigma, int k, int transpose, const m
   mor_solve_opts o;
   if (opts) o = *opts; else mor_default_opts(&o);
   if (o.precision != MOR_FP64 && o.precision != MOR_MIXED) return mor_fail(h, MOR_EINVAL, "bad precision");
+  if (o.solver != MOR_BICGSTAB && o.solver != MOR_GMRES && o.solver != MOR_BGMRES)
+    return mor_fail(h, MOR_EINVAL, "unknown solver %d", o.solver);
   if (o.precond_precision != -1 && o.precond_precision != MOR_FP64 && o.precond_precision != MOR_MIXED)
     return mor_fail(h, MOR_EINVAL, "bad precond_precision");
   if (o.precision == MOR_MIXED && o.precond_precision == MOR_FP64)
