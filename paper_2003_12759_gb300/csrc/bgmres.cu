@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, co
       q[0] = red[o][0];
       q[1] = red[o][1];
     }
-  } else {
+  } else if (g == 0) {
+    // one row group (K > 128): threads past KT (when KT < 256) hold nothing
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int kk = t + KT * u;
