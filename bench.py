@@ -423,7 +423,8 @@ def run_batch(args, ws, rank, local):
     mor.mor_set_batch(h, [w.A for w in sysl], [w.B[:, 0] for w in sysl], [w.C[:, 0] for w in sysl], fmt=fmt)
     nsys, off = mor.mor_batch_info(h)
     shifts = list(np.logspace(0, 4, 8).astype(np.complex128))
-    opts = mor.mor_default_opts(precision=mor.MOR_FP64 if args.precision == "fp64" else mor.MOR_MIXED)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64 if args.precision == "fp64" else mor.MOR_MIXED,
+                                use_graph=0 if args.no_graph else 1, graph_chunk=args.graph_chunk)
 
     def step():
         mor.mor_build_precond(h, shifts[0], 0, opts.precision)
@@ -442,7 +443,9 @@ def run_batch(args, ws, rank, local):
     e1 = torch.cuda.Event(enable_timing=True)
     clk.start()
     e0.record(stream)
+    torch.cuda.nvtx.range_push("timed_steps")     # lets a profiler select the timed region
     stats = [step() for _ in range(args.steps)]
+    torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -485,9 +488,11 @@ def run_mimo(args, ws, rank, local):
     = 8: 48 real shifts logspace(0, 4, 48), each solved for the whole input
     block B (primal) and output block C (transposed): 768 solves per step,
     FP32 in FP64 refinement, right-hand sides and solutions in device memory.
-    The preconditioner is a fresh SPAI per shift (the paper's "SPAI case"):
-    Algorithm 4's horizontal chain would be 48 factors deep for the last
-    shift of this sweep."""
+    The preconditioner is a fresh SPAI per shift (the paper's "SPAI case"),
+    shared by the shift's 8 columns: Algorithm 4's horizontal chain would be
+    48 factors deep for the last shift of this sweep.  --solver picks
+    lock-step BiCGSTAB or GMRES (one Krylov space per column) or block GMRES
+    (one block Krylov space per shift)."""
     import torch
     import paper_2003_12759_gb300 as mor
     import workloads as W
@@ -503,12 +508,17 @@ def run_mimo(args, ws, rank, local):
     RB = torch.from_numpy(np.ascontiguousarray(wl.B.T)).to(dev).to(torch.complex128).T
     RC = torch.from_numpy(np.ascontiguousarray(wl.C.T)).to(dev).to(torch.complex128).T
     shifts = list(wl.shifts)
-    opts = mor.mor_default_opts(precision=mor.MOR_FP64 if args.precision == "fp64" else mor.MOR_MIXED, precond=1)
+    solver = {"bicgstab": mor.MOR_BICGSTAB, "gmres": mor.MOR_GMRES, "bgmres": mor.MOR_BGMRES}[args.solver]
+    # a fresh SPAI per shift, built just before that shift's solves and shared by its
+    # 8 columns (precond 0 applies the chain, here the one factor built for the shift)
+    opts = mor.mor_default_opts(precision=mor.MOR_FP64 if args.precision == "fp64" else mor.MOR_MIXED, precond=0,
+                                solver=solver, restart=args.restart)
 
     def step():
         its, rel = [], 0.0
         for t, R in ((0, RB), (1, RC)):
             for z in shifts:
+                mor.mor_build_precond(h, z, t, opts.precision)
                 X, st, _ = mor.mor_solve_shifts(h, [z] * m, t, opts, R=R)
                 its += [x["iters"] for x in st]
                 rel = max(rel, max(x["relres"] for x in st))
@@ -609,6 +619,10 @@ def main():
                     help="convdiff: IRKA sweeps on the 3D convection-diffusion system (default); "
                          "batch: 256 uneven independent systems x 8 shifts")
     ap.add_argument("--nsys", type=int, default=256)
+    ap.add_argument("--solver", default="bicgstab", choices=["bicgstab", "gmres", "bgmres"],
+                    help="Krylov solver of the mimo workload (bgmres: the 8 right-hand sides of a shift share one "
+                         "block Krylov space)")
+    ap.add_argument("--restart", type=int, default=30, help="GMRES / block GMRES restart length")
     ap.add_argument("--kernels-only", action="store_true",
                     help="set up the workload, build a 7-factor chain and time the hot-loop SpMVs "
                          "a few times at the widths of --k-list (a short launch list for profilers)")
@@ -672,7 +686,8 @@ def main():
                     "config": {"workload": "batch_%d_laplace2d_uneven_n%d_8shifts" % (r["nsys"], r["rows"]),
                                "systems": r["nsys"], "rows": r["rows"], "shifts": "logspace(0,4,8), real",
                                "step": "SPAI + 7 reuse factors + all (system, shift) solves, one lock-step launch "
-                                       "sequence", "tol": 1e-8},
+                                       "sequence", "tol": 1e-8,
+                               "graphs": "off" if args.no_graph else "%d iterations per replay" % args.graph_chunk},
                     "clocks": r["clocks"], "gpu_launches": int(r["launches"]),
                     "batch": {"iters_mean": r["iters_mean"], "iters_max": r["iters_max"],
                               "max_relres": r["max_relres"]}}
@@ -684,7 +699,11 @@ def main():
             r = run_mimo(args, ws, rank, local)
             cfg_w = {"workload": "mimo_convdiff3d_%d^3_n%d_48shifts_m8_q8" % (args.grid_mimo, r["n"]),
                      "nnz": r["nnz"], "shifts": "logspace(0,4,48), real", "rhs": "B (n x 8), C (n x 8), device",
-                     "precond": "fresh SPAI per shift", "tol": 1e-8, "l2": "inputs larger than L2"}
+                     "precond": "fresh SPAI per shift", "tol": 1e-8, "l2": "inputs larger than L2",
+                     "solver": {"bicgstab": "lock-step BiCGSTAB, one Krylov space per column",
+                                "gmres": "lock-step GMRES(%d), one Krylov space per column" % args.restart,
+                                "bgmres": "block GMRES(%d), one block Krylov space per shift" % args.restart}[
+                                    args.solver]}
             extra = {"mimo": {"iters_mean": r["iters_mean"], "max_relres": r["max_relres"]}}
         else:
             r = run_second(args, ws, rank, local)

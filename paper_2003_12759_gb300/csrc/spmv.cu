@@ -34,12 +34,15 @@ template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 // so resident warps matter more than gathers in flight per thread: the
 // register allocation is held to a full SM of 256-thread blocks (32
 // registers) for lane slices of at most 16 bytes, and a row's nonzeros are
-// gathered in chunks (all gathers of a chunk in flight, the last chunk
-// predicated past the row's end).  A sweep of chunk depth x blocks per SM
-// (factor / operator SpMV, k = 7): 4 x 8 blocks 64 / 102 us, 8 x 8: 65 / 100,
-// 8 x 6: 75 / 113, 8 x 5: 76 / 109, 8 x 4: 77 / 104, 8 x 3: 94 / 132 -- at 32
+// gathered in whole chunks (all gathers of a chunk in flight) plus a
+// one-by-one remainder.  A sweep of chunk depth x blocks per SM with the
+// last chunk predicated past the row's end instead of the remainder (factor /
+// operator SpMV, k = 7): 4 x 8 blocks 64 / 102 us, 8 x 8: 65 / 100, 8 x 6:
+// 75 / 113, 8 x 5: 76 / 109, 8 x 4: 77 / 104, 8 x 3: 94 / 132 -- at 32
 // registers the compiler keeps only a few gathers in flight whatever the
-// chunk, and fewer resident warps cost more than deeper chunks gain.  FP64
+// chunk, and fewer resident warps cost more than deeper chunks gain; the
+// whole chunks with a one-by-one remainder measured 60 / 99 us (k = 7) and
+// 58 us (factor, k = 6) against 65 and 64 us predicated.  FP64
 // data keeps fewer blocks (6 in the factor kernel for two real columns, 5 in
 // the operator kernel), where 32 registers would spill.  Wider lane slices
 // take no bound and chunk 1.
@@ -47,13 +50,21 @@ template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 #define MOR_FACTOR_GCH 4
 #endif
 #ifndef MOR_OP_GCH
-#define MOR_OP_GCH 4
+#define MOR_OP_GCH 2
 #endif
 template <typename S, int CPT> constexpr bool narrow_slice() { return CPT * sizeof(S) <= 16; }
 template <typename S, int CPT> constexpr int factor_chunk() { return narrow_slice<S, CPT>() ? MOR_FACTOR_GCH : 1; }
 template <typename S, int CPT> constexpr int op_chunk() { return narrow_slice<S, CPT>() ? MOR_OP_GCH : 1; }
 #ifndef MOR_FACTOR_MINB
 #define MOR_FACTOR_MINB 8
+#endif
+// staged index / value loads for one-thread-per-row CSR (0: off): stage
+// entries per warp, gathers per chunk
+#ifndef MOR_FACTOR_STAGE
+#define MOR_FACTOR_STAGE 0
+#endif
+#ifndef MOR_FACTOR_STAGE_GCH
+#define MOR_FACTOR_STAGE_GCH 4
 #endif
 template <typename S, int CPT> constexpr int min_blocks() {
   return narrow_slice<S, CPT>() ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1 && MOR_FACTOR_MINB > 6)
@@ -129,30 +140,20 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
       S accA[CPT], accE[CPT];
 #pragma unroll
       for (int j = 0; j < CPT; ++j) { accA[j] = zero_<S>(); accE[j] = zero_<S>(); }
-      // chunks of GCH nonzeros, the last one predicated past the row's end
-      // (see the factor kernel); the sums run in storage order
-      for (int pc = p0; pc < p1; pc += GCH * step) {
+      int pc = p0;
+      for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
         int cc[GCH];
         R av[GCH], ev[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          const int q = pc + u * step;
-          const bool ok = q < p1;
-          cc[u] = ok ? __ldg(pv.col + q) : r;
-          av[u] = ok ? __ldg(a + q) : R(0);
-          if constexpr (ECSR) ev[u] = ok ? __ldg(e + q) : R(0);
+          cc[u] = __ldg(pv.col + pc + u * step);
+          av[u] = __ldg(a + pc + u * step);
+          if constexpr (ECSR) ev[u] = __ldg(e + pc + u * step);
           else ev[u] = R(0);
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
-        for (int u = 0; u < GCH; ++u) {
-          if (pc + u * step < p1) {
-            xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
-          } else {
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) xv[u].v[j] = zero_<S>();
-          }
-        }
+        for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
 #pragma unroll
         for (int u = 0; u < GCH; ++u)
 #pragma unroll
@@ -160,6 +161,19 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
             fma_r(accA[j], av[u], xv[u].v[j]);
             if constexpr (ECSR) fma_r(accE[j], ev[u], xv[u].v[j]);
           }
+      }
+      for (; pc < p1; pc += step) {
+        const int cc = __ldg(pv.col + pc);
+        const R av = __ldg(a + pc);
+        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+        if constexpr (ECSR) {
+          const R ev = __ldg(e + pc);
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) { fma_r(accA[j], av, xv.v[j]); fma_r(accE[j], ev, xv.v[j]); }
+        } else {
+#pragma unroll
+          for (int j = 0; j < CPT; ++j) fma_r(accA[j], av, xv.v[j]);
+        }
       }
       const int64_t q = (int64_t)r * ld + c0;
       if constexpr (!ECSR) {
@@ -232,6 +246,83 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
   const int rpb = blockDim.x / TPR;
   const int re = (int)re64;
   const bool sell = pv.fmt == FMT_SELL;
+#if MOR_FACTOR_STAGE > 0
+  // One thread per row on CSR: the warp's 32 consecutive rows own one
+  // contiguous range of the index and value arrays, which the warp loads
+  // cooperatively (coalesced) into shared memory when it fits the stage;
+  // every lane then reads its row from there and has all of its gathers in
+  // flight at once (one predicated chunk of MOR_FACTOR_STAGE_GCH).
+  if constexpr (TPR == 1) {
+    if (!sell) {
+      constexpr int STG = MOR_FACTOR_STAGE;
+      constexpr int SG = MOR_FACTOR_STAGE_GCH;
+      __shared__ int s_col[8][STG];
+      __shared__ V s_val[8][STG];
+      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      for (int base = (int)rb64 + ((int)threadIdx.x & ~31); base < re; base += rpb) {
+        const int r = base + lane;
+        const bool live = r < re;
+        int p0 = 0, p1 = 0;
+        if (live) { p0 = pv.rowptr[r]; p1 = pv.rowptr[r + 1]; }
+        const int last = (re - 1 - base) < 31 ? (re - 1 - base) : 31;
+        const int P0 = __shfl_sync(0xffffffffu, p0, 0);
+        const int P1 = __shfl_sync(0xffffffffu, p1, last);
+        Pack<S, CPT> acc;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc.v[j] = zero_<S>();
+        if (mask) {
+          const bool staged = (P1 - P0) <= STG;
+          if (staged) {
+            for (int q = P0 + lane; q < P1; q += 32) {
+              s_col[wid][q - P0] = __ldg(pv.col + q);
+              s_val[wid][q - P0] = f[q];
+            }
+            __syncwarp();
+          }
+          for (int pc = p0; pc < p1; pc += SG) {
+            int cc[SG];
+            W fv[SG];
+#pragma unroll
+            for (int u = 0; u < SG; ++u) {
+              const int q = pc + u;
+              const bool ok = q < p1;
+              cc[u] = ok ? (staged ? s_col[wid][q - P0] : __ldg(pv.col + q)) : r;
+              fv[u] = ok ? cvt_<W, V>::f(staged ? s_val[wid][q - P0] : f[q]) : W(0);
+            }
+            Pack<S, CPT> xv[SG];
+#pragma unroll
+            for (int u = 0; u < SG; ++u) {
+              if (pc + u < p1) {
+                xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld);
+              } else {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) xv[u].v[j] = zero_<S>();
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < SG; ++u)
+#pragma unroll
+              for (int j = 0; j < CPT; ++j) {
+                if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
+                else fma_r(acc.v[j], fv[u], xv[u].v[j]);
+              }
+          }
+          __syncwarp();     // the stage is rewritten by the next pass
+        }
+        if (live) {
+          const int64_t q = (int64_t)r * ld;
+          if (mask != (1u << CPT) - 1u) {
+            const Pack<S, CPT> xo = ldp<S, CPT>(x + q);
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) if (!((mask >> j) & 1u)) acc.v[j] = xo.v[j];
+          }
+          stp<S, CPT>(y + q, acc);
+        }
+      }
+      return;
+    }
+  }
+#endif
   for (int r = (int)rb64 + (int)threadIdx.x / TPR; r < re; r += rpb) {
     Pack<S, CPT> acc;
 #pragma unroll
@@ -250,32 +341,24 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
         p1 = pv.rowptr[r + 1];
         step = 1;
       }
-      // chunks of GCH nonzeros, the last one predicated past the row's end:
-      // the chunk's indices and values first, then all its gathers in flight,
-      // so that a row of at most GCH nonzeros costs one index round trip and
-      // one gather round trip.  The sum runs in storage order.  FP32 factor
-      // values under FP64 vectors are widened on load (W).
+      // chunks of GCH nonzeros: indices and values first, then every gather in flight
+      // whole chunks of GCH nonzeros (indices and values first, then every
+      // gather in flight), then the remainder one by one; the sum runs in
+      // storage order either way.  FP32 factor values under FP64 vectors are
+      // widened on load (W).
       constexpr int GCH = factor_chunk<S, CPT>();
-      for (int pc = p0; pc < p1; pc += GCH * step) {
+      int pc = p0;
+      for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
         int cc[GCH];
         W fv[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          const int q = pc + u * step;
-          const bool ok = q < p1;
-          cc[u] = ok ? __ldg(pv.col + q) : r;
-          fv[u] = ok ? cvt_<W, V>::f(f[q]) : W(0);
+          cc[u] = __ldg(pv.col + pc + u * step);
+          fv[u] = cvt_<W, V>::f(f[pc + u * step]);
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
-        for (int u = 0; u < GCH; ++u) {
-          if (pc + u * step < p1) {
-            xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
-          } else {
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) xv[u].v[j] = zero_<S>();
-          }
-        }
+        for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
 #pragma unroll
         for (int u = 0; u < GCH; ++u)
 #pragma unroll
@@ -283,6 +366,16 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
             if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
             else fma_r(acc.v[j], fv[u], xv[u].v[j]);
           }
+      }
+      for (; pc < p1; pc += step) {
+        const int cc = __ldg(pv.col + pc);
+        const W fv = cvt_<W, V>::f(f[pc]);
+        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv, xv.v[j]);
+          else fma_r(acc.v[j], fv, xv.v[j]);
+        }
       }
     }
     const int64_t q = (int64_t)r * ld + c0;
