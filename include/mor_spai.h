@@ -539,10 +539,12 @@ int mor_kernel_tally(int which, int vec_type, int64_t* counts);
  *               built preconditioner).
  * precision selects FP32/complex64 (MOR_MIXED) or FP64 vectors; complex
  * vectors are used when any sigma_c is complex.  `reps` launches are timed
- * after 3 untimed ones, each between its own pair of events and after a
- * write of twice the L2 size (no launch finds the previous one's data in
- * L2); *ms receives the mean duration of one launch.  The input vectors are
- * resident device buffers of n x k entries. */
+ * after 3 untimed ones, each after a read of twice the L2 size (no launch
+ * finds the previous one's data in L2); launches and flushes run back to
+ * back between one pair of events and the time of the flushes alone is
+ * subtracted, so *ms, the mean per launch, is the kernel's duration plus one
+ * inter-kernel gap.  The input vectors are resident device buffers of n x k
+ * entries. */
 int mor_time_kernel(mor_t h, int which, const mor_c64* sigma, int k, int precision, int reps,
                     double* ms);
 

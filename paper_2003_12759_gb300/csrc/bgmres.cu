@@ -30,14 +30,19 @@ constexpr int BG_PMAX = 8;       // right-hand sides per block
 // out[kk * P + b] = sum_r conj(V[r, kk]) W[r, b], kk < K, b < P.  The block's
 // threads form G = 256 / KT row groups of KT threads (KT = K rounded up to a
 // multiple of 32, at most 256); thread (g, t) owns the basis columns kk = t +
-// KT u (u < U) and all P columns of W, for the rows r0 + g, r0 + g + G, ...
-// of the block's contiguous row range.  The groups' sums meet in shared
-// memory, the blocks' partials are reduced in a fixed order by the last one.
+// KT u (u < U) and all P columns of W.  The block walks its contiguous row
+// range in tiles of BG_TILE rows: the tile's rows of W are staged in shared
+// memory (every thread reads all of them), and group g takes the tile rows
+// g, g + G, ..., whose V loads are independent (unrolled, all in flight).
+// The groups' sums meet in shared memory, the blocks' partials are reduced in
+// a fixed order by the last one.
+constexpr int BG_TILE = 32;
 template <typename S, int U>
 __global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, const S* __restrict__ V, int64_t ldv,
                                                      const S* __restrict__ W, int64_t ldw, double* part,
                                                      unsigned* counter, cdouble* out) {
   __shared__ double red[128 * BG_PMAX][2];
+  __shared__ S ws[BG_TILE][BG_PMAX];
   const int KT = K >= 256 ? 256 : ((K + 31) / 32) * 32;
   const int G = 256 / KT;
   const int g = threadIdx.x / KT, t = threadIdx.x % KT;
@@ -49,18 +54,25 @@ __global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, co
   const int64_t rpb = (n + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rpb;
   const int64_t r1 = r0 + rpb < n ? r0 + rpb : n;
-  if (g < G) {
-    for (int64_t r = r0 + g; r < r1; r += G) {
-      S w[BG_PMAX];
+  for (int64_t tr = r0; tr < r1; tr += BG_TILE) {
+    const int rows = (int)(r1 - tr < BG_TILE ? r1 - tr : BG_TILE);
+    __syncthreads();
+    for (int i = threadIdx.x; i < BG_TILE * BG_PMAX; i += blockDim.x) {
+      const int rr = i / BG_PMAX, b = i % BG_PMAX;
+      ws[rr][b] = (rr < rows && b < P) ? W[(tr + rr) * ldw + b] : S(0);
+    }
+    __syncthreads();
+    if (g < G) {
+#pragma unroll 4
+      for (int rr = g; rr < rows; rr += G) {
 #pragma unroll
-      for (int b = 0; b < BG_PMAX; ++b) w[b] = b < P ? W[r * ldw + b] : S(0);
+        for (int u = 0; u < U; ++u) {
+          const int kk = t + KT * u;
+          if (kk < K) {
+            const S v = conj_(V[(tr + rr) * ldv + kk]);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int kk = t + KT * u;
-        if (kk < K) {
-          const S v = conj_(V[r * ldv + kk]);
-#pragma unroll
-          for (int b = 0; b < BG_PMAX; ++b) fma_s(acc[u][b], v, w[b]);
+            for (int b = 0; b < BG_PMAX; ++b) fma_s(acc[u][b], v, ws[rr][b]);
+          }
         }
       }
     }
@@ -136,14 +148,19 @@ __global__ void __launch_bounds__(256) bg_update_kernel(int64_t n, int K, int P,
   const int rl = threadIdx.x >> 3;
   if (b >= P) return;
   for (int64_t r = (int64_t)blockIdx.x * 32 + rl; r < n; r += (int64_t)gridDim.x * 32) {
-    S acc = mode == 0 ? W[r * ldw + b] : S(0);
     const S* vr = V + r * ldv;
-    if (mode == 0) {
-      for (int kk = 0; kk < K; ++kk) acc -= vr[kk] * cs[kk * P + b];
-    } else {
-      for (int kk = 0; kk < K; ++kk) fma_s(acc, vr[kk], cs[kk * P + b]);
+    // four independent partial sums, combined in a fixed order
+    S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0);
+    int kk = 0;
+    for (; kk + 3 < K; kk += 4) {
+      fma_s(a0, vr[kk], cs[kk * P + b]);
+      fma_s(a1, vr[kk + 1], cs[(kk + 1) * P + b]);
+      fma_s(a2, vr[kk + 2], cs[(kk + 2) * P + b]);
+      fma_s(a3, vr[kk + 3], cs[(kk + 3) * P + b]);
     }
-    Y[r * ldy + b] = acc;
+    for (; kk < K; ++kk) fma_s(a0, vr[kk], cs[kk * P + b]);
+    const S sum = (a0 + a1) + (a2 + a3);
+    Y[r * ldy + b] = mode == 0 ? W[r * ldw + b] - sum : sum;
   }
 }
 
@@ -172,7 +189,7 @@ __global__ void bg_copy_kernel(int64_t n, int P, const S* __restrict__ src, int6
 
 int bgmres_max_cols() { return BG_PMAX; }
 
-int bgmres_dot_grid() { return 2 * mor_device_sms(); }
+int bgmres_dot_grid() { return 4 * mor_device_sms(); }
 
 size_t bgmres_part_doubles(int K, int P) { return (size_t)2 * K * P * (size_t)bgmres_dot_grid(); }
 

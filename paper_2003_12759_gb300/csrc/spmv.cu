@@ -58,14 +58,6 @@ template <typename S, int CPT> constexpr int op_chunk() { return narrow_slice<S,
 #ifndef MOR_FACTOR_MINB
 #define MOR_FACTOR_MINB 8
 #endif
-// staged index / value loads for one-thread-per-row CSR (0: off): stage
-// entries per warp, gathers per chunk
-#ifndef MOR_FACTOR_STAGE
-#define MOR_FACTOR_STAGE 0
-#endif
-#ifndef MOR_FACTOR_STAGE_GCH
-#define MOR_FACTOR_STAGE_GCH 4
-#endif
 template <typename S, int CPT> constexpr int min_blocks() {
   return narrow_slice<S, CPT>() ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1 && MOR_FACTOR_MINB > 6)
                                        ? 6 : MOR_FACTOR_MINB) : 1;
@@ -78,6 +70,75 @@ template <typename S, int CPT> constexpr int op_min_blocks() {
 }
 
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
+
+// L2 eviction priorities for the SpMVs of a preconditioner chain: every factor
+// of the chain (and the operator) shares one pattern, so the row pointers and
+// column indices are loaded with evict_last (kept across the chain's
+// launches), the factor values, read once per chain, with evict_first; the
+// output vector, the next factor's input, is written with the default policy.
+// MOR_L2_HINTS = 0 uses plain loads.
+#ifndef MOR_L2_HINTS
+#define MOR_L2_HINTS 0
+#endif
+struct L2Pol { uint64_t last, first; };
+__device__ __forceinline__ L2Pol l2_policies() {
+  L2Pol p{0, 0};
+#if MOR_L2_HINTS
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p.last));
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p.first));
+#endif
+  return p;
+}
+__device__ __forceinline__ int ldh(const int* a, uint64_t pol) {
+#if MOR_L2_HINTS
+  int v;
+  asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return __ldg(a);
+#endif
+}
+__device__ __forceinline__ float ldh(const float* a, uint64_t pol) {
+#if MOR_L2_HINTS
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return __ldg(a);
+#endif
+}
+__device__ __forceinline__ double ldh(const double* a, uint64_t pol) {
+#if MOR_L2_HINTS
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(a), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return __ldg(a);
+#endif
+}
+__device__ __forceinline__ cfloat ldh(const cfloat* a, uint64_t pol) {
+#if MOR_L2_HINTS
+  float x, y;
+  asm("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(x), "=f"(y) : "l"(a), "l"(pol));
+  return cfloat(x, y);
+#else
+  (void)pol;
+  return *a;
+#endif
+}
+__device__ __forceinline__ cdouble ldh(const cdouble* a, uint64_t pol) {
+#if MOR_L2_HINTS
+  double x, y;
+  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(x), "=d"(y) : "l"(a), "l"(pol));
+  return cdouble(x, y);
+#else
+  (void)pol;
+  return *a;
+#endif
+}
 
 
 // Y(:, c) = sE_c (E X(:, c)) + sA_c (A X(:, c)) [+ B(:, c)], with an optional
@@ -246,83 +307,7 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
   const int rpb = blockDim.x / TPR;
   const int re = (int)re64;
   const bool sell = pv.fmt == FMT_SELL;
-#if MOR_FACTOR_STAGE > 0
-  // One thread per row on CSR: the warp's 32 consecutive rows own one
-  // contiguous range of the index and value arrays, which the warp loads
-  // cooperatively (coalesced) into shared memory when it fits the stage;
-  // every lane then reads its row from there and has all of its gathers in
-  // flight at once (one predicated chunk of MOR_FACTOR_STAGE_GCH).
-  if constexpr (TPR == 1) {
-    if (!sell) {
-      constexpr int STG = MOR_FACTOR_STAGE;
-      constexpr int SG = MOR_FACTOR_STAGE_GCH;
-      __shared__ int s_col[8][STG];
-      __shared__ V s_val[8][STG];
-      const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-      for (int base = (int)rb64 + ((int)threadIdx.x & ~31); base < re; base += rpb) {
-        const int r = base + lane;
-        const bool live = r < re;
-        int p0 = 0, p1 = 0;
-        if (live) { p0 = pv.rowptr[r]; p1 = pv.rowptr[r + 1]; }
-        const int last = (re - 1 - base) < 31 ? (re - 1 - base) : 31;
-        const int P0 = __shfl_sync(0xffffffffu, p0, 0);
-        const int P1 = __shfl_sync(0xffffffffu, p1, last);
-        Pack<S, CPT> acc;
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) acc.v[j] = zero_<S>();
-        if (mask) {
-          const bool staged = (P1 - P0) <= STG;
-          if (staged) {
-            for (int q = P0 + lane; q < P1; q += 32) {
-              s_col[wid][q - P0] = __ldg(pv.col + q);
-              s_val[wid][q - P0] = f[q];
-            }
-            __syncwarp();
-          }
-          for (int pc = p0; pc < p1; pc += SG) {
-            int cc[SG];
-            W fv[SG];
-#pragma unroll
-            for (int u = 0; u < SG; ++u) {
-              const int q = pc + u;
-              const bool ok = q < p1;
-              cc[u] = ok ? (staged ? s_col[wid][q - P0] : __ldg(pv.col + q)) : r;
-              fv[u] = ok ? cvt_<W, V>::f(staged ? s_val[wid][q - P0] : f[q]) : W(0);
-            }
-            Pack<S, CPT> xv[SG];
-#pragma unroll
-            for (int u = 0; u < SG; ++u) {
-              if (pc + u < p1) {
-                xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld);
-              } else {
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) xv[u].v[j] = zero_<S>();
-              }
-            }
-#pragma unroll
-            for (int u = 0; u < SG; ++u)
-#pragma unroll
-              for (int j = 0; j < CPT; ++j) {
-                if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
-                else fma_r(acc.v[j], fv[u], xv[u].v[j]);
-              }
-          }
-          __syncwarp();     // the stage is rewritten by the next pass
-        }
-        if (live) {
-          const int64_t q = (int64_t)r * ld;
-          if (mask != (1u << CPT) - 1u) {
-            const Pack<S, CPT> xo = ldp<S, CPT>(x + q);
-#pragma unroll
-            for (int j = 0; j < CPT; ++j) if (!((mask >> j) & 1u)) acc.v[j] = xo.v[j];
-          }
-          stp<S, CPT>(y + q, acc);
-        }
-      }
-      return;
-    }
-  }
-#endif
+  const L2Pol pol = l2_policies();
   for (int r = (int)rb64 + (int)threadIdx.x / TPR; r < re; r += rpb) {
     Pack<S, CPT> acc;
 #pragma unroll
@@ -337,8 +322,8 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
         p1 = p0 + 32 * w;
         step = 32;
       } else {
-        p0 = pv.rowptr[r];
-        p1 = pv.rowptr[r + 1];
+        p0 = ldh(pv.rowptr + r, pol.last);
+        p1 = ldh(pv.rowptr + r + 1, pol.last);
         step = 1;
       }
       // chunks of GCH nonzeros: indices and values first, then every gather in flight
@@ -353,8 +338,8 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
         W fv[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          cc[u] = __ldg(pv.col + pc + u * step);
-          fv[u] = cvt_<W, V>::f(f[pc + u * step]);
+          cc[u] = ldh(pv.col + pc + u * step, pol.last);
+          fv[u] = cvt_<W, V>::f(ldh(f + pc + u * step, pol.first));
         }
         Pack<S, CPT> xv[GCH];
 #pragma unroll
@@ -368,8 +353,8 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
           }
       }
       for (; pc < p1; pc += step) {
-        const int cc = __ldg(pv.col + pc);
-        const W fv = cvt_<W, V>::f(f[pc]);
+        const int cc = ldh(pv.col + pc, pol.last);
+        const W fv = cvt_<W, V>::f(ldh(f + pc, pol.first));
         const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
