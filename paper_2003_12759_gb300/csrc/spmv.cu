@@ -76,9 +76,12 @@ template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
 // column indices are loaded with evict_last (kept across the chain's
 // launches), the factor values, read once per chain, with evict_first; the
 // output vector, the next factor's input, is written with the default policy.
+// Measured on the 100^3 sweep (complex64, L2 flushed before each launch):
+// factor SpMV k = 1: 30.2 -> 26.3 us, k = 6: 65.1 -> 60.0 us, k = 7: 65.6 ->
+// 63.4 us; the IRKA step time moved within run-to-run noise (294 vs 296 ms).
 // MOR_L2_HINTS = 0 uses plain loads.
 #ifndef MOR_L2_HINTS
-#define MOR_L2_HINTS 0
+#define MOR_L2_HINTS 1
 #endif
 struct L2Pol { uint64_t last, first; };
 __device__ __forceinline__ L2Pol l2_policies() {
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
   chunk_rows(sg, seg, blockIdx.x, rb64, re64);
   const int re = (int)re64;
   const bool sell = pv.fmt == FMT_SELL;
+  const L2Pol pol = l2_policies();
   const int ekind = ECSR ? EK_CSR : ov.ekind;   // E a general sparse matrix: compile-time branch
   constexpr int GCH = op_chunk<S, CPT>();
   if (act) {
@@ -194,8 +198,8 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
         p1 = p0 + 32 * wd;
         step = 32;
       } else {
-        p0 = pv.rowptr[r];
-        p1 = pv.rowptr[r + 1];
+        p0 = ldh(pv.rowptr + r, pol.last);
+        p1 = ldh(pv.rowptr + r + 1, pol.last);
         step = 1;
       }
       S accA[CPT], accE[CPT];
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
         R av[GCH], ev[GCH];
 #pragma unroll
         for (int u = 0; u < GCH; ++u) {
-          cc[u] = __ldg(pv.col + pc + u * step);
+          cc[u] = ldh(pv.col + pc + u * step, pol.last);
           av[u] = __ldg(a + pc + u * step);
           if constexpr (ECSR) ev[u] = __ldg(e + pc + u * step);
           else ev[u] = R(0);
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
           }
       }
       for (; pc < p1; pc += step) {
-        const int cc = __ldg(pv.col + pc);
+        const int cc = ldh(pv.col + pc, pol.last);
         const R av = __ldg(a + pc);
         const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
         if constexpr (ECSR) {
