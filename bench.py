@@ -258,7 +258,7 @@ def _spmv_bytes(kernel, k, n, nnz, precision_mixed, cplx):
     return nnz * (4 + s_fval) + 4 * (n + 1) + k * n * 2 * s_vec
 
 
-def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False):
+def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False, reuse=None):
     import torch
     import paper_2003_12759_gb300 as mor
     import workloads as W
@@ -276,7 +276,8 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False)
     opts = mor.mor_default_opts(precision=mor.MOR_FP64 if prec_name == "fp64" else mor.MOR_MIXED,
                                 batch=0 if one else 1, use_graph=0 if (one or args.no_graph) else 1,
                                 max_chain=args.max_chain, graph_chunk=args.graph_chunk,
-                                concurrent_sweeps=0 if args.serial_sweeps else 1)
+                                concurrent_sweeps=0 if args.serial_sweeps else 1,
+                                reuse=mor.MOR_REUSE_CHAIN if reuse is None else reuse)
     omega = np.logspace(0, 5, 1000)
     shifts = wl.shifts.copy()
 
@@ -606,6 +607,8 @@ def main():
     ap.add_argument("--max-chain", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-policy", action="store_true",
+                    help="skip timing the same iterations with the Frobenius-ratio reuse decision")
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip timing the plain FP64 one-shift-per-launch form next to the default")
     ap.add_argument("--fmt", default="auto", choices=["auto", "csr", "sell"])
@@ -758,6 +761,18 @@ def main():
             "ms_precond": float(np.mean([st["ms_precond"] for st in c["stats"]])),
             "ms_solve": float(np.mean([st["ms_solve"] for st in c["stats"]])),
             "speedup_of_mixed_multishift": r["value"] / c["value"]}
+    if not args.no_policy and ws == 1:
+        # the same iterations with the Frobenius-ratio reuse decision (MOR_REUSE_AUTO):
+        # the paper's unlimited chain above stays the headline
+        import paper_2003_12759_gb300 as mor_
+        p = run_ours(args, ws, rank, local, light=True, reuse=mor_.MOR_REUSE_AUTO)
+        line["reuse_auto"] = {
+            "value": p["value"], "unit": UNIT, "ms_per_step": 1000 * p["t"] / args.steps,
+            "chain_len": [st["chain_len"] for st in p["stats"]],
+            "builds_spai": [st["builds_spai"] for st in p["stats"]],
+            "iters_per_solve": float(np.mean([(st["iters_V"] + st["iters_W"]) / (2 * st["nsolve"])
+                                              for st in p["stats"]])),
+            "max_relres": max(st["max_relres"] for st in p["stats"])}
     if not args.no_cpu and ws == 1:
         # the oracle is FP64: its iterations per solve are those of the FP64 form of the
         # same algorithm (the comparator; parity tests tie its counts to the oracle's)

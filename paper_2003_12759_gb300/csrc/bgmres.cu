@@ -34,13 +34,12 @@ constexpr int BG_PMAX = 8;       // right-hand sides per block
 // range in tiles of BG_TILE rows: the tile's rows of W are staged in shared
 // memory (every thread reads all of them), and group g takes the tile rows
 // g, g + G, ..., whose V loads are independent (unrolled, all in flight).
-// The groups' sums meet in shared memory, the blocks' partials are reduced in
-// a fixed order by the last one.
+// The groups' sums meet in shared memory; bg_reduce sums the blocks'
+// partials in a fixed order.
 constexpr int BG_TILE = 32;
 template <typename S, int U>
 __global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, const S* __restrict__ V, int64_t ldv,
-                                                     const S* __restrict__ W, int64_t ldw, double* part,
-                                                     unsigned* counter, cdouble* out) {
+                                                     const S* __restrict__ W, int64_t ldw, double* part) {
   __shared__ double red[128 * BG_PMAX][2];
   __shared__ S ws[BG_TILE][BG_PMAX];
   const int KT = K >= 256 ? 256 : ((K + 31) / 32) * 32;
@@ -113,54 +112,63 @@ __global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, co
       }
     }
   }
-  __shared__ bool am_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  const volatile double* vp = part;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int blk = 0; blk < (int)gridDim.x; ++blk) {
-      re += vp[((size_t)blk * nout + o) * 2 + 0];
-      im += vp[((size_t)blk * nout + o) * 2 + 1];
-    }
-    out[o] = cdouble(re, im);
+}
+
+// out[o] = sum over the dot kernel's blocks of their partials, in block order
+// (one thread per output: the partials of an output are read coalesced)
+__global__ void bg_reduce_kernel(int nout, int nblk, const double* __restrict__ part, cdouble* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= nout) return;
+  double re = 0.0, im = 0.0;
+  for (int blk = 0; blk < nblk; ++blk) {
+    re += part[((size_t)blk * nout + o) * 2 + 0];
+    im += part[((size_t)blk * nout + o) * 2 + 1];
   }
-  __syncthreads();
-  if (threadIdx.x == 0) *counter = 0u;
+  out[o] = cdouble(re, im);
 }
 
 // mode 0: Y[r, b] = W[r, b] - sum_kk V[r, kk] C[kk * P + b]
 // mode 1: Y[r, b] =          sum_kk V[r, kk] C[kk * P + b]
-// Eight lanes per row (lane b < P computes column b), 32 rows per pass.
+// The block walks tiles of T <= 32 rows: the tile's rows of V (T x K) are
+// loaded into shared memory with coalesced loads, then thread (row rr, column
+// b) of the 32 x 8 layout sums over kk from shared memory (four independent
+// partial sums, combined in a fixed order).  Shared memory: C (K x P), then
+// the V tile (T x K).
 template <typename S>
-__global__ void __launch_bounds__(256) bg_update_kernel(int64_t n, int K, int P, const S* __restrict__ V, int64_t ldv,
-                                                        const cdouble* __restrict__ C, const S* W, int64_t ldw,
-                                                        int mode, S* Y, int64_t ldy) {
+__global__ void __launch_bounds__(256) bg_update_kernel(int64_t n, int K, int P, int T, const S* __restrict__ V,
+                                                        int64_t ldv, const cdouble* __restrict__ C, const S* W,
+                                                        int64_t ldw, int mode, S* Y, int64_t ldy) {
   extern __shared__ __align__(16) unsigned char bg_smem[];
   S* cs = reinterpret_cast<S*>(bg_smem);
+  S* vs = cs + (size_t)K * P;
   for (int t = threadIdx.x; t < K * P; t += blockDim.x) cs[t] = from_cd<S>(C[t]);
-  __syncthreads();
   const int b = threadIdx.x & 7;
   const int rl = threadIdx.x >> 3;
-  if (b >= P) return;
-  for (int64_t r = (int64_t)blockIdx.x * 32 + rl; r < n; r += (int64_t)gridDim.x * 32) {
-    const S* vr = V + r * ldv;
-    // four independent partial sums, combined in a fixed order
-    S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0);
-    int kk = 0;
-    for (; kk + 3 < K; kk += 4) {
-      fma_s(a0, vr[kk], cs[kk * P + b]);
-      fma_s(a1, vr[kk + 1], cs[(kk + 1) * P + b]);
-      fma_s(a2, vr[kk + 2], cs[(kk + 2) * P + b]);
-      fma_s(a3, vr[kk + 3], cs[(kk + 3) * P + b]);
+  const int64_t ntiles = (n + T - 1) / T;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * T;
+    const int rows = (int)(n - r0 < T ? n - r0 : T);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * K; i += blockDim.x) {
+      const int rr = i / K, kk = i % K;
+      vs[i] = V[(r0 + rr) * ldv + kk];
     }
-    for (; kk < K; ++kk) fma_s(a0, vr[kk], cs[kk * P + b]);
-    const S sum = (a0 + a1) + (a2 + a3);
-    Y[r * ldy + b] = mode == 0 ? W[r * ldw + b] - sum : sum;
+    __syncthreads();
+    if (rl < rows && b < P) {
+      const S* vr = vs + (size_t)rl * K;
+      S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0);
+      int kk = 0;
+      for (; kk + 3 < K; kk += 4) {
+        fma_s(a0, vr[kk], cs[kk * P + b]);
+        fma_s(a1, vr[kk + 1], cs[(kk + 1) * P + b]);
+        fma_s(a2, vr[kk + 2], cs[(kk + 2) * P + b]);
+        fma_s(a3, vr[kk + 3], cs[(kk + 3) * P + b]);
+      }
+      for (; kk < K; ++kk) fma_s(a0, vr[kk], cs[kk * P + b]);
+      const S sum = (a0 + a1) + (a2 + a3);
+      const int64_t r = r0 + rl;
+      Y[r * ldy + b] = mode == 0 ? W[r * ldw + b] - sum : sum;
+    }
   }
 }
 
@@ -195,29 +203,36 @@ size_t bgmres_part_doubles(int K, int P) { return (size_t)2 * K * P * (size_t)bg
 
 int bgmres_launch_dot(int st, int64_t n, int K, int P, const void* V, int64_t ldv, const void* W, int64_t ldw,
                       double* part, unsigned* counter, void* out, cudaStream_t s) {
+  (void)counter;
   if (K < 1 || K > 1024 || P < 1 || P > BG_PMAX) return (int)cudaErrorInvalidValue;
   const int grid = bgmres_dot_grid();
   const int U = (K + 255) / 256;
   BG_ST_SWITCH(st, {
-    if (U == 1) bg_dot_kernel<S, 1><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part, counter, (cdouble*)out);
-    else if (U == 2) bg_dot_kernel<S, 2><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part, counter, (cdouble*)out);
-    else bg_dot_kernel<S, 4><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part, counter, (cdouble*)out);
+    if (U == 1) bg_dot_kernel<S, 1><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part);
+    else if (U == 2) bg_dot_kernel<S, 2><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part);
+    else bg_dot_kernel<S, 4><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part);
   });
-  mor_count_launches(1);
+  const int nout = K * P;
+  bg_reduce_kernel<<<(nout + 255) / 256, 256, 0, s>>>(nout, grid, part, (cdouble*)out);
+  mor_count_launches(2);
   return (int)cudaGetLastError();
 }
 
 int bgmres_launch_update(int st, int64_t n, int K, int P, const void* V, int64_t ldv, const void* C, const void* W,
                          int64_t ldw, int mode, void* Y, int64_t ldy, cudaStream_t s) {
   if (K < 1 || P < 1 || P > BG_PMAX) return (int)cudaErrorInvalidValue;
-  const size_t sm = st_size(st) * (size_t)K * P;
-  if (sm > 160 * 1024) return (int)cudaErrorInvalidValue;
-  const int grid = (int)std::min<int64_t>((n + 31) / 32, (int64_t)mor_device_sms() * 8);
+  const size_t es = st_size(st);
+  const size_t cbytes = es * (size_t)K * P;
+  // rows per tile: the V tile and C within 96 KB of shared memory, at most 32
+  int T = (int)std::min<size_t>(32, ((size_t)96 * 1024 > cbytes ? ((size_t)96 * 1024 - cbytes) : 0) / (es * K));
+  if (T < 1) return (int)cudaErrorInvalidValue;
+  const size_t sm = cbytes + es * (size_t)T * K;
+  const int grid = (int)std::min<int64_t>((n + T - 1) / T, (int64_t)mor_device_sms() * 4);
   BG_ST_SWITCH(st, {
     cudaError_t e = cudaFuncSetAttribute(bg_update_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    bg_update_kernel<S><<<grid, 256, sm, s>>>(n, K, P, (const S*)V, ldv, (const cdouble*)C, (const S*)W, ldw, mode,
-                                              (S*)Y, ldy);
+    bg_update_kernel<S><<<grid, 256, sm, s>>>(n, K, P, T, (const S*)V, ldv, (const cdouble*)C, (const S*)W, ldw,
+                                              mode, (S*)Y, ldy);
   });
   mor_count_launches(1);
   return (int)cudaGetLastError();
