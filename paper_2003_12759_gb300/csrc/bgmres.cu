@@ -15,6 +15,7 @@
 #include "krylov_state.cuh"
 
 #include <algorithm>
+#include <cuda_pipeline.h>
 
 namespace {
 
@@ -36,15 +37,16 @@ constexpr int BG_PMAX = 8;       // right-hand sides per block
 // g, g + G, ..., whose V loads are independent (unrolled, all in flight).
 // The groups' sums meet in shared memory; bg_reduce sums the blocks'
 // partials in a fixed order.
-constexpr int BG_TILE = 32;
+constexpr int BG_RPT = 16;          // tile rows per thread of the dot kernel
 template <typename S, int U>
 __global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, const S* __restrict__ V, int64_t ldv,
                                                      const S* __restrict__ W, int64_t ldw, double* part) {
   __shared__ double red[128 * BG_PMAX][2];
-  __shared__ S ws[BG_TILE][BG_PMAX];
+  __shared__ S ws[BG_RPT * 8][BG_PMAX];
   const int KT = K >= 256 ? 256 : ((K + 31) / 32) * 32;
   const int G = 256 / KT;
   const int g = threadIdx.x / KT, t = threadIdx.x % KT;
+  const int TR = BG_RPT * G;                     // tile rows: 16 per thread
   S acc[U][BG_PMAX];
 #pragma unroll
   for (int u = 0; u < U; ++u)
@@ -53,24 +55,31 @@ __global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, co
   const int64_t rpb = (n + gridDim.x - 1) / gridDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rpb;
   const int64_t r1 = r0 + rpb < n ? r0 + rpb : n;
-  for (int64_t tr = r0; tr < r1; tr += BG_TILE) {
-    const int rows = (int)(r1 - tr < BG_TILE ? r1 - tr : BG_TILE);
+  for (int64_t tr = r0; tr < r1; tr += TR) {
+    const int rows = (int)(r1 - tr < TR ? r1 - tr : TR);
     __syncthreads();
-    for (int i = threadIdx.x; i < BG_TILE * BG_PMAX; i += blockDim.x) {
+    for (int i = threadIdx.x; i < TR * BG_PMAX; i += blockDim.x) {
       const int rr = i / BG_PMAX, b = i % BG_PMAX;
       ws[rr][b] = (rr < rows && b < P) ? W[(tr + rr) * ldw + b] : S(0);
     }
     __syncthreads();
     if (g < G) {
-#pragma unroll 4
-      for (int rr = g; rr < rows; rr += G) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int kk = t + KT * u;
-          if (kk < K) {
-            const S v = conj_(V[(tr + rr) * ldv + kk]);
+      for (int u = 0; u < U; ++u) {
+        const int kk = t + KT * u;
+        if (kk < K) {
+          // all 16 loads of the thread's rows in flight, then the products
+          S vr[BG_RPT];
 #pragma unroll
-            for (int b = 0; b < BG_PMAX; ++b) fma_s(acc[u][b], v, ws[rr][b]);
+          for (int i = 0; i < BG_RPT; ++i) {
+            const int rr = g + i * G;
+            vr[i] = rr < rows ? conj_(V[(tr + rr) * ldv + kk]) : S(0);
+          }
+#pragma unroll
+          for (int i = 0; i < BG_RPT; ++i) {
+            const int rr = g + i * G;
+#pragma unroll
+            for (int b = 0; b < BG_PMAX; ++b) fma_s(acc[u][b], vr[i], ws[rr < TR ? rr : 0][b]);
           }
         }
       }
@@ -114,17 +123,20 @@ __global__ void __launch_bounds__(256) bg_dot_kernel(int64_t n, int K, int P, co
   }
 }
 
-// out[o] = sum over the dot kernel's blocks of their partials, in block order
-// (one thread per output: the partials of an output are read coalesced)
+// out[o] = sum over the dot kernel's blocks of their partials: one warp per
+// output, lane l summing blocks l, l + 32, ..., then a fixed-order warp sum
 __global__ void bg_reduce_kernel(int nout, int nblk, const double* __restrict__ part, cdouble* __restrict__ out) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (o >= nout) return;
   double re = 0.0, im = 0.0;
-  for (int blk = 0; blk < nblk; ++blk) {
+  for (int blk = lane; blk < nblk; blk += 32) {
     re += part[((size_t)blk * nout + o) * 2 + 0];
     im += part[((size_t)blk * nout + o) * 2 + 1];
   }
-  out[o] = cdouble(re, im);
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane == 0) out[o] = cdouble(re, im);
 }
 
 // mode 0: Y[r, b] = W[r, b] - sum_kk V[r, kk] C[kk * P + b]
@@ -149,10 +161,13 @@ __global__ void __launch_bounds__(256) bg_update_kernel(int64_t n, int K, int P,
     const int64_t r0 = tile * T;
     const int rows = (int)(n - r0 < T ? n - r0 : T);
     __syncthreads();
+    // asynchronous copies: every element of the tile in flight at once
     for (int i = threadIdx.x; i < rows * K; i += blockDim.x) {
       const int rr = i / K, kk = i % K;
-      vs[i] = V[(r0 + rr) * ldv + kk];
+      __pipeline_memcpy_async(vs + i, V + (r0 + rr) * ldv + kk, sizeof(S));
     }
+    __pipeline_commit();
+    __pipeline_wait_prior(0);
     __syncthreads();
     if (rl < rows && b < P) {
       const S* vr = vs + (size_t)rl * K;
@@ -197,7 +212,7 @@ __global__ void bg_copy_kernel(int64_t n, int P, const S* __restrict__ src, int6
 
 int bgmres_max_cols() { return BG_PMAX; }
 
-int bgmres_dot_grid() { return 4 * mor_device_sms(); }
+int bgmres_dot_grid() { return 2 * mor_device_sms(); }
 
 size_t bgmres_part_doubles(int K, int P) { return (size_t)2 * K * P * (size_t)bgmres_dot_grid(); }
 
@@ -213,7 +228,7 @@ int bgmres_launch_dot(int st, int64_t n, int K, int P, const void* V, int64_t ld
     else bg_dot_kernel<S, 4><<<grid, 256, 0, s>>>(n, K, P, (const S*)V, ldv, (const S*)W, ldw, part);
   });
   const int nout = K * P;
-  bg_reduce_kernel<<<(nout + 255) / 256, 256, 0, s>>>(nout, grid, part, (cdouble*)out);
+  bg_reduce_kernel<<<(nout + 7) / 8, 256, 0, s>>>(nout, grid, part, (cdouble*)out);
   mor_count_launches(2);
   return (int)cudaGetLastError();
 }
