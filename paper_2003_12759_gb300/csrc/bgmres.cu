@@ -142,57 +142,35 @@ __global__ void bg_reduce_kernel(int nout, int nblk, const double* __restrict__ 
 // mode 0: Y[r, b] = W[r, b] - sum_kk V[r, kk] C[kk * P + b]
 // mode 1: Y[r, b] =          sum_kk V[r, kk] C[kk * P + b]
 // The block walks tiles of T <= 32 rows: the tile's rows of V (T x K) are
-// copied into shared memory asynchronously (16-byte copies when the rows
-// allow, double-buffered: the next tile is in flight while this one is
-// used), then thread (row rr, column b) of the 32 x 8 layout sums over kk
-// from shared memory (four independent partial sums, combined in a fixed
-// order).  Shared memory: C (K x P), then two V tiles (T x K each).
+// loaded into shared memory with coalesced loads, then thread (row rr, column
+// b) of the 32 x 8 layout sums over kk from shared memory (four independent
+// partial sums, combined in a fixed order).  Shared memory: C (K x P), then
+// the V tile (T x K).
 template <typename S>
-__global__ void __launch_bounds__(256) bg_update_kernel(int64_t n, int K, int P, int T, int vec16,
-                                                        const S* __restrict__ V, int64_t ldv,
-                                                        const cdouble* __restrict__ C, const S* W, int64_t ldw,
-                                                        int mode, S* Y, int64_t ldy) {
+__global__ void __launch_bounds__(256) bg_update_kernel(int64_t n, int K, int P, int T, const S* __restrict__ V,
+                                                        int64_t ldv, const cdouble* __restrict__ C, const S* W,
+                                                        int64_t ldw, int mode, S* Y, int64_t ldy) {
   extern __shared__ __align__(16) unsigned char bg_smem[];
   S* cs = reinterpret_cast<S*>(bg_smem);
-  const size_t cbytes = ((sizeof(S) * (size_t)K * P) + 15) / 16 * 16;
-  S* vbuf[2] = {reinterpret_cast<S*>(bg_smem + cbytes), reinterpret_cast<S*>(bg_smem + cbytes) + (size_t)T * K};
+  S* vs = cs + (size_t)K * P;
   for (int t = threadIdx.x; t < K * P; t += blockDim.x) cs[t] = from_cd<S>(C[t]);
   const int b = threadIdx.x & 7;
   const int rl = threadIdx.x >> 3;
   const int64_t ntiles = (n + T - 1) / T;
-  auto issue = [&](int64_t tile, S* buf) {
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * T;
     const int rows = (int)(n - r0 < T ? n - r0 : T);
-    if (vec16) {
-      const int cpr = (int)(K * sizeof(S) / 16);        // 16-byte chunks per row
-      for (int i = threadIdx.x; i < rows * cpr; i += blockDim.x) {
-        const int rr = i / cpr, c = i % cpr;
-        __pipeline_memcpy_async(reinterpret_cast<char*>(buf + (size_t)rr * K) + 16 * c,
-                                reinterpret_cast<const char*>(V + (r0 + rr) * ldv) + 16 * c, 16);
-      }
-    } else {
-      for (int i = threadIdx.x; i < rows * K; i += blockDim.x) {
-        const int rr = i / K, kk = i % K;
-        __pipeline_memcpy_async(buf + i, V + (r0 + rr) * ldv + kk, sizeof(S));
-      }
+    __syncthreads();
+    // asynchronous copies: every element of the tile in flight at once
+    for (int i = threadIdx.x; i < rows * K; i += blockDim.x) {
+      const int rr = i / K, kk = i % K;
+      __pipeline_memcpy_async(vs + i, V + (r0 + rr) * ldv + kk, sizeof(S));
     }
     __pipeline_commit();
-  };
-  int it = 0;
-  if ((int64_t)blockIdx.x < ntiles) issue(blockIdx.x, vbuf[0]);
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int64_t next = tile + gridDim.x;
-    if (next < ntiles) {
-      issue(next, vbuf[(it + 1) & 1]);
-      __pipeline_wait_prior(1);
-    } else {
-      __pipeline_wait_prior(0);
-    }
+    __pipeline_wait_prior(0);
     __syncthreads();
-    const int64_t r0 = tile * T;
-    const int rows = (int)(n - r0 < T ? n - r0 : T);
     if (rl < rows && b < P) {
-      const S* vr = vbuf[it & 1] + (size_t)rl * K;
+      const S* vr = vs + (size_t)rl * K;
       S a0 = S(0), a1 = S(0), a2 = S(0), a3 = S(0);
       int kk = 0;
       for (; kk + 3 < K; kk += 4) {
@@ -206,7 +184,6 @@ __global__ void __launch_bounds__(256) bg_update_kernel(int64_t n, int K, int P,
       const int64_t r = r0 + rl;
       Y[r * ldy + b] = mode == 0 ? W[r * ldw + b] - sum : sum;
     }
-    __syncthreads();          // this tile's buffer is refilled two tiles later
   }
 }
 
@@ -235,7 +212,7 @@ __global__ void bg_copy_kernel(int64_t n, int P, const S* __restrict__ src, int6
 
 int bgmres_max_cols() { return BG_PMAX; }
 
-int bgmres_dot_grid() { return 4 * mor_device_sms(); }
+int bgmres_dot_grid() { return 2 * mor_device_sms(); }
 
 size_t bgmres_part_doubles(int K, int P) { return (size_t)2 * K * P * (size_t)bgmres_dot_grid(); }
 
@@ -260,20 +237,17 @@ int bgmres_launch_update(int st, int64_t n, int K, int P, const void* V, int64_t
                          int64_t ldw, int mode, void* Y, int64_t ldy, cudaStream_t s) {
   if (K < 1 || P < 1 || P > BG_PMAX) return (int)cudaErrorInvalidValue;
   const size_t es = st_size(st);
-  const size_t cbytes = (es * (size_t)K * P + 15) / 16 * 16;
-  // rows per tile: C and two V tiles within 96 KB of shared memory, at most 32
-  const size_t room = (size_t)96 * 1024 > cbytes ? (size_t)96 * 1024 - cbytes : 0;
-  const int T = (int)std::min<size_t>(32, room / (2 * es * K));
+  const size_t cbytes = es * (size_t)K * P;
+  // rows per tile: the V tile and C within 96 KB of shared memory, at most 32
+  int T = (int)std::min<size_t>(32, ((size_t)96 * 1024 > cbytes ? ((size_t)96 * 1024 - cbytes) : 0) / (es * K));
   if (T < 1) return (int)cudaErrorInvalidValue;
-  const size_t sm = cbytes + 2 * es * (size_t)T * K;
-  // 16-byte copies when every row of the tile starts and ends on 16 bytes
-  const int vec16 = ((K * es) % 16 == 0 && (ldv * es) % 16 == 0 && ((uintptr_t)V % 16) == 0) ? 1 : 0;
+  const size_t sm = cbytes + es * (size_t)T * K;
   const int grid = (int)std::min<int64_t>((n + T - 1) / T, (int64_t)mor_device_sms() * 4);
   BG_ST_SWITCH(st, {
     cudaError_t e = cudaFuncSetAttribute(bg_update_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    bg_update_kernel<S><<<grid, 256, sm, s>>>(n, K, P, T, vec16, (const S*)V, ldv, (const cdouble*)C, (const S*)W,
-                                              ldw, mode, (S*)Y, ldy);
+    bg_update_kernel<S><<<grid, 256, sm, s>>>(n, K, P, T, (const S*)V, ldv, (const cdouble*)C, (const S*)W, ldw,
+                                              mode, (S*)Y, ldy);
   });
   mor_count_launches(1);
   return (int)cudaGetLastError();
