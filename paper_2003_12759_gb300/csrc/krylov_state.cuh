@@ -106,11 +106,6 @@ __device__ __forceinline__ Pack<S, CPT> ldp(const S* p) {
   if constexpr (CPT * sizeof(S) == 16) {
     const float4 t = *reinterpret_cast<const float4*>(p);
     memcpy(&o, &t, 16);
-  } else if constexpr (CPT * sizeof(S) == 32) {
-    const float4 t0 = reinterpret_cast<const float4*>(p)[0];
-    const float4 t1 = reinterpret_cast<const float4*>(p)[1];
-    memcpy(&o, &t0, 16);
-    memcpy(reinterpret_cast<char*>(&o) + 16, &t1, 16);
   } else {
 #pragma unroll
     for (int j = 0; j < CPT; ++j) o.v[j] = p[j];
@@ -123,12 +118,6 @@ __device__ __forceinline__ void stp(S* p, const Pack<S, CPT>& o) {
     float4 t;
     memcpy(&t, &o, 16);
     *reinterpret_cast<float4*>(p) = t;
-  } else if constexpr (CPT * sizeof(S) == 32) {
-    float4 t0, t1;
-    memcpy(&t0, &o, 16);
-    memcpy(&t1, reinterpret_cast<const char*>(&o) + 16, 16);
-    reinterpret_cast<float4*>(p)[0] = t0;
-    reinterpret_cast<float4*>(p)[1] = t1;
   } else {
 #pragma unroll
     for (int j = 0; j < CPT; ++j) p[j] = o.v[j];

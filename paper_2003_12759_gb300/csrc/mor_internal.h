@@ -6,12 +6,6 @@
 #include <string>
 #include <vector>
 
-// two lanes of 24 / 32 bytes for complex64 rows of stride 6 / 8 instead of
-// four 16-byte lanes (an experiment; off)
-#ifndef MOR_WIDE_LANES
-#define MOR_WIDE_LANES 0
-#endif
-
 // scalar type codes for runtime dispatch
 enum ScalarType { ST_F32 = 0, ST_F64 = 1, ST_C32 = 2, ST_C64 = 3 };
 inline bool st_is_cplx(int st) { return st >= ST_C32; }
@@ -81,9 +75,6 @@ inline int row_stride(int st, int k) {
 inline void lane_shape(int st, int ld, int* tpr, int* cpt) {
   const int es = (int)st_size(st);
   const int c = 16 / es;
-#if MOR_WIDE_LANES
-  if (st == ST_C32 && (ld == 6 || ld == 8)) { *tpr = 2; *cpt = ld / 2; return; }
-#endif
   if (ld * es < 16 || ld % c != 0) { *tpr = 1; *cpt = ld; return; }
   *cpt = c;
   *tpr = next_pow2(ld / c);

@@ -18,9 +18,6 @@ int dispatch_shape(int st, int ld, F&& f) {
   MOR_SHAPE_CASE(ST_F64, double, 4, 2) MOR_SHAPE_CASE(ST_F64, double, 8, 2) MOR_SHAPE_CASE(ST_F64, double, 1, 3)
   MOR_SHAPE_CASE(ST_C32, cfloat, 1, 1) MOR_SHAPE_CASE(ST_C32, cfloat, 1, 2) MOR_SHAPE_CASE(ST_C32, cfloat, 2, 2)
   MOR_SHAPE_CASE(ST_C32, cfloat, 4, 2) MOR_SHAPE_CASE(ST_C32, cfloat, 8, 2)
-#if MOR_WIDE_LANES
-  MOR_SHAPE_CASE(ST_C32, cfloat, 2, 3) MOR_SHAPE_CASE(ST_C32, cfloat, 2, 4)
-#endif
   MOR_SHAPE_CASE(ST_C64, cdouble, 1, 1) MOR_SHAPE_CASE(ST_C64, cdouble, 2, 1) MOR_SHAPE_CASE(ST_C64, cdouble, 4, 1)
   MOR_SHAPE_CASE(ST_C64, cdouble, 8, 1) MOR_SHAPE_CASE(ST_C64, cdouble, 16, 1)
   return (int)cudaErrorInvalidValue;

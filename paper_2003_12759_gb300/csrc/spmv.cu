@@ -53,24 +53,20 @@ template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 #define MOR_OP_GCH 2
 #endif
 template <typename S, int CPT> constexpr bool narrow_slice() { return CPT * sizeof(S) <= 16; }
-template <typename S, int CPT> constexpr bool wide32_slice() { return MOR_WIDE_LANES && CPT * sizeof(S) > 16 && CPT * sizeof(S) <= 32; }
-template <typename S, int CPT> constexpr int factor_chunk() {
-  return narrow_slice<S, CPT>() ? MOR_FACTOR_GCH : (wide32_slice<S, CPT>() ? 2 : 1);
-}
+template <typename S, int CPT> constexpr int factor_chunk() { return narrow_slice<S, CPT>() ? MOR_FACTOR_GCH : 1; }
 template <typename S, int CPT> constexpr int op_chunk() { return narrow_slice<S, CPT>() ? MOR_OP_GCH : 1; }
 #ifndef MOR_FACTOR_MINB
 #define MOR_FACTOR_MINB 8
 #endif
 template <typename S, int CPT> constexpr int min_blocks() {
   return narrow_slice<S, CPT>() ? ((sizeof(S) == 8 && !is_cplx<S>::value && CPT > 1 && MOR_FACTOR_MINB > 6)
-                                       ? 6 : MOR_FACTOR_MINB) : (wide32_slice<S, CPT>() ? 6 : 1);
+                                       ? 6 : MOR_FACTOR_MINB) : 1;
 }
 #ifndef MOR_OP_MINB
 #define MOR_OP_MINB 8
 #endif
 template <typename S, int CPT> constexpr int op_min_blocks() {
-  return narrow_slice<S, CPT>() ? (sizeof(typename real_of<S>::type) == 8 ? 5 : MOR_OP_MINB)
-                                : (wide32_slice<S, CPT>() ? 5 : 1);
+  return narrow_slice<S, CPT>() ? (sizeof(typename real_of<S>::type) == 8 ? 5 : MOR_OP_MINB) : 1;
 }
 
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
