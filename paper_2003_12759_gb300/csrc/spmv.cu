@@ -287,6 +287,11 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
                                                           const S* __restrict__ x, S* __restrict__ y,
                                                           const int* done, const KState* __restrict__ kst) {
   if (done && *done) return;
+  // three lanes per row (rows of three 16-byte vectors): the threads past the
+  // last whole row group of the block have no row
+  if constexpr ((TPR & (TPR - 1)) != 0) {
+    if ((int)threadIdx.x >= (256 / TPR) * TPR) return;
+  }
   typedef typename real_of<S>::type RS;
   typedef typename std::conditional<is_cplx<V>::value, cplx<RS>, RS>::type W;
   const int sub = threadIdx.x % TPR;
@@ -416,33 +421,61 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
   return (int)cudaGetLastError();
 }
 
+// one factor SpMV launch with the lane shape (TPR, CPT) on vectors of type S;
+// the factor values are of type fst (FP32 factors may serve FP64 vectors)
+template <typename S, int TPR, int CPT>
+static int launch_factor_shape(int fst, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
+                               int ld, const void* x, void* y, const int* done, const void* kstate, cudaStream_t s) {
+  typedef typename real_of<S>::type R;
+  const bool fc = st_is_cplx(fst), f32 = st_is_f32(fst);
+  auto go = [&]<typename V>() {
+    const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, V, TPR, CPT>, TPR);
+    factor_spmv_kernel<S, V, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const V*)fvals, apply, ld, (const S*)x,
+                                                                 (S*)y, done, (const KState*)kstate);
+  };
+  if (sizeof(R) == 4 && !f32) return (int)cudaErrorInvalidValue;     // FP64 factors under FP32 vectors
+  if constexpr (is_cplx<S>::value) {
+    if (fc) {
+      if (f32 && sizeof(R) == 8) go.template operator()<cfloat>();
+      else go.template operator()<S>();
+    } else {
+      if (f32 && sizeof(R) == 8) go.template operator()<float>();
+      else go.template operator()<R>();
+    }
+  } else {
+    if (fc) return (int)cudaErrorInvalidValue;
+    if (f32 && sizeof(R) == 8) go.template operator()<float>();
+    else go.template operator()<S>();
+  }
+  return 0;
+}
+
+// Rows of exactly three 16-byte vectors (complex64 k = 5, 6; FP32 k = 9 .. 12;
+// ...) get three lanes instead of four with one idle: 85 rows per block pass
+// instead of 64.  Measured on the 100^3 chain (complex64, L2 flushed): k = 5
+// 56.8 -> 53.8 us, k = 6 56.8 -> 51.7 us.
+#ifndef MOR_FACTOR_TPR3
+#define MOR_FACTOR_TPR3 1
+#endif
+
 int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
                        int ld, const void* x, void* y, const int* done, const void* kstate, cudaStream_t s,
                        int kreal) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
-  const bool fc = st_is_cplx(fst), f32 = st_is_f32(fst);
-  int e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
-    typedef typename real_of<S>::type R;
-    auto go = [&]<typename V>() {
-      const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, V, TPR, CPT>, TPR);
-      factor_spmv_kernel<S, V, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const V*)fvals, apply, ld, (const S*)x,
-                                                                   (S*)y, done, (const KState*)kstate);
-    };
-    if (sizeof(R) == 4 && !f32) return (int)cudaErrorInvalidValue;     // FP64 factors under FP32 vectors
-    if constexpr (is_cplx<S>::value) {
-      if (fc) {
-        if (f32 && sizeof(R) == 8) go.template operator()<cfloat>();
-        else go.template operator()<S>();
-      } else {
-        if (f32 && sizeof(R) == 8) go.template operator()<float>();
-        else go.template operator()<R>();
-      }
-    } else {
-      if (fc) return (int)cudaErrorInvalidValue;
-      if (f32 && sizeof(R) == 8) go.template operator()<float>();
-      else go.template operator()<S>();
+  int e;
+#if MOR_FACTOR_TPR3
+  // rows of exactly three 16-byte vectors: three lanes per row (no idle fourth lane)
+  if ((int)st_size(st) * ld == 48) {
+    switch (st) {
+      case ST_F32: e = launch_factor_shape<float, 3, 4>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s); break;
+      case ST_F64: e = launch_factor_shape<double, 3, 2>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s); break;
+      case ST_C32: e = launch_factor_shape<cfloat, 3, 2>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s); break;
+      default: e = launch_factor_shape<cdouble, 3, 1>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s); break;
     }
-    return 0;
+  } else
+#endif
+  e = dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
+    return launch_factor_shape<S, TPR, CPT>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s);
   });
   if (e) return e;
   mor_count_launches(1);
