@@ -258,6 +258,40 @@ def _spmv_bytes(kernel, k, n, nnz, precision_mixed, cplx):
     return nnz * (4 + s_fval) + 4 * (n + 1) + k * n * 2 * s_vec
 
 
+def weighted_roofline(per, peak):
+    """The roofline of the dominant SpMV over the widths a run used.  per maps
+    a kernel name to {"rows": [{"k", "complex", "launches", "ms", "bytes",
+    "GBs", "traffic"}, ...]} (one row per width that launched, with its live
+    time per launch and algorithmic bytes).  The dominant kernel is the one
+    with the most launches x time; achieved = its launch-weighted bytes over
+    its launch-weighted time, traffic its launch-weighted DRAM bytes (None
+    unless every width has a profile).  Returns (roofline dict, per-kernel
+    summary)."""
+    tot = {}
+    for kn, v in per.items():
+        t = sum(r["launches"] * r["ms"] for r in v["rows"])
+        b = sum(r["launches"] * r["bytes"] for r in v["rows"])
+        n = sum(r["launches"] for r in v["rows"])
+        tot[kn] = (t, b, n)
+    dom = max(per, key=lambda x: tot[x][0])
+    t, b, nl = tot[dom]
+    rows = per[dom]["rows"]
+    ach = b / (t * 1e-3) / 1e9 if t > 0 else 0.0
+    tr = [r.get("traffic") for r in rows]
+    traffic = (sum(r["launches"] * r["traffic"] for r in rows) / nl) if (tr and all(x is not None for x in tr)) else None
+    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": traffic, "ms_per_launch": t / max(1, nl), "algorithmic_bytes_per_launch": int(b / max(1, nl)),
+            "weighting": "launches of the timed steps by width k (time per launch with L2 flushed, launch overhead "
+                         "subtracted)",
+            "widths": [{kk: r[kk] for kk in ("k", "complex", "launches", "ms", "GBs")} for r in rows]}
+    all_t = sum(x[0] for x in tot.values())
+    other = {kn: {"ms_per_launch": tot[kn][0] / max(1, tot[kn][2]),
+                  "GBs": (tot[kn][1] / (tot[kn][0] * 1e-3) / 1e9) if tot[kn][0] > 0 else None,
+                  "launches": int(tot[kn][2]), "share_of_spmv_time": tot[kn][0] / max(1e-30, all_t)}
+             for kn in per}
+    return roof, other
+
+
 def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False, reuse=None):
     import torch
     import paper_2003_12759_gb300 as mor
@@ -347,26 +381,10 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False,
                 rows.append({"k": k, "complex": cplx, "launches": int(counts[k]), "ms": ms, "bytes": int(b),
                              "GBs": b / (ms * 1e-3) / 1e9,
                              "traffic": profiled_traffic(kname, k, fmt_name, args.grid) if cplx else None})
-        tot_t = sum(r["launches"] * r["ms"] for r in rows)
-        tot_b = sum(r["launches"] * r["bytes"] for r in rows)
-        per[kname] = {"rows": rows, "ms_total": tot_t, "bytes_total": tot_b,
-                      "GBs": tot_b / (tot_t * 1e-3) / 1e9 if tot_t > 0 else None}
-    dom = max(per, key=lambda x: per[x]["ms_total"])
-    P = per[dom]
-    nl = sum(r["launches"] for r in P["rows"])
-    tr = [r["traffic"] for r in P["rows"]]
-    traffic = (sum(r["launches"] * r["traffic"] for r in P["rows"]) / nl) if (tr and all(x is not None for x in tr)) else None
-    ach = P["GBs"]
-    roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "peak_kind": "burst, " + peak_kind, "traffic": traffic,
-            "ms_per_launch": P["ms_total"] / nl, "algorithmic_bytes_per_launch": int(P["bytes_total"] / nl),
-            "weighting": "launches of the timed steps by width k (CUDA-event time per width, L2 flushed)",
-            "widths": [{kk: r[kk] for kk in ("k", "complex", "launches", "ms", "GBs")} for r in P["rows"]],
-            "format": {1: "csr", 2: "sell-32"}.get(info["format"], info["format"])}
-    other = {kn: {"ms_per_launch": (v["ms_total"] / max(1, sum(r["launches"] for r in v["rows"]))),
-                  "GBs": v["GBs"], "launches": int(sum(r["launches"] for r in v["rows"])),
-                  "share_of_spmv_time": v["ms_total"] / max(1e-30, sum(x["ms_total"] for x in per.values()))}
-             for kn, v in per.items()}
+        per[kname] = {"rows": rows}
+    roof, other = weighted_roofline(per, peak)
+    roof.update({"peak_kind": "burst, " + peak_kind,
+                 "format": {1: "csr", 2: "sell-32"}.get(info["format"], info["format"])})
     out.update({"roofline": roof, "kernels": other})
     mor.mor_destroy(h)
     # ---- end to end through the public API with host buffers: a fresh handle,

@@ -30,3 +30,27 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_weighted_roofline_is_the_launch_weighted_mix():
+    """The roofline weights each width by its launches: achieved = sum of
+    launches x bytes over sum of launches x time of the dominant kernel; the
+    traffic is reported only when every width has a profile."""
+    sys.path.insert(0, ROOT)
+    import bench
+    per = {"factor_spmv": {"rows": [
+               {"k": 1, "complex": True, "launches": 300, "ms": 0.02, "bytes": 100e6, "GBs": 5000.0, "traffic": 90e6},
+               {"k": 7, "complex": True, "launches": 100, "ms": 0.06, "bytes": 200e6, "GBs": 3333.3, "traffic": 210e6}]},
+           "op_spmv": {"rows": [
+               {"k": 7, "complex": True, "launches": 20, "ms": 0.09, "bytes": 230e6, "GBs": 2555.6, "traffic": None}]}}
+    roof, other = bench.weighted_roofline(per, 6000.0)
+    assert roof["kernel"] == "factor_spmv"
+    t = 300 * 0.02 + 100 * 0.06
+    b = 300 * 100e6 + 100 * 200e6
+    assert abs(roof["achieved"] - b / (t * 1e-3) / 1e9) < 1e-9
+    assert abs(roof["frac"] - roof["achieved"] / 6000.0) < 1e-12
+    assert abs(roof["traffic"] - (300 * 90e6 + 100 * 210e6) / 400) < 1.0
+    assert roof["algorithmic_bytes_per_launch"] == int(b / 400)
+    assert abs(other["factor_spmv"]["share_of_spmv_time"] - t / (t + 20 * 0.09)) < 1e-12
+    per["factor_spmv"]["rows"][1]["traffic"] = None
+    assert bench.weighted_roofline(per, 6000.0)[0]["traffic"] is None
