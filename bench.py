@@ -281,8 +281,8 @@ def weighted_roofline(per, peak):
     traffic = (sum(r["launches"] * r["traffic"] for r in rows) / nl) if (tr and all(x is not None for x in tr)) else None
     roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": traffic, "ms_per_launch": t / max(1, nl), "algorithmic_bytes_per_launch": int(b / max(1, nl)),
-            "weighting": "launches of the timed steps by width k (time per launch with L2 flushed, launch overhead "
-                         "subtracted)",
+            "weighting": "launches of the timed steps by width k; time per launch by CUDA events, each launch after "
+                         "a read of twice the L2 size, the reads' own time subtracted",
             "widths": [{kk: r[kk] for kk in ("k", "complex", "launches", "ms", "GBs")} for r in rows]}
     all_t = sum(x[0] for x in tot.values())
     other = {kn: {"ms_per_launch": tot[kn][0] / max(1, tot[kn][2]),
