@@ -49,6 +49,11 @@ template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 #ifndef MOR_FACTOR_GCH
 #define MOR_FACTOR_GCH 4
 #endif
+// remainder of a row (fewer entries than a chunk) gathered as one chunk (1)
+// or one entry at a time (0)
+#ifndef MOR_FACTOR_TAIL
+#define MOR_FACTOR_TAIL 1
+#endif
 #ifndef MOR_OP_GCH
 #define MOR_OP_GCH 2
 #endif
@@ -275,6 +280,32 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
                                      (cdouble*)red.out, (int*)red.done);
 }
 
+// R entries of a factor row starting at position pc (stride step): indices
+// and values first, then all R gathers in flight, then the products in
+// storage order.
+template <int R, typename S, typename V, typename W, int CPT>
+__device__ __forceinline__ void factor_gather(Pack<S, CPT>& acc, const int* __restrict__ col,
+                                              const V* __restrict__ f, int pc, int step, int ld, int c0,
+                                              const S* __restrict__ x, const L2Pol& pol) {
+  int cc[R];
+  W fv[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    cc[u] = ldh(col + pc + u * step, pol.last);
+    fv[u] = cvt_<W, V>::f(ldh(f + pc + u * step, pol.first));
+  }
+  Pack<S, CPT> xv[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+#pragma unroll
+  for (int u = 0; u < R; ++u)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
+      else fma_r(acc.v[j], fv[u], xv[u].v[j]);
+    }
+}
+
 // Y(:, c) = F X(:, c) where the factor applies to column c, else Y(:, c) = X(:, c).
 // With Krylov states (kst), lanes whose columns of the block's segment have all
 // stopped leave their rows of Y as they were.
@@ -335,42 +366,32 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
         p1 = ldh(pv.rowptr + r + 1, pol.last);
         step = 1;
       }
-      // chunks of GCH nonzeros: indices and values first, then every gather in flight
-      // whole chunks of GCH nonzeros (indices and values first, then every
-      // gather in flight), then the remainder one by one; the sum runs in
-      // storage order either way.  FP32 factor values under FP64 vectors are
-      // widened on load (W).
+      // whole chunks of GCH entries, then the remainder (fewer than GCH) as one
+      // more chunk, so that a row of c GCH + t entries waits on c + 1 rounds
+      // of gathers; the sum runs in storage order either way.  FP32 factor
+      // values under FP64 vectors are widened on load (W).
       constexpr int GCH = factor_chunk<S, CPT>();
       int pc = p0;
-      for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
-        int cc[GCH];
-        W fv[GCH];
-#pragma unroll
-        for (int u = 0; u < GCH; ++u) {
-          cc[u] = ldh(pv.col + pc + u * step, pol.last);
-          fv[u] = cvt_<W, V>::f(ldh(f + pc + u * step, pol.first));
-        }
-        Pack<S, CPT> xv[GCH];
-#pragma unroll
-        for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
-#pragma unroll
-        for (int u = 0; u < GCH; ++u)
-#pragma unroll
-          for (int j = 0; j < CPT; ++j) {
-            if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
-            else fma_r(acc.v[j], fv[u], xv[u].v[j]);
-          }
+      for (; pc + (GCH - 1) * step < p1; pc += GCH * step)
+        factor_gather<GCH, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
+#if MOR_FACTOR_TAIL
+      if constexpr (GCH > 4) {
+        for (; pc + 3 * step < p1; pc += 4 * step)
+          factor_gather<4, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
       }
-      for (; pc < p1; pc += step) {
-        const int cc = ldh(pv.col + pc, pol.last);
-        const W fv = cvt_<W, V>::f(ldh(f + pc, pol.first));
-        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
-#pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-          if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv, xv.v[j]);
-          else fma_r(acc.v[j], fv, xv.v[j]);
+      if constexpr (GCH > 1) {
+        const int rem = (p1 - pc) / step;     // 0 .. 3
+        if constexpr (GCH > 3) {
+          if (rem == 3) factor_gather<3, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
         }
+        if constexpr (GCH > 2) {
+          if (rem == 2) factor_gather<2, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
+        }
+        if (rem == 1) factor_gather<1, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
       }
+#else
+      for (; pc < p1; pc += step) factor_gather<1, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
+#endif
     }
     const int64_t q = (int64_t)r * ld + c0;
     if (mask != (1u << CPT) - 1u) {

@@ -112,3 +112,52 @@ def test_chain_apply_every_width(h, wl, fmt, precision, real):
                 bnd = abs(f) @ bnd
             err = np.abs(Y[:, c] - ref)
             assert np.all(err <= 30 * u * L * bnd + 1e-300), (k, c, float(np.max(err / (bnd + 1e-300))))
+
+
+def _irregular_rows_system(n=2000, seed=31):
+    """Tridiagonal rows plus 100 rows of 40 extra entries (rows 600..699): rows
+    of 3 entries (no whole gather chunk, only a remainder) next to rows of up
+    to 43 (many chunks and every remainder length), in one launch."""
+    rng = np.random.default_rng(seed)
+    T = sp.diags([np.ones(n - 1), np.zeros(n), np.ones(n - 1)], [-1, 0, 1], format="lil")
+    for i in range(600, 700):
+        for j in rng.choice(n, 40, replace=False):
+            if abs(int(j) - i) > 1:
+                T[i, int(j)] = 0.1 * rng.standard_normal()
+    R = sp.csr_matrix(T)
+    dg = np.asarray(abs(R).sum(axis=1)).ravel() + rng.uniform(1.0, 2.0, n)
+    A = sp.csr_matrix(-(R + sp.diags(dg)))
+    A.sort_indices()
+    return A, rng.standard_normal((n, 1)), rng.standard_normal((n, 1))
+
+
+@pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
+@pytest.mark.parametrize("real", [True, False])
+def test_chain_apply_irregular_rows(h, precision, real):
+    """The CSR factor SpMV over rows of very different lengths, every width,
+    against the oracle's chain apply with the GPU's factor values."""
+    A, B, C = _irregular_rows_system()
+    n = A.shape[0]
+    mor.mor_set_system(h, A, B, C, fmt=mor.MOR_FMT_CSR)
+    s = [2.0, 6.0] if real else [2.0 + 1.0j, 6.0 + 0.5j]
+    mor.mor_build_precond(h, s[0], 0, precision)
+    mor.mor_update_precond(h, s[1], 0)
+    rowptr, col = mor.mor_get_pattern(h, 0)
+    assert np.diff(rowptr).max() >= 40
+    F = []
+    for i in range(2):
+        vals, _, _ = mor.mor_get_factor(h, 0, i)
+        F.append(sp.csr_matrix((vals.real if real else vals, col, rowptr), shape=(n, n)))
+    u = U64 if precision == mor.MOR_FP64 else U32
+    for k in KS:
+        sig = np.array([s[c % 2] for c in range(k)], dtype=complex)
+        X = _x(n, k, real, precision, 300 + k)
+        Y = mor.mor_apply_precond(h, sig, X, real=real)
+        for c in range(k):
+            L = c % 2 + 1
+            ref = ospai.chain_apply(F[:L], X[:, c])
+            bnd = np.abs(X[:, c])
+            for f in F[:L]:
+                bnd = abs(f) @ bnd
+            err = np.abs(Y[:, c] - ref)
+            assert np.all(err <= 30 * u * L * bnd + 1e-300), (k, c, float(np.max(err / (bnd + 1e-300))))
