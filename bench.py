@@ -246,16 +246,24 @@ def max_over_ranks(ws, x):
     return float(t.item())
 
 
-def _spmv_bytes(kernel, k, n, nnz, precision_mixed, cplx):
+FORMATS = {"auto": 0, "csr": 1, "sell": 2, "dia": 3}
+FORMAT_NAMES = {1: "csr", 2: "sell", 3: "dia"}
+
+
+def _spmv_bytes(kernel, k, n, nnz, precision_mixed, cplx, fmt=1):
     """Algorithmic bytes of one launch over k columns: the pattern and values
     once, each vector entry read or written once (the operator SpMV of the
-    BiCGSTAB loop also reads the second vector of its fused dot product)."""
+    BiCGSTAB loop also reads the second vector of its fused dot product).
+    CSR and SELL count their column indices and row pointers; the diagonal
+    layout has none (a column is the row plus its diagonal's offset), and its
+    padding entries are not counted either: only the nnz values."""
     s_vec = (8 if cplx else 4) if precision_mixed else (16 if cplx else 8)
     s_val = 4 if precision_mixed else 8
     s_fval = s_val * (2 if cplx else 1)
+    idx = 0 if fmt == 3 else 1
     if kernel == "op_spmv":
-        return nnz * (4 + s_val) + 4 * (n + 1) + s_val * n + k * n * 3 * s_vec
-    return nnz * (4 + s_fval) + 4 * (n + 1) + k * n * 2 * s_vec
+        return nnz * (4 * idx + s_val) + 4 * (n + 1) * idx + s_val * n + k * n * 3 * s_vec
+    return nnz * (4 * idx + s_fval) + 4 * (n + 1) * idx + k * n * 2 * s_vec
 
 
 def weighted_roofline(per, peak):
@@ -302,7 +310,7 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False,
     wl = W.convdiff3d_siso(N=args.grid)
     n = wl.n
     h = mor.mor_create(local, stream)
-    fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
+    fmt = FORMATS[args.fmt]
     mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E, fmt=fmt)
     info = mor.mor_get_info(h)
     prec_name = precision or args.precision
@@ -361,7 +369,7 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False,
     nnz = info["nnz"]
     mixed = opts.precision == mor.MOR_MIXED
     peak, peak_kind = peaks()
-    fmt_name = {1: "csr", 2: "sell"}.get(info["format"], "?")
+    fmt_name = FORMAT_NAMES.get(info["format"], "?")
     per = {}
     Lc = mor.mor_chain_info(h, 0)[0]
     _, sf, stt = mor.mor_get_factor(h, 0, Lc - 1)
@@ -377,14 +385,14 @@ def run_ours(args, ws, rank, local, precision=None, one_shift=None, light=False,
                 if wi == 1 and not cplx and last_factor_complex:
                     continue      # the timed factor (the chain's last) would make the vectors complex
                 ms = mor.mor_time_kernel(h, wi, sig, opts.precision, reps=20)
-                b = _spmv_bytes(kname, k, n, nnz, mixed, cplx)
+                b = _spmv_bytes(kname, k, n, nnz, mixed, cplx, info["format"])
                 rows.append({"k": k, "complex": cplx, "launches": int(counts[k]), "ms": ms, "bytes": int(b),
                              "GBs": b / (ms * 1e-3) / 1e9,
                              "traffic": profiled_traffic(kname, k, fmt_name, args.grid) if cplx else None})
         per[kname] = {"rows": rows}
     roof, other = weighted_roofline(per, peak)
     roof.update({"peak_kind": "burst, " + peak_kind,
-                 "format": {1: "csr", 2: "sell-32"}.get(info["format"], info["format"])})
+                 "format": {1: "csr", 2: "sell-32", 3: "dia"}.get(info["format"], info["format"])})
     out.update({"roofline": roof, "kernels": other})
     mor.mor_destroy(h)
     # ---- end to end through the public API with host buffers: a fresh handle,
@@ -438,7 +446,7 @@ def run_batch(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     sysl = W.uneven_laplace2d_batch(num_systems=args.nsys)
     h = mor.mor_create(local, stream)
-    fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
+    fmt = FORMATS[args.fmt]
     mor.mor_set_batch(h, [w.A for w in sysl], [w.B[:, 0] for w in sysl], [w.C[:, 0] for w in sysl], fmt=fmt)
     nsys, off = mor.mor_batch_info(h)
     shifts = list(np.logspace(0, 4, 8).astype(np.complex128))
@@ -519,7 +527,7 @@ def run_mimo(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     wl = W.convdiff3d_mimo(N=args.grid_mimo, m=8)
     h = mor.mor_create(local, stream)
-    fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
+    fmt = FORMATS[args.fmt]
     mor.mor_set_system(h, wl.A, wl.B, wl.C, fmt=fmt)
     n, m = wl.A.shape[0], wl.B.shape[1]
     dev = torch.device("cuda", local)
@@ -596,7 +604,7 @@ def kernels_only(args):
     import workloads as W
     wl = W.convdiff3d_siso(N=args.grid)
     h = mor.mor_create(0)
-    fmt = {"auto": mor.MOR_FMT_AUTO, "csr": mor.MOR_FMT_CSR, "sell": mor.MOR_FMT_SELL}[args.fmt]
+    fmt = FORMATS[args.fmt]
     mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E, fmt=fmt)
     prec = mor.MOR_FP64 if args.precision == "fp64" else mor.MOR_MIXED
     # seven shift columns, as in the converged IRKA sweeps of this workload (5 complex + 2 real)
@@ -629,7 +637,7 @@ def main():
                     help="skip timing the same iterations with the Frobenius-ratio reuse decision")
     ap.add_argument("--no-comparator", action="store_true",
                     help="skip timing the plain FP64 one-shift-per-launch form next to the default")
-    ap.add_argument("--fmt", default="auto", choices=["auto", "csr", "sell"])
+    ap.add_argument("--fmt", default="auto", choices=list(FORMATS))
     ap.add_argument("--graph-chunk", type=int, default=16, help="Krylov iterations per CUDA-graph replay")
     ap.add_argument("--no-graph", action="store_true", help="launch the Krylov iterations one by one")
     ap.add_argument("--serial-sweeps", action="store_true",

@@ -104,8 +104,15 @@ enum mor_format {
                           choice is kept for the process by pattern signature
                           (device, n, nnz, kind of E, hash of the pattern) */
     MOR_FMT_CSR = 1,   /* compressed sparse row, one thread per row      */
-    MOR_FMT_SELL = 2   /* SELL-C-sigma with C = 32, sigma = 1 (slices of 32 rows,
+    MOR_FMT_SELL = 2,  /* SELL-C-sigma with C = 32, sigma = 1 (slices of 32 rows,
                           column-major inside a slice: coalesced loads)   */
+    MOR_FMT_DIA = 3    /* diagonal layout: one value array per distinct
+                          offset c - r, column = row + offset (no column
+                          indices; values and gathers coalesced).  Only for
+                          patterns with at most 32 distinct diagonals and at
+                          most 25% padding (structured-grid stencils);
+                          MOR_EINVAL otherwise.  The autotuner times it
+                          whenever the pattern qualifies. */
 };
 
 /* Options of a solve sweep.  mor_default_opts fills the defaults shown. */

@@ -38,7 +38,7 @@ MOR_FP64, MOR_MIXED = 0, 1
 MOR_BICGSTAB = 0
 MOR_GMRES = 1
 MOR_BGMRES = 2
-MOR_FMT_AUTO, MOR_FMT_CSR, MOR_FMT_SELL = 0, 1, 2
+MOR_FMT_AUTO, MOR_FMT_CSR, MOR_FMT_SELL, MOR_FMT_DIA = 0, 1, 2, 3
 MOR_REUSE_CHAIN, MOR_REUSE_FIRST, MOR_REUSE_AUTO = 0, 1, 2
 MOR_MAX_R = 64
 MOR_MAX_IO = 8

@@ -8,7 +8,8 @@
 //   * its transpose and the map between the two orders;
 //   * the shadow sets I_j = union over k in J_j of the pattern of column k
 //     (the rows a column least-squares problem of Eq. gen-precond-par touches);
-//   * the SELL-32 layout (slices of 32 rows, column-major inside a slice).
+//   * the SELL-32 layout (slices of 32 rows, column-major inside a slice);
+//   * the diagonal (DIA) layout of patterns with few distinct diagonals.
 #pragma once
 #include <algorithm>
 #include <climits>
@@ -155,6 +156,43 @@ inline void sell_layout(const HostCSR& S, std::vector<int64_t>& sptr, std::vecto
       }
     }
   }
+}
+
+// Diagonal layout: the distinct offsets c - r of the pattern, ascending, and
+// every entry (r, c) at position d n + r, d the index of its offset (so the
+// entries of one diagonal are contiguous and ordered by row, and a row's
+// entries come in the order of its columns).  Positions of no entry are
+// padding (value 0).  Returns false, with nothing set, when the pattern has
+// more than max_diag offsets or its ndiag n stored entries exceed max_fill
+// times its entries (or 2^31).
+inline bool dia_layout(const HostCSR& S, int max_diag, double max_fill, std::vector<int32_t>& offsets,
+                       std::vector<int64_t>& lay) {
+  const int64_t n = S.n;
+  const int64_t nnz = (int64_t)S.col.size();
+  std::vector<int32_t> offs;
+  for (int64_t r = 0; r < n; ++r) {
+    for (int32_t p = S.rowptr[r]; p < S.rowptr[r + 1]; ++p) {
+      const int32_t o = (int32_t)(S.col[p] - r);
+      if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
+        offs.push_back(o);
+        if ((int)offs.size() > max_diag) return false;
+      }
+    }
+  }
+  std::sort(offs.begin(), offs.end());
+  const int64_t nlay = (int64_t)offs.size() * n;
+  if (nnz == 0 || (double)nlay > max_fill * (double)nnz || nlay > (int64_t)INT32_MAX) return false;
+  std::vector<int64_t> out(nnz);
+  for (int64_t r = 0; r < n; ++r) {
+    for (int32_t p = S.rowptr[r]; p < S.rowptr[r + 1]; ++p) {
+      const int32_t o = (int32_t)(S.col[p] - r);
+      const int64_t d = std::lower_bound(offs.begin(), offs.end(), o) - offs.begin();
+      out[p] = d * n + r;
+    }
+  }
+  offsets.swap(offs);
+  lay.swap(out);
+  return true;
 }
 
 }  // namespace mor_host

@@ -42,6 +42,8 @@ struct OpData {
   int64_t n = 0, nnz = 0, nlay = 0;     // rows, CSR entries, stored layout entries
   DBuf rowptr, col;                      // CSR (device)
   DBuf sptr, scol;                       // SELL-32 layout (device)
+  DBuf doff;                             // DIA offsets (device)
+  int ndiag = 0;
   DBuf a64, a32, e64, e32;               // values in layout order
   DBuf ca64, ce64, ca32, ce32;           // values in CSR order (column data for the other op's SPAI)
   DBuf outpos;                           // int64 per column-entry: position in this op's layout
@@ -60,6 +62,8 @@ struct OpData {
     v.rowptr = rowptr.as<int32_t>();
     v.col = (fmt == FMT_SELL) ? scol.as<int32_t>() : col.as<int32_t>();
     v.sptr = sptr.as<int64_t>();
+    v.doff = doff.as<int32_t>();
+    v.ndiag = ndiag;
     return v;
   }
 };

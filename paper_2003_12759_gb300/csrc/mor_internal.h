@@ -12,19 +12,27 @@ inline bool st_is_cplx(int st) { return st >= ST_C32; }
 inline bool st_is_f32(int st) { return st == ST_F32 || st == ST_C32; }
 inline size_t st_size(int st) { return st == ST_F32 ? 4 : (st == ST_C64 ? 16 : 8); }
 
-enum { FMT_CSR = 1, FMT_SELL = 2 };
+enum { FMT_CSR = 1, FMT_SELL = 2, FMT_DIA = 3 };
+// patterns with at most this many distinct diagonals (and at most 25% padding)
+// may be stored in the diagonal layout
+#define MOR_DIA_MAXDIAG 32
 enum { EK_IDENTITY = 0, EK_DIAG = 1, EK_CSR = 2 };
 
 // Device view of a stored sparse pattern (CSR, or SELL-32 with sigma = 1).
 // SELL: rows are cut into slices of 32; slice s holds width_s = (sptr[s+1] -
 // sptr[s]) / 32 slots, slot t of row 32 s + l is at sptr[s] + 32 t + l.
 // Padding slots carry col = the row itself and value 0.
+// DIA: ndiag distinct offsets doff[0] < ... (column = row + doff[d]); the
+// entry of row r on diagonal d is at d n + r; positions with no entry (and
+// columns outside 0 .. n - 1) hold value 0.
 struct PatView {
   int fmt;
   int n;
   const int32_t* rowptr;  // CSR
   const int32_t* col;     // CSR col, or SELL col (padded)
   const int64_t* sptr;    // SELL slice offsets (nslices + 1)
+  const int32_t* doff;    // DIA offsets (ndiag)
+  int ndiag;
 };
 
 // Real-valued operator data for y = sE * (E x) + sA * (A x).

@@ -145,6 +145,7 @@ using mor_host::merge_pattern;
 using mor_host::transpose_pattern;
 using mor_host::shadow_sets;
 using mor_host::sell_layout;
+using mor_host::dia_layout;
 
 int fetch_csr(mor_t h, const mor_csr* M, bool dev, const char* name, HostCSR& out) {
   if (!M || M->n <= 0 || M->nnz < 0 || !M->rowptr || (M->nnz > 0 && (!M->col || !M->val)))
@@ -244,11 +245,22 @@ int build_op(mor_t h, OpData& op, const HostCSR& S, const std::vector<double>& s
   op.h_col = S.col;
   std::vector<int64_t> sptr;
   std::vector<int32_t> scol;
+  std::vector<int32_t> doffs;
+  op.ndiag = 0;
+  op.doff.release();
   if (fmt == FMT_SELL) {
     sell_layout(S, sptr, scol, op.h_lay);
     op.nlay = (int64_t)scol.size();
     // the kernels index stored entries with 32-bit positions
     if (op.nlay > (int64_t)INT32_MAX) return mor_fail(h, MOR_EINVAL, "SELL layout exceeds 2^31 stored entries");
+  } else if (fmt == FMT_DIA) {
+    if (!dia_layout(S, MOR_DIA_MAXDIAG, 1.25, doffs, op.h_lay))
+      return mor_fail(h, MOR_EINVAL, "the pattern has more than %d diagonals or more than 25%% padding in the "
+                                     "diagonal layout", MOR_DIA_MAXDIAG);
+    op.ndiag = (int)doffs.size();
+    op.nlay = (int64_t)op.ndiag * S.n;
+    op.sptr.release();
+    op.scol.release();
   } else {
     op.h_lay.resize(op.nnz);
     for (int64_t p = 0; p < op.nnz; ++p) op.h_lay[p] = p;
@@ -262,6 +274,7 @@ int build_op(mor_t h, OpData& op, const HostCSR& S, const std::vector<double>& s
     MOR_TRY(upload(h, op.sptr, sptr));
     MOR_TRY(upload(h, op.scol, scol));
   }
+  if (fmt == FMT_DIA) MOR_TRY(upload(h, op.doff, doffs));
   std::vector<double> la = permute_to_layout(sa, op.h_lay, op.nlay);
   std::vector<float> la32(la.begin(), la.end());
   MOR_TRY(upload(h, op.a64, la));
@@ -281,38 +294,56 @@ int build_op(mor_t h, OpData& op, const HostCSR& S, const std::vector<double>& s
   return MOR_OK;
 }
 
-// time the FP32 operator SpMV (k = 1 real and k = 8 complex) of a built op
+// Score of a built op's layout for the autotuner: the FP32 operator SpMV
+// (k = 1 real plus k = 8 complex) and four factor SpMVs in the same layout
+// (complex64 values, zero, k = 1 plus k = 8 complex), CUDA-event time of the
+// best of three repetitions after one untimed.  A BiCGSTAB iteration applies
+// the operator twice and the preconditioner chain twice, and the chains of
+// the sweeps hold several factors, so the factor SpMV carries the weight.
 double time_op(mor_t h, OpData& op, int& status) {
   status = MOR_OK;
   const int64_t n = op.n;
-  DBuf x, y;
-  if (x.alloc(n * 8 * sizeof(cfloat)) != cudaSuccess || y.alloc(n * 8 * sizeof(cfloat)) != cudaSuccess) {
+  DBuf x, y, fv, ap;
+  if (x.alloc(n * 8 * sizeof(cfloat)) != cudaSuccess || y.alloc(n * 8 * sizeof(cfloat)) != cudaSuccess ||
+      fv.alloc((size_t)op.nlay * sizeof(cfloat)) != cudaSuccess || ap.alloc(8 * sizeof(int)) != cudaSuccess) {
     status = MOR_ENOMEM;
     return 1e30;
   }
   cudaMemsetAsync(x.p, 0, n * 8 * sizeof(cfloat), h->stream);
+  cudaMemsetAsync(fv.p, 0, (size_t)op.nlay * sizeof(cfloat), h->stream);
+  const int ones[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+  cudaMemcpyAsync(ap.p, ones, sizeof(ones), cudaMemcpyHostToDevice, h->stream);
   OpVals ov{h->ekind, op.a32.p, op.e32.p, h->ediag32.p};
   Coef cf[8];
   for (int c = 0; c < 8; ++c) cf[c] = mor_coef(h, mor_c64{1.0 + c, 0.5});
   PatView pv = op.view();
-  cudaEvent_t e0, e1;
+  cudaEvent_t e0, e1, e2;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
+  cudaEventCreate(&e2);
+  float best_op = 1e30f, best_f = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {
     cudaEventRecord(e0, h->stream);
     launch_op_spmv(ST_F32, h->seg, pv, ov, cf, 1, x.p, y.p, nullptr, nullptr, h->stream);
     launch_op_spmv(ST_C32, h->seg, pv, ov, cf, 8, x.p, y.p, nullptr, nullptr, h->stream);
     cudaEventRecord(e1, h->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (rep > 0) best = std::min(best, ms);
+    launch_factor_spmv(ST_C32, ST_C32, h->seg, pv, fv.p, ap.as<int>(), 1, x.p, y.p, nullptr, nullptr, h->stream);
+    launch_factor_spmv(ST_C32, ST_C32, h->seg, pv, fv.p, ap.as<int>(), 8, x.p, y.p, nullptr, nullptr, h->stream);
+    cudaEventRecord(e2, h->stream);
+    cudaEventSynchronize(e2);
+    float m1 = 0.f, m2 = 0.f;
+    cudaEventElapsedTime(&m1, e0, e1);
+    cudaEventElapsedTime(&m2, e1, e2);
+    if (rep > 0) {
+      best_op = std::min(best_op, m1);
+      best_f = std::min(best_f, m2);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
   if (cudaGetLastError() != cudaSuccess) status = MOR_ECUDA;
-  return best;
+  return (double)best_op + 4.0 * (double)best_f;
 }
 
 int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std::vector<double>* Ediag, const double* B,
@@ -321,7 +352,7 @@ int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std:
   const int64_t n = A.n;
   if (m < 1 || m > MOR_MAX_IO || q < 1 || q > MOR_MAX_IO) return mor_fail(h, MOR_EINVAL, "m and q must be in [1, %d]", MOR_MAX_IO);
   if (!B || !C) return mor_fail(h, MOR_EINVAL, "B and C are required");
-  if (format < MOR_FMT_AUTO || format > MOR_FMT_SELL) return mor_fail(h, MOR_EINVAL, "unknown format %d", format);
+  if (format < MOR_FMT_AUTO || format > MOR_FMT_DIA) return mor_fail(h, MOR_EINVAL, "unknown format %d", format);
   h->has_sys = false;
   h->P.chain.clear(); h->T.chain.clear();
   h->P.chain_prec = h->T.chain_prec = -1;
@@ -363,14 +394,30 @@ int set_system_common(mor_t h, const HostCSR& A, const HostCSR* Ecsr, const std:
   if (fmt == MOR_FMT_AUTO && cached_format(key, &fmt)) {
     MOR_TRY(build_op(h, h->P, S, sa, se, fmt, Ecsr != nullptr));
   } else if (fmt == MOR_FMT_AUTO) {
-    int st1 = 0, st2 = 0;
+    // time the operator SpMV in every layout the pattern admits: CSR, SELL-32,
+    // and the diagonal layout when the pattern has few diagonals
+    int st1 = 0, st2 = 0, st3 = 0, last = FMT_CSR;
     MOR_TRY(build_op(h, h->P, S, sa, se, FMT_CSR, Ecsr != nullptr));
     double tc = time_op(h, h->P, st1);
-    double ts = 1e300;
-    if (build_op(h, h->P, S, sa, se, FMT_SELL, Ecsr != nullptr) == MOR_OK) ts = time_op(h, h->P, st2);
-    if (st1 != MOR_OK || st2 != MOR_OK) return mor_fail(h, MOR_ECUDA, "format autotuning failed");
-    fmt = (ts <= tc) ? FMT_SELL : FMT_CSR;
-    if (fmt == FMT_CSR) MOR_TRY(build_op(h, h->P, S, sa, se, FMT_CSR, Ecsr != nullptr));
+    double ts = 1e300, td = 1e300;
+    if (build_op(h, h->P, S, sa, se, FMT_SELL, Ecsr != nullptr) == MOR_OK) {
+      ts = time_op(h, h->P, st2);
+      last = FMT_SELL;
+    }
+    {
+      std::vector<int32_t> offs;
+      std::vector<int64_t> lay;
+      if (dia_layout(S, MOR_DIA_MAXDIAG, 1.25, offs, lay)) {
+        MOR_TRY(build_op(h, h->P, S, sa, se, FMT_DIA, Ecsr != nullptr));
+        td = time_op(h, h->P, st3);
+        last = FMT_DIA;
+      }
+    }
+    if (st1 != MOR_OK || st2 != MOR_OK || st3 != MOR_OK) return mor_fail(h, MOR_ECUDA, "format autotuning failed");
+    fmt = FMT_CSR;
+    if (ts <= tc && ts <= td) fmt = FMT_SELL;
+    if (td < tc && td < ts) fmt = FMT_DIA;
+    if (fmt != last) MOR_TRY(build_op(h, h->P, S, sa, se, fmt, Ecsr != nullptr));
     store_format(key, fmt);
   } else {
     MOR_TRY(build_op(h, h->P, S, sa, se, fmt, Ecsr != nullptr));

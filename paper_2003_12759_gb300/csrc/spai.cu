@@ -253,11 +253,204 @@ int spai_launch(const SpaiArgs& a, const ColData<V>& cd, void* out, cudaStream_t
 
 // lanes per column: each lane owns at most 4 rows of the |I_j| x |J_j| block
 template <typename S, typename V>
+int spai_reg_launch(const SpaiArgs& a, const ColData<V>& cd, void* out, cudaStream_t s);
+template <typename S> size_t spai_reg_smem(const SpaiArgs& a, int nw);
+
+#ifndef MOR_SPAI_REG
+#define MOR_SPAI_REG 1
+#endif
+
+template <typename S, typename V>
 int spai_dispatch(const SpaiArgs& a, const ColData<V>& cd, void* out, cudaStream_t s) {
+#if MOR_SPAI_REG
+  // small columns (the 7-point stencil's 25 x 7) on registers, when one
+  // warp's staging fits the default 48 KB of shared memory
+  if (a.nImax <= 32 && a.nJmax <= 8 && spai_reg_smem<S>(a, 1) <= 48 * 1024)
+    return spai_reg_launch<S, V>(a, cd, out, s);
+#endif
   if (a.nImax <= 16) return spai_launch<S, V, 4>(a, cd, out, s);
   if (a.nImax <= 32) return spai_launch<S, V, 8>(a, cd, out, s);
   if (a.nImax <= 64) return spai_launch<S, V, 16>(a, cd, out, s);
   return spai_launch<S, V, 32>(a, cd, out, s);
+}
+
+// value of lane src (a lane index of the whole warp)
+template <typename T> __device__ __forceinline__ T shfl_s(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <typename R> __device__ __forceinline__ cplx<R> shfl_s(cplx<R> v, int src) {
+  return cplx<R>(__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src));
+}
+
+// The same column least squares for small columns (|I_j| <= 32, |J_j| <= 8:
+// the 7-point stencil has 25 x 7) with the block held in registers during
+// the factorisation: groups of 8 lanes, lane l of a group owning rows l,
+// l + 8, l + 16, l + 24 of all 8 columns.  The gather still stages G through
+// shared memory (entries land on rows found by search in I_j); then every
+// Householder step, the application of the reflectors to the later columns
+// and to the right-hand side, and the back substitution run on registers
+// with the loops unrolled, in the order (and with the sums) of spai_kernel.
+// The row of the pivot of step c < 8 is row c, held by lane c of the group
+// in its first register, which is where the back substitution reads R.
+template <typename S, typename V>
+__global__ void __launch_bounds__(128) spai_reg_kernel(SpaiArgs a, ColData<V> cd, S* __restrict__ out) {
+  typedef typename real_of<S>::type R;
+  constexpr int LPC = 8, NR = 4, NJ = 8, CPW = 32 / LPC;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int grp = lane / LPC, gl = lane % LPC, gbase = lane & ~(LPC - 1);
+  unsigned char* base = smem + ((size_t)wid * CPW + grp) * col_bytes<S, LPC>(a.nImax, a.nJmax);
+  S* G = (S*)base;                                   // nJmax columns of nImax rows
+  S* rhs = G + (size_t)a.nImax * a.nJmax;
+  int* Il = (int*)(rhs + a.nImax + 2 * a.nJmax);
+  const int ld = a.nImax;
+  const cplx<V> cnew[2] = {cplx<V>((V)a.cnew.sEr, (V)a.cnew.sEi), cplx<V>((V)a.cnew.sAr, (V)a.cnew.sAi)};
+  const cplx<V> cold[2] = {cplx<V>((V)a.cold.sEr, (V)a.cold.sEi), cplx<V>((V)a.cold.sAr, (V)a.cold.sAi)};
+
+  for (int j0 = (blockIdx.x * nw + wid) * CPW; j0 < a.n; j0 += gridDim.x * nw * CPW) {
+    const int j = j0 + grp;
+    const bool valid = j < a.n;
+    int64_t i0 = 0;
+    int nI = 0, c0 = 0, nJ = 0;
+    if (valid) {
+      i0 = a.iptr[j];
+      nI = (int)(a.iptr[j + 1] - i0);
+      c0 = a.colptr[j];
+      nJ = a.colptr[j + 1] - c0;
+    }
+    for (int t = gl; t < nI; t += LPC) Il[t] = a.iidx[i0 + t];
+    for (int t = gl; t < nJ * ld; t += LPC) G[t] = S(0);
+    for (int t = gl; t < nI; t += LPC) rhs[t] = S(0);
+    __syncwarp();
+    for (int t = 0; t < nJ; ++t) {
+      const int kc = a.colidx[c0 + t];
+      const int q0 = a.colptr[kc], q1 = a.colptr[kc + 1];
+      for (int q = q0 + gl; q < q1; q += LPC) {
+        const int row = a.colidx[q];
+        G[t * ld + find_row(Il, nI, row)] = to_s<S, V>(entry(cd, a.ekind, cnew, q, row, kc));
+      }
+    }
+    if (valid) {
+      if (!a.update) {
+        if (gl == 0) rhs[find_row(Il, nI, j)] = S(1);
+      } else {
+        for (int q = c0 + gl; q < c0 + nJ; q += LPC) {
+          const int row = a.colidx[q];
+          rhs[find_row(Il, nI, row)] = to_s<S, V>(entry(cd, a.ekind, cold, q, row, j));
+        }
+      }
+    }
+    __syncwarp();
+    // the block and the right-hand side into registers (zero past the sizes)
+    S g[NJ][NR], rv[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int rr = gl + LPC * i;
+      const bool in = rr < nI;
+      const S rh = rhs[in ? rr : 0];             // indices clamped into the group's block
+      rv[i] = in ? rh : S(0);
+#pragma unroll
+      for (int t = 0; t < NJ; ++t) {
+        const bool e = in && t < nJ;
+        const S gv = G[e ? t * ld + rr : 0];
+        g[t][i] = e ? gv : S(0);
+      }
+    }
+    __syncwarp();
+    bool singular = false;
+    S rd[NJ];
+#pragma unroll
+    for (int c = 0; c < NJ; ++c) {
+      const bool act = c < nJ;
+      // rows >= c: all of a lane's rows but possibly its first (c < 8)
+      R s2 = R(0);
+#pragma unroll
+      for (int i = 0; i < NR; ++i)
+        if (i > 0 || gl >= c) s2 += abs2_(g[c][i]);
+      s2 = act ? s2 : R(0);
+      s2 = group_sum<LPC>(s2);
+      S x0 = shfl_s(g[c][0], gbase + c);     // every lane shuffles; inactive groups take zero
+      if (!act) x0 = S(0);
+      const R alpha = sqrt(s2);
+      const bool ok = act && (alpha > R(0));
+      if (act && !ok) singular = true;
+      const R ax0 = sqrt(abs2_(x0));
+      const S ph = (ax0 > R(0)) ? x0 * (R(1) / ax0) : S(1);
+      const S v0 = x0 + ph * alpha;
+      const R vn2 = s2 - ax0 * ax0 + abs2_(v0);
+      const R beta = ok ? R(2) / vn2 : R(0);
+      if (ok && gl == c) g[c][0] = v0;
+      rd[c] = ok ? -(ph * alpha) : S(0);
+#pragma unroll
+      for (int c2 = c + 1; c2 < NJ; ++c2) {
+        const bool act2 = ok && c2 < nJ;
+        S w = S(0);
+#pragma unroll
+        for (int i = 0; i < NR; ++i)
+          if (i > 0 || gl >= c) fma_s(w, conj_(g[c][i]), g[c2][i]);
+        w = act2 ? w : S(0);
+        w = group_sum<LPC>(w);
+        const S bw = w * beta;
+        if (act2) {
+#pragma unroll
+          for (int i = 0; i < NR; ++i)
+            if (i > 0 || gl >= c) g[c2][i] -= g[c][i] * bw;
+        }
+      }
+      {
+        S w = S(0);
+#pragma unroll
+        for (int i = 0; i < NR; ++i)
+          if (i > 0 || gl >= c) fma_s(w, conj_(g[c][i]), rv[i]);
+        w = ok ? w : S(0);
+        w = group_sum<LPC>(w);
+        const S bw = w * beta;
+        if (ok) {
+#pragma unroll
+          for (int i = 0; i < NR; ++i)
+            if (i > 0 || gl >= c) rv[i] -= g[c][i] * bw;
+        }
+      }
+    }
+    // back substitution R q = (Q^H rhs)(0:nJ): row c of R and of the rotated
+    // right-hand side sit in lane c's first registers
+    S qv[NJ];
+#pragma unroll
+    for (int c = NJ - 1; c >= 0; --c) {
+      S acc = rv[0];
+#pragma unroll
+      for (int c2 = c + 1; c2 < NJ; ++c2)
+        if (c2 < nJ) acc -= g[c2][0] * qv[c2];
+      acc = shfl_s(acc, gbase + c);
+      qv[c] = (c < nJ && !singular) ? div_s(acc, rd[c]) : S(0);
+    }
+    if (valid && singular && gl == 0) atomicAdd(a.nsingular, 1);
+    S mine = qv[0];
+#pragma unroll
+    for (int c = 1; c < NJ; ++c)
+      if (gl == c) mine = qv[c];
+    if (gl < nJ) out[a.outpos[c0 + gl]] = mine;
+    __syncwarp();
+  }
+}
+
+// shared memory of a block of nw warps of spai_reg_kernel (the gather's staging)
+template <typename S> size_t spai_reg_smem(const SpaiArgs& a, int nw) { return col_bytes<S, 8>(a.nImax, a.nJmax) * 4 * nw; }
+
+template <typename S, typename V>
+int spai_reg_launch(const SpaiArgs& a, const ColData<V>& cd, void* out, cudaStream_t s) {
+  constexpr int CPW = 4;
+  int nw = 4;
+  while (nw > 1 && spai_reg_smem<S>(a, nw) > 48 * 1024) nw >>= 1;
+  const size_t sm = spai_reg_smem<S>(a, nw);
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spai_reg_kernel<S, V>, nw * 32, sm);
+  if (e != cudaSuccess || occ < 1) occ = 1;
+  const int sms = mor_device_sms();
+  const int64_t per_block = (int64_t)nw * CPW;
+  int64_t blocks = ((int64_t)a.n + per_block - 1) / per_block;
+  blocks = std::min<int64_t>(blocks, (int64_t)sms * occ);
+  spai_reg_kernel<S, V><<<(unsigned)std::max<int64_t>(blocks, 1), nw * 32, sm, s>>>(a, cd, (S*)out);
+  mor_count_launches(1);
+  return (int)cudaGetLastError();
 }
 
 }  // namespace

@@ -49,11 +49,6 @@ template <typename S> struct CoefS { S sE[MOR_LDMAX]; S sA[MOR_LDMAX]; };
 #ifndef MOR_FACTOR_GCH
 #define MOR_FACTOR_GCH 4
 #endif
-// remainder of a row (fewer entries than a chunk) gathered as one chunk (1)
-// or one entry at a time (0)
-#ifndef MOR_FACTOR_TAIL
-#define MOR_FACTOR_TAIL 1
-#endif
 #ifndef MOR_OP_GCH
 #define MOR_OP_GCH 2
 #endif
@@ -72,6 +67,21 @@ template <typename S, int CPT> constexpr int min_blocks() {
 #endif
 template <typename S, int CPT> constexpr int op_min_blocks() {
   return narrow_slice<S, CPT>() ? (sizeof(typename real_of<S>::type) == 8 ? 5 : MOR_OP_MINB) : 1;
+}
+// the operator SpMV in the diagonal layout: no index loads, so a row's loads
+// are independent and deeper chunks cost only registers
+#ifndef MOR_OP_DIA_GCH
+#define MOR_OP_DIA_GCH 4
+#endif
+#ifndef MOR_OP_DIA_MINB
+#define MOR_OP_DIA_MINB 8
+#endif
+template <typename S, int CPT, bool DIA> constexpr int op_blocks() {
+  return (DIA && narrow_slice<S, CPT>() && sizeof(typename real_of<S>::type) == 4) ? MOR_OP_DIA_MINB
+                                                                                  : op_min_blocks<S, CPT>();
+}
+template <typename S, int CPT, bool DIA> constexpr int op_gch() {
+  return (DIA && narrow_slice<S, CPT>()) ? MOR_OP_DIA_GCH : op_chunk<S, CPT>();
 }
 
 template <typename S> __device__ __forceinline__ S zero_() { return S(0); }
@@ -149,13 +159,41 @@ __device__ __forceinline__ cdouble ldh(const cdouble* a, uint64_t pol) {
 }
 
 
+// R diagonals d .. d + R - 1 of an operator row r in the diagonal layout
+// (column clamped into range: out-of-range columns are padding of value 0).
+template <int R, bool ECSR, typename S, typename RV, int CPT>
+__device__ __forceinline__ void op_dia_gather(S (&accA)[CPT], S (&accE)[CPT], const int* __restrict__ doff,
+                                              const RV* __restrict__ a, const RV* __restrict__ e, int d, int r, int n,
+                                              int ld, int c0, const S* __restrict__ x) {
+  int cc[R];
+  RV av[R], ev[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int c = r + __ldg(doff + d + u);
+    cc[u] = c < 0 ? 0 : (c >= n ? n - 1 : c);
+    av[u] = __ldg(a + (d + u) * n + r);
+    if constexpr (ECSR) ev[u] = __ldg(e + (d + u) * n + r);
+    else ev[u] = RV(0);
+  }
+  Pack<S, CPT> xv[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+#pragma unroll
+  for (int u = 0; u < R; ++u)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      fma_r(accA[j], av[u], xv[u].v[j]);
+      if constexpr (ECSR) fma_r(accE[j], ev[u], xv[u].v[j]);
+    }
+}
+
 // Y(:, c) = sE_c (E X(:, c)) + sA_c (A X(:, c)) [+ B(:, c)], with an optional
 // fused per-column reduction.  TPR lanes per row, lane `sub` owns the CPT
 // columns sub * CPT ... sub * CPT + CPT - 1 of the n x ld blocks.  The
 // coefficients are read from shared memory where they are used and row
 // indices are 32-bit, to hold the register bound of op_min_blocks.
-template <typename S, int TPR, int CPT, bool ECSR>
-__global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(SegView sg, PatView pv, OpVals ov,
+template <typename S, int TPR, int CPT, bool ECSR, bool DIA>
+__global__ void __launch_bounds__(256, (op_blocks<S, CPT, DIA>())) op_spmv_kernel(SegView sg, PatView pv, OpVals ov,
                                                                                 CoefS<S> cf, int ld,
                                                                                 const S* __restrict__ x, S* __restrict__ y,
                                                                                 const S* __restrict__ bv, RedArgs red) {
@@ -192,57 +230,74 @@ __global__ void __launch_bounds__(256, op_min_blocks<S, CPT>()) op_spmv_kernel(S
   const bool sell = pv.fmt == FMT_SELL;
   const L2Pol pol = l2_policies();
   const int ekind = ECSR ? EK_CSR : ov.ekind;   // E a general sparse matrix: compile-time branch
-  constexpr int GCH = op_chunk<S, CPT>();
+  constexpr int GCH = op_gch<S, CPT, DIA>();
+  static_assert(GCH <= 4, "the remainder below takes at most 3 diagonals");
   if (act) {
     for (int r = (int)rb64 + (int)threadIdx.x / TPR; r < re; r += rpb) {
-      int p0, p1, step;
-      if (sell) {
-        const int64_t base = pv.sptr[r >> 5];
-        const int wd = (int)((pv.sptr[(r >> 5) + 1] - base) >> 5);
-        p0 = (int)base + (r & 31);
-        p1 = p0 + 32 * wd;
-        step = 32;
-      } else {
-        p0 = ldh(pv.rowptr + r, pol.last);
-        p1 = ldh(pv.rowptr + r + 1, pol.last);
-        step = 1;
-      }
       S accA[CPT], accE[CPT];
 #pragma unroll
       for (int j = 0; j < CPT; ++j) { accA[j] = zero_<S>(); accE[j] = zero_<S>(); }
-      int pc = p0;
-      for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
-        int cc[GCH];
-        R av[GCH], ev[GCH];
-#pragma unroll
-        for (int u = 0; u < GCH; ++u) {
-          cc[u] = ldh(pv.col + pc + u * step, pol.last);
-          av[u] = __ldg(a + pc + u * step);
-          if constexpr (ECSR) ev[u] = __ldg(e + pc + u * step);
-          else ev[u] = R(0);
-        }
-        Pack<S, CPT> xv[GCH];
-#pragma unroll
-        for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
-#pragma unroll
-        for (int u = 0; u < GCH; ++u)
-#pragma unroll
-          for (int j = 0; j < CPT; ++j) {
-            fma_r(accA[j], av[u], xv[u].v[j]);
-            if constexpr (ECSR) fma_r(accE[j], ev[u], xv[u].v[j]);
+      if constexpr (DIA) {
+        int d = 0;
+        for (; d + GCH <= pv.ndiag; d += GCH)
+          op_dia_gather<GCH, ECSR, S, R, CPT>(accA, accE, pv.doff, a, e, d, r, pv.n, ld, c0, x);
+        if constexpr (GCH > 1) {
+          const int rem = pv.ndiag - d;     // 0 .. GCH - 1
+          if constexpr (GCH > 3) {
+            if (rem == 3) op_dia_gather<3, ECSR, S, R, CPT>(accA, accE, pv.doff, a, e, d, r, pv.n, ld, c0, x);
           }
-      }
-      for (; pc < p1; pc += step) {
-        const int cc = ldh(pv.col + pc, pol.last);
-        const R av = __ldg(a + pc);
-        const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
-        if constexpr (ECSR) {
-          const R ev = __ldg(e + pc);
-#pragma unroll
-          for (int j = 0; j < CPT; ++j) { fma_r(accA[j], av, xv.v[j]); fma_r(accE[j], ev, xv.v[j]); }
+          if constexpr (GCH > 2) {
+            if (rem == 2) op_dia_gather<2, ECSR, S, R, CPT>(accA, accE, pv.doff, a, e, d, r, pv.n, ld, c0, x);
+          }
+          if (rem == 1) op_dia_gather<1, ECSR, S, R, CPT>(accA, accE, pv.doff, a, e, d, r, pv.n, ld, c0, x);
+        }
+      } else {
+        int p0, p1, step;
+        if (sell) {
+          const int64_t base = pv.sptr[r >> 5];
+          const int wd = (int)((pv.sptr[(r >> 5) + 1] - base) >> 5);
+          p0 = (int)base + (r & 31);
+          p1 = p0 + 32 * wd;
+          step = 32;
         } else {
+          p0 = ldh(pv.rowptr + r, pol.last);
+          p1 = ldh(pv.rowptr + r + 1, pol.last);
+          step = 1;
+        }
+        int pc = p0;
+        for (; pc + (GCH - 1) * step < p1; pc += GCH * step) {
+          int cc[GCH];
+          R av[GCH], ev[GCH];
 #pragma unroll
-          for (int j = 0; j < CPT; ++j) fma_r(accA[j], av, xv.v[j]);
+          for (int u = 0; u < GCH; ++u) {
+            cc[u] = ldh(pv.col + pc + u * step, pol.last);
+            av[u] = __ldg(a + pc + u * step);
+            if constexpr (ECSR) ev[u] = __ldg(e + pc + u * step);
+            else ev[u] = R(0);
+          }
+          Pack<S, CPT> xv[GCH];
+#pragma unroll
+          for (int u = 0; u < GCH; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+#pragma unroll
+          for (int u = 0; u < GCH; ++u)
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+              fma_r(accA[j], av[u], xv[u].v[j]);
+              if constexpr (ECSR) fma_r(accE[j], ev[u], xv[u].v[j]);
+            }
+        }
+        for (; pc < p1; pc += step) {
+          const int cc = ldh(pv.col + pc, pol.last);
+          const R av = __ldg(a + pc);
+          const Pack<S, CPT> xv = ldp<S, CPT>(x + (int64_t)cc * ld + c0);
+          if constexpr (ECSR) {
+            const R ev = __ldg(e + pc);
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) { fma_r(accA[j], av, xv.v[j]); fma_r(accE[j], ev, xv.v[j]); }
+          } else {
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) fma_r(accA[j], av, xv.v[j]);
+          }
         }
       }
       const int64_t q = (int64_t)r * ld + c0;
@@ -306,13 +361,41 @@ __device__ __forceinline__ void factor_gather(Pack<S, CPT>& acc, const int* __re
     }
 }
 
+// R diagonals d .. d + R - 1 of row r in the diagonal layout: value at
+// (d + u) n + r, column r + doff[d + u].  A column outside 0 .. n - 1 is
+// padding (value 0): the index is clamped into range so that every load is
+// in bounds and unconditional.
+template <int R, typename S, typename V, typename W, int CPT>
+__device__ __forceinline__ void factor_dia_gather(Pack<S, CPT>& acc, const int* __restrict__ doff,
+                                                  const V* __restrict__ f, int d, int r, int n, int ld, int c0,
+                                                  const S* __restrict__ x, const L2Pol& pol) {
+  int cc[R];
+  W fv[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int c = r + __ldg(doff + d + u);
+    cc[u] = c < 0 ? 0 : (c >= n ? n - 1 : c);
+    fv[u] = cvt_<W, V>::f(ldh(f + (d + u) * n + r, pol.first));
+  }
+  Pack<S, CPT> xv[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) xv[u] = ldp<S, CPT>(x + (int64_t)cc[u] * ld + c0);
+#pragma unroll
+  for (int u = 0; u < R; ++u)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) {
+      if constexpr (is_cplx<V>::value) fma_s(acc.v[j], fv[u], xv[u].v[j]);
+      else fma_r(acc.v[j], fv[u], xv[u].v[j]);
+    }
+}
+
 // Y(:, c) = F X(:, c) where the factor applies to column c, else Y(:, c) = X(:, c).
 // With Krylov states (kst), lanes whose columns of the block's segment have all
 // stopped leave their rows of Y as they were.
 // Kept lean (32-bit row indices, a column bit mask, the copy-through value
 // loaded only at the end) so that the register bound of min_blocks holds
 // without spills.
-template <typename S, typename V, int TPR, int CPT>
+template <typename S, typename V, int TPR, int CPT, bool DIA>
 __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(SegView sg, PatView pv, const V* __restrict__ f,
                                                           const int* __restrict__ apply, int ld,
                                                           const S* __restrict__ x, S* __restrict__ y,
@@ -352,7 +435,29 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
     Pack<S, CPT> acc;
 #pragma unroll
     for (int j = 0; j < CPT; ++j) acc.v[j] = zero_<S>();
-    if (mask) {
+    // whole chunks of GCH entries, then the remainder (fewer than GCH) as one
+    // more chunk, so that a row of c GCH + t entries waits on c + 1 rounds of
+    // gathers; the sum runs in storage order (columns ascending) either way.
+    // FP32 factor values under FP64 vectors are widened on load (W).
+    constexpr int GCH = factor_chunk<S, CPT>();
+    static_assert(GCH <= 4, "the remainder below takes at most 3 entries");
+    if constexpr (DIA) {
+      if (mask) {
+      const int nd = pv.ndiag, n = pv.n;
+      int d = 0;
+      for (; d + GCH <= nd; d += GCH) factor_dia_gather<GCH, S, V, W, CPT>(acc, pv.doff, f, d, r, n, ld, c0, x, pol);
+      if constexpr (GCH > 1) {
+        const int rem = nd - d;
+        if constexpr (GCH > 3) {
+          if (rem == 3) factor_dia_gather<3, S, V, W, CPT>(acc, pv.doff, f, d, r, n, ld, c0, x, pol);
+        }
+        if constexpr (GCH > 2) {
+          if (rem == 2) factor_dia_gather<2, S, V, W, CPT>(acc, pv.doff, f, d, r, n, ld, c0, x, pol);
+        }
+        if (rem == 1) factor_dia_gather<1, S, V, W, CPT>(acc, pv.doff, f, d, r, n, ld, c0, x, pol);
+      }
+      }
+    } else if (mask) {
       int p0, p1, step;
       if (sell) {
         const int64_t base = pv.sptr[r >> 5];
@@ -366,19 +471,9 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
         p1 = ldh(pv.rowptr + r + 1, pol.last);
         step = 1;
       }
-      // whole chunks of GCH entries, then the remainder (fewer than GCH) as one
-      // more chunk, so that a row of c GCH + t entries waits on c + 1 rounds
-      // of gathers; the sum runs in storage order either way.  FP32 factor
-      // values under FP64 vectors are widened on load (W).
-      constexpr int GCH = factor_chunk<S, CPT>();
       int pc = p0;
       for (; pc + (GCH - 1) * step < p1; pc += GCH * step)
         factor_gather<GCH, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
-#if MOR_FACTOR_TAIL
-      if constexpr (GCH > 4) {
-        for (; pc + 3 * step < p1; pc += 4 * step)
-          factor_gather<4, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
-      }
       if constexpr (GCH > 1) {
         const int rem = (p1 - pc) / step;     // 0 .. 3
         if constexpr (GCH > 3) {
@@ -389,9 +484,6 @@ __global__ void __launch_bounds__(256, min_blocks<S, CPT>()) factor_spmv_kernel(
         }
         if (rem == 1) factor_gather<1, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
       }
-#else
-      for (; pc < p1; pc += step) factor_gather<1, S, V, W, CPT>(acc, pv.col, f, pc, step, ld, c0, x, pol);
-#endif
     }
     const int64_t q = (int64_t)r * ld + c0;
     if (mask != (1u << CPT) - 1u) {
@@ -425,14 +517,18 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
         cf.sA[c] = (S)q.sAr;
       }
     }
+    auto go = [&]<bool ECSR, bool DIA>() {
+      const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT, ECSR, DIA>, TPR);
+      op_spmv_kernel<S, TPR, CPT, ECSR, DIA><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y,
+                                                                       (const S*)b, ra);
+    };
+    const bool dia = pv.fmt == FMT_DIA;
     if (ov.ekind == EK_CSR) {
-      const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT, true>, TPR);
-      op_spmv_kernel<S, TPR, CPT, true><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y,
-                                                                  (const S*)b, ra);
+      if (dia) go.template operator()<true, true>();
+      else go.template operator()<true, false>();
     } else {
-      const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT, false>, TPR);
-      op_spmv_kernel<S, TPR, CPT, false><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y,
-                                                                   (const S*)b, ra);
+      if (dia) go.template operator()<false, true>();
+      else go.template operator()<false, false>();
     }
     return 0;
   });
@@ -450,9 +546,14 @@ static int launch_factor_shape(int fst, const SegView& sg, const PatView& pv, co
   typedef typename real_of<S>::type R;
   const bool fc = st_is_cplx(fst), f32 = st_is_f32(fst);
   auto go = [&]<typename V>() {
-    const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, V, TPR, CPT>, TPR);
-    factor_spmv_kernel<S, V, TPR, CPT><<<g.nblocks, 256, 0, s>>>(g, pv, (const V*)fvals, apply, ld, (const S*)x,
-                                                                 (S*)y, done, (const KState*)kstate);
+    auto run = [&]<bool DIA>() {
+      const SegView g = fit_grid(sg, (const void*)factor_spmv_kernel<S, V, TPR, CPT, DIA>, TPR);
+      factor_spmv_kernel<S, V, TPR, CPT, DIA><<<g.nblocks, 256, 0, s>>>(g, pv, (const V*)fvals, apply, ld,
+                                                                        (const S*)x, (S*)y, done,
+                                                                        (const KState*)kstate);
+    };
+    if (pv.fmt == FMT_DIA) run.template operator()<true>();
+    else run.template operator()<false>();
   };
   if (sizeof(R) == 4 && !f32) return (int)cudaErrorInvalidValue;     // FP64 factors under FP32 vectors
   if constexpr (is_cplx<S>::value) {

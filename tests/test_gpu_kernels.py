@@ -60,13 +60,23 @@ def _set(h, wl, fmt=mor.MOR_FMT_AUTO):
         mor.mor_set_system(h, wl.A, wl.B, wl.C, E=wl.E, fmt=fmt)
 
 
+def _dia_ok(name):
+    """Stencil patterns have few diagonals; the random ones are refused by the diagonal layout."""
+    return not name.startswith("rand")
+
+
 @pytest.mark.parametrize("name", list(SYSTEMS))
-@pytest.mark.parametrize("fmt", [mor.MOR_FMT_CSR, mor.MOR_FMT_SELL])
+@pytest.mark.parametrize("fmt", [mor.MOR_FMT_CSR, mor.MOR_FMT_SELL, mor.MOR_FMT_DIA])
 @pytest.mark.parametrize("transpose", [0, 1])
 @pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
 def test_operator_spmv(h, name, fmt, transpose, precision):
     wl = SYSTEMS[name]()
+    if fmt == mor.MOR_FMT_DIA and not _dia_ok(name):
+        with pytest.raises(mor.MorError, match="diagonals"):
+            _set(h, wl, fmt)
+        return
     _set(h, wl, fmt)
+    assert mor.mor_get_info(h)["format"] == fmt
     rng = np.random.default_rng(10)
     for k in (1, 3, 16):
         sig = np.array([2.0 + 0.5j * c if c % 2 else 10.0 * (c + 1) for c in range(k)], dtype=complex)
@@ -108,12 +118,15 @@ def _oracle_factor_csr(h, wl, M_new, M_old, transpose):
     return np.asarray(X[dense_rows, col]).ravel(), rowptr, col
 
 
-@pytest.mark.parametrize("name", ["laplace2d_n1369", "convdiff3d_n2197", "rand_csrE_n700"])
+@pytest.mark.parametrize("name,fmt", [("laplace2d_n1369", mor.MOR_FMT_SELL), ("convdiff3d_n2197", mor.MOR_FMT_SELL),
+                                      ("rand_csrE_n700", mor.MOR_FMT_SELL), ("convdiff3d_n2197", mor.MOR_FMT_DIA)])
 @pytest.mark.parametrize("transpose", [0, 1])
 @pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
-def test_spai_build_and_update(h, name, transpose, precision):
+def test_spai_build_and_update(h, name, fmt, transpose, precision):
+    """Factors written into the storage layout (SELL-32: padded slices; DIA:
+    diagonals) and read back in CSR order, against the oracle."""
     wl = SYSTEMS[name]()
-    _set(h, wl, mor.MOR_FMT_SELL)
+    _set(h, wl, fmt)
     s1, s2 = 12.0 + 3.0j, 20.0 - 1.0j
     mor.mor_build_precond(h, s1, transpose, precision)
     mor.mor_update_precond(h, s2, transpose)

@@ -5,7 +5,8 @@ Every width selects its own row layout and lane shape (one thread per row
 for narrow rows, otherwise one 16-byte vector per lane with idle lanes past
 the row's end), so each (scalar type, k) pair instantiates a different
 kernel shape: FP64 and FP32 (real shifts, MOR_REAL_VECTORS), complex128 and
-complex64 (complex shifts).  CSR and SELL-32, primal and transposed.
+complex64 (complex shifts).  CSR, SELL-32 and the diagonal layout, primal
+and transposed.
 
 Bounds (each output is a sum of at most row-nnz + 1 products):
   * operator:  |y - y_ref| <= 30 u (|sE| |E| + |sA| |A|) |x|;
@@ -60,7 +61,7 @@ def _x(n, k, real, precision, seed):
     return X
 
 
-@pytest.mark.parametrize("fmt", [mor.MOR_FMT_CSR, mor.MOR_FMT_SELL])
+@pytest.mark.parametrize("fmt", [mor.MOR_FMT_CSR, mor.MOR_FMT_SELL, mor.MOR_FMT_DIA])
 @pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
 @pytest.mark.parametrize("real", [True, False])
 @pytest.mark.parametrize("transpose", [0, 1])
@@ -83,7 +84,7 @@ def test_operator_every_width(h, wl, fmt, precision, real, transpose):
             assert np.all(err <= 30 * u * bnd + 1e-300), (k, c, float(np.max(err / (bnd + 1e-300))))
 
 
-@pytest.mark.parametrize("fmt", [mor.MOR_FMT_CSR, mor.MOR_FMT_SELL])
+@pytest.mark.parametrize("fmt", [mor.MOR_FMT_CSR, mor.MOR_FMT_SELL, mor.MOR_FMT_DIA])
 @pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
 @pytest.mark.parametrize("real", [True, False])
 def test_chain_apply_every_width(h, wl, fmt, precision, real):
@@ -161,3 +162,37 @@ def test_chain_apply_irregular_rows(h, precision, real):
                 bnd = abs(f) @ bnd
             err = np.abs(Y[:, c] - ref)
             assert np.all(err <= 30 * u * L * bnd + 1e-300), (k, c, float(np.max(err / (bnd + 1e-300))))
+
+
+@pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
+def test_solve_diagonal_layout_equals_csr(h, wl, precision):
+    """The same shifted solves with the operator and the chain stored in the
+    diagonal layout and in CSR: the layouts sum a row's entries in the same
+    (column) order, the diagonal layout adding exact zeros for its padding, so
+    the solves take the same iterations and agree to rounding."""
+    s = [4.0 + 1.0j, 9.0 + 2.0j, 30.0]
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((wl.n, 3)) + 0j
+    out = {}
+    for fmt in (mor.MOR_FMT_CSR, mor.MOR_FMT_DIA):
+        mor.mor_set_system(h, wl.A, wl.B, wl.C, E_diag=wl.E, fmt=fmt)
+        assert mor.mor_get_info(h)["format"] == fmt
+        mor.mor_build_precond(h, s[0], 0, precision)
+        mor.mor_update_precond(h, s[1], 0)
+        mor.mor_update_precond(h, s[2], 0)
+        X, st, code = mor.mor_solve_shifts(h, s, 0, mor.mor_default_opts(precision=precision), R=R)
+        assert code == mor.MOR_OK
+        out[fmt] = (X, [x["iters"] for x in st])
+    (Xc, ic), (Xd, idg) = out[mor.MOR_FMT_CSR], out[mor.MOR_FMT_DIA]
+    assert ic == idg
+    np.testing.assert_allclose(Xd, Xc, rtol=0, atol=1e-12 * np.abs(Xc).max())
+
+
+def test_diagonal_layout_refuses_irregular_rows(h):
+    """A pattern with hundreds of distinct diagonals is refused with MOR_EINVAL;
+    the automatic choice then stays among CSR and SELL-32."""
+    A, B, C = _irregular_rows_system()
+    with pytest.raises(mor.MorError, match="diagonals"):
+        mor.mor_set_system(h, A, B, C, fmt=mor.MOR_FMT_DIA)
+    mor.mor_set_system(h, A, B, C, fmt=mor.MOR_FMT_AUTO)
+    assert mor.mor_get_info(h)["format"] in (mor.MOR_FMT_CSR, mor.MOR_FMT_SELL)

@@ -1,6 +1,7 @@
 """The host-side sparsity construction of the library (csrc/host_pattern.h:
 the static pattern S = pattern(A) + pattern(E) + diagonal with aligned
-values, its transpose, the SPAI shadow sets I_j and the SELL-32 layout) is
+values, its transpose, the SPAI shadow sets I_j, the SELL-32 layout and the
+diagonal layout) is
 plain C++: compiled here with g++ and checked against the oracle's pattern
 and shadow sets (oracle.spai.spai_pattern / pattern_sets, which take I_j as
 the pattern of column j of S S) and against scipy's transpose.  No GPU."""
@@ -56,6 +57,12 @@ int main() {
   std::vector<int64_t> sptr, lay; std::vector<int32_t> scol;
   sell_layout(S, sptr, scol, lay);
   pr(sptr, " %lld"); pr(scol, " %d"); pr(lay, " %lld");
+  for (int md : {32, 3}) {
+    std::vector<int32_t> offs; std::vector<int64_t> dlay;
+    const bool ok = dia_layout(S, md, 1.25, offs, dlay);
+    printf("%d\n", ok ? 1 : 0);
+    pr(offs, " %d"); pr(dlay, " %lld");
+  }
   return 0;
 }
 """
@@ -93,7 +100,9 @@ def _run(exe, A, E):
            "Trp": arr(4, int), "Tcol": arr(5, int), "t2p": arr(6, int),
            "IprimT": arr(7, int), "IidxT": arr(8, int), "nIJ_T": tuple(map(int, lines[9].split())),
            "IprimS": arr(10, int), "IidxS": arr(11, int), "nIJ_S": tuple(map(int, lines[12].split())),
-           "sptr": arr(13, int), "scol": arr(14, int), "lay": arr(15, int)}
+           "sptr": arr(13, int), "scol": arr(14, int), "lay": arr(15, int),
+           "dia_ok": int(lines[16]), "doffs": arr(17, int), "dlay": arr(18, int),
+           "dia3_ok": int(lines[19]), "doffs3": arr(20, int), "dlay3": arr(21, int)}
     return out
 
 
@@ -141,3 +150,17 @@ def test_pattern_transpose_shadows_and_sell_match_oracle(harness, name):
     assert np.array_equal(scol[lay], got["Scol"])
     assert scol.min() >= 0 and scol.max() < n
     assert len(np.unique(lay)) == len(lay)
+    # diagonal layout: eligible only with at most 32 diagonals and at most 25% padding; then the
+    # offsets are the distinct c - r ascending and entry (r, c) sits at d n + r
+    rows_all = np.repeat(np.arange(n), lens)
+    offs = np.unique(got["Scol"] - rows_all)
+    eligible = len(offs) <= 32 and len(offs) * n <= 1.25 * len(rows_all)
+    assert got["dia_ok"] == int(eligible), (name, len(offs))
+    assert eligible == name.startswith("convdiff")           # 7 diagonals; the random ones have hundreds
+    if eligible:
+        assert np.array_equal(got["doffs"], offs)
+        d = np.searchsorted(offs, got["Scol"] - rows_all)
+        assert np.array_equal(got["dlay"], d * n + rows_all)
+    else:
+        assert len(got["doffs"]) == 0 and len(got["dlay"]) == 0
+    assert got["dia3_ok"] == 0 and len(got["doffs3"]) == 0      # more than 3 diagonals
