@@ -290,8 +290,18 @@ template <typename R> __device__ __forceinline__ cplx<R> shfl_s(cplx<R> v, int s
 // with the loops unrolled, in the order (and with the sums) of spai_kernel.
 // The row of the pivot of step c < 8 is row c, held by lane c of the group
 // in its first register, which is where the back substitution reads R.
+// blocks per SM the register allocation is held to.  Measured on the 100^3
+// pattern (10^6 columns, 25 x 7 blocks), build / reuse update in ms, complex64
+// and FP32: 1 block (168 registers) 2.43 / 2.31 and 1.50 / 1.43; 4 blocks
+// (118) 2.13 / 2.00 and 1.49 / 1.44; 5 blocks (96) 2.01 / 1.91 and 1.29 /
+// 1.23.  Complex128 blocks keep their registers (236 a thread; any bound
+// spills kilobytes).
+#ifndef MOR_SPAI_REG_MINB
+#define MOR_SPAI_REG_MINB 5
+#endif
+template <typename S> constexpr int spai_reg_minb() { return sizeof(S) == 16 ? 1 : MOR_SPAI_REG_MINB; }
 template <typename S, typename V>
-__global__ void __launch_bounds__(128) spai_reg_kernel(SpaiArgs a, ColData<V> cd, S* __restrict__ out) {
+__global__ void __launch_bounds__(128, spai_reg_minb<S>()) spai_reg_kernel(SpaiArgs a, ColData<V> cd, S* __restrict__ out) {
   typedef typename real_of<S>::type R;
   constexpr int LPC = 8, NR = 4, NJ = 8, CPW = 32 / LPC;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -379,8 +389,11 @@ __global__ void __launch_bounds__(128) spai_reg_kernel(SpaiArgs a, ColData<V> cd
       const R beta = ok ? R(2) / vn2 : R(0);
       if (ok && gl == c) g[c][0] = v0;
       rd[c] = ok ? -(ph * alpha) : S(0);
+      // the later columns c2 > c (a fixed trip count, so that both loops unroll
+      // and the block stays in registers)
 #pragma unroll
-      for (int c2 = c + 1; c2 < NJ; ++c2) {
+      for (int c2 = 1; c2 < NJ; ++c2) {
+        if (c2 <= c) continue;
         const bool act2 = ok && c2 < nJ;
         S w = S(0);
 #pragma unroll
