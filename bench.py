@@ -185,10 +185,11 @@ def cpu_baseline(grid, iters_per_solve, chain_len, ncols=20000, nits=None, max_p
 
 def spmv_source_sha():
     """First 16 hex digits of the SHA-256 over the sources the SpMV kernels are
-    compiled from (spmv.cu and the headers it includes), in a fixed order."""
+    compiled from (spmv.cu, spmv_dia.cu and the headers they include), in a
+    fixed order."""
     d = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2003_12759_gb300", "csrc")
     hs = hashlib.sha256()
-    for f in ("spmv.cu", "krylov_state.cuh", "mor_internal.h", "shape_dispatch.cuh", "mor_types.cuh"):
+    for f in ("spmv.cu", "spmv_dia.cu", "krylov_state.cuh", "mor_internal.h", "shape_dispatch.cuh", "mor_types.cuh"):
         hs.update(open(os.path.join(d, f), "rb").read())
     return hs.hexdigest()[:16]
 

@@ -29,7 +29,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 # the kernel files dispatch shapes with C++20 template lambdas; the host runtime stays C++17
-CXX20 = {"spmv.cu", "krylov.cu", "gmres.cu"}
+CXX20 = {"spmv.cu", "spmv_dia.cu", "krylov.cu", "gmres.cu"}
 
 
 def nvcc() -> str:

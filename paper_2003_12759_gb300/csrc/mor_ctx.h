@@ -43,6 +43,7 @@ struct OpData {
   DBuf rowptr, col;                      // CSR (device)
   DBuf sptr, scol;                       // SELL-32 layout (device)
   DBuf doff;                             // DIA offsets (device)
+  std::vector<int32_t> h_doff;           // DIA offsets (host)
   int ndiag = 0;
   DBuf a64, a32, e64, e32;               // values in layout order
   DBuf ca64, ce64, ca32, ce32;           // values in CSR order (column data for the other op's SPAI)
@@ -64,6 +65,7 @@ struct OpData {
     v.sptr = sptr.as<int64_t>();
     v.doff = doff.as<int32_t>();
     v.ndiag = ndiag;
+    v.h_doff = h_doff.empty() ? nullptr : h_doff.data();
     return v;
   }
 };

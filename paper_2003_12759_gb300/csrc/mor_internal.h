@@ -33,6 +33,7 @@ struct PatView {
   const int64_t* sptr;    // SELL slice offsets (nslices + 1)
   const int32_t* doff;    // DIA offsets (ndiag)
   int ndiag;
+  const int32_t* h_doff;  // DIA offsets, host copy (launch set-up; not read by kernels)
 };
 
 // Real-valued operator data for y = sE * (E x) + sA * (A x).
@@ -170,6 +171,10 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
 // kstate (nullable): the per-(segment, column) Krylov states of the solve the
 // factor is applied in; lanes whose columns have all stopped skip their rows
 // (their rows of y are left as they were).
+// factor SpMV in the diagonal layout specialised to 5 or 7 diagonals and FP32 /
+// complex64 vectors (spmv_dia.cu): -1 when it does not apply, else 0
+int launch_factor_dia_nd(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals, const int* apply,
+                         int ld, const void* x, void* y, const int* done, const void* kstate, cudaStream_t s);
 int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, const void* fvals,
                        const int* apply, int ld, const void* x, void* y, const int* done,
                        const void* kstate, cudaStream_t s, int kreal = -1);

@@ -275,6 +275,7 @@ int build_op(mor_t h, OpData& op, const HostCSR& S, const std::vector<double>& s
     MOR_TRY(upload(h, op.scol, scol));
   }
   if (fmt == FMT_DIA) MOR_TRY(upload(h, op.doff, doffs));
+  op.h_doff = doffs;
   std::vector<double> la = permute_to_layout(sa, op.h_lay, op.nlay);
   std::vector<float> la32(la.begin(), la.end());
   MOR_TRY(upload(h, op.a64, la));

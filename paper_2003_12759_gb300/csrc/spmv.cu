@@ -159,6 +159,18 @@ __device__ __forceinline__ cdouble ldh(const cdouble* a, uint64_t pol) {
 }
 
 
+// Per-diagonal constants of the operator SpMV in the diagonal layout for a
+// pattern of ND diagonals (ND = 0: read at run time), passed by value (the
+// constant bank): offsets, offsets times the row stride, and the start of
+// each diagonal's A (and E) values.
+template <int ND> struct OpDiaC {
+  long long offld[ND];
+  int off[ND];
+  const void* ad[ND];
+  const void* ed[ND];
+};
+template <> struct OpDiaC<0> { int unused; };
+
 // R diagonals d .. d + R - 1 of an operator row r in the diagonal layout
 // (column clamped into range: out-of-range columns are padding of value 0).
 template <int R, bool ECSR, typename S, typename RV, int CPT>
@@ -192,11 +204,12 @@ __device__ __forceinline__ void op_dia_gather(S (&accA)[CPT], S (&accE)[CPT], co
 // columns sub * CPT ... sub * CPT + CPT - 1 of the n x ld blocks.  The
 // coefficients are read from shared memory where they are used and row
 // indices are 32-bit, to hold the register bound of op_min_blocks.
-template <typename S, int TPR, int CPT, bool ECSR, bool DIA>
+template <typename S, int TPR, int CPT, bool ECSR, bool DIA, int ND>
 __global__ void __launch_bounds__(256, (op_blocks<S, CPT, DIA>())) op_spmv_kernel(SegView sg, PatView pv, OpVals ov,
                                                                                 CoefS<S> cf, int ld,
                                                                                 const S* __restrict__ x, S* __restrict__ y,
-                                                                                const S* __restrict__ bv, RedArgs red) {
+                                                                                const S* __restrict__ bv, RedArgs red,
+                                                                                OpDiaC<ND> dc) {
   typedef typename real_of<S>::type R;
   if (red.done && *red.done) return;
   __shared__ S csE[MOR_LDMAX], csA[MOR_LDMAX];
@@ -237,7 +250,35 @@ __global__ void __launch_bounds__(256, (op_blocks<S, CPT, DIA>())) op_spmv_kerne
       S accA[CPT], accE[CPT];
 #pragma unroll
       for (int j = 0; j < CPT; ++j) { accA[j] = zero_<S>(); accE[j] = zero_<S>(); }
-      if constexpr (DIA) {
+      if constexpr (DIA && ND > 0) {
+        if (r + dc.off[0] >= 0 && r + dc.off[ND - 1] < pv.n) {
+          // interior row: every column r + o_d in range, no clamp
+          const S* xr = x + (int64_t)r * ld + c0;
+#pragma unroll
+          for (int d0 = 0; d0 < ND; d0 += 4) {
+            R av[4], ev[4];
+            Pack<S, CPT> xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (d0 + u < ND) {
+                av[u] = ((const R* __restrict__)dc.ad[d0 + u])[r];
+                if constexpr (ECSR) ev[u] = ((const R* __restrict__)dc.ed[d0 + u])[r];
+                xv[u] = ldp<S, CPT>(xr + dc.offld[d0 + u]);
+              }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (d0 + u < ND) {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                  fma_r(accA[j], av[u], xv[u].v[j]);
+                  if constexpr (ECSR) fma_r(accE[j], ev[u], xv[u].v[j]);
+                }
+              }
+          }
+        } else {
+          for (int d = 0; d < ND; ++d) op_dia_gather<1, ECSR, S, R, CPT>(accA, accE, pv.doff, a, e, d, r, pv.n, ld, c0, x);
+        }
+      } else if constexpr (DIA) {
         int d = 0;
         for (; d + GCH <= pv.ndiag; d += GCH)
           op_dia_gather<GCH, ECSR, S, R, CPT>(accA, accE, pv.doff, a, e, d, r, pv.n, ld, c0, x);
@@ -517,10 +558,29 @@ int launch_op_spmv(int st, const SegView& sg, const PatView& pv, const OpVals& o
         cf.sA[c] = (S)q.sAr;
       }
     }
+    auto run = [&]<bool ECSR, bool DIA, int ND>() {
+      OpDiaC<ND> dc{};
+      if constexpr (ND > 0) {
+        typedef typename real_of<S>::type R;
+        for (int d = 0; d < ND; ++d) {
+          dc.off[d] = pv.h_doff[d];
+          dc.offld[d] = (long long)pv.h_doff[d] * ld;
+          dc.ad[d] = (const R*)ov.a + (size_t)d * pv.n;
+          dc.ed[d] = ECSR ? (const void*)((const R*)ov.e + (size_t)d * pv.n) : nullptr;
+        }
+      }
+      const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT, ECSR, DIA, ND>, TPR);
+      op_spmv_kernel<S, TPR, CPT, ECSR, DIA, ND><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y,
+                                                                           (const S*)b, ra, dc);
+    };
+    // the diagonal layout with 5 or 7 diagonals and FP32 / complex64 vectors:
+    // the per-diagonal constants by value (OpDiaC)
     auto go = [&]<bool ECSR, bool DIA>() {
-      const SegView g = fit_grid(sg, (const void*)op_spmv_kernel<S, TPR, CPT, ECSR, DIA>, TPR);
-      op_spmv_kernel<S, TPR, CPT, ECSR, DIA><<<g.nblocks, 256, 0, s>>>(g, pv, ov, cf, ld, (const S*)x, (S*)y,
-                                                                       (const S*)b, ra);
+      if constexpr (DIA && sizeof(typename real_of<S>::type) == 4 && narrow_slice<S, CPT>()) {
+        if (pv.h_doff && pv.ndiag == 7) return run.template operator()<ECSR, true, 7>();
+        if (pv.h_doff && pv.ndiag == 5) return run.template operator()<ECSR, true, 5>();
+      }
+      run.template operator()<ECSR, DIA, 0>();
     };
     const bool dia = pv.fmt == FMT_DIA;
     if (ov.ekind == EK_CSR) {
@@ -584,7 +644,12 @@ int launch_factor_spmv(int st, int fst, const SegView& sg, const PatView& pv, co
                        int ld, const void* x, void* y, const int* done, const void* kstate, cudaStream_t s,
                        int kreal) {
   if (ld < 1 || ld > MOR_LDMAX) return (int)cudaErrorInvalidValue;
-  int e;
+  int e = launch_factor_dia_nd(st, fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s);
+  if (e == 0) {
+    mor_count_launches(1);
+    mor_tally(1, st, kreal < 0 ? ld : kreal);
+    return (int)cudaGetLastError();
+  }
 #if MOR_FACTOR_TPR3
   // rows of exactly three 16-byte vectors: three lanes per row (no idle fourth lane)
   if ((int)st_size(st) * ld == 48) {
