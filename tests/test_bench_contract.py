@@ -54,3 +54,19 @@ def test_weighted_roofline_is_the_launch_weighted_mix():
     assert abs(other["factor_spmv"]["share_of_spmv_time"] - t / (t + 20 * 0.09)) < 1e-12
     per["factor_spmv"]["rows"][1]["traffic"] = None
     assert bench.weighted_roofline(per, 6000.0)[0]["traffic"] is None
+
+
+def test_spmv_bytes_by_layout():
+    """Algorithmic bytes of one SpMV launch: CSR counts its column indices and
+    row pointers, the diagonal layout has none (and its padding is not
+    counted); the vectors are the same in both."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n, nnz, k = 1000, 6900, 6
+    for kern, vec in (("factor_spmv", 2), ("op_spmv", 3)):
+        csr = bench._spmv_bytes(kern, k, n, nnz, True, True, bench.FORMATS["csr"])
+        dia = bench._spmv_bytes(kern, k, n, nnz, True, True, bench.FORMATS["dia"])
+        assert csr - dia == nnz * 4 + 4 * (n + 1)
+        vals = nnz * (8 if kern == "factor_spmv" else 4) + (4 * n if kern == "op_spmv" else 0)
+        assert dia == vals + vec * k * n * 8
+    assert bench.FORMAT_NAMES[bench.FORMATS["dia"]] == "dia"
