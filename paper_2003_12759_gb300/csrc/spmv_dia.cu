@@ -45,8 +45,21 @@ __device__ __forceinline__ void mac(Pack<S, CPT>& acc, const W fv, const Pack<S,
   }
 }
 
+// diagonals per chunk (values and gathers of a chunk in flight together) and
+// blocks per SM the registers are held to.  Measured (k = 3 / 6 / 7 / 8, us
+// per launch, L2 flushed): chunk 4 at 8 blocks (32 registers) 29.2 / 38.5 /
+// 46.6 / 43.6; chunk 8 at 6 (40) 27.2 / 36.4 / 50.6 / 49.8; at 5 (48) 27.2 /
+// 39.4 / 51.8 / 50.7; at 4 (56) 25.1 / 37.4 / 45.6 / 42.5; chunk 2 at 8
+// 28.2 / 38.4 / 46.6 / 46.6 -- within a few percent of one another.
+#ifndef MOR_DIA_ND_CHUNK
+#define MOR_DIA_ND_CHUNK 4
+#endif
+#ifndef MOR_DIA_ND_MINB
+#define MOR_DIA_ND_MINB 8
+#endif
+
 template <typename S, typename V, int TPR, int CPT, int ND>
-__global__ void __launch_bounds__(256, 8) factor_dia_nd_kernel(SegView sg, DiaConst<ND> dc, int n,
+__global__ void __launch_bounds__(256, MOR_DIA_ND_MINB) factor_dia_nd_kernel(SegView sg, DiaConst<ND> dc, int n,
                                                                const int* __restrict__ apply, int ld,
                                                                const S* __restrict__ x, S* __restrict__ y,
                                                                const int* done, const KState* __restrict__ kst) {
@@ -86,19 +99,20 @@ __global__ void __launch_bounds__(256, 8) factor_dia_nd_kernel(SegView sg, DiaCo
     if (mask) {
       if (r + dc.off[0] >= 0 && r + dc.off[ND - 1] < n) {
         const S* xr = x + (int64_t)r * ld + c0;
-        // chunks of four diagonals: values and gathers of a chunk in flight together
+        // chunks of CH diagonals: values and gathers of a chunk in flight together
+        constexpr int CH = MOR_DIA_ND_CHUNK;
 #pragma unroll
-        for (int d0 = 0; d0 < ND; d0 += 4) {
-          W fv[4];
-          Pack<S, CPT> xv[4];
+        for (int d0 = 0; d0 < ND; d0 += CH) {
+          W fv[CH];
+          Pack<S, CPT> xv[CH];
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < CH; ++u)
             if (d0 + u < ND) {
               fv[u] = cvt_<W, V>::f(((const V* __restrict__)dc.fd[d0 + u])[r]);
               xv[u] = ldp<S, CPT>(xr + dc.offld[d0 + u]);
             }
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < CH; ++u)
             if (d0 + u < ND) mac<S, V, W, CPT>(acc, fv[u], xv[u]);
         }
       } else {
