@@ -196,3 +196,46 @@ def test_diagonal_layout_refuses_irregular_rows(h):
         mor.mor_set_system(h, A, B, C, fmt=mor.MOR_FMT_DIA)
     mor.mor_set_system(h, A, B, C, fmt=mor.MOR_FMT_AUTO)
     assert mor.mor_get_info(h)["format"] in (mor.MOR_FMT_CSR, mor.MOR_FMT_SELL)
+
+
+@pytest.mark.parametrize("precision", [mor.MOR_FP64, mor.MOR_MIXED])
+@pytest.mark.parametrize("real", [True, False])
+def test_five_diagonal_layout_every_width(h, precision, real):
+    """A 2D five-point pattern (41 x 41 grid: 5 diagonals, offsets 0, +-1, +-41)
+    in the diagonal layout: the operator and a two-factor chain at every width,
+    elementwise against the oracle (the kernels specialised to 5 diagonals and
+    their edge rows, within +-41 rows of either end)."""
+    wl = W.laplace2d_siso(N=41)
+    A = sp.csr_matrix(wl.A)
+    n = A.shape[0]
+    mor.mor_set_system(h, A, wl.B, wl.C, fmt=mor.MOR_FMT_DIA)
+    assert mor.mor_get_info(h)["format"] == mor.MOR_FMT_DIA
+    u = U64 if precision == mor.MOR_FP64 else U32
+    Aa = abs(A)
+    for k in KS:
+        sig = _shifts(k, real)
+        X = _x(n, k, real, precision, 400 + k)
+        Y = mor.mor_apply_operator(h, sig, X, precision=precision, real=real)
+        for c in range(k):
+            ref = oop.A_sigma(A, None, sig[c]) @ X[:, c]
+            bnd = abs(sig[c]) * np.abs(X[:, c]) + Aa @ np.abs(X[:, c])
+            assert np.all(np.abs(Y[:, c] - ref) <= 30 * u * bnd + 1e-300), (k, c)
+    s = [3.0, 8.0] if real else [3.0 + 1.0j, 8.0 + 0.5j]
+    mor.mor_build_precond(h, s[0], 0, precision)
+    mor.mor_update_precond(h, s[1], 0)
+    rowptr, col = mor.mor_get_pattern(h, 0)
+    F = []
+    for i in range(2):
+        vals, _, _ = mor.mor_get_factor(h, 0, i)
+        F.append(sp.csr_matrix((vals.real if real else vals, col, rowptr), shape=(n, n)))
+    for k in KS:
+        sig = np.array([s[c % 2] for c in range(k)], dtype=complex)
+        X = _x(n, k, real, precision, 500 + k)
+        Y = mor.mor_apply_precond(h, sig, X, real=real)
+        for c in range(k):
+            L = c % 2 + 1
+            ref = ospai.chain_apply(F[:L], X[:, c])
+            bnd = np.abs(X[:, c])
+            for f in F[:L]:
+                bnd = abs(f) @ bnd
+            assert np.all(np.abs(Y[:, c] - ref) <= 30 * u * L * bnd + 1e-300), (k, c)
