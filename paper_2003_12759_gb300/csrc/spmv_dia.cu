@@ -66,8 +66,8 @@ __global__ void __launch_bounds__(256, MOR_DIA_ND_MINB) factor_dia_nd_kernel(Seg
   typedef typename real_of<S>::type RS;
   typedef typename std::conditional<is_cplx<V>::value, cplx<RS>, RS>::type W;
   if (done && *done) return;
-  // three lanes per row (rows of three 16-byte vectors): the threads past the
-  // last whole row group of the block have no row
+  // three or five lanes per row: the threads past the last whole row group of
+  // the block have no row
   if constexpr ((TPR & (TPR - 1)) != 0) {
     if ((int)threadIdx.x >= (256 / TPR) * TPR) return;
   }
@@ -185,10 +185,15 @@ int launch_factor_dia_nd(int st, int fst, const SegView& sg, const PatView& pv, 
   if (pv.fmt != FMT_DIA || !pv.h_doff || (pv.ndiag != 5 && pv.ndiag != 7)) return -1;
   if (st != ST_C32 && st != ST_F32) return -1;
   if (ld < 1 || ld > MOR_LDMAX) return -1;
-  // rows of exactly three 16-byte vectors: three lanes per row, as factor_spmv_kernel
+  // rows of exactly three (five) 16-byte vectors: three (five) lanes per row,
+  // no idle lane (the power-of-two mapping would give four or eight)
   if ((int)st_size(st) * ld == 48) {
     if (st == ST_C32) return launch_shape<cfloat, 3, 2>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s);
     return launch_shape<float, 3, 4>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s);
+  }
+  if ((int)st_size(st) * ld == 80) {
+    if (st == ST_C32) return launch_shape<cfloat, 5, 2>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s);
+    return launch_shape<float, 5, 4>(fst, sg, pv, fvals, apply, ld, x, y, done, kstate, s);
   }
   return dispatch_shape(st, ld, [&]<typename S, int TPR, int CPT>() -> int {
     if constexpr (std::is_same<S, cfloat>::value || std::is_same<S, float>::value)
