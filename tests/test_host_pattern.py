@@ -164,3 +164,72 @@ def test_pattern_transpose_shadows_and_sell_match_oracle(harness, name):
     else:
         assert len(got["doffs"]) == 0 and len(got["dlay"]) == 0
     assert got["dia3_ok"] == 0 and len(got["doffs3"]) == 0      # more than 3 diagonals
+
+
+DIA_HARNESS = r"""
+#include <cstdio>
+#include "host_pattern.h"
+using namespace mor_host;
+int main() {
+  long n, nnz; int maxd; double fill;
+  if (scanf("%ld %ld %d %lf", &n, &nnz, &maxd, &fill) != 4) return 1;
+  HostCSR S; S.n = n; S.rowptr.resize(n + 1); S.col.resize(nnz);
+  for (auto& x : S.rowptr) if (scanf("%d", &x) != 1) return 1;
+  for (auto& x : S.col) if (scanf("%d", &x) != 1) return 1;
+  std::vector<int32_t> offs; std::vector<int64_t> lay;
+  const bool ok = dia_layout(S, maxd, fill, offs, lay);
+  printf("%d %zu %zu\n", ok ? 1 : 0, offs.size(), lay.size());
+  return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def dia_harness(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("dia_layout")
+    (d / "h.cpp").write_text(DIA_HARNESS)
+    exe = d / "h"
+    subprocess.run([cxx, "-O2", "-std=c++17", "-pthread", "-I", CSRC, str(d / "h.cpp"), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+def _banded(n, offsets):
+    """Pattern with the given diagonals, every in-range position present."""
+    rows, cols = [], []
+    for o in offsets:
+        for r in range(max(0, -o), min(n, n - o)):
+            rows.append(r)
+            cols.append(r + o)
+    M = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    M.sort_indices()
+    return M
+
+
+def _dia_run(exe, M, maxd=32, fill=1.25):
+    n = M.shape[0]
+    inp = "%d %d %d %.17g\n%s\n%s\n" % (n, M.nnz, maxd, fill, " ".join(map(str, M.indptr)),
+                                        " ".join(map(str, M.indices)))
+    ok, no, nl = map(int, subprocess.run([exe], input=inp, capture_output=True, text=True,
+                                         check=True).stdout.split())
+    return ok, no, nl
+
+
+def test_dia_layout_limits(dia_harness):
+    """The diagonal layout takes at most max_diag diagonals and at most max_fill
+    stored entries per nonzero: 32 diagonals pass and 33 do not; the padding
+    bound is checked on both sides of 1.25."""
+    n = 400
+    M32 = _banded(n, list(range(-16, 16)))           # 32 diagonals
+    ok, no, nl = _dia_run(dia_harness, M32)
+    assert (ok, no, nl) == (1, 32, M32.nnz)
+    M33 = _banded(n, list(range(-16, 17)))
+    assert _dia_run(dia_harness, M33)[0] == 0
+    # two far diagonals: stored entries 3 n against nnz = 3 n - 2 o
+    o = 60
+    M3 = _banded(n, [-o, 0, o])
+    fill = 3 * n / M3.nnz
+    assert _dia_run(dia_harness, M3, fill=fill * 1.001)[0] == 1
+    assert _dia_run(dia_harness, M3, fill=fill * 0.999)[0] == 0
