@@ -36,11 +36,6 @@ inline int grid_for(int64_t threads, int cap) {
   if (cap > 0 && b > cap) b = cap;
   return (int)(b < 1 ? 1 : b);
 }
-inline int grid_rows(int st, int64_t n, int ld, int cap) {
-  int tpr, cpt;
-  lane_shape(st, ld, &tpr, &cpt);
-  return grid_for(n * tpr, cap);
-}
 
 // lane geometry shared by the elementwise kernels: segment, rows, owned columns
 #define MOR_LANE_SETUP                                  \
@@ -113,7 +108,7 @@ __global__ void __launch_bounds__(256) update_xr_kernel(SegView sg, int ld, S* _
   const KState* sts = st + (size_t)seg * ld;
   S alpha[CPT], omega[CPT], v0[CPT], v1[CPT];
   int act[CPT];
-  bool any = false;
+  bool any = false, all = true;
 #pragma unroll
   for (int j = 0; j < CPT; ++j) {
     act[j] = lane_on ? sts[c0 + j].active : 0;
@@ -122,6 +117,7 @@ __global__ void __launch_bounds__(256) update_xr_kernel(SegView sg, int ld, S* _
     v0[j] = S(0);
     v1[j] = S(0);
     any |= (act[j] != 0);
+    all &= (act[j] != 0);
   }
   if (any) {
     for (int64_t i = rb + threadIdx.x / TPR; i < re; i += rpb) {
@@ -129,7 +125,10 @@ __global__ void __launch_bounds__(256) update_xr_kernel(SegView sg, int ld, S* _
       Pack<S, CPT> xv = ldp<S, CPT>(x + q);
       const Pack<S, CPT> pv = ldp<S, CPT>(ph + q), shv = ldp<S, CPT>(sh + q), svv = ldp<S, CPT>(sv + q),
                          tv = ldp<S, CPT>(t + q), rh = ldp<S, CPT>(rhat + q);
-      Pack<S, CPT> rn = ldp<S, CPT>(r + q);
+      // r is read only to carry stopped columns through: a lane whose columns
+      // are all active overwrites every one of them
+      Pack<S, CPT> rn;
+      if (!all) rn = ldp<S, CPT>(r + q);
 #pragma unroll
       for (int j = 0; j < CPT; ++j) {
         if (act[j]) {
