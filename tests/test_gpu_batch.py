@@ -105,3 +105,33 @@ def test_batch_failed_mixed_columns_fall_back_to_fp64(h):
             assert st1[i][c]["fallback"] == 1 and st1[i][c]["status"] == mor.MOR_OK
             rel = np.linalg.norm(b - oop.A_sigma(w.A, w.E, s) @ X[off[i]:off[i + 1], c]) / np.linalg.norm(b)
             assert rel <= 1.001e-8, (i, c, rel)
+
+
+def test_batch_of_equal_systems_in_the_diagonal_layout(h):
+    """A batch of equal 2D Laplacians (the block-diagonal pattern has 5
+    diagonals, with padding where a diagonal crosses from one system into the
+    next) stored in the diagonal layout: every (system, shift) solution at the
+    1e-8 true residual of its own system, and the same iterations and
+    solutions as the CSR layout."""
+    sysl = [W.laplace2d_siso(N=20, seed=s) for s in range(4)]
+    shifts = [2.0, 20.0, 200.0 + 10.0j]
+    out = {}
+    for fmt in (mor.MOR_FMT_CSR, mor.MOR_FMT_DIA):
+        mor.mor_set_batch(h, [w.A for w in sysl], [w.B[:, 0] for w in sysl], [w.C[:, 0] for w in sysl], fmt=fmt)
+        assert mor.mor_get_info(h)["format"] == fmt
+        nsys, off = mor.mor_batch_info(h)
+        mor.mor_build_precond(h, shifts[0], 0, mor.MOR_MIXED)
+        for s in shifts[1:]:
+            mor.mor_update_precond(h, s, 0)
+        X, stats, code = mor.mor_batch_solve(h, shifts, 0, mor.mor_default_opts(precision=mor.MOR_MIXED))
+        assert code == mor.MOR_OK
+        for i, w in enumerate(sysl):
+            xs = X[off[i]:off[i + 1]]
+            b = w.B[:, 0]
+            for c, s in enumerate(shifts):
+                M = oop.A_sigma(w.A, w.E, s)
+                assert np.linalg.norm(b - M @ xs[:, c]) <= 1.001e-8 * np.linalg.norm(b), (fmt, i, c)
+        out[fmt] = (X, [[x["iters"] for x in st] for st in stats])
+    (Xc, ic), (Xd, idg) = out[mor.MOR_FMT_CSR], out[mor.MOR_FMT_DIA]
+    assert ic == idg
+    np.testing.assert_allclose(Xd, Xc, rtol=0, atol=1e-12 * np.abs(Xc).max())
